@@ -1,0 +1,342 @@
+#!/usr/bin/env python3
+"""Benchmark of volumetric field synthesis (voxels/s).
+
+Workload: 21x21 orders (M = 441), 32 layers, output 256 x 256 x 256 voxels (8
+planes per layer), synthetic solved layers (workloads.random_layer_set, seed
+= rank). A step is one scw_synthesize: phases (a), mode contraction (b),
+pruned inverse FFT (c). W (597 MB) and the output (403 MB) are both larger
+than the 129 MB L2, so no flush is needed between steps.
+
+Prints ONE JSON line on rank 0. With --impl reference the FP64 CPU oracle is
+timed instead (bounded sample of the same workload on the host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+U_ORD, L_LAYERS, F_XY, PLANES_PER_LAYER = 21, 32, 256, 8
+LAM, X_PERIOD, DZ = 1.0, 16.0, 0.25
+WORKLOAD = "single_wavelength_21x21_orders_32_layers_256cubed"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+def geometry():
+    zb = np.arange(L_LAYERS + 1) * DZ
+    Fz = L_LAYERS * PLANES_PER_LAYER
+    zp = zb[0] + (np.arange(Fz) + 0.5) * ((zb[-1] - zb[0]) / Fz)
+    return zb, zp
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        finally:
+            os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample_rate(W, g, a, zb, zp, seconds=12.0, max_planes=64):
+    """Voxels/s of the FP64 oracle (spectrum + direct sum) on whole planes of
+    the same workload, planes taken from the start until ~`seconds` elapse."""
+    from oracle import cw, synth
+    ls = cw.LayerSet(lam=LAM, X=X_PERIOD, Y=X_PERIOD, U=U_ORD, V=U_ORD, z_bounds=zb, W=W, gamma=g, alpha=a,
+                     p_inc=None, p_ref=None, p_trn=None)
+    xs, ys = synth.pixel_coords(ls, F_XY, F_XY)
+    t0 = time.perf_counter()
+    n = 0
+    for z in zp[:max_planes]:
+        S = synth.spectrum_at(ls, float(z))
+        synth.field_direct(ls, S, xs, ys)
+        n += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return n * F_XY * F_XY / dt, n, dt
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import workloads as wl
+    zb, zp = geometry()
+    W, g, a, *_ = wl.random_layer_set(0, U_ORD, U_ORD, L_LAYERS)
+    W = W.astype(np.complex128)
+    for _ in range(args.warmup):
+        oracle_sample_rate(W, g, a, zb, zp, seconds=0.0, max_planes=1)
+    rates, planes = [], 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, n, _ = oracle_sample_rate(W, g, a, zb, zp, seconds=0.0, max_planes=2)
+        rates.append(r)
+        planes += n
+    dt = time.perf_counter() - t0
+    value = planes * F_XY * F_XY / dt
+    cores = blas_threads()
+    line = {"impl": "reference", "metric": "field voxels/s", "value": value, "unit": "voxels/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "orders": "21x21", "layers": L_LAYERS,
+                                            "grid": [F_XY, F_XY, L_LAYERS * PLANES_PER_LAYER],
+                                            "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cores, "kind": "oracle",
+                             "sample": "2 whole 256x256 planes per step (spectrum + direct sum), FP64 NumPy"},
+            "e2e": {"value": value, "unit": "voxels/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    import paper_2404_07293_gb300 as scw
+    import workloads as wl
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    zb, zp = geometry()
+    Fz = len(zp)
+    voxels = F_XY * F_XY * Fz
+
+    W, g, a, *_ = wl.random_layer_set(rank, U_ORD, U_ORD, L_LAYERS)
+    Wd = torch.from_numpy(W).to(dev)
+    gd = torch.from_numpy(g).to(dev)
+    ad = torch.from_numpy(a).to(dev)
+
+    def make_plan(precision, host_io=False):
+        return scw.Plan(U_ORD, U_ORD, L_LAYERS, LAM, X_PERIOD, X_PERIOD, zb, F_XY, F_XY, zp,
+                        precision=precision, host_io=host_io, k_split=args.k_split)
+
+    stream = torch.cuda.current_stream(dev)
+    plan = make_plan(args.precision)
+    t0 = time.perf_counter()
+    plan.set_layers(Wd, gd, ad)
+    torch.cuda.synchronize(dev)
+    plan_ms = plan.info()["convert_ms"]
+    out = torch.empty(plan.out_shape(), dtype=torch.complex64, device=dev)
+
+    def barrier():
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        plan.synthesize(out)
+    plan.check()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plan.enable_timing(True)
+    with ClockSampler(local) as clocks:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.synthesize(out)
+        ev1.record(stream)
+        barrier()
+    kt = plan.timings()
+    plan.enable_timing(False)
+    plan.check()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * voxels * args.steps / (ms * 1e-3)
+    info = plan.info()
+
+    # roofline of the dominant kernel: algorithmic bytes per launch / live launch time
+    hbm, bf16_tf, peak_kind = peaks()
+    M = U_ORD * U_ORD
+    w_bytes = L_LAYERS * 3 * M * 4 * M * 8            # W read once (8 B per complex in every mode but FP16)
+    if args.precision == "fp16":
+        w_bytes //= 2
+    s_bytes = Fz * 3 * M * 8                           # spectrum written once
+    out_bytes = 3 * voxels * 8                         # field written once
+    t_bytes = Fz * 3 * U_ORD * F_XY * 8                # x-pass rows read once
+    contract_gbs = (w_bytes + s_bytes) / (kt["contract_ms"] * 1e-3) / 1e9
+    ypass_gbs = (out_bytes + t_bytes) / (kt["ypass_ms"] * 1e-3) / 1e9
+    dominant = "contract" if kt["contract_ms"] >= kt["ypass_ms"] else "ypass"
+    if dominant == "contract":
+        roof = {"kernel": "contract_tc_kernel" if args.precision != "fp32" else "contract_fp32_kernel",
+                "bound": "hbm", "achieved": contract_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": contract_gbs / hbm, "traffic": None,
+                "algorithmic_bytes": w_bytes + s_bytes, "launch_ms": kt["contract_ms"]}
+    else:
+        roof = {"kernel": "ypass_kernel", "bound": "hbm", "achieved": ypass_gbs, "peak": hbm, "unit": "GB/s",
+                "frac": ypass_gbs / hbm, "traffic": None, "algorithmic_bytes": out_bytes + t_bytes,
+                "launch_ms": kt["ypass_ms"]}
+    roof["peak_source"] = f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"
+    whole_bytes = w_bytes + out_bytes
+    step_roofline_ms = whole_bytes / (hbm * 1e9) * 1e3
+
+    # end to end through the C ABI with HOST buffers (H2D of W/gamma/alpha, D2H of the field)
+    e2e = None
+    if not args.no_e2e:
+        del out
+        hplan = make_plan(args.precision, host_io=True)
+        Wh = torch.from_numpy(W).pin_memory().numpy()
+        gh = torch.from_numpy(g).pin_memory().numpy()
+        ah = torch.from_numpy(a).pin_memory().numpy()
+        oh = torch.empty(hplan.out_shape(), dtype=torch.complex64).pin_memory().numpy()
+        for _ in range(max(1, args.warmup // 2)):
+            hplan.synthesize_host(Wh, gh, ah, out=oh)
+        n_e2e = max(2, min(args.steps, 10))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            hplan.synthesize_host(Wh, gh, ah, out=oh)
+        t_e2e = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([t_e2e], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        hplan.check()
+        e2e = {"value": world * voxels * n_e2e / t_e2e, "unit": "voxels/s",
+               "h2d_bytes_per_step": W.nbytes + g.nbytes + a.nbytes, "d2h_bytes_per_step": oh.nbytes,
+               "steps": n_e2e, "ms_per_step": 1e3 * t_e2e / n_e2e,
+               "includes": "H2D of W, gamma, alpha; W conversion; synthesis; D2H of the field"}
+        hplan.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rate, n, dt = oracle_sample_rate(W.astype(np.complex128), g, a, zb, zp, seconds=args.cpu_seconds)
+        cpu = {"value": rate, "unit": "voxels/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": f"{n} whole 256x256 planes of layer 1 (FP64 spectrum + direct sum), {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "field voxels/s", "value": value, "unit": "voxels/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "fp32", "split_bf16": "bf16x3->fp32", "fp16": "fp16x2->fp32"}[args.precision],
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "orders": "21x21", "M": M, "layers": L_LAYERS,
+                       "grid": [F_XY, F_XY, Fz], "precision": args.precision, "k_split": info["k_split"],
+                       "l2": "inputs larger than L2 (W 597 MB, field 403 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof,
+            "step_roofline": {"bytes": whole_bytes, "ms": step_roofline_ms,
+                              "frac": step_roofline_ms / (ms / args.steps)},
+            "kernel_ms": {k: kt[k] for k in ("phases_ms", "contract_ms", "xpass_ms", "ypass_ms", "total_ms")},
+            "ypass_gbs": ypass_gbs, "contract_gbs": contract_gbs,
+            "plan_convert_ms": plan_ms,
+            "gpu_launches": info["kernels_per_synthesis"] * args.steps,
+            "clocks": clocks.summary(),
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["split_bf16", "fp32", "fp16"], default="split_bf16")
+    ap.add_argument("--k-split", dest="k_split", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+    return run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * scw.h -- C ABI of libscw, GB300 (sm_103a) volumetric field synthesis for the
+ * coupled-wave method of Sun, Reddy and Mayerich, "sCWatter: open source
+ * coupled wave scattering simulation for spectroscopy and microscopy"
+ * (arXiv 2404.07293).
+ *
+ * What the library computes (paper Sec. 2.3, 2.6 and 4.1):
+ *   For every output plane z and every Fourier order m = (u, v), the per-plane
+ *   spectrum S_c[m](z) of the electric field (c = x, y, z), and then the field
+ *       E_c(x_i, y_j, z) = sum_m S_c[m](z) exp(2 pi i (u_m x_i / X + v_m y_j / Y))   (Eq. 10)
+ *   on the pixels x_i = x0 + i X/Fx, y_j = y0 + j Y/Fy (one lateral period).
+ *   Inside layer l (z_{l-1} <= z < z_l; the last layer also takes z = z_L):
+ *       S(z) = W_l (alpha_l o g(z)),  g_j = exp(i k gamma_j (z - z_ref,j)),      (Eq. 30-31, 34)
+ *   where k = 2 pi / lambda, modes j in [0, 2M) are forward (z_ref = z_{l-1})
+ *   and modes j in [2M, 4M) are backward (z_ref = z_l); W_l holds the E-field
+ *   rows of the layer's eigenvectors (rows c*M + m; the E_z rows already carry
+ *   the Psi convolution of Eq. 33).
+ *   Above the sample (z < z0) and below it (z > z_L), with flag SCW_FLAG_EXTERIOR:
+ *       S = p_inc exp(i k s_t (z - z_inc)) + p_ref exp(-i k s_t (z - z0))          (Eq. 9)
+ *       S = p_trn exp(i k s_b (z - z_L))
+ *   with s_t = s_z(n_top), s_b = s_z(n_bot) from Eq. 2 on the decaying branch.
+ *
+ * Orders (Sec. 2.2): u in [-floor(U/2), floor((U-1)/2)], likewise v, flat
+ * index m = (v + floor(V/2)) U + (u + floor(U/2)); s_x = lambda u / X,
+ * s_y = lambda v / Y (Eq. 6).
+ *
+ * Conventions for every entry point:
+ *   - complex64 is two packed floats (re, im); complex128 two packed doubles.
+ *   - "DEVICE" pointers are CUDA global memory on the current device; "HOST"
+ *     pointers are ordinary (ideally pinned) host memory.
+ *   - The caller owns every buffer it passes and keeps it alive until the work
+ *     queued on the stream has finished. A plan owns its own workspace and
+ *     frees it in scw_plan_destroy.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All GPU work is asynchronous on that stream; no entry point except
+ *     scw_plan_check, scw_synthesize_host and plan creation synchronises.
+ *   - Errors are returned as scw_status, with a message in scw_last_error()
+ *     (thread-local). Nothing traps on the device: kernels record problems in
+ *     a device error word that scw_plan_check reads back.
+ *   - There is no CPU fallback: without a usable sm_103a device every entry
+ *     point that would launch work returns SCW_ERR_CUDA.
+ */
+#ifndef SCW_H
+#define SCW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scw_plan_s* scw_plan_t;
+
+typedef enum {
+  SCW_OK = 0,
+  SCW_ERR_INVALID_ARGUMENT = 1, /* a size, pointer or value is out of range       */
+  SCW_ERR_UNSUPPORTED = 2,      /* valid but not handled by this build           */
+  SCW_ERR_OUT_OF_MEMORY = 3,    /* a workspace allocation failed                 */
+  SCW_ERR_CUDA = 4,             /* a CUDA runtime/driver call failed             */
+  SCW_ERR_TIMEOUT = 5,          /* a device-side bounded wait ran out            */
+  SCW_ERR_NUMERIC = 6,          /* non-finite value detected                     */
+  SCW_ERR_STATE = 7             /* call order violated (e.g. no layers set)     */
+} scw_status;
+
+/* Arithmetic of the mode contraction (the other steps are FP64-argument /
+ * FP32-value phases and an FP32 inverse FFT in every mode). */
+typedef enum {
+  SCW_PREC_FP32 = 0,        /* FP32 SIMT complex GEMM (the plain path)                 */
+  SCW_PREC_SPLIT_BF16 = 1,  /* tcgen05: W = hi + lo (BF16), C = hi + lo, 3 products,
+                               FP32 accumulation in tensor memory                       */
+  SCW_PREC_FP16 = 2         /* tcgen05: W in FP16, C = hi + lo (FP16), 2 products      */
+} scw_precision;
+
+enum {
+  SCW_FLAG_EXTERIOR = 1u, /* planes outside [z0, z_L] allowed (needs p_inc/p_ref/p_trn) */
+  SCW_FLAG_HOST_IO = 2u   /* plan also owns device copies of W/gamma/alpha/p for
+                             scw_synthesize_host                                        */
+};
+
+typedef struct {
+  int U, V, L;              /* orders along x and y (M = U V), number of layers        */
+  double lambda, X, Y;      /* vacuum wavelength and lateral period, same length unit   */
+  const double* z_bounds;   /* HOST [L+1], strictly ascending z_0 .. z_L                */
+  int Fx, Fy, Fz;           /* output grid: Fx, Fy multiples of 8 in [8, 4096]; Fz >= 1 */
+  const double* z_planes;   /* HOST [Fz], non-decreasing                                 */
+  double x0, y0;            /* position of output pixel (0, 0)                          */
+  double n_top;             /* real refractive index above the sample                   */
+  double n_bot_re, n_bot_im;/* complex refractive index below the sample                */
+  double z_inc;             /* plane at which p_inc is given (the paper's z-bar)        */
+  int precision;            /* scw_precision                                             */
+  unsigned flags;           /* SCW_FLAG_*                                                */
+  int k_split;              /* contraction split along the 4M modes; 0 = choose         */
+} scw_desc;
+
+typedef struct {
+  int M;                    /* U V                                                       */
+  int active_layers;        /* layers that hold at least one plane                       */
+  int planes_per_layer_pad; /* plane slots per layer in the contraction (multiple of 8)  */
+  int k_split;              /* split actually used                                       */
+  int exterior_planes;      /* planes outside [z0, z_L]                                  */
+  size_t workspace_bytes;   /* device bytes owned by the plan                            */
+  double convert_ms;        /* GPU time of the last W conversion (scw_plan_set_layers)   */
+  int kernels_per_synthesis;/* kernel launches queued by one scw_synthesize              */
+} scw_plan_info;
+
+/* Validate `desc`, assign planes to layers (Sec. 2.6.2: half-open layers, the
+ * last one closed), build the order/twiddle tables and allocate the
+ * workspace. Synchronous. On success *out owns the workspace.
+ * Errors: INVALID_ARGUMENT (sizes, non-ascending z, planes outside [z0,z_L]
+ * without SCW_FLAG_EXTERIOR), UNSUPPORTED (sizes above the build's limits),
+ * OUT_OF_MEMORY, CUDA (no sm_103a device). */
+scw_status scw_plan_create(const scw_desc* desc, scw_plan_t* out);
+
+/* Free everything the plan owns. NULL is accepted. */
+scw_status scw_plan_destroy(scw_plan_t plan);
+
+/* Attach the solved layers (the output of the connection-equation solve,
+ * Sec. 2.5.4 and Sec. 4.1's per-layer precompute):
+ *   W      DEVICE complex64  [L][3M][4M] row-major, rows c*M + m
+ *   gamma  DEVICE complex128 [L][4M]  modes [0,2M) forward, [2M,4M) backward
+ *   alpha  DEVICE complex128 [L][4M]
+ *   p_inc, p_ref, p_trn  DEVICE complex128 [3][M], required with
+ *          SCW_FLAG_EXTERIOR, otherwise may be NULL
+ * The plan keeps gamma/alpha/p pointers (not copies) and converts W once into
+ * the layout of the chosen precision (split-BF16 hi/lo, FP16, or the
+ * transposed FP32 copy), queued on `stream`. W itself is not kept. */
+scw_status scw_plan_set_layers(scw_plan_t plan, const void* W, const void* gamma,
+                               const void* alpha, const void* p_inc, const void* p_ref,
+                               const void* p_trn, void* stream);
+
+/* The whole hot path: phases (a), contraction (b), inverse FFT (c).
+ *   out  DEVICE complex64 [3][Fz][Fy][Fx], x fastest (component-major). */
+scw_status scw_synthesize(scw_plan_t plan, void* out, void* stream);
+
+/* Steps (a)+(b) only: the per-plane spectra.
+ *   S  DEVICE complex64 [Fz][3][M] (S[z][c][m], Eq. 34 / Eq. 9). */
+scw_status scw_spectrum(scw_plan_t plan, void* S, void* stream);
+
+/* Step (c) only: recompose E from caller-given spectra (Eq. 10).
+ *   S    DEVICE complex64 [Fz][3][M];  out DEVICE complex64 [3][Fz][Fy][Fx]. */
+scw_status scw_recompose(scw_plan_t plan, const void* S, void* out, void* stream);
+
+/* End-to-end through host memory (plan created with SCW_FLAG_HOST_IO): copy
+ * W/gamma/alpha/p from HOST buffers of the shapes above, convert, synthesise
+ * and copy the field back into HOST `out` [3][Fz][Fy][Fx]. Synchronises the
+ * stream before returning. p_* may be NULL without SCW_FLAG_EXTERIOR. */
+scw_status scw_synthesize_host(scw_plan_t plan, const void* W, const void* gamma,
+                               const void* alpha, const void* p_inc, const void* p_ref,
+                               const void* p_trn, void* out, void* stream);
+
+/* Synchronise `stream` and read (then clear) the plan's device error word:
+ * SCW_OK, SCW_ERR_TIMEOUT (a bounded device wait ran out) or SCW_ERR_CUDA. */
+scw_status scw_plan_check(scw_plan_t plan, void* stream);
+
+/* Device-side wait limit in nanoseconds for the plan's kernels (default 2 s). */
+scw_status scw_plan_set_timeout_ns(scw_plan_t plan, uint64_t ns);
+
+scw_status scw_plan_get_info(scw_plan_t plan, scw_plan_info* info);
+
+/* Per-step kernel durations, measured with CUDA events recorded on the
+ * launching stream between the kernels of each scw_synthesize call while
+ * timing is enabled (at most 4096 calls are kept). */
+typedef struct {
+  int calls;             /* synthesize calls averaged                      */
+  double phases_ms;      /* step (a) incl. exterior planes, per call       */
+  double contract_ms;    /* step (b)                                       */
+  double xpass_ms;       /* step (c), x direction                          */
+  double ypass_ms;       /* step (c), y direction and the field stores     */
+  double total_ms;       /* first to last event                            */
+} scw_kernel_times;
+
+/* on != 0 starts a new timing window (previous events are dropped). */
+scw_status scw_plan_enable_timing(scw_plan_t plan, int on);
+/* Synchronises on the recorded events, returns per-call averages and clears them. */
+scw_status scw_plan_get_timings(scw_plan_t plan, scw_kernel_times* t);
+
+const char* scw_status_string(scw_status s);
+const char* scw_last_error(void);
+int scw_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCW_H */

@@ -1,0 +1,160 @@
+"""GB300-native volumetric field synthesis for the coupled-wave method of
+arXiv 2404.07293 (sCWatter): thin Python binding over libscw (include/scw.h).
+
+Every step of the hot path runs in the library's CUDA kernels; this module
+only checks tensor shapes/dtypes and passes pointers and the current torch
+stream. PyTorch provides device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import (FLAG_EXTERIOR, FLAG_HOST_IO, PRECISION, ScwDesc, ScwError, ScwKernelTimes, ScwPlanInfo, check,
+                   load)
+
+__all__ = ["Plan", "ScwError", "load", "PRECISION"]
+
+
+def _stream_handle(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, dtype, shape, name):
+    a = np.asarray(a)
+    if a.dtype != dtype or tuple(a.shape) != tuple(shape) or not a.flags.c_contiguous:
+        raise ValueError(f"{name} must be a C-contiguous {np.dtype(dtype).name} array of shape {tuple(shape)}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Plan:
+    """One synthesis configuration (scw_plan_create) and its workspace."""
+
+    def __init__(self, U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0,
+                 n_bot=1.0, z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0):
+        self._lib = load()
+        self.U, self.V, self.L = int(U), int(V), int(L)
+        self.M = self.U * self.V
+        self.Fx, self.Fy = int(Fx), int(Fy)
+        self._zb = np.ascontiguousarray(z_bounds, dtype=np.float64)
+        self._zp = np.ascontiguousarray(z_planes, dtype=np.float64)
+        self.Fz = len(self._zp)
+        if len(self._zb) != self.L + 1:
+            raise ValueError("z_bounds must have L+1 entries")
+        self.exterior = bool(exterior)
+        nb = complex(n_bot)
+        d = ScwDesc(U=self.U, V=self.V, L=self.L, lam=float(lam), X=float(X), Y=float(Y),
+                    z_bounds=self._zb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    Fx=self.Fx, Fy=self.Fy, Fz=self.Fz,
+                    z_planes=self._zp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    x0=float(x0), y0=float(y0), n_top=float(n_top), n_bot_re=nb.real, n_bot_im=nb.imag,
+                    z_inc=float(self._zb[0] if z_inc is None else z_inc),
+                    precision=PRECISION[precision], flags=(FLAG_EXTERIOR if exterior else 0)
+                    | (FLAG_HOST_IO if host_io else 0), k_split=int(k_split))
+        h = ctypes.c_void_p()
+        check(self._lib.scw_plan_create(ctypes.byref(d), ctypes.byref(h)), "scw_plan_create")
+        self._h = h
+        self._keep = ()
+
+    # ------------------------------------------------------------------ inputs
+    def set_layers(self, W, gamma, alpha, p_inc=None, p_ref=None, p_trn=None, stream=None):
+        """W complex64 [L][3M][4M]; gamma, alpha complex128 [L][4M]; p_* complex128 [3][M]."""
+        import torch
+        L, M = self.L, self.M
+        args = [_dev_ptr(W, torch.complex64, (L, 3 * M, 4 * M), "W"),
+                _dev_ptr(gamma, torch.complex128, (L, 4 * M), "gamma"),
+                _dev_ptr(alpha, torch.complex128, (L, 4 * M), "alpha")]
+        for p, n in ((p_inc, "p_inc"), (p_ref, "p_ref"), (p_trn, "p_trn")):
+            args.append(ctypes.c_void_p(0) if p is None else _dev_ptr(p, torch.complex128, (3, M), n))
+        check(self._lib.scw_plan_set_layers(self._h, *args, _stream_handle(stream)), "scw_plan_set_layers")
+        self._keep = (W, gamma, alpha, p_inc, p_ref, p_trn)  # W until its conversion has run
+
+    # ------------------------------------------------------------------ compute
+    def out_shape(self):
+        return (3, self.Fz, self.Fy, self.Fx)
+
+    def synthesize(self, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.out_shape(), dtype=torch.complex64, device="cuda")
+        check(self._lib.scw_synthesize(self._h, _dev_ptr(out, torch.complex64, self.out_shape(), "out"),
+                                       _stream_handle(stream)), "scw_synthesize")
+        return out
+
+    def spectrum(self, S=None, stream=None):
+        import torch
+        shape = (self.Fz, 3, self.M)
+        if S is None:
+            S = torch.empty(shape, dtype=torch.complex64, device="cuda")
+        check(self._lib.scw_spectrum(self._h, _dev_ptr(S, torch.complex64, shape, "S"), _stream_handle(stream)),
+              "scw_spectrum")
+        return S
+
+    def recompose(self, S, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.out_shape(), dtype=torch.complex64, device="cuda")
+        check(self._lib.scw_recompose(self._h, _dev_ptr(S, torch.complex64, (self.Fz, 3, self.M), "S"),
+                                      _dev_ptr(out, torch.complex64, self.out_shape(), "out"),
+                                      _stream_handle(stream)), "scw_recompose")
+        return out
+
+    def synthesize_host(self, W, gamma, alpha, p_inc=None, p_ref=None, p_trn=None, out=None, stream=None):
+        """End to end through host memory (plan created with host_io=True)."""
+        L, M = self.L, self.M
+        if out is None:
+            out = np.empty(self.out_shape(), dtype=np.complex64)
+        args = [_host_ptr(W, np.complex64, (L, 3 * M, 4 * M), "W"),
+                _host_ptr(gamma, np.complex128, (L, 4 * M), "gamma"),
+                _host_ptr(alpha, np.complex128, (L, 4 * M), "alpha")]
+        for p, n in ((p_inc, "p_inc"), (p_ref, "p_ref"), (p_trn, "p_trn")):
+            args.append(ctypes.c_void_p(0) if p is None else _host_ptr(p, np.complex128, (3, M), n))
+        args.append(_host_ptr(out, np.complex64, self.out_shape(), "out"))
+        check(self._lib.scw_synthesize_host(self._h, *args, _stream_handle(stream)), "scw_synthesize_host")
+        return out
+
+    def check(self, stream=None):
+        check(self._lib.scw_plan_check(self._h, _stream_handle(stream)), "scw_plan_check")
+
+    def set_timeout_ns(self, ns):
+        check(self._lib.scw_plan_set_timeout_ns(self._h, int(ns)), "scw_plan_set_timeout_ns")
+
+    def enable_timing(self, on=True):
+        check(self._lib.scw_plan_enable_timing(self._h, 1 if on else 0), "scw_plan_enable_timing")
+
+    def timings(self) -> dict:
+        t = ScwKernelTimes()
+        check(self._lib.scw_plan_get_timings(self._h, ctypes.byref(t)), "scw_plan_get_timings")
+        return {f: getattr(t, f) for f, _ in ScwKernelTimes._fields_}
+
+    def info(self) -> dict:
+        i = ScwPlanInfo()
+        check(self._lib.scw_plan_get_info(self._h, ctypes.byref(i)), "scw_plan_get_info")
+        return {f: getattr(i, f) for f, _ in ScwPlanInfo._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.scw_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,89 @@
+"""ctypes declarations of the C ABI in include/scw.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_size_t, c_uint, c_uint64, c_void_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libscw.so")
+
+SCW_OK = 0
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARGUMENT", 2: "UNSUPPORTED", 3: "OUT_OF_MEMORY", 4: "CUDA",
+                5: "TIMEOUT", 6: "NUMERIC", 7: "STATE"}
+PRECISION = {"fp32": 0, "split_bf16": 1, "fp16": 2}
+FLAG_EXTERIOR = 1
+FLAG_HOST_IO = 2
+
+
+class ScwDesc(ctypes.Structure):
+    _fields_ = [("U", c_int), ("V", c_int), ("L", c_int),
+                ("lam", c_double), ("X", c_double), ("Y", c_double),
+                ("z_bounds", POINTER(c_double)),
+                ("Fx", c_int), ("Fy", c_int), ("Fz", c_int),
+                ("z_planes", POINTER(c_double)),
+                ("x0", c_double), ("y0", c_double),
+                ("n_top", c_double), ("n_bot_re", c_double), ("n_bot_im", c_double),
+                ("z_inc", c_double),
+                ("precision", c_int), ("flags", c_uint), ("k_split", c_int)]
+
+
+class ScwPlanInfo(ctypes.Structure):
+    _fields_ = [("M", c_int), ("active_layers", c_int), ("planes_per_layer_pad", c_int),
+                ("k_split", c_int), ("exterior_planes", c_int), ("workspace_bytes", c_size_t),
+                ("convert_ms", c_double), ("kernels_per_synthesis", c_int)]
+
+
+class ScwKernelTimes(ctypes.Structure):
+    _fields_ = [("calls", c_int), ("phases_ms", c_double), ("contract_ms", c_double), ("xpass_ms", c_double),
+                ("ypass_ms", c_double), ("total_ms", c_double)]
+
+
+# name -> (restype, argtypes); mirrors include/scw.h
+SIGNATURES = {
+    "scw_plan_create": (c_int, [POINTER(ScwDesc), POINTER(c_void_p)]),
+    "scw_plan_destroy": (c_int, [c_void_p]),
+    "scw_plan_set_layers": (c_int, [c_void_p] + [c_void_p] * 6 + [c_void_p]),
+    "scw_synthesize": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "scw_spectrum": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "scw_recompose": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "scw_synthesize_host": (c_int, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
+    "scw_plan_check": (c_int, [c_void_p, c_void_p]),
+    "scw_plan_set_timeout_ns": (c_int, [c_void_p, c_uint64]),
+    "scw_plan_get_info": (c_int, [c_void_p, POINTER(ScwPlanInfo)]),
+    "scw_plan_enable_timing": (c_int, [c_void_p, c_int]),
+    "scw_plan_get_timings": (c_int, [c_void_p, POINTER(ScwKernelTimes)]),
+    "scw_status_string": (c_char_p, [c_int]),
+    "scw_last_error": (c_char_p, []),
+    "scw_version": (c_int, []),
+}
+
+_lib = None
+
+
+class ScwError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+
+
+def load():
+    """Load libscw.so from the package directory; raises if it was never built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2404_07293_gb300.build` "
+                               "(there is no CPU fallback)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(status: int, where: str) -> None:
+    if status != SCW_OK:
+        msg = load().scw_last_error()
+        raise ScwError(status, where, msg.decode() if msg else "")

@@ -1,0 +1,241 @@
+// Step (a): per-plane mode weights c_j(z) = alpha_j exp(i k gamma_j (z - z_ref,j))
+// (paper Eq. 7 and Eq. 30-31, with the per-layer precompute of Sec. 4.1), the
+// exterior spectra of Eq. 9, and the one-off conversions of W.
+//
+// Phase arithmetic: the argument is range-reduced in FP64 in units of cycles,
+//   t = Re(gamma) (z - z_ref) / lambda,  r = t - rint(t)  (|r| <= 1/2),
+// and only the reduced r goes to FP32 sincospif(2 r); the decay
+// exp(-2 pi Im(gamma) (z - z_ref) / lambda) takes its exponent from FP64 too.
+// Large k Re(gamma) z therefore loses no digits, and evanescent Im(gamma)
+// never overflows: with forward modes referenced to the layer top and backward
+// modes to its bottom the exponent is never positive inside a layer.
+#include "scw_internal.cuh"
+
+namespace scw {
+
+__device__ __forceinline__ float2 mode_factor(double2 g, double dz, double inv_lam) {
+  const double t = (g.x * inv_lam) * dz;           // cycles
+  const double r = t - rint(t);
+  const float ex = (float)((g.y * inv_lam) * dz) * -6.2831853071795865f;
+  float s, c;
+  sincospif(2.0f * (float)r, &s, &c);
+  const float mag = expf(ex);
+  return make_float2(c * mag, s * mag);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+template <typename T> __device__ __forceinline__ T to_lp(float x);
+template <> __device__ __forceinline__ __nv_bfloat16 to_lp<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ __half to_lp<__half>(float x) { return __float2half_rn(x); }
+template <typename T> __device__ __forceinline__ float from_lp(T x);
+template <> __device__ __forceinline__ float from_lp<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <> __device__ __forceinline__ float from_lp<__half>(__half x) { return __half2float(x); }
+
+template <typename T>
+struct Pair { T a, b; };
+
+// B operand of the tensor-core contraction, [unit][NB][8M] with NB = 2 F_pad:
+// row f holds (Re c_j, -Im c_j) at columns (2j, 2j+1), row F_pad + f holds
+// (Im c_j, Re c_j); with A = W viewed as interleaved reals this gives
+// [Re S | Im S] (the complex product as one real GEMM). hi = round(x),
+// lo = round(x - hi).
+template <typename T>
+__global__ void phases_tc_kernel(const LayerUnit* __restrict__ units, const double* __restrict__ zplanes,
+                                 const double* __restrict__ zb, const double2* __restrict__ gamma,
+                                 const double2* __restrict__ alpha, int M, int F_pad, double inv_lam,
+                                 T* __restrict__ Bhi, T* __restrict__ Blo) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  const LayerUnit u = units[blockIdx.z];
+  const int M4 = 4 * M;
+  if (j >= M4) return;
+  const size_t K8 = (size_t)8 * M;
+  const int NB = 2 * F_pad;
+  float2 cv = make_float2(0.f, 0.f);
+  if (f < u.nf) {
+    const double z = zplanes[u.f0 + f];
+    const double zref = (j < 2 * M) ? zb[u.layer] : zb[u.layer + 1];
+    const double2 g = gamma[(size_t)u.layer * M4 + j];
+    const double2 a = alpha[(size_t)u.layer * M4 + j];
+    cv = cmulf(make_float2((float)a.x, (float)a.y), mode_factor(g, z - zref, inv_lam));
+  }
+  const float v0[2] = {cv.x, -cv.y};
+  const float v1[2] = {cv.y, cv.x};
+  const size_t base = (size_t)blockIdx.z * NB * K8;  // B is per work unit
+  const size_t i0 = base + (size_t)f * K8 + 2 * (size_t)j;
+  const size_t i1 = base + (size_t)(F_pad + f) * K8 + 2 * (size_t)j;
+  Pair<T> h0, l0, h1, l1;
+  h0.a = to_lp<T>(v0[0]); h0.b = to_lp<T>(v0[1]);
+  l0.a = to_lp<T>(v0[0] - from_lp<T>(h0.a)); l0.b = to_lp<T>(v0[1] - from_lp<T>(h0.b));
+  h1.a = to_lp<T>(v1[0]); h1.b = to_lp<T>(v1[1]);
+  l1.a = to_lp<T>(v1[0] - from_lp<T>(h1.a)); l1.b = to_lp<T>(v1[1] - from_lp<T>(h1.b));
+  *reinterpret_cast<Pair<T>*>(Bhi + i0) = h0;
+  *reinterpret_cast<Pair<T>*>(Blo + i0) = l0;
+  *reinterpret_cast<Pair<T>*>(Bhi + i1) = h1;
+  *reinterpret_cast<Pair<T>*>(Blo + i1) = l1;
+}
+
+// FP32 path: C[unit][j][f] complex64, plane index fastest.
+__global__ void phases_fp32_kernel(const LayerUnit* __restrict__ units, const double* __restrict__ zplanes,
+                                   const double* __restrict__ zb, const double2* __restrict__ gamma,
+                                   const double2* __restrict__ alpha, int M, int F_pad, double inv_lam,
+                                   float2* __restrict__ C) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  const LayerUnit u = units[blockIdx.y];
+  const int M4 = 4 * M;
+  if (idx >= M4 * F_pad) return;
+  const int j = idx / F_pad;
+  const int f = idx - j * F_pad;
+  float2 cv = make_float2(0.f, 0.f);
+  if (f < u.nf) {
+    const double z = zplanes[u.f0 + f];
+    const double zref = (j < 2 * M) ? zb[u.layer] : zb[u.layer + 1];
+    const double2 g = gamma[(size_t)u.layer * M4 + j];
+    const double2 a = alpha[(size_t)u.layer * M4 + j];
+    cv = cmulf(make_float2((float)a.x, (float)a.y), mode_factor(g, z - zref, inv_lam));
+  }
+  C[((size_t)blockIdx.y * M4 + j) * F_pad + f] = cv;  // C is per work unit
+}
+
+// Exterior planes (Eq. 9 with the reflected wave travelling towards -z):
+// S_part[0][f][c M + m].
+__global__ void exterior_kernel(const int* __restrict__ ext_planes, const double* __restrict__ zplanes,
+                                double z0, double zL, double z_inc, const double2* __restrict__ sz_top,
+                                const double2* __restrict__ sz_bot, const double2* __restrict__ p_inc,
+                                const double2* __restrict__ p_ref, const double2* __restrict__ p_trn,
+                                int M, double inv_lam, float2* __restrict__ S) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int f = ext_planes[blockIdx.y];
+  const double z = zplanes[f];
+  float2* out = S + (size_t)f * 3 * M;
+  if (z < z0) {
+    const double2 st = sz_top[m];
+    const float2 gi = mode_factor(st, z - z_inc, inv_lam);
+    const float2 gr = mode_factor(st, -(z - z0), inv_lam);
+    for (int c = 0; c < 3; ++c) {
+      const double2 a = p_inc[c * M + m], b = p_ref[c * M + m];
+      const float2 x = cmulf(make_float2((float)a.x, (float)a.y), gi);
+      const float2 y = cmulf(make_float2((float)b.x, (float)b.y), gr);
+      out[c * M + m] = make_float2(x.x + y.x, x.y + y.y);
+    }
+  } else {
+    const double2 sb = sz_bot[m];
+    const float2 gt = mode_factor(sb, z - zL, inv_lam);
+    for (int c = 0; c < 3; ++c) {
+      const double2 a = p_trn[c * M + m];
+      out[c * M + m] = cmulf(make_float2((float)a.x, (float)a.y), gt);
+    }
+  }
+}
+
+// ---- one-off conversions of W (plan time) -----------------------------------
+__global__ void convert_split_bf16_kernel(const float4* __restrict__ W, uint2* __restrict__ hi,
+                                          uint2* __restrict__ lo, size_t n4) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = W[i];
+    const float x[4] = {v.x, v.y, v.z, v.w};
+    __nv_bfloat16 h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      h[q] = __float2bfloat16_rn(x[q]);
+      l[q] = __float2bfloat16_rn(x[q] - __bfloat162float(h[q]));
+    }
+    hi[i] = *reinterpret_cast<uint2*>(h);
+    lo[i] = *reinterpret_cast<uint2*>(l);
+  }
+}
+
+__global__ void convert_fp16_kernel(const float4* __restrict__ W, uint2* __restrict__ out, size_t n4) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 v = W[i];
+    __half h[4] = {__float2half_rn(v.x), __float2half_rn(v.y), __float2half_rn(v.z), __float2half_rn(v.w)};
+    out[i] = *reinterpret_cast<uint2*>(h);
+  }
+}
+
+// Wt[l][c][r] = W[l][r][c], 32x32 tiles through shared memory.
+__global__ void transpose_layers_kernel(const float2* __restrict__ W, float2* __restrict__ Wt, int rows,
+                                        int cols) {
+  __shared__ float2 tile[32][33];
+  const size_t lay = (size_t)blockIdx.z * rows * cols;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[i][threadIdx.x] = W[lay + (size_t)r * cols + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) Wt[lay + (size_t)c * rows + r] = tile[threadIdx.x][i];
+  }
+}
+
+static int grid_for(size_t n, int block) {
+  size_t g = (n + block - 1) / block;
+  if (g > 152 * 32) g = 152 * 32;
+  if (g == 0) g = 1;
+  return (int)g;
+}
+
+cudaError_t launch_convert_split_bf16(const float2* W, __nv_bfloat16* hi, __nv_bfloat16* lo,
+                                      size_t n_complex, cudaStream_t st) {
+  const size_t n4 = n_complex / 2;  // 2 complex = 4 floats; 4M columns keep this exact
+  convert_split_bf16_kernel<<<grid_for(n4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(W),
+                                                               reinterpret_cast<uint2*>(hi),
+                                                               reinterpret_cast<uint2*>(lo), n4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_convert_fp16(const float2* W, __half* h, size_t n_complex, cudaStream_t st) {
+  const size_t n4 = n_complex / 2;
+  convert_fp16_kernel<<<grid_for(n4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(W),
+                                                         reinterpret_cast<uint2*>(h), n4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_layers(const float2* W, float2* Wt, int L, int rows, int cols, cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32, L), block(32, 8);
+  transpose_layers_kernel<<<grid, block, 0, st>>>(W, Wt, rows, cols);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phases_tc(const Plan& p, cudaStream_t st) {
+  const int n_units = (int)p.units.size();
+  if (n_units == 0) return cudaSuccess;
+  dim3 grid((4 * p.M + 127) / 128, p.F_pad, n_units);
+  const double inv_lam = 1.0 / p.lambda;
+  if (p.precision == SCW_PREC_SPLIT_BF16)
+    phases_tc_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(
+        p.d_units, p.d_zplanes, p.d_zbounds, p.gamma, p.alpha, p.M, p.F_pad, inv_lam,
+        static_cast<__nv_bfloat16*>(p.Bhi), static_cast<__nv_bfloat16*>(p.Blo));
+  else
+    phases_tc_kernel<__half><<<grid, 128, 0, st>>>(p.d_units, p.d_zplanes, p.d_zbounds, p.gamma, p.alpha,
+                                                   p.M, p.F_pad, inv_lam, static_cast<__half*>(p.Bhi),
+                                                   static_cast<__half*>(p.Blo));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phases_fp32(const Plan& p, cudaStream_t st) {
+  const int n_units = (int)p.units.size();
+  if (n_units == 0) return cudaSuccess;
+  const int n = 4 * p.M * p.F_pad;
+  dim3 grid((n + 255) / 256, n_units);
+  phases_fp32_kernel<<<grid, 256, 0, st>>>(p.d_units, p.d_zplanes, p.d_zbounds, p.gamma, p.alpha, p.M,
+                                           p.F_pad, 1.0 / p.lambda, p.Cf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exterior(const Plan& p, cudaStream_t st) {
+  if (p.n_exterior == 0) return cudaSuccess;
+  dim3 grid((p.M + 127) / 128, p.n_exterior);
+  const double z0 = p.z_bounds.front(), zL = p.z_bounds.back();
+  exterior_kernel<<<grid, 128, 0, st>>>(p.d_ext_planes, p.d_zplanes, z0, zL, p.z_inc, p.d_sz_top, p.d_sz_bot,
+                                        p.p_inc, p.p_ref, p.p_trn, p.M, 1.0 / p.lambda, p.S_part);
+  return cudaGetLastError();
+}
+
+}  // namespace scw

@@ -1,0 +1,95 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports every
+symbol include/scw.h declares, and rejects bad descriptors before touching a device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2404_07293_gb300 as scw
+from paper_2404_07293_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(scw_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(_lib.LIB_PATH):
+        from paper_2404_07293_gb300 import build
+        build.build()
+    return _lib.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_symbols()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in _lib.SIGNATURES, f"binding lacks {n}"
+
+
+def test_status_strings_and_version(lib):
+    assert lib.scw_version() >= 1
+    for s in range(8):
+        assert lib.scw_status_string(s)
+    assert lib.scw_status_string(99) == b"unknown status"
+
+
+def _desc(**kw):
+    zb = np.array([0.0, 0.25, 0.5])
+    zp = np.array([0.1, 0.3])
+    base = dict(U=3, V=3, L=2, lam=1.0, X=2.0, Y=2.0, Fx=16, Fy=16, Fz=2, x0=0.0, y0=0.0, n_top=1.0,
+                n_bot_re=1.0, n_bot_im=0.0, z_inc=0.0, precision=0, flags=0, k_split=0)
+    base.update(kw)
+    zb = base.pop("zb", zb)
+    zp = base.pop("zp", zp)
+    d = _lib.ScwDesc(**base)
+    d.z_bounds = zb.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.z_planes = zp.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return d, (zb, zp)
+
+
+@pytest.mark.parametrize("bad", [
+    dict(U=0), dict(L=0), dict(lam=0.0), dict(X=-1.0), dict(Fx=12), dict(Fy=4), dict(Fx=8192), dict(Fz=0),
+    dict(precision=7), dict(k_split=-1), dict(n_top=0.0),
+    dict(zb=np.array([0.0, 0.5, 0.5])), dict(zp=np.array([0.3, 0.1])), dict(zp=np.array([0.1, np.nan])),
+])
+def test_bad_descriptors_are_rejected(lib, bad):
+    d, keep = _desc(**bad)
+    h = ctypes.c_void_p()
+    st = lib.scw_plan_create(ctypes.byref(d), ctypes.byref(h))
+    assert st == 1, (st, lib.scw_last_error())
+    assert not h.value
+    assert lib.scw_last_error()
+
+
+def test_null_arguments(lib):
+    h = ctypes.c_void_p()
+    assert lib.scw_plan_create(None, ctypes.byref(h)) == 1
+    assert lib.scw_synthesize(None, None, None) == 1
+    assert lib.scw_plan_set_layers(None, None, None, None, None, None, None, None) == 1
+    assert lib.scw_plan_destroy(None) == 0
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    """On a machine without a usable sm_103a device plan creation fails loudly."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    d, keep = _desc()
+    h = ctypes.c_void_p()
+    st = lib.scw_plan_create(ctypes.byref(d), ctypes.byref(h))
+    assert st == 4
+    with pytest.raises(scw.ScwError):
+        scw.Plan(3, 3, 2, 1.0, 2.0, 2.0, [0, 0.25, 0.5], 16, 16, [0.1, 0.3])
