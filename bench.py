@@ -27,9 +27,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-U_ORD, L_LAYERS, F_XY, PLANES_PER_LAYER = 21, 32, 256, 8
+U_ORD, F_XY = 21, 256
+L_LAYERS, PLANES_PER_LAYER = 32, 8   # overridable with --layers / --planes-per-layer (profiling cases)
 LAM, X_PERIOD, DZ = 1.0, 16.0, 0.25
-WORKLOAD = "single_wavelength_21x21_orders_32_layers_256cubed"
+
+
+def workload_name():
+    fz = L_LAYERS * PLANES_PER_LAYER
+    return f"single_wavelength_21x21_orders_{L_LAYERS}_layers_256x256x{fz}"
 
 
 def peaks():
@@ -110,20 +115,22 @@ def dist_setup():
     return world, rank, local
 
 
-def oracle_sample_rate(W, g, a, zb, zp, seconds=12.0, max_planes=64):
+def oracle_sample_rate(W, g, a, zb, zp, seconds=12.0, max_planes=None):
     """Voxels/s of the FP64 oracle (spectrum + direct sum) on whole planes of
-    the same workload, planes taken from the start until ~`seconds` elapse."""
+    the same workload, planes taken in order until ~`seconds` elapse or
+    `max_planes` planes are done (cycling through the volume)."""
     from oracle import cw, synth
     ls = cw.LayerSet(lam=LAM, X=X_PERIOD, Y=X_PERIOD, U=U_ORD, V=U_ORD, z_bounds=zb, W=W, gamma=g, alpha=a,
                      p_inc=None, p_ref=None, p_trn=None)
     xs, ys = synth.pixel_coords(ls, F_XY, F_XY)
     t0 = time.perf_counter()
     n = 0
-    for z in zp[:max_planes]:
+    while True:
+        z = zp[n % len(zp)]
         S = synth.spectrum_at(ls, float(z))
         synth.field_direct(ls, S, xs, ys)
         n += 1
-        if time.perf_counter() - t0 > seconds:
+        if (max_planes is not None and n >= max_planes) or time.perf_counter() - t0 > seconds:
             break
     dt = time.perf_counter() - t0
     return n * F_XY * F_XY / dt, n, dt
@@ -158,7 +165,7 @@ def run_reference(args, world, rank):
     line = {"impl": "reference", "metric": "field voxels/s", "value": value, "unit": "voxels/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "orders": "21x21", "layers": L_LAYERS,
+            "data": "synthetic", "config": {"workload": workload_name(), "orders": "21x21", "layers": L_LAYERS,
                                             "grid": [F_XY, F_XY, L_LAYERS * PLANES_PER_LAYER],
                                             "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cores, "kind": "oracle",
@@ -255,6 +262,31 @@ def run_ours(args, world, rank, local):
     whole_bytes = w_bytes + out_bytes
     step_roofline_ms = whole_bytes / (hbm * 1e9) * 1e3
 
+    # the other contraction precisions on the same inputs (same step, same timing rules)
+    variants = {}
+    if args.compare:
+        for prec in ("fp32", "split_bf16", "fp16"):
+            if prec == args.precision:
+                continue
+            vp = make_plan(prec)
+            vp.set_layers(Wd, gd, ad)
+            for _ in range(args.warmup):
+                vp.synthesize(out)
+            vp.enable_timing(True)
+            barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                vp.synthesize(out)
+            e1.record(stream)
+            barrier()
+            vk = vp.timings()
+            vp.check()
+            vms = e0.elapsed_time(e1) / args.steps
+            variants[prec] = {"value": world * voxels / (vms * 1e-3), "ms_per_step": vms,
+                              "contract_ms": vk["contract_ms"], "k_split": vp.info()["k_split"]}
+            vp.close()
+
     # end to end through the C ABI with HOST buffers (H2D of W/gamma/alpha, D2H of the field)
     e2e = None
     if not args.no_e2e:
@@ -287,7 +319,8 @@ def run_ours(args, world, rank, local):
     if rank == 0 and not args.no_cpu_baseline:
         rate, n, dt = oracle_sample_rate(W.astype(np.complex128), g, a, zb, zp, seconds=args.cpu_seconds)
         cpu = {"value": rate, "unit": "voxels/s", "cores": blas_threads(), "kind": "oracle",
-               "sample": f"{n} whole 256x256 planes of layer 1 (FP64 spectrum + direct sum), {dt:.1f} s"}
+               "sample": f"{n} whole 256x256 planes in z order, cycling the volume (FP64 spectrum + direct sum), "
+                             f"{dt:.1f} s"}
 
     if rank == 0:
         line = {
@@ -296,7 +329,7 @@ def run_ours(args, world, rank, local):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "fp32", "split_bf16": "bf16x3->fp32", "fp16": "fp16x2->fp32"}[args.precision],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "orders": "21x21", "M": M, "layers": L_LAYERS,
+            "config": {"workload": workload_name(), "orders": "21x21", "M": M, "layers": L_LAYERS,
                        "grid": [F_XY, F_XY, Fz], "precision": args.precision, "k_split": info["k_split"],
                        "l2": "inputs larger than L2 (W 597 MB, field 403 MB)",
                        "parallelism": f"replicas x{world}"},
@@ -310,6 +343,7 @@ def run_ours(args, world, rank, local):
             "clocks": clocks.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "variants": variants or None,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -329,7 +363,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--compare", action="store_true", help="also time the other contraction precisions")
+    ap.add_argument("--layers", type=int, default=32)
+    ap.add_argument("--planes-per-layer", type=int, default=8)
     args = ap.parse_args()
+    global L_LAYERS, PLANES_PER_LAYER
+    L_LAYERS, PLANES_PER_LAYER = args.layers, args.planes_per_layer
     if args.warmup < 3:
         args.warmup = 3
     world, rank, local = dist_setup()

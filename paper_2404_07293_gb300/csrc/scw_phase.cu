@@ -2,13 +2,17 @@
 // (paper Eq. 7 and Eq. 30-31, with the per-layer precompute of Sec. 4.1), the
 // exterior spectra of Eq. 9, and the one-off conversions of W.
 //
-// Phase arithmetic: the argument is range-reduced in FP64 in units of cycles,
+// Phase arithmetic: the argument is range-reduced in units of cycles,
 //   t = Re(gamma) (z - z_ref) / lambda,  r = t - rint(t)  (|r| <= 1/2),
-// and only the reduced r goes to FP32 sincospif(2 r); the decay
-// exp(-2 pi Im(gamma) (z - z_ref) / lambda) takes its exponent from FP64 too.
-// Large k Re(gamma) z therefore loses no digits, and evanescent Im(gamma)
-// never overflows: with forward modes referenced to the layer top and backward
-// modes to its bottom the exponent is never positive inside a layer.
+// and only the reduced r goes to FP32 sincospif(2 r); the decay is
+// exp(-2 pi Im(gamma) (z - z_ref) / lambda). The per-mode factors
+// Re(gamma)/lambda and the per-plane offsets z - z_ref are formed in FP64 once
+// and carried as float pairs (hi + lo); the per-plane product t then uses an
+// exact FP32 two-product, because FP64 throughput on this part is a small
+// fraction of FP32. Large k Re(gamma) z therefore loses no digits, and
+// evanescent Im(gamma) never overflows: with forward modes referenced to the
+// layer top and backward modes to its bottom the exponent is never positive
+// inside a layer.
 #include "scw_internal.cuh"
 
 namespace scw {
@@ -37,67 +41,128 @@ template <> __device__ __forceinline__ float from_lp<__half>(__half x) { return 
 template <typename T>
 struct Pair { T a, b; };
 
+// Per-plane offsets from both reference planes of a unit's layer, split into
+// float pairs (hi + lo == the FP64 difference to ~2^-48 relative).
+struct PlaneOffsets {
+  float f_hi[kMaxPlanesPerLayer], f_lo[kMaxPlanesPerLayer];  // z - z_{l-1}
+  float b_hi[kMaxPlanesPerLayer], b_lo[kMaxPlanesPerLayer];  // z - z_l
+};
+
+__device__ __forceinline__ void load_offsets(PlaneOffsets& o, const LayerUnit& u, const double* zplanes,
+                                             const double* zb) {
+  for (int f = threadIdx.x; f < u.nf; f += blockDim.x) {
+    const double z = zplanes[u.f0 + f];
+    const double df = z - zb[u.layer], db = z - zb[u.layer + 1];
+    o.f_hi[f] = (float)df;
+    o.f_lo[f] = (float)(df - (double)o.f_hi[f]);
+    o.b_hi[f] = (float)db;
+    o.b_lo[f] = (float)(db - (double)o.b_hi[f]);
+  }
+}
+
+// exp(i k gamma dz) from a = Re(gamma)/lambda split as a_hi + a_lo, c = -2 pi Im(gamma)/lambda
+// and dz = d_hi + d_lo. The cycle count t = a dz is formed exactly enough in FP32
+// (two-product: p + e == a_hi d_hi exactly), each part range-reduced on its own,
+// so no FP64 instruction runs per plane.
+__device__ __forceinline__ float2 mode_factor_df(float a_hi, float a_lo, float c, float d_hi, float d_lo) {
+  const float p = a_hi * d_hi;
+  const float e = fmaf(a_hi, d_hi, -p);
+  const float t_lo = fmaf(a_hi, d_lo, fmaf(a_lo, d_hi, e));
+  const float r = (p - rintf(p)) + (t_lo - rintf(t_lo));
+  float sn, cs;
+  sincospif(2.0f * r, &sn, &cs);
+  const float mag = expf(c * (d_hi + d_lo));
+  return make_float2(cs * mag, sn * mag);
+}
+
+struct ModeConst {
+  float a_hi, a_lo, c;
+  float2 alpha;
+};
+
+__device__ __forceinline__ ModeConst mode_const(double2 g, double2 al, double inv_lam) {
+  ModeConst m;
+  const double a = g.x * inv_lam;
+  m.a_hi = (float)a;
+  m.a_lo = (float)(a - (double)m.a_hi);
+  m.c = (float)(g.y * inv_lam) * -6.2831853071795865f;
+  m.alpha = make_float2((float)al.x, (float)al.y);
+  return m;
+}
+
 // B operand of the tensor-core contraction, [unit][NB][8M] with NB = 2 F_pad:
 // row f holds (Re c_j, -Im c_j) at columns (2j, 2j+1), row F_pad + f holds
 // (Im c_j, Re c_j); with A = W viewed as interleaved reals this gives
 // [Re S | Im S] (the complex product as one real GEMM). hi = round(x),
-// lo = round(x - hi).
+// lo = round(x - hi). One thread per mode j loops over the unit's planes.
 template <typename T>
-__global__ void phases_tc_kernel(const LayerUnit* __restrict__ units, const double* __restrict__ zplanes,
-                                 const double* __restrict__ zb, const double2* __restrict__ gamma,
-                                 const double2* __restrict__ alpha, int M, int F_pad, double inv_lam,
-                                 T* __restrict__ Bhi, T* __restrict__ Blo) {
+__global__ void __launch_bounds__(128) phases_tc_kernel(const LayerUnit* __restrict__ units,
+                                                        const double* __restrict__ zplanes,
+                                                        const double* __restrict__ zb,
+                                                        const double2* __restrict__ gamma,
+                                                        const double2* __restrict__ alpha, int M, int F_pad,
+                                                        double inv_lam, T* __restrict__ Bhi, T* __restrict__ Blo) {
+  __shared__ PlaneOffsets off;
+  const LayerUnit u = units[blockIdx.y];
+  load_offsets(off, u, zplanes, zb);
+  __syncthreads();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int f = blockIdx.y;
-  const LayerUnit u = units[blockIdx.z];
   const int M4 = 4 * M;
   if (j >= M4) return;
   const size_t K8 = (size_t)8 * M;
   const int NB = 2 * F_pad;
-  float2 cv = make_float2(0.f, 0.f);
-  if (f < u.nf) {
-    const double z = zplanes[u.f0 + f];
-    const double zref = (j < 2 * M) ? zb[u.layer] : zb[u.layer + 1];
-    const double2 g = gamma[(size_t)u.layer * M4 + j];
-    const double2 a = alpha[(size_t)u.layer * M4 + j];
-    cv = cmulf(make_float2((float)a.x, (float)a.y), mode_factor(g, z - zref, inv_lam));
+  const ModeConst mc = mode_const(gamma[(size_t)u.layer * M4 + j], alpha[(size_t)u.layer * M4 + j], inv_lam);
+  const bool fwd = j < 2 * M;
+  const size_t base = (size_t)blockIdx.y * NB * K8 + 2 * (size_t)j;  // B is per work unit
+  for (int f = 0; f < F_pad; ++f) {
+    float2 cv = make_float2(0.f, 0.f);
+    if (f < u.nf) {
+      const float dh = fwd ? off.f_hi[f] : off.b_hi[f];
+      const float dl = fwd ? off.f_lo[f] : off.b_lo[f];
+      cv = cmulf(mc.alpha, mode_factor_df(mc.a_hi, mc.a_lo, mc.c, dh, dl));
+    }
+    const float v0[2] = {cv.x, -cv.y};
+    const float v1[2] = {cv.y, cv.x};
+    Pair<T> h0, l0, h1, l1;
+    h0.a = to_lp<T>(v0[0]); h0.b = to_lp<T>(v0[1]);
+    l0.a = to_lp<T>(v0[0] - from_lp<T>(h0.a)); l0.b = to_lp<T>(v0[1] - from_lp<T>(h0.b));
+    h1.a = to_lp<T>(v1[0]); h1.b = to_lp<T>(v1[1]);
+    l1.a = to_lp<T>(v1[0] - from_lp<T>(h1.a)); l1.b = to_lp<T>(v1[1] - from_lp<T>(h1.b));
+    const size_t i0 = base + (size_t)f * K8, i1 = base + (size_t)(F_pad + f) * K8;
+    *reinterpret_cast<Pair<T>*>(Bhi + i0) = h0;
+    *reinterpret_cast<Pair<T>*>(Blo + i0) = l0;
+    *reinterpret_cast<Pair<T>*>(Bhi + i1) = h1;
+    *reinterpret_cast<Pair<T>*>(Blo + i1) = l1;
   }
-  const float v0[2] = {cv.x, -cv.y};
-  const float v1[2] = {cv.y, cv.x};
-  const size_t base = (size_t)blockIdx.z * NB * K8;  // B is per work unit
-  const size_t i0 = base + (size_t)f * K8 + 2 * (size_t)j;
-  const size_t i1 = base + (size_t)(F_pad + f) * K8 + 2 * (size_t)j;
-  Pair<T> h0, l0, h1, l1;
-  h0.a = to_lp<T>(v0[0]); h0.b = to_lp<T>(v0[1]);
-  l0.a = to_lp<T>(v0[0] - from_lp<T>(h0.a)); l0.b = to_lp<T>(v0[1] - from_lp<T>(h0.b));
-  h1.a = to_lp<T>(v1[0]); h1.b = to_lp<T>(v1[1]);
-  l1.a = to_lp<T>(v1[0] - from_lp<T>(h1.a)); l1.b = to_lp<T>(v1[1] - from_lp<T>(h1.b));
-  *reinterpret_cast<Pair<T>*>(Bhi + i0) = h0;
-  *reinterpret_cast<Pair<T>*>(Blo + i0) = l0;
-  *reinterpret_cast<Pair<T>*>(Bhi + i1) = h1;
-  *reinterpret_cast<Pair<T>*>(Blo + i1) = l1;
 }
 
-// FP32 path: C[unit][j][f] complex64, plane index fastest.
-__global__ void phases_fp32_kernel(const LayerUnit* __restrict__ units, const double* __restrict__ zplanes,
-                                   const double* __restrict__ zb, const double2* __restrict__ gamma,
-                                   const double2* __restrict__ alpha, int M, int F_pad, double inv_lam,
-                                   float2* __restrict__ C) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+// FP32 path: C[unit][j][f] complex64, plane index fastest; one thread per mode.
+__global__ void __launch_bounds__(128) phases_fp32_kernel(const LayerUnit* __restrict__ units,
+                                                          const double* __restrict__ zplanes,
+                                                          const double* __restrict__ zb,
+                                                          const double2* __restrict__ gamma,
+                                                          const double2* __restrict__ alpha, int M, int F_pad,
+                                                          double inv_lam, float2* __restrict__ C) {
+  __shared__ PlaneOffsets off;
   const LayerUnit u = units[blockIdx.y];
+  load_offsets(off, u, zplanes, zb);
+  __syncthreads();
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int M4 = 4 * M;
-  if (idx >= M4 * F_pad) return;
-  const int j = idx / F_pad;
-  const int f = idx - j * F_pad;
-  float2 cv = make_float2(0.f, 0.f);
-  if (f < u.nf) {
-    const double z = zplanes[u.f0 + f];
-    const double zref = (j < 2 * M) ? zb[u.layer] : zb[u.layer + 1];
-    const double2 g = gamma[(size_t)u.layer * M4 + j];
-    const double2 a = alpha[(size_t)u.layer * M4 + j];
-    cv = cmulf(make_float2((float)a.x, (float)a.y), mode_factor(g, z - zref, inv_lam));
+  if (j >= M4) return;
+  const ModeConst mc = mode_const(gamma[(size_t)u.layer * M4 + j], alpha[(size_t)u.layer * M4 + j], inv_lam);
+  const bool fwd = j < 2 * M;
+  float2* dst = C + ((size_t)blockIdx.y * M4 + j) * F_pad;  // C is per work unit
+  for (int f = 0; f < F_pad; f += 2) {
+    float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+    if (f < u.nf)
+      c0 = cmulf(mc.alpha, mode_factor_df(mc.a_hi, mc.a_lo, mc.c, fwd ? off.f_hi[f] : off.b_hi[f],
+                                          fwd ? off.f_lo[f] : off.b_lo[f]));
+    if (f + 1 < u.nf)
+      c1 = cmulf(mc.alpha, mode_factor_df(mc.a_hi, mc.a_lo, mc.c, fwd ? off.f_hi[f + 1] : off.b_hi[f + 1],
+                                          fwd ? off.f_lo[f + 1] : off.b_lo[f + 1]));
+    *reinterpret_cast<float4*>(dst + f) = make_float4(c0.x, c0.y, c1.x, c1.y);
   }
-  C[((size_t)blockIdx.y * M4 + j) * F_pad + f] = cv;  // C is per work unit
 }
 
 // Exterior planes (Eq. 9 with the reflected wave travelling towards -z):
@@ -206,7 +271,7 @@ cudaError_t launch_transpose_layers(const float2* W, float2* Wt, int L, int rows
 cudaError_t launch_phases_tc(const Plan& p, cudaStream_t st) {
   const int n_units = (int)p.units.size();
   if (n_units == 0) return cudaSuccess;
-  dim3 grid((4 * p.M + 127) / 128, p.F_pad, n_units);
+  dim3 grid((4 * p.M + 127) / 128, n_units);
   const double inv_lam = 1.0 / p.lambda;
   if (p.precision == SCW_PREC_SPLIT_BF16)
     phases_tc_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(
@@ -222,9 +287,8 @@ cudaError_t launch_phases_tc(const Plan& p, cudaStream_t st) {
 cudaError_t launch_phases_fp32(const Plan& p, cudaStream_t st) {
   const int n_units = (int)p.units.size();
   if (n_units == 0) return cudaSuccess;
-  const int n = 4 * p.M * p.F_pad;
-  dim3 grid((n + 255) / 256, n_units);
-  phases_fp32_kernel<<<grid, 256, 0, st>>>(p.d_units, p.d_zplanes, p.d_zbounds, p.gamma, p.alpha, p.M,
+  dim3 grid((4 * p.M + 127) / 128, n_units);
+  phases_fp32_kernel<<<grid, 128, 0, st>>>(p.d_units, p.d_zplanes, p.d_zbounds, p.gamma, p.alpha, p.M,
                                            p.F_pad, 1.0 / p.lambda, p.Cf);
   return cudaGetLastError();
 }
