@@ -175,6 +175,35 @@ scw_status scw_plan_enable_timing(scw_plan_t plan, int on);
 /* Synchronises on the recorded events, returns per-call averages and clears them. */
 scw_status scw_plan_get_timings(scw_plan_t plan, scw_kernel_times* t);
 
+/* ---- allocation-free recompose ------------------------------------------------
+ * The paper has no counterpart to this entry point: it exists for callers that
+ * cannot allocate device memory -- code that runs inside a host framework's own
+ * memory pool, latency-critical loops that must not pay cudaMalloc's implicit
+ * device synchronisation, or processes that forbid allocation after start-up.
+ * Such callers cannot create a plan (plan creation allocates its workspace), so
+ * this call takes the sizes directly and does the recompose step of
+ * scw_recompose (Eq. 10: x-pass and y-pass) with the same kernels.
+ *
+ *   S    DEVICE complex64 [Fz][3][U V] spectra (caller-owned input)
+ *   out  DEVICE complex64 [3][Fz][Fy][Fx] field (caller-owned output, 16-byte aligned)
+ *   U, V, X, Y, Fx, Fy, x0, y0 as in scw_desc; Fz planes.
+ *
+ * Its scratch is one fixed array of SCW_NOALLOC_SCRATCH_BYTES (64 MiB) compiled
+ * into the library as a __device__ variable: every GPU on which the library is
+ * loaded holds those 64 MiB until the process exits. A call needs
+ *   3 Fz V Fx * 8 bytes + (Fx/8) U * 8 + (Fy/8) V * 8 + 4 Fz (+ alignment)
+ * and returns SCW_ERR_UNSUPPORTED, without launching anything, when that is
+ * above the limit. It calls no cudaMalloc, cudaFree or other allocating routine.
+ * The first call on a device (with that device current) looks up the array's
+ * device address with cudaGetSymbolAddress; make that first call before any
+ * stream capture. Every call on a device shares the array and it keeps the last
+ * call's contents; each call rewrites all of the scratch it reads, so nothing
+ * has to be cleared, but calls whose work overlaps on the GPU (different
+ * streams, no ordering between them) race on the scratch and corrupt each other. */
+#define SCW_NOALLOC_SCRATCH_BYTES (64u << 20)
+scw_status scw_recompose_noalloc(int U, int V, double X, double Y, int Fx, int Fy, int Fz, double x0,
+                                 double y0, const void* S, void* out, void* stream);
+
 const char* scw_status_string(scw_status s);
 const char* scw_last_error(void);
 int scw_version(void);

@@ -53,6 +53,8 @@ SIGNATURES = {
     "scw_plan_get_info": (c_int, [c_void_p, POINTER(ScwPlanInfo)]),
     "scw_plan_enable_timing": (c_int, [c_void_p, c_int]),
     "scw_plan_get_timings": (c_int, [c_void_p, POINTER(ScwKernelTimes)]),
+    "scw_recompose_noalloc": (c_int, [c_int, c_int, c_double, c_double, c_int, c_int, c_int, c_double, c_double,
+                                      c_void_p, c_void_p, c_void_p]),
     "scw_status_string": (c_char_p, [c_int]),
     "scw_last_error": (c_char_p, []),
     "scw_version": (c_int, []),

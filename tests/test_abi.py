@@ -93,3 +93,13 @@ def test_no_cpu_fallback_without_gpu(lib):
     assert st == 4
     with pytest.raises(scw.ScwError):
         scw.Plan(3, 3, 2, 1.0, 2.0, 2.0, [0, 0.25, 0.5], 16, 16, [0.1, 0.3])
+
+
+def test_noalloc_rejects_sizes_above_its_scratch(lib):
+    """The allocation-free recompose checks its fixed scratch size on the host,
+    before looking at the device or launching anything."""
+    dummy = ctypes.c_void_p(256)  # never dereferenced: the size check comes first
+    st = lib.scw_recompose_noalloc(21, 21, 16.0, 16.0, 4096, 4096, 100, 0.0, 0.0, dummy, dummy, None)
+    assert st == 2
+    assert b"scratch" in lib.scw_last_error()
+    assert lib.scw_recompose_noalloc(21, 21, 16.0, 16.0, 256, 256, 8, 0.0, 0.0, None, dummy, None) == 1
