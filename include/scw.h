@@ -74,8 +74,11 @@ typedef enum {
 
 enum {
   SCW_FLAG_EXTERIOR = 1u, /* planes outside [z0, z_L] allowed (needs p_inc/p_ref/p_trn) */
-  SCW_FLAG_HOST_IO = 2u   /* plan also owns device copies of W/gamma/alpha/p for
+  SCW_FLAG_HOST_IO = 2u,  /* plan also owns device copies of W/gamma/alpha/p for
                              scw_synthesize_host                                        */
+  SCW_FLAG_AUTOTUNE = 4u  /* time the best contraction schedules on the device at plan
+                             creation (otherwise a makespan model picks the split);
+                             results are cached per device and problem shape           */
 };
 
 typedef struct {
@@ -102,6 +105,11 @@ typedef struct {
   size_t workspace_bytes;   /* device bytes owned by the plan                            */
   double convert_ms;        /* GPU time of the last W conversion (scw_plan_set_layers)   */
   int kernels_per_synthesis;/* kernel launches queued by one scw_synthesize              */
+  int items;                /* 1, or the batch size                                      */
+  int contract_ctas;        /* persistent CTAs of the tensor-core contraction            */
+  int contract_tasks;       /* (item, unit, row tile, split) tasks they share            */
+  double schedule_max_load; /* longest CTA's work in K-stages (+2 per task)              */
+  double schedule_mean_load;/* mean CTA work in the same unit                            */
 } scw_plan_info;
 
 /* Validate `desc`, assign planes to layers (Sec. 2.6.2: half-open layers, the
@@ -130,8 +138,31 @@ scw_status scw_plan_set_layers(scw_plan_t plan, const void* W, const void* gamma
                                const void* p_trn, void* stream);
 
 /* The whole hot path: phases (a), contraction (b), inverse FFT (c).
- *   out  DEVICE complex64 [3][Fz][Fy][Fx], x fastest (component-major). */
+ *   out  DEVICE complex64 [3][Fz][Fy][Fx], x fastest (component-major).
+ * The first call for a given `out` launches the kernels and captures them into
+ * a CUDA graph; later calls with the same `out` replay the graph (one launch).
+ * scw_plan_set_layers and scw_plan_set_timeout_ns drop the graph. */
 scw_status scw_synthesize(scw_plan_t plan, void* out, void* stream);
+
+/* ---- batched sweep (e.g. many wavenumbers of a spectroscopic measurement,
+ * Sec. 4.5): n independent items, each with its own orders, layers, grid and
+ * wavelength, synthesised by one set of kernels -- one persistent tensor-core
+ * contraction over a longest-first task schedule of all items, and batched
+ * phase / recompose launches -- replayed as one CUDA graph. All items share the
+ * precision; on the tensor-core path they also share the plane-slot count
+ * (the largest item's). SCW_FLAG_HOST_IO is not available here.
+ *   descs  HOST [n] descriptors (copied); k_split 0 lets the autotuner choose. */
+scw_status scw_plan_batched_create(const scw_desc* descs, int n, scw_plan_t* out);
+/* As scw_plan_set_layers, for item `item` of a batched plan. */
+scw_status scw_plan_batched_set_layers(scw_plan_t plan, int item, const void* W, const void* gamma,
+                                       const void* alpha, const void* p_inc, const void* p_ref,
+                                       const void* p_trn, void* stream);
+/* Synthesise every item: outs is a HOST array of n DEVICE pointers, item i's
+ * field complex64 [3][Fz_i][Fy_i][Fx_i]. Waits for the previous call's work on
+ * `stream` to have consumed the pointer table, then queues one graph launch. */
+scw_status scw_synthesize_batched(scw_plan_t plan, void* const* outs, void* stream);
+/* Human-readable record of the split choice (model and timed candidates). */
+const char* scw_plan_tune_report(scw_plan_t plan);
 
 /* Steps (a)+(b) only: the per-plane spectra.
  *   S  DEVICE complex64 [Fz][3][M] (S[z][c][m], Eq. 34 / Eq. 9). */
@@ -165,6 +196,7 @@ typedef struct {
   int calls;             /* synthesize calls averaged                      */
   double phases_ms;      /* step (a) incl. exterior planes, per call       */
   double contract_ms;    /* step (b)                                       */
+  double recompose_ms;   /* step (c): both directions and the field stores */
   double xpass_ms;       /* step (c), x direction                          */
   double ypass_ms;       /* step (c), y direction and the field stores     */
   double total_ms;       /* first to last event                            */
@@ -188,19 +220,21 @@ scw_status scw_plan_get_timings(scw_plan_t plan, scw_kernel_times* t);
  *   out  DEVICE complex64 [3][Fz][Fy][Fx] field (caller-owned output, 16-byte aligned)
  *   U, V, X, Y, Fx, Fy, x0, y0 as in scw_desc; Fz planes.
  *
- * Its scratch is one fixed array of SCW_NOALLOC_SCRATCH_BYTES (64 MiB) compiled
+ * Its scratch is one fixed array of SCW_NOALLOC_SCRATCH_BYTES (8 MiB) compiled
  * into the library as a __device__ variable: every GPU on which the library is
- * loaded holds those 64 MiB until the process exits. A call needs
- *   3 Fz V Fx * 8 bytes + (Fx/8) U * 8 + (Fy/8) V * 8 + 4 Fz (+ alignment)
- * and returns SCW_ERR_UNSUPPORTED, without launching anything, when that is
- * above the limit. It calls no cudaMalloc, cudaFree or other allocating routine.
+ * loaded holds those 8 MiB until the process exits. A call needs its fold
+ * twiddle tables and plane tables,
+ *   8 (Fx/8) Ur + 8 (Fy/8) Vr + 12 Fz bytes (each table 256-byte aligned),
+ * with Ur, Vr the order counts U, V padded to a multiple of 8 after an offset
+ * of at most 7, and returns SCW_ERR_UNSUPPORTED, without launching anything,
+ * when that is above the limit. It calls no cudaMalloc, cudaFree or other allocating routine.
  * The first call on a device (with that device current) looks up the array's
  * device address with cudaGetSymbolAddress; make that first call before any
  * stream capture. Every call on a device shares the array and it keeps the last
  * call's contents; each call rewrites all of the scratch it reads, so nothing
  * has to be cleared, but calls whose work overlaps on the GPU (different
  * streams, no ordering between them) race on the scratch and corrupt each other. */
-#define SCW_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define SCW_NOALLOC_SCRATCH_BYTES (8u << 20)
 scw_status scw_recompose_noalloc(int U, int V, double X, double Y, int Fx, int Fy, int Fz, double x0,
                                  double y0, const void* S, void* out, void* stream);
 

@@ -11,10 +11,29 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (FLAG_EXTERIOR, FLAG_HOST_IO, PRECISION, ScwDesc, ScwError, ScwKernelTimes, ScwPlanInfo, check,
-                   load)
+from ._lib import (FLAG_AUTOTUNE, FLAG_EXTERIOR, FLAG_HOST_IO, PRECISION, ScwDesc, ScwError, ScwKernelTimes,
+                   ScwPlanInfo, check, load)
 
-__all__ = ["Plan", "ScwError", "load", "PRECISION"]
+__all__ = ["Plan", "BatchedPlan", "ScwError", "load", "PRECISION"]
+
+
+def _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0, n_bot=1.0,
+               z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0, autotune=False):
+    """scw_desc for one item plus the host arrays it points to (keep them alive)."""
+    zb = np.ascontiguousarray(z_bounds, dtype=np.float64)
+    zp = np.ascontiguousarray(z_planes, dtype=np.float64)
+    if len(zb) != int(L) + 1:
+        raise ValueError("z_bounds must have L+1 entries")
+    nb = complex(n_bot)
+    flags = (FLAG_EXTERIOR if exterior else 0) | (FLAG_HOST_IO if host_io else 0) | (FLAG_AUTOTUNE if autotune else 0)
+    d = ScwDesc(U=int(U), V=int(V), L=int(L), lam=float(lam), X=float(X), Y=float(Y),
+                z_bounds=zb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                Fx=int(Fx), Fy=int(Fy), Fz=len(zp),
+                z_planes=zp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                x0=float(x0), y0=float(y0), n_top=float(n_top), n_bot_re=nb.real, n_bot_im=nb.imag,
+                z_inc=float(zb[0] if z_inc is None else z_inc),
+                precision=PRECISION[precision], flags=flags, k_split=int(k_split))
+    return d, (zb, zp)
 
 
 def _stream_handle(stream):
@@ -47,26 +66,16 @@ class Plan:
     """One synthesis configuration (scw_plan_create) and its workspace."""
 
     def __init__(self, U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0,
-                 n_bot=1.0, z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0):
+                 n_bot=1.0, z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0,
+                 autotune=False):
         self._lib = load()
         self.U, self.V, self.L = int(U), int(V), int(L)
         self.M = self.U * self.V
         self.Fx, self.Fy = int(Fx), int(Fy)
-        self._zb = np.ascontiguousarray(z_bounds, dtype=np.float64)
-        self._zp = np.ascontiguousarray(z_planes, dtype=np.float64)
-        self.Fz = len(self._zp)
-        if len(self._zb) != self.L + 1:
-            raise ValueError("z_bounds must have L+1 entries")
         self.exterior = bool(exterior)
-        nb = complex(n_bot)
-        d = ScwDesc(U=self.U, V=self.V, L=self.L, lam=float(lam), X=float(X), Y=float(Y),
-                    z_bounds=self._zb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                    Fx=self.Fx, Fy=self.Fy, Fz=self.Fz,
-                    z_planes=self._zp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                    x0=float(x0), y0=float(y0), n_top=float(n_top), n_bot_re=nb.real, n_bot_im=nb.imag,
-                    z_inc=float(self._zb[0] if z_inc is None else z_inc),
-                    precision=PRECISION[precision], flags=(FLAG_EXTERIOR if exterior else 0)
-                    | (FLAG_HOST_IO if host_io else 0), k_split=int(k_split))
+        d, (self._zb, self._zp) = _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0, y0, n_top, n_bot,
+                                             z_inc, precision, exterior, host_io, k_split, autotune)
+        self.Fz = len(self._zp)
         h = ctypes.c_void_p()
         check(self._lib.scw_plan_create(ctypes.byref(d), ctypes.byref(h)), "scw_plan_create")
         self._h = h
@@ -147,6 +156,93 @@ class Plan:
         i = ScwPlanInfo()
         check(self._lib.scw_plan_get_info(self._h, ctypes.byref(i)), "scw_plan_get_info")
         return {f: getattr(i, f) for f, _ in ScwPlanInfo._fields_}
+
+    def tune_report(self) -> str:
+        r = self._lib.scw_plan_tune_report(self._h)
+        return r.decode() if r else ""
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.scw_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BatchedPlan:
+    """Many independent items (e.g. the wavenumbers of a sweep) synthesised by
+    one set of kernels and replayed as one CUDA graph (scw_plan_batched_create).
+
+    ``items`` is a list of keyword dicts with the arguments of ``Plan`` (without
+    ``precision``/``host_io``)."""
+
+    def __init__(self, items, precision="split_bf16", autotune=False):
+        self._lib = load()
+        n = len(items)
+        descs = (ScwDesc * n)()
+        self._keep_desc = []
+        self.shapes = []
+        self.sizes = []
+        for i, kw in enumerate(items):
+            kw = dict(kw)
+            d, keep = _make_desc(precision=precision, autotune=autotune, **kw)
+            descs[i] = d
+            self._keep_desc.append(keep)
+            M = int(kw["U"]) * int(kw["V"])
+            self.sizes.append((int(kw["L"]), M))
+            self.shapes.append((3, len(keep[1]), int(kw["Fy"]), int(kw["Fx"])))
+        h = ctypes.c_void_p()
+        check(self._lib.scw_plan_batched_create(descs, n, ctypes.byref(h)), "scw_plan_batched_create")
+        self._h = h
+        self._keep = [()] * n
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def set_layers(self, i, W, gamma, alpha, p_inc=None, p_ref=None, p_trn=None, stream=None):
+        import torch
+        L, M = self.sizes[i]
+        args = [_dev_ptr(W, torch.complex64, (L, 3 * M, 4 * M), "W"),
+                _dev_ptr(gamma, torch.complex128, (L, 4 * M), "gamma"),
+                _dev_ptr(alpha, torch.complex128, (L, 4 * M), "alpha")]
+        for p, nme in ((p_inc, "p_inc"), (p_ref, "p_ref"), (p_trn, "p_trn")):
+            args.append(ctypes.c_void_p(0) if p is None else _dev_ptr(p, torch.complex128, (3, M), nme))
+        check(self._lib.scw_plan_batched_set_layers(self._h, int(i), *args, _stream_handle(stream)),
+              "scw_plan_batched_set_layers")
+        self._keep[i] = (W, gamma, alpha, p_inc, p_ref, p_trn)
+
+    def synthesize(self, outs=None, stream=None):
+        import torch
+        if outs is None:
+            outs = [torch.empty(s, dtype=torch.complex64, device="cuda") for s in self.shapes]
+        ptrs = (ctypes.c_void_p * len(outs))(*[_dev_ptr(o, torch.complex64, s, "out").value
+                                              for o, s in zip(outs, self.shapes)])
+        check(self._lib.scw_synthesize_batched(self._h, ptrs, _stream_handle(stream)), "scw_synthesize_batched")
+        return outs
+
+    def check(self, stream=None):
+        check(self._lib.scw_plan_check(self._h, _stream_handle(stream)), "scw_plan_check")
+
+    def enable_timing(self, on=True):
+        check(self._lib.scw_plan_enable_timing(self._h, 1 if on else 0), "scw_plan_enable_timing")
+
+    def timings(self) -> dict:
+        t = ScwKernelTimes()
+        check(self._lib.scw_plan_get_timings(self._h, ctypes.byref(t)), "scw_plan_get_timings")
+        return {f: getattr(t, f) for f, _ in ScwKernelTimes._fields_}
+
+    def info(self) -> dict:
+        i = ScwPlanInfo()
+        check(self._lib.scw_plan_get_info(self._h, ctypes.byref(i)), "scw_plan_get_info")
+        return {f: getattr(i, f) for f, _ in ScwPlanInfo._fields_}
+
+    def tune_report(self) -> str:
+        r = self._lib.scw_plan_tune_report(self._h)
+        return r.decode() if r else ""
 
     def close(self):
         if getattr(self, "_h", None):

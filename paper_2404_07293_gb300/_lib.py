@@ -14,6 +14,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARGUMENT", 2: "UNSUPPORTED", 3: "OUT_OF_MEM
 PRECISION = {"fp32": 0, "split_bf16": 1, "fp16": 2}
 FLAG_EXTERIOR = 1
 FLAG_HOST_IO = 2
+FLAG_AUTOTUNE = 4
 
 
 class ScwDesc(ctypes.Structure):
@@ -31,12 +32,14 @@ class ScwDesc(ctypes.Structure):
 class ScwPlanInfo(ctypes.Structure):
     _fields_ = [("M", c_int), ("active_layers", c_int), ("planes_per_layer_pad", c_int),
                 ("k_split", c_int), ("exterior_planes", c_int), ("workspace_bytes", c_size_t),
-                ("convert_ms", c_double), ("kernels_per_synthesis", c_int)]
+                ("convert_ms", c_double), ("kernels_per_synthesis", c_int), ("items", c_int),
+                ("contract_ctas", c_int), ("contract_tasks", c_int), ("schedule_max_load", c_double),
+                ("schedule_mean_load", c_double)]
 
 
 class ScwKernelTimes(ctypes.Structure):
-    _fields_ = [("calls", c_int), ("phases_ms", c_double), ("contract_ms", c_double), ("xpass_ms", c_double),
-                ("ypass_ms", c_double), ("total_ms", c_double)]
+    _fields_ = [("calls", c_int), ("phases_ms", c_double), ("contract_ms", c_double), ("recompose_ms", c_double),
+                ("xpass_ms", c_double), ("ypass_ms", c_double), ("total_ms", c_double)]
 
 
 # name -> (restype, argtypes); mirrors include/scw.h
@@ -48,6 +51,10 @@ SIGNATURES = {
     "scw_spectrum": (c_int, [c_void_p, c_void_p, c_void_p]),
     "scw_recompose": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scw_synthesize_host": (c_int, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
+    "scw_plan_batched_create": (c_int, [POINTER(ScwDesc), c_int, POINTER(c_void_p)]),
+    "scw_plan_batched_set_layers": (c_int, [c_void_p, c_int] + [c_void_p] * 6 + [c_void_p]),
+    "scw_synthesize_batched": (c_int, [c_void_p, POINTER(c_void_p), c_void_p]),
+    "scw_plan_tune_report": (c_char_p, [c_void_p]),
     "scw_plan_check": (c_int, [c_void_p, c_void_p]),
     "scw_plan_set_timeout_ns": (c_int, [c_void_p, c_uint64]),
     "scw_plan_get_info": (c_int, [c_void_p, POINTER(ScwPlanInfo)]),

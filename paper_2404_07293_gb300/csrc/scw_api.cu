@@ -1,15 +1,18 @@
 // Host side of libscw: argument validation, plane-to-layer assignment,
-// order / twiddle tables, workspace ownership and the launch sequence of
-// scw_synthesize. See include/scw.h for the contract of each entry point.
+// order / twiddle tables, workspace ownership, the contraction schedule and its
+// autotuner, CUDA-graph replay, and the launch sequence of scw_synthesize and
+// scw_synthesize_batched. See include/scw.h for the contract of each entry point.
 #include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <numeric>
+#include <queue>
 
 #include "scw_internal.cuh"
-
-struct scw_plan_s : public scw::Plan {};
 
 namespace scw {
 
@@ -21,7 +24,8 @@ scw_status set_error(scw_status s, const std::string& msg) {
 }
 
 scw_status cuda_error(cudaError_t e, const char* what) {
-  return set_error(SCW_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return set_error(e == cudaErrorMemoryAllocation ? SCW_ERR_OUT_OF_MEMORY : SCW_ERR_CUDA,
+                   std::string(what) + ": " + cudaGetErrorString(e));
 }
 
 // s_z = sqrt(n^2 - sx^2 - sy^2) on the decaying branch (Eq. 2): principal
@@ -54,19 +58,38 @@ static cudaError_t upload(T** p, const std::vector<T>& v, size_t& total) {
   return cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
 }
 
-static void free_plan(Plan* p) {
+static void free_item(Plan* p) {
   if (!p) return;
-  void* ptrs[] = {p->d_err,   p->d_units,  p->d_zplanes, p->d_zbounds, p->d_nsplit, p->d_nsplit1,
-                  p->d_ext_planes, p->d_sz_top, p->d_sz_bot, p->d_twx, p->d_twy,   p->Whi,
-                  p->Wlo,     p->Wh,       p->Wt,        p->Bhi,       p->Blo,      p->Cf,
-                  p->S_part,  p->T,        p->hio_W,     p->hio_gamma, p->hio_alpha, p->hio_p,
-                  p->hio_out};
+  void* ptrs[] = {p->d_units,   p->d_zplanes, p->d_zbounds, p->d_nsplit,   p->d_nsplit1, p->d_ext_planes,
+                  p->d_sz_top,  p->d_sz_bot,  p->d_twx,     p->d_twy,      p->Whi,       p->Wlo,
+                  p->Wh,        p->Wt,        p->Bhi,       p->Blo,        p->Cf,        p->S_part,
+                  p->T,         p->hio_W,     p->hio_gamma, p->hio_alpha,  p->hio_p,     p->hio_out};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
   if (p->ev1) cudaEventDestroy(p->ev1);
-  for (cudaEvent_t ev : p->tev) cudaEventDestroy(ev);
-  delete static_cast<scw_plan_s*>(p);
+  delete p;
+}
+
+cudaError_t allow_max_smem(const void* kernel) {
+  static std::mutex mu;
+  static std::vector<std::pair<const void*, int>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& d : done)
+    if (d.first == kernel && d.second == dev) return cudaSuccess;
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  // the dynamic limit plus the kernel's static shared memory may not exceed the opt-in maximum
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.push_back({kernel, dev});
+  return e;
 }
 
 static int round_planes(int nf) {
@@ -76,33 +99,14 @@ static int round_planes(int nf) {
   return -1;
 }
 
-}  // namespace scw
-
-using namespace scw;
-
-extern "C" {
-
-int scw_version(void) { return 1; }
-
-const char* scw_last_error(void) { return g_last_error.c_str(); }
-
-const char* scw_status_string(scw_status s) {
-  switch (s) {
-    case SCW_OK: return "ok";
-    case SCW_ERR_INVALID_ARGUMENT: return "invalid argument";
-    case SCW_ERR_UNSUPPORTED: return "unsupported";
-    case SCW_ERR_OUT_OF_MEMORY: return "out of memory";
-    case SCW_ERR_CUDA: return "CUDA error";
-    case SCW_ERR_TIMEOUT: return "device wait timed out";
-    case SCW_ERR_NUMERIC: return "non-finite value";
-    case SCW_ERR_STATE: return "call order violated";
-  }
-  return "unknown status";
+static int device_sms() {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
 }
 
-scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
-  if (!out) return set_error(SCW_ERR_INVALID_ARGUMENT, "out is NULL");
-  *out = nullptr;
+// ---------------------------------------------------------------- one item ---
+static scw_status validate_desc(const scw_desc* d) {
   if (!d) return set_error(SCW_ERR_INVALID_ARGUMENT, "desc is NULL");
   if (d->U < 1 || d->V < 1 || d->L < 1) return set_error(SCW_ERR_INVALID_ARGUMENT, "U, V and L must be >= 1");
   if ((long long)d->U * d->V > kMaxM) return set_error(SCW_ERR_UNSUPPORTED, "U*V exceeds 4096");
@@ -125,7 +129,10 @@ scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
       return set_error(SCW_ERR_INVALID_ARGUMENT, "z_planes must be non-decreasing");
   }
   if (!(d->n_top > 0)) return set_error(SCW_ERR_INVALID_ARGUMENT, "n_top must be positive");
+  return SCW_OK;
+}
 
+static scw_status check_device() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");
@@ -135,27 +142,19 @@ scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
   if (prop.major != 10 || prop.minor != 3)
     return set_error(SCW_ERR_CUDA, "libscw is built for sm_103a (GB300); device is sm_" + std::to_string(prop.major) +
                                        std::to_string(prop.minor));
+  return SCW_OK;
+}
 
-  Plan* p = new (std::nothrow) scw_plan_s();
-  if (!p) return set_error(SCW_ERR_OUT_OF_MEMORY, "host allocation failed");
-  p->U = d->U; p->V = d->V; p->M = d->U * d->V; p->L = d->L;
-  p->Fx = d->Fx; p->Fy = d->Fy; p->Fz = d->Fz;
-  p->lambda = d->lambda; p->X = d->X; p->Y = d->Y; p->x0 = d->x0; p->y0 = d->y0;
-  p->n_top = d->n_top; p->n_bot_re = d->n_bot_re; p->n_bot_im = d->n_bot_im; p->z_inc = d->z_inc;
-  p->precision = d->precision; p->flags = d->flags;
-  p->z_bounds.assign(d->z_bounds, d->z_bounds + d->L + 1);
-  p->z_planes.assign(d->z_planes, d->z_planes + d->Fz);
-
-  // plane -> region: half-open layers [z_{l-1}, z_l), the last one closed (Sec. 2.6.2)
+// Plane assignment and the natural plane-slot count of a descriptor.
+static scw_status assign_planes(Plan* p, std::vector<int>& ext, int& max_nf) {
   const double z0 = p->z_bounds.front(), zL = p->z_bounds.back();
   p->plane_region.resize(p->Fz);
-  std::vector<int> ext;
   for (int f = 0; f < p->Fz; ++f) {
     const double z = p->z_planes[f];
     int r;
     if (z < z0) r = -1;
     else if (z > zL) r = p->L;
-    else {
+    else {  // half-open layers [z_{l-1}, z_l), the last one closed (Sec. 2.6.2)
       r = (int)(std::upper_bound(p->z_bounds.begin(), p->z_bounds.end(), z) - p->z_bounds.begin()) - 1;
       r = std::min(r, p->L - 1);
     }
@@ -163,58 +162,32 @@ scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
     if (r < 0 || r >= p->L) ext.push_back(f);
   }
   p->n_exterior = (int)ext.size();
-  if (p->n_exterior && !(p->flags & SCW_FLAG_EXTERIOR)) {
-    free_plan(p);
+  if (p->n_exterior && !(p->flags & SCW_FLAG_EXTERIOR))
     return set_error(SCW_ERR_INVALID_ARGUMENT, "planes outside [z0, zL] need SCW_FLAG_EXTERIOR");
-  }
-  // active layers, split into chunks of at most kMaxPlanesPerLayer planes
-  int max_nf = 0;
-  for (int f = 0; f < p->Fz;) {
+  max_nf = 0;
+  for (int f = 0; f < p->Fz;) {  // active layers, split into chunks of at most kMaxPlanesPerLayer planes
     const int r = p->plane_region[f];
     int g = f;
     while (g < p->Fz && p->plane_region[g] == r) ++g;
-    if (r >= 0 && r < p->L) {
+    if (r >= 0 && r < p->L)
       for (int s = f; s < g; s += kMaxPlanesPerLayer) {
         LayerUnit u{r, s, std::min(kMaxPlanesPerLayer, g - s), 0};
         p->units.push_back(u);
         max_nf = std::max(max_nf, u.nf);
       }
-    }
     f = g;
   }
-  p->F_pad = std::max(8, round_planes(std::max(max_nf, 1)));
-  p->NB = 2 * p->F_pad;
+  return SCW_OK;
+}
 
-  // split of the 4M modes: aim for ~4 waves of work units, keep >= 4 K-stages per unit
-  const int n_units = (int)p->units.size();
-  const int K = 4 * p->M;
-  if (d->k_split > 0) {
-    p->k_split = d->k_split;
-  } else if (n_units > 0) {
-    const int slots = prop.multiProcessorCount * 2 * 4;
-    const bool fp32 = p->precision == SCW_PREC_FP32;
-    const int per_split_units = n_units * (fp32 ? (3 * p->M + 255) / 256 : (3 * p->M + 127) / 128);
-    int ks = (slots + per_split_units - 1) / per_split_units;
-    const int min_k = fp32 ? 128 : 4 * 32;  // modes per split (4 K-stages of 32 complex)
-    ks = std::max(1, std::min(ks, std::max(1, K / min_k)));
-    if (fp32) {  // shared-memory slice of C per CTA stays <= 96 KB
-      const int fch = p->F_pad >= 16 ? 16 : 8;
-      const int need = (int)(((size_t)K * fch * 8 + 96 * 1024 - 1) / (96 * 1024));
-      ks = std::max(ks, need);
-    }
-    p->k_split = ks;
-  }
-  if (p->k_split > K) p->k_split = K;
-  if (p->precision == SCW_PREC_FP32) {
-    const int fch = p->F_pad >= 16 ? 16 : 8;
-    const size_t per = (K + p->k_split - 1) / p->k_split;
-    if (per * fch * 8 > 200 * 1024) {
-      free_plan(p);
-      return set_error(SCW_ERR_UNSUPPORTED, "k_split too small for the FP32 contraction's shared memory");
-    }
-  }
+#define SCW_TRY(x)                                   \
+  do {                                               \
+    cudaError_t _e = (x);                            \
+    if (_e != cudaSuccess) return cuda_error(_e, #x); \
+  } while (0)
 
-  // host tables
+// Tables and every buffer except S_part (whose size depends on the split).
+static scw_status build_item(Plan* p, const std::vector<int>& ext) {
   std::vector<double2> szt(p->M), szb(p->M);
   for (int m = 0; m < p->M; ++m) {
     const int u = m % p->U - p->U / 2, v = m / p->U - p->V / 2;
@@ -224,54 +197,46 @@ scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
     szt[m] = make_double2(a.real(), a.imag());
     szb[m] = make_double2(b.real(), b.imag());
   }
+  // fold tables: order u at index p = u + U/2 + rot, rot = (-(U/2)) mod 8, rows padded to a multiple of 8
+  ItemDev& it = p->item;
+  std::memset(&it, 0, sizeof(it));
+  it.rotU = (8 - (p->U / 2) % 8) % 8;
+  it.rotV = (8 - (p->V / 2) % 8) % 8;
+  it.Up = (p->U + it.rotU + 7) / 8 * 8;
+  it.Vp = (p->V + it.rotV + 7) / 8 * 8;
   const int Qx = p->Fx / 8, Qy = p->Fy / 8;
-  std::vector<float2> twx((size_t)Qx * p->U), twy((size_t)Qy * p->V);
+  std::vector<float2> twx((size_t)Qx * it.Up, make_float2(0.f, 0.f)), twy((size_t)Qy * it.Vp, make_float2(0.f, 0.f));
   for (int b = 0; b < Qx; ++b)
     for (int ui = 0; ui < p->U; ++ui) {
       const int u = ui - p->U / 2;
-      twx[(size_t)b * p->U + ui] = cis_cycles((double)u * b / p->Fx + u * p->x0 / p->X);
+      twx[(size_t)(ui + it.rotU) * Qx + b] = cis_cycles((double)u * b / p->Fx + u * p->x0 / p->X);  // [p][b]
     }
   for (int b = 0; b < Qy; ++b)
     for (int vi = 0; vi < p->V; ++vi) {
       const int v = vi - p->V / 2;
-      twy[(size_t)b * p->V + vi] = cis_cycles((double)v * b / p->Fy + v * p->y0 / p->Y);
+      twy[(size_t)b * it.Vp + vi + it.rotV] = cis_cycles((double)v * b / p->Fy + v * p->y0 / p->Y);
     }
-  std::vector<int> nsplit(p->Fz), ones(p->Fz, 1);
-  for (int f = 0; f < p->Fz; ++f) nsplit[f] = (p->plane_region[f] >= 0 && p->plane_region[f] < p->L) ? p->k_split : 1;
-
+  std::vector<int> ones(p->Fz, 1);
   size_t& tot = p->workspace_bytes;
   const size_t L = p->L, M = p->M;
-#define SCW_TRY(x)                                   \
-  do {                                               \
-    cudaError_t _e = (x);                            \
-    if (_e != cudaSuccess) {                         \
-      free_plan(p);                                  \
-      if (_e == cudaErrorMemoryAllocation)           \
-        return set_error(SCW_ERR_OUT_OF_MEMORY, #x); \
-      return cuda_error(_e, #x);                     \
-    }                                                \
-  } while (0)
-  SCW_TRY(dalloc(&p->d_err, 1, tot));
-  SCW_TRY(cudaMemset(p->d_err, 0, sizeof(int)));
+  const size_t n_units = p->units.size();
   SCW_TRY(upload(&p->d_units, p->units, tot));
   SCW_TRY(upload(&p->d_zplanes, p->z_planes, tot));
   SCW_TRY(upload(&p->d_zbounds, p->z_bounds, tot));
-  SCW_TRY(upload(&p->d_nsplit, nsplit, tot));
   SCW_TRY(upload(&p->d_nsplit1, ones, tot));
   SCW_TRY(upload(&p->d_ext_planes, ext, tot));
   SCW_TRY(upload(&p->d_sz_top, szt, tot));
   SCW_TRY(upload(&p->d_sz_bot, szb, tot));
   SCW_TRY(upload(&p->d_twx, twx, tot));
   SCW_TRY(upload(&p->d_twy, twy, tot));
-  SCW_TRY(dalloc(&p->S_part, (size_t)p->k_split * p->Fz * 3 * M, tot));
-  SCW_TRY(cudaMemset(p->S_part, 0, (size_t)p->k_split * p->Fz * 3 * M * sizeof(float2)));
   SCW_TRY(dalloc(&p->T, (size_t)p->Fz * 3 * p->V * p->Fx, tot));
   if (n_units > 0) {
     if (p->precision == SCW_PREC_FP32) {
       SCW_TRY(dalloc(&p->Wt, L * 3 * M * 4 * M, tot));
-      SCW_TRY(dalloc(&p->Cf, (size_t)n_units * 4 * M * p->F_pad, tot));
+      SCW_TRY(dalloc(&p->Cf, n_units * 4 * M * p->F_pad, tot));
     } else {
-      const size_t nA = L * 3 * M * 8 * M, nB = (size_t)n_units * p->NB * 8 * M;
+      const size_t nk = (8 * M + 63) / 64;
+      const size_t nA = L * 3 * M * nk * 64, nB = n_units * nk * p->NB * 64;
       if (p->precision == SCW_PREC_SPLIT_BF16) {
         SCW_TRY(dalloc(&p->Whi, nA, tot));
         SCW_TRY(dalloc(&p->Wlo, nA, tot));
@@ -285,11 +250,6 @@ scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
       p->Blo = bl;
       SCW_TRY(cudaMemset(p->Bhi, 0, nB * 2));
       SCW_TRY(cudaMemset(p->Blo, 0, nB * 2));
-      std::string why;
-      if (!encode_tensor_maps(*p, why)) {
-        free_plan(p);
-        return set_error(SCW_ERR_CUDA, why);
-      }
     }
   }
   if (p->flags & SCW_FLAG_HOST_IO) {
@@ -301,8 +261,664 @@ scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
   }
   SCW_TRY(cudaEventCreate(&p->ev0));
   SCW_TRY(cudaEventCreate(&p->ev1));
-#undef SCW_TRY
-  *out = static_cast<scw_plan_s*>(p);
+  return SCW_OK;
+}
+
+// S_part and the split table for the chosen k_split, then the kernels' view of the item.
+static scw_status finish_item(Plan* p) {
+  size_t& tot = p->workspace_bytes;
+  if (p->S_part) {
+    cudaFree(p->S_part);
+    p->S_part = nullptr;
+  }
+  if (p->d_nsplit) {
+    cudaFree(p->d_nsplit);
+    p->d_nsplit = nullptr;
+  }
+  const size_t M = p->M;
+  std::vector<int> nsplit(p->Fz);
+  for (int f = 0; f < p->Fz; ++f) nsplit[f] = (p->plane_region[f] >= 0 && p->plane_region[f] < p->L) ? p->k_split : 1;
+  SCW_TRY(upload(&p->d_nsplit, nsplit, tot));
+  SCW_TRY(dalloc(&p->S_part, (size_t)p->k_split * p->Fz * 3 * M, tot));
+  SCW_TRY(cudaMemset(p->S_part, 0, (size_t)p->k_split * p->Fz * 3 * M * sizeof(float2)));
+  ItemDev& it = p->item;
+  it.units = p->d_units;
+  it.zplanes = p->d_zplanes;
+  it.zbounds = p->d_zbounds;
+  it.gamma = p->gamma;
+  it.alpha = p->alpha;
+  it.Ahi = p->precision == SCW_PREC_SPLIT_BF16 ? static_cast<const void*>(p->Whi) : static_cast<const void*>(p->Wh);
+  it.Alo = p->Wlo;
+  it.Bhi = p->Bhi;
+  it.Blo = p->Blo;
+  it.S_part = p->S_part;
+  it.nsplit = p->d_nsplit;
+  it.twx = p->d_twx;
+  it.twy = p->d_twy;
+  it.T = p->T;
+  it.split_stride = (size_t)p->Fz * 3 * M;
+  it.inv_lam = 1.0 / p->lambda;
+  it.M = p->M; it.U = p->U; it.V = p->V; it.Fx = p->Fx; it.Fy = p->Fy; it.Fz = p->Fz;
+  it.F_pad = p->F_pad;
+  it.k_split = p->k_split;
+  it.n_tiles = (3 * p->M + 127) / 128;
+  it.nk = (8 * p->M + 63) / 64;
+  it.n_units = (int)p->units.size();
+  return SCW_OK;
+}
+
+static scw_status create_item(const scw_desc* d, int force_F_pad, Plan** out) {
+  *out = nullptr;
+  Plan* p = new (std::nothrow) Plan();
+  if (!p) return set_error(SCW_ERR_OUT_OF_MEMORY, "host allocation failed");
+  p->U = d->U; p->V = d->V; p->M = d->U * d->V; p->L = d->L;
+  p->Fx = d->Fx; p->Fy = d->Fy; p->Fz = d->Fz;
+  p->lambda = d->lambda; p->X = d->X; p->Y = d->Y; p->x0 = d->x0; p->y0 = d->y0;
+  p->n_top = d->n_top; p->n_bot_re = d->n_bot_re; p->n_bot_im = d->n_bot_im; p->z_inc = d->z_inc;
+  p->precision = d->precision; p->flags = d->flags;
+  p->z_bounds.assign(d->z_bounds, d->z_bounds + d->L + 1);
+  p->z_planes.assign(d->z_planes, d->z_planes + d->Fz);
+  std::vector<int> ext;
+  int max_nf = 0;
+  scw_status s = assign_planes(p, ext, max_nf);
+  if (s != SCW_OK) {
+    free_item(p);
+    return s;
+  }
+  p->F_pad = std::max({8, round_planes(std::max(max_nf, 1)), force_F_pad});
+  p->NB = 2 * p->F_pad;
+  p->k_split = std::max(1, d->k_split);
+  s = build_item(p, ext);
+  if (s != SCW_OK) {
+    free_item(p);
+    return s;
+  }
+  *out = p;
+  return SCW_OK;
+}
+
+// ------------------------------------------------------- contraction schedule ---
+struct TaskCost {
+  double cost;
+  int4 t;
+};
+
+static void item_tasks(const Plan* p, int item, int ks, std::vector<TaskCost>& out) {
+  const int nk = (8 * p->M + 63) / 64;
+  const int per = (nk + ks - 1) / ks;
+  const int tiles = (3 * p->M + 127) / 128;
+  for (int u = 0; u < (int)p->units.size(); ++u)
+    for (int t = 0; t < tiles; ++t)
+      for (int s = 0; s < ks; ++s) {
+        const int kc = std::max(0, std::min(nk, s * per + per) - s * per);
+        out.push_back({kc + 2.0, make_int4(item, u, t, s)});  // +2 stages: epilogue and hand-off
+      }
+}
+
+// Longest-processing-time-first assignment of tasks to G persistent CTAs.
+static void lpt(std::vector<TaskCost>& tasks, int G, std::vector<int>& cta_off, std::vector<int4>& order,
+                double& max_load, double& mean_load) {
+  std::stable_sort(tasks.begin(), tasks.end(), [](const TaskCost& a, const TaskCost& b) { return a.cost > b.cost; });
+  using E = std::pair<double, int>;
+  std::priority_queue<E, std::vector<E>, std::greater<E>> heap;
+  for (int g = 0; g < G; ++g) heap.push({0.0, g});
+  std::vector<std::vector<int4>> per(G);
+  for (const auto& tc : tasks) {
+    E e = heap.top();
+    heap.pop();
+    per[e.second].push_back(tc.t);
+    heap.push({e.first + tc.cost, e.second});
+  }
+  max_load = 0;
+  double sum = 0;
+  while (!heap.empty()) {
+    max_load = std::max(max_load, heap.top().first);
+    sum += heap.top().first;
+    heap.pop();
+  }
+  mean_load = G ? sum / G : 0;
+  cta_off.assign(G + 1, 0);
+  order.clear();
+  for (int g = 0; g < G; ++g) {
+    cta_off[g] = (int)order.size();
+    order.insert(order.end(), per[g].begin(), per[g].end());
+  }
+  cta_off[G] = (int)order.size();
+}
+
+static int schedule_grid(int n_tasks, int NB, bool bf16) {
+  return std::max(1, std::min(n_tasks, device_sms() * tc_ctas_per_sm(NB, bf16)));
+}
+
+// Makespan (in K-stages) of a set of per-item splits under LPT.
+static double model_makespan(const std::vector<Plan*>& items, const std::vector<int>& ks, int NB, bool bf16) {
+  std::vector<TaskCost> t;
+  for (size_t i = 0; i < items.size(); ++i) item_tasks(items[i], (int)i, ks[i], t);
+  if (t.empty()) return 0;
+  std::vector<int> off;
+  std::vector<int4> order;
+  double mx, mean;
+  lpt(t, schedule_grid((int)t.size(), NB, bf16), off, order, mx, mean);
+  return mx;
+}
+
+static scw_status upload_schedule(const std::vector<Plan*>& items, int NB, bool bf16, TcSchedule& s) {
+  std::vector<TaskCost> t;
+  for (size_t i = 0; i < items.size(); ++i) item_tasks(items[i], (int)i, items[i]->k_split, t);
+  if (s.d_tasks) cudaFree(s.d_tasks);
+  if (s.d_cta_off) cudaFree(s.d_cta_off);
+  s.d_tasks = nullptr;
+  s.d_cta_off = nullptr;
+  s.n_tasks = (int)t.size();
+  if (t.empty()) {
+    s.grid = 0;
+    return SCW_OK;
+  }
+  s.grid = schedule_grid(s.n_tasks, NB, bf16);
+  std::vector<int> off;
+  std::vector<int4> order;
+  lpt(t, s.grid, off, order, s.max_load, s.mean_load);
+  size_t tot = 0;
+  SCW_TRY(upload(&s.d_tasks, order, tot));
+  SCW_TRY(upload(&s.d_cta_off, off, tot));
+  return SCW_OK;
+}
+
+// k_split per item from a target number of K-stages per task.
+static std::vector<int> splits_for_target(const std::vector<Plan*>& items, int target) {
+  std::vector<int> ks;
+  for (auto* p : items) {
+    const int nk = (8 * p->M + 63) / 64;
+    ks.push_back(std::max(1, std::min(16, (nk + target / 2) / target)));
+  }
+  return ks;
+}
+
+// FP32 path: ~4 waves of work units and a shared-memory slice of C <= 96 KB per CTA.
+static int fp32_split(const Plan* p) {
+  const int K = 4 * p->M;
+  const int slots = device_sms() * 2 * 4;
+  const int per_split_units = (int)p->units.size() * ((3 * p->M + 255) / 256);
+  int ks = per_split_units ? (slots + per_split_units - 1) / per_split_units : 1;
+  ks = std::max(1, std::min(ks, std::max(1, K / 128)));
+  const int fch = p->F_pad >= 16 ? 16 : 8;
+  ks = std::max(ks, (int)(((size_t)K * fch * 8 + 96 * 1024 - 1) / (96 * 1024)));
+  return std::min(ks, K);
+}
+
+}  // namespace scw
+
+using namespace scw;
+
+// ------------------------------------------------------------------ the plan ---
+struct scw_plan_s {
+  std::vector<Plan*> items;
+  bool batched = false;
+  int precision = 0;
+  bool tc = false, bf16 = false;
+  int NB = 16, F_pad = 8;
+  uint64_t timeout_ns = 2000000000ull;
+  int* d_err = nullptr;
+  // tables over all items
+  ItemDev* d_items = nullptr;      // batched plans only
+  int2* d_unit_entries = nullptr;
+  int n_unit_entries = 0;
+  int2* d_plane_entries = nullptr;
+  int n_plane_entries = 0;
+  TcSchedule sched;
+  float2** d_outs = nullptr;
+  float2** h_outs = nullptr;       // pinned
+  int max_M = 0, max_Qx = 0, max_V = 0;
+  size_t rec_smem = 0;
+  // graph replay
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  const void* graph_key = nullptr;
+  bool direct_done = false;
+  // timing
+  bool timing = false;
+  std::vector<cudaEvent_t> tev;
+  size_t tev_used = 0;
+  int kernels_per_synthesis = 0;
+  std::string tune_report;
+};
+
+static void free_plan(scw_plan_t P) {
+  if (!P) return;
+  for (auto* p : P->items) free_item(p);
+  void* ptrs[] = {P->d_err, P->d_items, P->d_unit_entries, P->d_plane_entries, P->sched.d_tasks,
+                  P->sched.d_cta_off, P->d_outs};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  if (P->h_outs) cudaFreeHost(P->h_outs);
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
+  for (cudaEvent_t ev : P->tev) cudaEventDestroy(ev);
+  delete P;
+}
+
+static void invalidate_graph(scw_plan_t P) {
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  P->gexec = nullptr;
+  P->graph_key = nullptr;
+  P->direct_done = false;
+}
+
+static scw_status upload_items(scw_plan_t P, cudaStream_t st) {
+  if (!P->batched) return SCW_OK;
+  std::vector<ItemDev> h(P->items.size());
+  for (size_t i = 0; i < P->items.size(); ++i) h[i] = P->items[i]->item;
+  cudaError_t e = cudaMemcpyAsync(P->d_items, h.data(), h.size() * sizeof(ItemDev), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "uploading item descriptors");
+  e = cudaStreamSynchronize(st);  // h is a local copy
+  if (e != cudaSuccess) return cuda_error(e, "uploading item descriptors");
+  return SCW_OK;
+}
+
+// Event slot k of the current timed call (nullptr when timing is off).
+static constexpr int kMarks = 5;  // events per timed call: before (a), (b), x-pass, y-pass; after
+
+static cudaEvent_t timing_event(scw_plan_t P, int k) {
+  if (!P->timing) return nullptr;
+  const size_t i = P->tev_used + (size_t)k;
+  if (i >= kMarks * 4096) return nullptr;
+  while (P->tev.size() <= i) {
+    cudaEvent_t ev;
+    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
+    P->tev.push_back(ev);
+  }
+  return P->tev[i];
+}
+
+static void mark(scw_plan_t P, int k, cudaStream_t st, bool marks) {
+  if (!marks) return;
+  cudaEvent_t ev = timing_event(P, k);
+  if (ev) cudaEventRecord(ev, st);
+}
+
+// Steps (a) and (b) for every item.
+static scw_status enqueue_spectrum(scw_plan_t P, cudaStream_t st, bool marks, int& n) {
+  cudaError_t e;
+  const ItemDev& one = P->items[0]->item;
+  const ItemDev* items = P->batched ? P->d_items : nullptr;
+  mark(P, 0, st, marks);
+  if (P->tc) {
+    e = launch_phases_tc(one, items, P->d_unit_entries, P->n_unit_entries, P->max_M, P->F_pad, P->bf16, st);
+    if (e != cudaSuccess) return cuda_error(e, "phase kernel launch");
+    if (P->n_unit_entries) ++n;
+  } else {
+    for (auto* p : P->items)
+      if (!p->units.empty()) {
+        e = launch_phases_fp32(*p, st);
+        if (e != cudaSuccess) return cuda_error(e, "phase kernel launch");
+        ++n;
+      }
+  }
+  for (auto* p : P->items)
+    if (p->n_exterior) {
+      e = launch_exterior(*p, st);
+      if (e != cudaSuccess) return cuda_error(e, "exterior kernel launch");
+      ++n;
+    }
+  mark(P, 1, st, marks);
+  if (P->tc) {
+    e = launch_contract_tc(one, items, P->sched, P->NB, P->bf16, P->d_err, P->timeout_ns, st);
+    if (e != cudaSuccess) return cuda_error(e, "contraction kernel launch");
+    if (P->sched.n_tasks) ++n;
+  } else {
+    for (auto* p : P->items)
+      if (!p->units.empty()) {
+        e = launch_contract_fp32(*p, st);
+        if (e != cudaSuccess) return cuda_error(e, "contraction kernel launch");
+        ++n;
+      }
+  }
+  return SCW_OK;
+}
+
+static scw_status enqueue_synthesis(scw_plan_t P, float2* out_one, cudaStream_t st, bool marks, int& n) {
+  n = 0;
+  scw_status s = enqueue_spectrum(P, st, marks, n);
+  if (s != SCW_OK) return s;
+  const ItemDev& one = P->items[0]->item;
+  const ItemDev* items = P->batched ? P->d_items : nullptr;
+  mark(P, 2, st, marks);
+  cudaError_t e = launch_xpass(one, items, P->d_plane_entries, P->n_plane_entries, P->max_M, st);
+  if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
+  mark(P, 3, st, marks);
+  e = launch_ypass(one, items, P->d_plane_entries, P->n_plane_entries, P->max_Qx, P->max_V, out_one, P->d_outs, st);
+  if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
+  mark(P, 4, st, marks);
+  n += 2;
+  if (marks && P->timing && P->tev_used + kMarks <= P->tev.size()) P->tev_used += kMarks;
+  return SCW_OK;
+}
+
+// Timed launches go out directly (with events between kernels); otherwise the
+// first call for a given output launches directly and captures the same
+// sequence into a CUDA graph, later calls replay the graph.
+static scw_status run_synthesis(scw_plan_t P, float2* out_one, cudaStream_t st) {
+  int n = 0;
+  if (P->timing) {
+    scw_status s = enqueue_synthesis(P, out_one, st, true, n);
+    P->kernels_per_synthesis = n;
+    return s;
+  }
+  const void* key = P->batched ? static_cast<const void*>(P->d_outs) : static_cast<const void*>(out_one);
+  if (P->gexec && P->graph_key == key) {
+    cudaError_t e = cudaGraphLaunch(P->gexec, st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaGraphLaunch");
+    return SCW_OK;
+  }
+  scw_status s = enqueue_synthesis(P, out_one, st, false, n);
+  if (s != SCW_OK) return s;
+  P->kernels_per_synthesis = n;
+  invalidate_graph(P);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamBeginCapture");
+  s = enqueue_synthesis(P, out_one, P->cap_stream, false, n);
+  e = cudaStreamEndCapture(P->cap_stream, &g);
+  if (s != SCW_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&P->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    P->gexec = nullptr;
+    return cuda_error(e, "cudaGraphInstantiate");
+  }
+  P->graph_key = key;
+  return SCW_OK;
+}
+
+// Choose the contraction splits: a makespan model over targets of K-stages per
+// task, then (SCW_FLAG_AUTOTUNE) timing of the best model candidates on the
+// device; the choice is cached per device, order counts, plane slots and precision.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune_cache;
+
+static scw_status choose_splits(scw_plan_t P, bool timed, const std::vector<int>& user_ks) {
+  if (!P->tc) {
+    for (size_t i = 0; i < P->items.size(); ++i) {
+      Plan* p = P->items[i];
+      p->k_split = user_ks[i] > 0 ? user_ks[i] : fp32_split(p);
+      scw_status s = finish_item(p);
+      if (s != SCW_OK) return s;
+    }
+    return SCW_OK;
+  }
+  bool all_user = true;
+  for (int k : user_ks) all_user = all_user && k > 0;
+  std::vector<int> best_ks;
+  if (all_user) {
+    best_ks = user_ks;
+  } else {
+    static const int targets[] = {4, 6, 8, 10, 12, 16, 24, 32, 48, 64};
+    std::vector<std::pair<double, int>> cand;
+    for (int T : targets) {
+      auto ks = splits_for_target(P->items, T);
+      double ms = model_makespan(P->items, ks, P->NB, P->bf16);
+      int ntask = 0;
+      for (size_t i = 0; i < ks.size(); ++i) ntask += ks[i];
+      cand.push_back({ms * (1.0 + 1e-6 * ntask), T});
+    }
+    std::sort(cand.begin(), cand.end());
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, dev);
+    std::string key = std::string(prop.name) + "|" + std::to_string(P->NB) + "|" + std::to_string(P->bf16);
+    for (auto* p : P->items) key += "|" + std::to_string(p->M) + "x" + std::to_string(p->units.size());
+    int chosen = cand.front().second;
+    bool cached = false;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto itc = g_tune_cache.find(key);
+      if (itc != g_tune_cache.end()) {
+        chosen = itc->second;
+        cached = true;
+      }
+    }
+    P->tune_report = "model: T=" + std::to_string(cand.front().second) + " makespan " +
+                     std::to_string(cand.front().first);
+    if (timed && !cached) {
+      // time the three best model candidates with the real kernel on the plan's buffers
+      const int n_try = std::min<int>(3, (int)cand.size());
+      float best_ms = 1e30f;
+      cudaStream_t ts = P->cap_stream;
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      for (int c = 0; c < n_try; ++c) {
+        const int T = cand[c].second;
+        auto ks = splits_for_target(P->items, T);
+        for (size_t i = 0; i < P->items.size(); ++i) {
+          P->items[i]->k_split = ks[i];
+          scw_status s = finish_item(P->items[i]);
+          if (s != SCW_OK) return s;
+        }
+        scw_status s = upload_items(P, ts);
+        if (s != SCW_OK) return s;
+        s = upload_schedule(P->items, P->NB, P->bf16, P->sched);
+        if (s != SCW_OK) return s;
+        const ItemDev* items = P->batched ? P->d_items : nullptr;
+        launch_contract_tc(P->items[0]->item, items, P->sched, P->NB, P->bf16, P->d_err, P->timeout_ns, ts);
+        cudaEventRecord(a, ts);
+        for (int r = 0; r < 3; ++r)
+          launch_contract_tc(P->items[0]->item, items, P->sched, P->NB, P->bf16, P->d_err, P->timeout_ns, ts);
+        cudaEventRecord(b, ts);
+        cudaError_t e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) return cuda_error(e, "autotune timing");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        P->tune_report += "; T=" + std::to_string(T) + " " + std::to_string(ms / 3) + " ms";
+        if (ms < best_ms) {
+          best_ms = ms;
+          chosen = T;
+        }
+      }
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      cudaMemset(P->d_err, 0, sizeof(int));
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune_cache[key] = chosen;
+    }
+    best_ks = splits_for_target(P->items, chosen);
+    for (size_t i = 0; i < P->items.size(); ++i)
+      if (user_ks[i] > 0) best_ks[i] = user_ks[i];
+    P->tune_report += "; chosen T=" + std::to_string(chosen) + (cached ? " (cached)" : "");
+  }
+  for (size_t i = 0; i < P->items.size(); ++i) {
+    P->items[i]->k_split = best_ks[i];
+    scw_status s = finish_item(P->items[i]);
+    if (s != SCW_OK) return s;
+  }
+  return upload_schedule(P->items, P->NB, P->bf16, P->sched);
+}
+
+// Shared tail of single and batched plan creation.
+static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, bool timed) {
+  size_t tot = 0;
+  SCW_TRY(dalloc(&P->d_err, 1, tot));
+  SCW_TRY(cudaMemset(P->d_err, 0, sizeof(int)));
+  SCW_TRY(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  std::vector<int2> ue, pe;
+  for (size_t i = 0; i < P->items.size(); ++i) {
+    Plan* p = P->items[i];
+    for (int u = 0; u < (int)p->units.size(); ++u) ue.push_back(make_int2((int)i, u));
+    for (int f = 0; f < p->Fz; ++f) pe.push_back(make_int2((int)i, f));
+    P->max_M = std::max(P->max_M, p->M);
+    P->max_Qx = std::max(P->max_Qx, p->Fx / 8);
+    P->max_V = std::max(P->max_V, p->V);
+    P->rec_smem = std::max(P->rec_smem, recompose_smem_bytes(p->V, p->item.Up, p->item.Vp));
+  }
+  P->n_unit_entries = (int)ue.size();
+  P->n_plane_entries = (int)pe.size();
+  SCW_TRY(upload(&P->d_unit_entries, ue, tot));
+  SCW_TRY(upload(&P->d_plane_entries, pe, tot));
+  SCW_TRY(dalloc(&P->d_outs, P->items.size(), tot));
+  SCW_TRY(cudaMallocHost(reinterpret_cast<void**>(&P->h_outs), P->items.size() * sizeof(float2*)));
+  if (P->batched) SCW_TRY(dalloc(&P->d_items, P->items.size(), tot));
+  scw_status s = choose_splits(P, timed, user_ks);
+  if (s != SCW_OK) return s;
+  return upload_items(P, P->cap_stream);
+}
+
+static scw_status check_item_index(scw_plan_t P, int item) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+  if (item < 0 || item >= (int)P->items.size()) return set_error(SCW_ERR_INVALID_ARGUMENT, "item index out of range");
+  return SCW_OK;
+}
+
+// W into the chosen precision's layout (transposed FP32, or tile-major swizzled 16-bit).
+static cudaError_t convert_w(Plan* p, const float2* w, cudaStream_t st) {
+  if (p->precision == SCW_PREC_FP32) return launch_transpose_layers(w, p->Wt, p->L, 3 * p->M, 4 * p->M, st);
+  if (p->precision == SCW_PREC_SPLIT_BF16) return launch_convert_tiled(w, p->Whi, p->Wlo, p->L, p->M, true, st);
+  return launch_convert_tiled(w, p->Wh, nullptr, p->L, p->M, false, st);
+}
+
+static scw_status set_layers_item(scw_plan_t P, int idx, const void* W, const void* gamma, const void* alpha,
+                                  const void* p_inc, const void* p_ref, const void* p_trn, cudaStream_t st) {
+  Plan* p = P->items[idx];
+  if (!W || !gamma || !alpha) return set_error(SCW_ERR_INVALID_ARGUMENT, "W, gamma and alpha are required");
+  if ((p->flags & SCW_FLAG_EXTERIOR) && (!p_inc || !p_ref || !p_trn))
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "SCW_FLAG_EXTERIOR needs p_inc, p_ref and p_trn");
+  if ((reinterpret_cast<uintptr_t>(W) & 15u) != 0) return set_error(SCW_ERR_INVALID_ARGUMENT, "W must be 16-byte aligned");
+  p->gamma = static_cast<const double2*>(gamma);
+  p->alpha = static_cast<const double2*>(alpha);
+  p->p_inc = static_cast<const double2*>(p_inc);
+  p->p_ref = static_cast<const double2*>(p_ref);
+  p->p_trn = static_cast<const double2*>(p_trn);
+  p->item.gamma = p->gamma;
+  p->item.alpha = p->alpha;
+  const float2* w = static_cast<const float2*>(W);
+  cudaError_t e = cudaEventRecord(p->ev0, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+  if (!p->units.empty()) {
+    e = convert_w(p, w, st);
+    if (e != cudaSuccess) return cuda_error(e, "W conversion launch");
+  }
+  e = cudaEventRecord(p->ev1, st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+  p->convert_pending = true;
+  p->layers_set = true;
+  if (P->batched) {
+    e = cudaMemcpyAsync(P->d_items + idx, &p->item, sizeof(ItemDev), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "item descriptor upload");
+  } else {
+    invalidate_graph(P);  // the graph holds the item by value
+  }
+  return SCW_OK;
+}
+
+extern "C" {
+
+int scw_version(void) { return 2; }
+
+const char* scw_last_error(void) { return g_last_error.c_str(); }
+
+const char* scw_status_string(scw_status s) {
+  switch (s) {
+    case SCW_OK: return "ok";
+    case SCW_ERR_INVALID_ARGUMENT: return "invalid argument";
+    case SCW_ERR_UNSUPPORTED: return "unsupported";
+    case SCW_ERR_OUT_OF_MEMORY: return "out of memory";
+    case SCW_ERR_CUDA: return "CUDA error";
+    case SCW_ERR_TIMEOUT: return "device wait timed out";
+    case SCW_ERR_NUMERIC: return "non-finite value";
+    case SCW_ERR_STATE: return "call order violated";
+  }
+  return "unknown status";
+}
+
+scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
+  if (!out) return set_error(SCW_ERR_INVALID_ARGUMENT, "out is NULL");
+  *out = nullptr;
+  scw_status s = validate_desc(d);
+  if (s != SCW_OK) return s;
+  s = check_device();
+  if (s != SCW_OK) return s;
+  scw_plan_t P = new (std::nothrow) scw_plan_s();
+  if (!P) return set_error(SCW_ERR_OUT_OF_MEMORY, "host allocation failed");
+  Plan* p = nullptr;
+  s = create_item(d, 0, &p);
+  if (s != SCW_OK) {
+    free_plan(P);
+    return s;
+  }
+  P->items.push_back(p);
+  P->precision = d->precision;
+  P->tc = d->precision != SCW_PREC_FP32;
+  P->bf16 = d->precision == SCW_PREC_SPLIT_BF16;
+  P->F_pad = p->F_pad;
+  P->NB = p->NB;
+  s = finish_plan(P, {d->k_split}, (d->flags & SCW_FLAG_AUTOTUNE) != 0);
+  if (s != SCW_OK) {
+    free_plan(P);
+    return s;
+  }
+  *out = P;
+  return SCW_OK;
+}
+
+scw_status scw_plan_batched_create(const scw_desc* descs, int n, scw_plan_t* out) {
+  if (!out) return set_error(SCW_ERR_INVALID_ARGUMENT, "out is NULL");
+  *out = nullptr;
+  if (!descs || n < 1) return set_error(SCW_ERR_INVALID_ARGUMENT, "need at least one item");
+  for (int i = 0; i < n; ++i) {
+    scw_status s = validate_desc(&descs[i]);
+    if (s != SCW_OK) return set_error(s, "item " + std::to_string(i) + ": " + g_last_error);
+    if (descs[i].precision != descs[0].precision)
+      return set_error(SCW_ERR_INVALID_ARGUMENT, "all items of a batch share one precision");
+    if (descs[i].flags & SCW_FLAG_HOST_IO)
+      return set_error(SCW_ERR_UNSUPPORTED, "SCW_FLAG_HOST_IO is for single plans");
+  }
+  scw_status s = check_device();
+  if (s != SCW_OK) return s;
+  scw_plan_t P = new (std::nothrow) scw_plan_s();
+  if (!P) return set_error(SCW_ERR_OUT_OF_MEMORY, "host allocation failed");
+  P->batched = true;
+  P->precision = descs[0].precision;
+  P->tc = P->precision != SCW_PREC_FP32;
+  P->bf16 = P->precision == SCW_PREC_SPLIT_BF16;
+  // every item of a tensor-core batch shares one plane-slot count (one N for the MMA)
+  int fpad = 8;
+  for (int i = 0; i < n; ++i) {
+    Plan probe;
+    probe.L = descs[i].L;
+    probe.Fz = descs[i].Fz;
+    probe.flags = descs[i].flags | SCW_FLAG_EXTERIOR;
+    probe.z_bounds.assign(descs[i].z_bounds, descs[i].z_bounds + descs[i].L + 1);
+    probe.z_planes.assign(descs[i].z_planes, descs[i].z_planes + descs[i].Fz);
+    std::vector<int> ext;
+    int max_nf = 0;
+    assign_planes(&probe, ext, max_nf);
+    fpad = std::max(fpad, round_planes(std::max(max_nf, 1)));
+  }
+  std::vector<int> user_ks;
+  bool timed = false;
+  for (int i = 0; i < n; ++i) {
+    Plan* p = nullptr;
+    s = create_item(&descs[i], P->tc ? fpad : 0, &p);
+    if (s != SCW_OK) {
+      free_plan(P);
+      return set_error(s, "item " + std::to_string(i) + ": " + g_last_error);
+    }
+    P->items.push_back(p);
+    user_ks.push_back(descs[i].k_split);
+    timed = timed || (descs[i].flags & SCW_FLAG_AUTOTUNE);
+  }
+  P->F_pad = fpad;
+  P->NB = 2 * fpad;
+  s = finish_plan(P, user_ks, timed);
+  if (s != SCW_OK) {
+    free_plan(P);
+    return s;
+  }
+  *out = P;
   return SCW_OK;
 }
 
@@ -314,128 +930,83 @@ scw_status scw_plan_destroy(scw_plan_t plan) {
   return SCW_OK;
 }
 
-scw_status scw_plan_set_layers(scw_plan_t p, const void* W, const void* gamma, const void* alpha, const void* p_inc,
+scw_status scw_plan_set_layers(scw_plan_t P, const void* W, const void* gamma, const void* alpha, const void* p_inc,
                                const void* p_ref, const void* p_trn, void* stream) {
-  if (!p) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
-  if (!W || !gamma || !alpha) return set_error(SCW_ERR_INVALID_ARGUMENT, "W, gamma and alpha are required");
-  if ((p->flags & SCW_FLAG_EXTERIOR) && (!p_inc || !p_ref || !p_trn))
-    return set_error(SCW_ERR_INVALID_ARGUMENT, "SCW_FLAG_EXTERIOR needs p_inc, p_ref and p_trn");
-  if ((reinterpret_cast<uintptr_t>(W) & 15u) != 0) return set_error(SCW_ERR_INVALID_ARGUMENT, "W must be 16-byte aligned");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  p->gamma = static_cast<const double2*>(gamma);
-  p->alpha = static_cast<const double2*>(alpha);
-  p->p_inc = static_cast<const double2*>(p_inc);
-  p->p_ref = static_cast<const double2*>(p_ref);
-  p->p_trn = static_cast<const double2*>(p_trn);
-  const size_t L = p->L, M = p->M;
-  const float2* w = static_cast<const float2*>(W);
-  cudaError_t e = cudaEventRecord(p->ev0, st);
-  if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
-  if (!p->units.empty()) {
-    if (p->precision == SCW_PREC_FP32) e = launch_transpose_layers(w, p->Wt, p->L, 3 * p->M, 4 * p->M, st);
-    else if (p->precision == SCW_PREC_SPLIT_BF16) e = launch_convert_split_bf16(w, p->Whi, p->Wlo, L * 3 * M * 4 * M, st);
-    else e = launch_convert_fp16(w, p->Wh, L * 3 * M * 4 * M, st);
-    if (e != cudaSuccess) return cuda_error(e, "W conversion launch");
-  }
-  e = cudaEventRecord(p->ev1, st);
-  if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
-  p->convert_pending = true;
-  p->layers_set = true;
-  return SCW_OK;
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+  if (P->batched) return set_error(SCW_ERR_STATE, "batched plan: use scw_plan_batched_set_layers");
+  return set_layers_item(P, 0, W, gamma, alpha, p_inc, p_ref, p_trn, static_cast<cudaStream_t>(stream));
 }
 
-// Event slot k of the current timed call (nullptr when timing is off).
-static cudaEvent_t timing_event(scw_plan_t p, int k) {
-  if (!p->timing) return nullptr;
-  const size_t i = p->tev_used + (size_t)k;
-  if (i >= 5 * 4096) return nullptr;
-  while (p->tev.size() <= i) {
-    cudaEvent_t ev;
-    if (cudaEventCreate(&ev) != cudaSuccess) return nullptr;
-    p->tev.push_back(ev);
-  }
-  return p->tev[i];
+scw_status scw_plan_batched_set_layers(scw_plan_t P, int item, const void* W, const void* gamma, const void* alpha,
+                                       const void* p_inc, const void* p_ref, const void* p_trn, void* stream) {
+  scw_status s = check_item_index(P, item);
+  if (s != SCW_OK) return s;
+  return set_layers_item(P, item, W, gamma, alpha, p_inc, p_ref, p_trn, static_cast<cudaStream_t>(stream));
 }
 
-static void mark(scw_plan_t p, int k, cudaStream_t st) {
-  cudaEvent_t ev = timing_event(p, k);
-  if (ev) cudaEventRecord(ev, st);
-}
-
-static scw_status run_spectrum(scw_plan_t p, cudaStream_t st, int& launches) {
-  cudaError_t e;
-  launches = 0;
-  mark(p, 0, st);
-  if (!p->units.empty()) {
-    e = (p->precision == SCW_PREC_FP32) ? launch_phases_fp32(*p, st) : launch_phases_tc(*p, st);
-    if (e != cudaSuccess) return cuda_error(e, "phase kernel launch");
-    ++launches;
-  }
-  if (p->n_exterior) {
-    e = launch_exterior(*p, st);
-    if (e != cudaSuccess) return cuda_error(e, "exterior kernel launch");
-    ++launches;
-  }
-  mark(p, 1, st);
-  if (!p->units.empty()) {
-    e = (p->precision == SCW_PREC_FP32) ? launch_contract_fp32(*p, st) : launch_contract_tc(*p, st);
-    if (e != cudaSuccess) return cuda_error(e, "contraction kernel launch");
-    ++launches;
-  }
-  return SCW_OK;
-}
-
-scw_status scw_synthesize(scw_plan_t p, void* out, void* stream) {
-  if (!p || !out) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and out are required");
-  if (!p->layers_set) return set_error(SCW_ERR_STATE, "scw_plan_set_layers has not been called");
+scw_status scw_synthesize(scw_plan_t P, void* out, void* stream) {
+  if (!P || !out) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and out are required");
+  if (P->batched) return set_error(SCW_ERR_STATE, "batched plan: use scw_synthesize_batched");
+  if (!P->items[0]->layers_set) return set_error(SCW_ERR_STATE, "scw_plan_set_layers has not been called");
   if ((reinterpret_cast<uintptr_t>(out) & 15u) != 0) return set_error(SCW_ERR_INVALID_ARGUMENT, "out must be 16-byte aligned");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int n = 0;
-  scw_status s = run_spectrum(p, st, n);
-  if (s != SCW_OK) return s;
-  mark(p, 2, st);
-  cudaError_t e = launch_xpass(*p, p->S_part, p->Fz, p->d_nsplit, st);
-  if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
-  mark(p, 3, st);
-  e = launch_ypass(*p, static_cast<float2*>(out), st);
-  if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
-  mark(p, 4, st);
-  if (p->timing && p->tev_used + 5 <= p->tev.size()) p->tev_used += 5;
-  p->kernels_per_synthesis = n + 2;
-  return SCW_OK;
+  return run_synthesis(P, static_cast<float2*>(out), static_cast<cudaStream_t>(stream));
 }
 
-scw_status scw_spectrum(scw_plan_t p, void* S, void* stream) {
-  if (!p || !S) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and S are required");
-  if (!p->layers_set) return set_error(SCW_ERR_STATE, "scw_plan_set_layers has not been called");
+scw_status scw_synthesize_batched(scw_plan_t P, void* const* outs, void* stream) {
+  if (!P || !outs) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and outs are required");
+  if (!P->batched) return set_error(SCW_ERR_STATE, "single plan: use scw_synthesize");
+  for (size_t i = 0; i < P->items.size(); ++i) {
+    if (!P->items[i]->layers_set) return set_error(SCW_ERR_STATE, "item " + std::to_string(i) + " has no layers");
+    if (!outs[i] || (reinterpret_cast<uintptr_t>(outs[i]) & 15u) != 0)
+      return set_error(SCW_ERR_INVALID_ARGUMENT, "every out must be non-NULL and 16-byte aligned");
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the previous call's copy of the pointer table must have been consumed before it is rewritten
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
+  for (size_t i = 0; i < P->items.size(); ++i) P->h_outs[i] = static_cast<float2*>(outs[i]);
+  e = cudaMemcpyAsync(P->d_outs, P->h_outs, P->items.size() * sizeof(float2*), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_error(e, "output table upload");
+  return run_synthesis(P, nullptr, st);
+}
+
+scw_status scw_spectrum(scw_plan_t P, void* S, void* stream) {
+  if (!P || !S) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and S are required");
+  if (P->batched) return set_error(SCW_ERR_STATE, "not available on a batched plan");
+  if (!P->items[0]->layers_set) return set_error(SCW_ERR_STATE, "scw_plan_set_layers has not been called");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int n = 0;
-  scw_status s = run_spectrum(p, st, n);
+  scw_status s = enqueue_spectrum(P, st, false, n);
   if (s != SCW_OK) return s;
-  cudaError_t e = launch_gather_spectrum(*p, static_cast<float2*>(S), st);
+  cudaError_t e = launch_gather_spectrum(*P->items[0], static_cast<float2*>(S), st);
   if (e != cudaSuccess) return cuda_error(e, "gather launch");
   return SCW_OK;
 }
 
-scw_status scw_recompose(scw_plan_t p, const void* S, void* out, void* stream) {
-  if (!p || !S || !out) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan, S and out are required");
+scw_status scw_recompose(scw_plan_t P, const void* S, void* out, void* stream) {
+  if (!P || !S || !out) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan, S and out are required");
+  if (P->batched) return set_error(SCW_ERR_STATE, "not available on a batched plan");
   if ((reinterpret_cast<uintptr_t>(out) & 15u) != 0) return set_error(SCW_ERR_INVALID_ARGUMENT, "out must be 16-byte aligned");
-  cudaError_t e = launch_recompose(*p, static_cast<const float2*>(S), p->Fz, p->d_nsplit1, static_cast<float2*>(out),
-                                   static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Plan* p = P->items[0];
+  cudaError_t e = launch_recompose(p->item, nullptr, P->d_plane_entries, P->n_plane_entries, P->max_Qx, P->rec_smem,
+                                   static_cast<const float2*>(S), p->d_nsplit1, static_cast<float2*>(out), nullptr, st);
   if (e != cudaSuccess) return cuda_error(e, "recompose launch");
   return SCW_OK;
 }
 
-scw_status scw_synthesize_host(scw_plan_t p, const void* W, const void* gamma, const void* alpha, const void* p_inc,
+scw_status scw_synthesize_host(scw_plan_t P, const void* W, const void* gamma, const void* alpha, const void* p_inc,
                                const void* p_ref, const void* p_trn, void* out, void* stream) {
-  if (!p || !W || !gamma || !alpha || !out) return set_error(SCW_ERR_INVALID_ARGUMENT, "missing argument");
+  if (!P || !W || !gamma || !alpha || !out) return set_error(SCW_ERR_INVALID_ARGUMENT, "missing argument");
+  if (P->batched) return set_error(SCW_ERR_STATE, "not available on a batched plan");
+  Plan* p = P->items[0];
   if (!(p->flags & SCW_FLAG_HOST_IO)) return set_error(SCW_ERR_STATE, "plan was created without SCW_FLAG_HOST_IO");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t L = p->L, M = p->M;
   cudaError_t e;
-#define SCW_CP(dst, src, bytes, kind)                          \
-  do {                                                         \
-    e = cudaMemcpyAsync((dst), (src), (bytes), (kind), st);    \
+#define SCW_CP(dst, src, bytes, kind)                              \
+  do {                                                             \
+    e = cudaMemcpyAsync((dst), (src), (bytes), (kind), st);        \
     if (e != cudaSuccess) return cuda_error(e, "cudaMemcpyAsync"); \
   } while (0)
   SCW_CP(p->hio_W, W, L * 3 * M * 4 * M * sizeof(float2), cudaMemcpyHostToDevice);
@@ -448,9 +1019,15 @@ scw_status scw_synthesize_host(scw_plan_t p, const void* W, const void* gamma, c
     SCW_CP(p->hio_p + 6 * M, p_trn, 3 * M * sizeof(double2), cudaMemcpyHostToDevice);
     pi = p->hio_p; pr = p->hio_p + 3 * M; pt = p->hio_p + 6 * M;
   }
-  scw_status s = scw_plan_set_layers(p, p->hio_W, p->hio_gamma, p->hio_alpha, pi, pr, pt, stream);
-  if (s != SCW_OK) return s;
-  s = scw_synthesize(p, p->hio_out, stream);
+  // same device buffers every call: the layers are re-attached without dropping the graph
+  if (!p->layers_set || p->gamma != p->hio_gamma) {
+    scw_status s = set_layers_item(P, 0, p->hio_W, p->hio_gamma, p->hio_alpha, pi, pr, pt, st);
+    if (s != SCW_OK) return s;
+  } else {
+    e = convert_w(p, p->hio_W, st);
+    if (e != cudaSuccess) return cuda_error(e, "W conversion launch");
+  }
+  scw_status s = run_synthesis(P, p->hio_out, st);
   if (s != SCW_OK) return s;
   SCW_CP(out, p->hio_out, (size_t)3 * p->Fz * p->Fy * p->Fx * sizeof(float2), cudaMemcpyDeviceToHost);
 #undef SCW_CP
@@ -459,53 +1036,55 @@ scw_status scw_synthesize_host(scw_plan_t p, const void* W, const void* gamma, c
   return SCW_OK;
 }
 
-scw_status scw_plan_check(scw_plan_t p, void* stream) {
-  if (!p) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+scw_status scw_plan_check(scw_plan_t P, void* stream) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");
   int word = 0;
-  e = cudaMemcpy(&word, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  e = cudaMemcpy(&word, P->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_error(e, "reading the device error word");
   if (word) {
-    cudaMemset(p->d_err, 0, sizeof(int));
+    cudaMemset(P->d_err, 0, sizeof(int));
     return set_error(SCW_ERR_TIMEOUT, "device error word " + std::to_string(word) +
-                                          " (1: stage fill, 2: stage free, 4: accumulator, 8: drain)");
+                                          " (1: stage fill, 2: stage free, 4: accumulator, 8: drain, 16: dependency)");
   }
   return SCW_OK;
 }
 
-scw_status scw_plan_set_timeout_ns(scw_plan_t p, uint64_t ns) {
-  if (!p) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+scw_status scw_plan_set_timeout_ns(scw_plan_t P, uint64_t ns) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
   if (ns == 0) return set_error(SCW_ERR_INVALID_ARGUMENT, "timeout must be positive");
-  p->timeout_ns = ns;
+  P->timeout_ns = ns;
+  invalidate_graph(P);
   return SCW_OK;
 }
 
-scw_status scw_plan_enable_timing(scw_plan_t p, int on) {
-  if (!p) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
-  p->timing = on != 0;
-  p->tev_used = 0;
+scw_status scw_plan_enable_timing(scw_plan_t P, int on) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+  P->timing = on != 0;
+  P->tev_used = 0;
   return SCW_OK;
 }
 
-scw_status scw_plan_get_timings(scw_plan_t p, scw_kernel_times* t) {
-  if (!p || !t) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and t are required");
+scw_status scw_plan_get_timings(scw_plan_t P, scw_kernel_times* t) {
+  if (!P || !t) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and t are required");
   std::memset(t, 0, sizeof(*t));
-  const size_t calls = p->tev_used / 5;
+  const size_t calls = P->tev_used / kMarks;
   for (size_t c = 0; c < calls; ++c) {
-    cudaEvent_t* ev = &p->tev[5 * c];
-    cudaError_t e = cudaEventSynchronize(ev[4]);
+    cudaEvent_t* ev = &P->tev[kMarks * c];
+    cudaError_t e = cudaEventSynchronize(ev[kMarks - 1]);
     if (e != cudaSuccess) return cuda_error(e, "cudaEventSynchronize");
-    float ms[4], tot;
-    for (int k = 0; k < 4; ++k) {
+    float ms[kMarks - 1], tot;
+    for (int k = 0; k < kMarks - 1; ++k) {
       e = cudaEventElapsedTime(&ms[k], ev[k], ev[k + 1]);
       if (e != cudaSuccess) return cuda_error(e, "cudaEventElapsedTime");
     }
-    cudaEventElapsedTime(&tot, ev[0], ev[4]);
+    cudaEventElapsedTime(&tot, ev[0], ev[kMarks - 1]);
     t->phases_ms += ms[0];
     t->contract_ms += ms[1];
     t->xpass_ms += ms[2];
     t->ypass_ms += ms[3];
+    t->recompose_ms += ms[2] + ms[3];
     t->total_ms += tot;
   }
   t->calls = (int)calls;
@@ -514,29 +1093,40 @@ scw_status scw_plan_get_timings(scw_plan_t p, scw_kernel_times* t) {
     t->contract_ms /= calls;
     t->xpass_ms /= calls;
     t->ypass_ms /= calls;
+    t->recompose_ms /= calls;
     t->total_ms /= calls;
   }
-  p->tev_used = 0;
+  P->tev_used = 0;
   return SCW_OK;
 }
 
-scw_status scw_plan_get_info(scw_plan_t p, scw_plan_info* info) {
-  if (!p || !info) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and info are required");
-  if (p->convert_pending) {
-    float ms = 0.f;
-    if (cudaEventSynchronize(p->ev1) == cudaSuccess && cudaEventElapsedTime(&ms, p->ev0, p->ev1) == cudaSuccess)
-      p->convert_ms = ms;
-    p->convert_pending = false;
+scw_status scw_plan_get_info(scw_plan_t P, scw_plan_info* info) {
+  if (!P || !info) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and info are required");
+  std::memset(info, 0, sizeof(*info));
+  for (auto* p : P->items) {
+    if (p->convert_pending) {
+      float ms = 0.f;
+      if (cudaEventSynchronize(p->ev1) == cudaSuccess && cudaEventElapsedTime(&ms, p->ev0, p->ev1) == cudaSuccess)
+        p->convert_ms = ms;
+      p->convert_pending = false;
+    }
+    info->M = std::max(info->M, p->M);
+    info->active_layers += (int)p->units.size();
+    info->k_split = std::max(info->k_split, p->k_split);
+    info->exterior_planes += p->n_exterior;
+    info->workspace_bytes += p->workspace_bytes;
+    info->convert_ms += p->convert_ms;
   }
-  info->M = p->M;
-  info->active_layers = (int)p->units.size();
-  info->planes_per_layer_pad = p->F_pad;
-  info->k_split = p->k_split;
-  info->exterior_planes = p->n_exterior;
-  info->workspace_bytes = p->workspace_bytes;
-  info->convert_ms = p->convert_ms;
-  info->kernels_per_synthesis = p->kernels_per_synthesis;
+  info->planes_per_layer_pad = P->F_pad;
+  info->kernels_per_synthesis = P->kernels_per_synthesis;
+  info->items = (int)P->items.size();
+  info->contract_ctas = P->sched.grid;
+  info->contract_tasks = P->sched.n_tasks;
+  info->schedule_max_load = P->sched.max_load;
+  info->schedule_mean_load = P->sched.mean_load;
   return SCW_OK;
 }
+
+const char* scw_plan_tune_report(scw_plan_t P) { return P ? P->tune_report.c_str() : ""; }
 
 }  // extern "C"

@@ -84,12 +84,12 @@ cudaError_t launch_contract_fp32(const Plan& p, cudaStream_t st) {
   const size_t smem = (size_t)per * FCH * sizeof(float2);
   cudaError_t e;
   if (wide) {
-    e = cudaFuncSetAttribute(contract_fp32_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_max_smem(reinterpret_cast<const void*>(contract_fp32_kernel<16>));
     if (e != cudaSuccess) return e;
     contract_fp32_kernel<16><<<grid, 128, smem, st>>>(p.Wt, p.Cf, p.d_units, n_rblk, p.k_split, p.M, p.F_pad, p.Fz,
                                                       p.S_part);
   } else {
-    e = cudaFuncSetAttribute(contract_fp32_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_max_smem(reinterpret_cast<const void*>(contract_fp32_kernel<8>));
     if (e != cudaSuccess) return e;
     contract_fp32_kernel<8><<<grid, 128, smem, st>>>(p.Wt, p.Cf, p.d_units, n_rblk, p.k_split, p.M, p.F_pad, p.Fz,
                                                      p.S_part);

@@ -9,32 +9,23 @@
 //               A_hi B_hi + A_hi B_lo + A_lo B_hi accumulate in one FP32 TMEM tile.
 //   FP16:       A in FP16, B = B_hi + B_lo (FP16); two products.
 //
-// One CTA = 4 warps per work unit (active layer, 128-row tile, K split):
-//   warp 0 lane 0   TMA producer (3D tensor maps, 128-byte swizzle, no multicast)
+// Persistent, warp-specialised kernel. Work is a list of tasks (item, unit,
+// 128-row tile, K split), grouped per CTA on the host longest-first; every role
+// walks the same list:
+//   warp 0 lane 0   producer: contiguous cp.async.bulk copies (no multicast) of
+//                   the pre-swizzled tile-major A tiles (L2 evict-first: W is
+//                   streamed once) and B chunks (evict-last: re-read by every row
+//                   tile) into a ring of shared-memory stages (full/empty mbarriers)
 //   warp 1 lane 0   tcgen05.mma issuer (M = 128, N = NB, K = 16 per instruction)
-//   all 4 warps     epilogue: tcgen05.ld 32 lanes x 8 columns, coalesced stores
-//                   of the partial spectrum S_part[split][plane][row].
-// Shared-memory stages are recycled through full/empty mbarriers; every wait is
-// bounded by a %globaltimer deadline and reports through the error word.
-#include <cudaTypedefs.h>
-
+//                   into one of two TMEM accumulators (acc_full/acc_empty)
+//   warps 2-5       epilogue: tcgen05.ld 32 lanes x 8 columns of the other
+//                   accumulator, coalesced stores of S_part[split][plane][row]
+// so loads, MMAs and the previous task's epilogue overlap. Every wait is bounded
+// by a %globaltimer deadline; a timeout sets the error word and all roles stop.
 #include "scw_internal.cuh"
 #include "scw_ptx.cuh"
 
 namespace scw {
-
-struct TcArgs {
-  const LayerUnit* units;
-  int n_tiles;   // ceil(3M / 128)
-  int ksplit;
-  int nk;        // K stages of 64 reals: ceil(8M / 64)
-  int rows;      // 3M
-  int Fz;
-  int F_pad;
-  float2* S_part;
-  int* err;
-  uint64_t timeout_ns;
-};
 
 template <int NB, bool SPLIT>
 struct TcCfg {
@@ -42,51 +33,70 @@ struct TcCfg {
   static constexpr uint32_t B_BYTES = (uint32_t)NB * 64u * 2u;
   static constexpr int NA = SPLIT ? 2 : 1;
   static constexpr uint32_t STAGE_BYTES = NA * A_BYTES + 2 * B_BYTES;
-  // two CTAs per SM while at least two stages fit in ~110 KB, else one CTA with up to ~220 KB
+  // two CTAs per SM while at least three stages fit in ~110 KB, else one CTA with up to ~220 KB
   static constexpr int STAGES_2 = (int)(110u * 1024u / STAGE_BYTES);
-  static constexpr int STAGES = STAGES_2 >= 2 ? (STAGES_2 > 8 ? 8 : STAGES_2)
-                                              : (int)(220u * 1024u / STAGE_BYTES);
+  static constexpr int CTAS_PER_SM = STAGES_2 >= 3 ? 2 : 1;
+  static constexpr int STAGES_RAW = CTAS_PER_SM == 2 ? STAGES_2 : (int)(220u * 1024u / STAGE_BYTES);
+  static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
   static constexpr uint32_t SMEM = STAGES * STAGE_BYTES + 1024u;
-  static constexpr uint32_t TMEM_COLS = NB <= 32 ? 32u : (NB <= 64 ? 64u : (NB <= 128 ? 128u : 256u));
+  static constexpr uint32_t ACC_COLS = NB <= 32 ? 32u : (NB <= 64 ? 64u : (NB <= 128 ? 128u : 256u));
+  static constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
 };
 
-template <int NB, bool SPLIT>
-__global__ void __launch_bounds__(128) contract_tc_kernel(const __grid_constant__ CUtensorMap tmAhi,
-                                                          const __grid_constant__ CUtensorMap tmAlo,
-                                                          const __grid_constant__ CUtensorMap tmBhi,
-                                                          const __grid_constant__ CUtensorMap tmBlo, TcArgs args) {
+struct TaskGeom {
+  int kb, kcount, layer, unit, tile, split, f0, nf, rt;
+};
+
+__device__ __forceinline__ TaskGeom task_geom(const int4 tk, const ItemDev& it) {
+  TaskGeom g;
+  const LayerUnit u = it.units[tk.y];
+  const int per = (it.nk + it.k_split - 1) / it.k_split;
+  g.kb = tk.w * per;
+  g.kcount = max(0, min(it.nk, g.kb + per) - g.kb);
+  g.layer = u.layer;
+  g.unit = tk.y;
+  g.tile = tk.z;
+  g.split = tk.w;
+  g.f0 = u.f0;
+  g.nf = u.nf;
+  g.rt = min(128, 3 * it.M - 128 * tk.z);  // rows of this tile that exist
+  return g;
+}
+
+template <int NB, bool SPLIT, bool BATCH>
+__global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant__ ItemDev one,
+                                                          const ItemDev* __restrict__ items,
+                                                          const int4* __restrict__ tasks,
+                                                          const int* __restrict__ cta_off, int* err,
+                                                          uint64_t timeout_ns) {
   using Cfg = TcCfg<NB, SPLIT>;
   constexpr int STAGES = Cfg::STAGES;
+  constexpr int FP = NB / 2;  // plane slots
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
-  __shared__ int issued_s, consumed_s;
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  const int split = blockIdx.x % args.ksplit;
-  const int rest = blockIdx.x / args.ksplit;
-  const int tile = rest % args.n_tiles;
-  const int ui = rest / args.n_tiles;
-  const LayerUnit u = args.units[ui];
-  const int per = (args.nk + args.ksplit - 1) / args.ksplit;
-  const int kb = split * per;
-  const int kcount = max(0, min(args.nk, kb + per) - kb);
-  const uint64_t deadline = ptx::globaltimer() + args.timeout_ns;
+  const int t_begin = cta_off[blockIdx.x], t_end = cta_off[blockIdx.x + 1];
+  const uint64_t deadline = ptx::globaltimer() + timeout_ns;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       ptx::mbar_init(ptx::smem_u32(&full_bar[i]), 1);
       ptx::mbar_init(ptx::smem_u32(&empty_bar[i]), 1);
     }
-    ptx::mbar_init(ptx::smem_u32(&acc_bar), 1);
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(ptx::smem_u32(&accf_bar[i]), 1);
+      ptx::mbar_init(ptx::smem_u32(&acce_bar[i]), 4);  // one arrival per epilogue warp
+    }
+    ptx::mbar_init(ptx::smem_u32(&drain_bar), 1);
     abort_s = 0;
-    issued_s = 0;
-    consumed_s = 0;
     ptx::fence_mbar_init();
   }
   if (warp == 0) {
@@ -98,109 +108,164 @@ __global__ void __launch_bounds__(128) contract_tc_kernel(const __grid_constant_
   ptx::tc_fence_after();
   const uint32_t tmem = tmem_base_s;
 
-  if (kcount > 0 && warp == 0 && lane == 0) {
-    // ---------------- TMA producer ----------------
-    ptx::prefetch_tensormap(&tmAhi);
-    if (SPLIT) ptx::prefetch_tensormap(&tmAlo);
-    ptx::prefetch_tensormap(&tmBhi);
-    ptx::prefetch_tensormap(&tmBlo);
-    int i = 0;
-    for (; i < kcount; ++i) {
-      const int st = i % STAGES;
-      const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-      if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[st]), ph ^ 1u, deadline)) {
-        atomicOr(args.err, DEV_ERR_TIMEOUT_EMPTY);
-        abort_s = 1;
-        break;
+  if (warp == 0 && lane == 0) {
+    // ---------------- bulk-copy producer ----------------
+    const uint64_t pol_a = ptx::policy_evict_first(), pol_b = ptx::policy_evict_last();
+    int st = 0;
+    uint32_t ph = 0;
+    int issued = 0;
+    for (int t = t_begin; t < t_end && !abort_s; ++t) {
+      const int4 tk = tasks[t];
+      const ItemDev& it = BATCH ? items[tk.x] : one;
+      const TaskGeom g = task_geom(tk, it);
+      const int R = 3 * it.M;
+      // element offsets of this tile's first chunk in A and of the unit's first chunk in B
+      const size_t a0 = (size_t)g.layer * R * it.nk * 64 + (size_t)g.tile * 128 * it.nk * 64;
+      const size_t b0 = (size_t)g.unit * it.nk * NB * 64;
+      const uint32_t a_bytes = (uint32_t)g.rt * 128u;
+      const uint32_t tx = Cfg::NA * a_bytes + 2u * Cfg::B_BYTES;
+      const uint16_t* Ah = static_cast<const uint16_t*>(it.Ahi);
+      const uint16_t* Al = static_cast<const uint16_t*>(it.Alo);
+      const uint16_t* Bh = static_cast<const uint16_t*>(it.Bhi);
+      const uint16_t* Bl = static_cast<const uint16_t*>(it.Blo);
+      for (int i = 0; i < g.kcount; ++i) {
+        if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[st]), ph ^ 1u, deadline)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_EMPTY);
+          abort_s = 1;
+          break;
+        }
+        const uint32_t fb = ptx::smem_u32(&full_bar[st]);
+        ptx::mbar_arrive_expect_tx(fb, tx);
+        const int kc = g.kb + i;
+        const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
+        const size_t ao = a0 + (size_t)kc * g.rt * 64;
+        ptx::bulk_load(sa, Ah + ao, a_bytes, fb, pol_a);
+        if (SPLIT) ptx::bulk_load(sa + Cfg::A_BYTES, Al + ao, a_bytes, fb, pol_a);
+        const uint32_t sb = sa + Cfg::NA * Cfg::A_BYTES;
+        const size_t bo = b0 + (size_t)kc * NB * 64;
+        ptx::bulk_load(sb, Bh + bo, Cfg::B_BYTES, fb, pol_b);
+        ptx::bulk_load(sb + Cfg::B_BYTES, Bl + bo, Cfg::B_BYTES, fb, pol_b);
+        ++issued;
+        if (++st == STAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
       }
-      if (abort_s) break;
-      const uint32_t fb = ptx::smem_u32(&full_bar[st]);
-      ptx::mbar_arrive_expect_tx(fb, Cfg::STAGE_BYTES);
-      const int k0 = (kb + i) * 64;
-      const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
-      ptx::tma_load_3d(sa, &tmAhi, k0, tile * 128, u.layer, fb);
-      if (SPLIT) ptx::tma_load_3d(sa + Cfg::A_BYTES, &tmAlo, k0, tile * 128, u.layer, fb);
-      const uint32_t sb = sa + Cfg::NA * Cfg::A_BYTES;
-      ptx::tma_load_3d(sb, &tmBhi, k0, 0, ui, fb);
-      ptx::tma_load_3d(sb + Cfg::B_BYTES, &tmBlo, k0, 0, ui, fb);
     }
-    issued_s = i;
-  } else if (kcount > 0 && warp == 1 && lane == 0) {
+    if (abort_s) {
+      // let the last issued copies land before the CTA's shared memory goes away
+      const uint64_t d2 = ptx::globaltimer() + timeout_ns;
+      for (int back = 1; back <= STAGES && back <= issued; ++back) {
+        const int i = issued - back;
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[i % STAGES]), (uint32_t)(i / STAGES) & 1u, d2)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
+          break;
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
     // ---------------- tcgen05.mma issuer ----------------
     constexpr uint32_t idesc = ptx::idesc_f16(SPLIT, 128, NB);
-    int i = 0;
-    for (; i < kcount; ++i) {
-      const int st = i % STAGES;
-      const uint32_t ph = (uint32_t)(i / STAGES) & 1u;
-      if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[st]), ph, deadline)) {
-        atomicOr(args.err, DEV_ERR_TIMEOUT_FULL);
+    int st = 0;
+    uint32_t ph = 0;
+    int lt = 0;
+    for (int t = t_begin; t < t_end && !abort_s; ++t, ++lt) {
+      const int4 tk = tasks[t];
+      const ItemDev& it = BATCH ? items[tk.x] : one;
+      const TaskGeom g = task_geom(tk, it);
+      const int acc = lt & 1;
+      if (!ptx::mbar_wait(ptx::smem_u32(&acce_bar[acc]), ((uint32_t)(lt >> 1) & 1u) ^ 1u, deadline)) {
+        atomicOr(err, DEV_ERR_TIMEOUT_ACCUM);
         abort_s = 1;
         break;
       }
       ptx::tc_fence_after();
-      const uint32_t a_hi = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
-      const uint32_t a_lo = a_hi + Cfg::A_BYTES;
-      const uint32_t b_hi = a_hi + Cfg::NA * Cfg::A_BYTES;
-      const uint32_t b_lo = b_hi + Cfg::B_BYTES;
-      const uint64_t dah = ptx::sw128_desc(a_hi), dal = ptx::sw128_desc(a_lo);
-      const uint64_t dbh = ptx::sw128_desc(b_hi), dbl = ptx::sw128_desc(b_lo);
+      const uint32_t d_tmem = tmem + (uint32_t)acc * Cfg::ACC_COLS;
+      for (int i = 0; i < g.kcount; ++i) {
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[st]), ph, deadline)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_FULL);
+          abort_s = 1;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t a_hi = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
+        const uint32_t a_lo = a_hi + Cfg::A_BYTES;
+        const uint32_t b_hi = a_hi + Cfg::NA * Cfg::A_BYTES;
+        const uint32_t b_lo = b_hi + Cfg::B_BYTES;
+        const uint64_t dah = ptx::sw128_desc(a_hi), dal = ptx::sw128_desc(a_lo);
+        const uint64_t dbh = ptx::sw128_desc(b_hi), dbl = ptx::sw128_desc(b_lo);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        // K advance of 16 elements = 32 bytes inside the 128-byte swizzle row
-        const uint64_t o = (uint64_t)(2 * kk);
-        ptx::mma_f16(tmem, dah + o, dbh + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-        ptx::mma_f16(tmem, dah + o, dbl + o, idesc, 1u);
-        if (SPLIT) ptx::mma_f16(tmem, dal + o, dbh + o, idesc, 1u);
+        for (int kk = 0; kk < 4; ++kk) {
+          // K advance of 16 elements = 32 bytes inside the 128-byte swizzle row
+          const uint64_t o = (uint64_t)(2 * kk);
+          ptx::mma_f16(d_tmem, dah + o, dbh + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+          ptx::mma_f16(d_tmem, dah + o, dbl + o, idesc, 1u);
+          if (SPLIT) ptx::mma_f16(d_tmem, dal + o, dbh + o, idesc, 1u);
+        }
+        ptx::mma_commit(ptx::smem_u32(&empty_bar[st]));
+        if (++st == STAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
       }
-      ptx::mma_commit(ptx::smem_u32(&empty_bar[st]));
+      ptx::mma_commit(ptx::smem_u32(&accf_bar[acc]));
     }
-    consumed_s = i;
-    ptx::mma_commit(ptx::smem_u32(&acc_bar));  // always arrives, even after an abort
-  }
-  __syncwarp();
-
-  // ---------------- epilogue ----------------
-  bool ok = true;
-  if (kcount > 0) {
-    ok = ptx::mbar_wait(ptx::smem_u32(&acc_bar), 0u, deadline);
-    if (!ok) atomicOr(args.err, DEV_ERR_TIMEOUT_ACCUM);
-  }
-  const int all_ok = __syncthreads_and(ok ? 1 : 0);
-  ptx::tc_fence_after();
-  const bool have_acc = (kcount > 0) && all_ok && !abort_s;
-  const int row = tile * 128 + warp * 32 + lane;
-  float2* dst = args.S_part + ((size_t)split * args.Fz + u.f0) * args.rows;
-  const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-  for (int f0 = 0; f0 < args.F_pad; f0 += 8) {
-    uint32_t re[8], im[8];
-    if (have_acc) {
-      ptx::tmem_ld_x8(lane_addr + (uint32_t)f0, re);
-      ptx::tmem_ld_x8(lane_addr + (uint32_t)(args.F_pad + f0), im);
-      ptx::tmem_wait_ld();
-    } else {
-#pragma unroll
-      for (int q = 0; q < 8; ++q) re[q] = im[q] = 0u;
+    if (abort_s) {
+      // issued MMAs must finish before the tensor memory is released
+      ptx::mma_commit(ptx::smem_u32(&drain_bar));
+      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::globaltimer() + timeout_ns))
+        atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
     }
-    if (row < args.rows) {
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int grp = warp & 3;  // TMEM lanes 32*grp .. 32*grp+31
+    // partial spectra are read back right after this kernel: keep them in L2 while W streams through
+    const uint64_t pol_s = ptx::policy_evict_last();
+    int lt = 0;
+    for (int t = t_begin; t < t_end && !abort_s; ++t, ++lt) {
+      const int4 tk = tasks[t];
+      const ItemDev& it = BATCH ? items[tk.x] : one;
+      const TaskGeom g = task_geom(tk, it);
+      const int acc = lt & 1;
+      const bool ok = ptx::mbar_wait(ptx::smem_u32(&accf_bar[acc]), (uint32_t)(lt >> 1) & 1u, deadline);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT_ACCUM);
+        abort_s = 1;
+        break;
+      }
+      ptx::tc_fence_after();
+      const int rows = 3 * it.M;
+      const int row = g.tile * 128 + grp * 32 + lane;
+      float2* dst = it.S_part + ((size_t)g.split * it.Fz + g.f0) * rows;
+      const uint32_t lane_addr = tmem + (uint32_t)acc * Cfg::ACC_COLS + ((uint32_t)(grp * 32) << 16);
+#pragma unroll 1
+      for (int f0 = 0; f0 < FP; f0 += 8) {
+        uint32_t re[8], im[8];
+        if (g.kcount > 0) {
+          ptx::tmem_ld_x8(lane_addr + (uint32_t)f0, re);
+          ptx::tmem_ld_x8(lane_addr + (uint32_t)(FP + f0), im);
+          ptx::tmem_wait_ld();
+        } else {
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        if (f0 + q < u.nf)
-          dst[(size_t)(f0 + q) * args.rows + row] = make_float2(__uint_as_float(re[q]), __uint_as_float(im[q]));
+          for (int q = 0; q < 8; ++q) re[q] = im[q] = 0u;
+        }
+        if (row < rows) {
+#pragma unroll
+          for (int q = 0; q < 8; ++q)
+            if (f0 + q < g.nf)
+              ptx::st_global_hint(dst + (size_t)(f0 + q) * rows + row,
+                                  make_float2(__uint_as_float(re[q]), __uint_as_float(im[q])), pol_s);
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&acce_bar[acc]));
     }
   }
 
   // ---------------- teardown ----------------
+  __syncwarp();
   ptx::tc_fence_before();
-  __syncthreads();
-  if (abort_s && threadIdx.x == 0) {
-    // let copies that were issued but never consumed land before the CTA exits
-    const uint64_t d2 = ptx::globaltimer() + args.timeout_ns;
-    for (int i = consumed_s; i < issued_s; ++i)
-      if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[i % STAGES]), (uint32_t)(i / STAGES) & 1u, d2)) {
-        atomicOr(args.err, DEV_ERR_TIMEOUT_DRAIN);
-        break;
-      }
-  }
   __syncthreads();
   if (warp == 0) {
     ptx::tc_fence_after();
@@ -209,95 +274,55 @@ __global__ void __launch_bounds__(128) contract_tc_kernel(const __grid_constant_
 }
 
 // ---------------------------------------------------------------- host side ---
-static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
-  return fn;
-}
-
-static bool encode_3d(CUtensorMap* map, CUtensorMapDataType dt, const void* base, uint64_t d0, uint64_t d1,
-                      uint64_t d2, uint32_t b0, uint32_t b1, std::string& why) {
-  auto fn = encode_fn();
-  if (!fn) {
-    why = "cuTensorMapEncodeTiled is not available from the driver";
-    return false;
-  }
-  const cuuint64_t dims[3] = {d0, d1, d2};
-  const cuuint64_t strides[2] = {d0 * 2, d0 * d1 * 2};  // 16-bit elements
-  const cuuint32_t box[3] = {b0, b1, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = fn(map, dt, 3, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    why = "cuTensorMapEncodeTiled failed with CUresult " + std::to_string((int)r);
-    return false;
-  }
-  return true;
-}
-
-bool encode_tensor_maps(Plan& p, std::string& why) {
-  const uint64_t K8 = 8ull * p.M, R = 3ull * p.M;
-  const bool bf = p.precision == SCW_PREC_SPLIT_BF16;
-  const CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-  const void* a_hi = bf ? static_cast<const void*>(p.Whi) : static_cast<const void*>(p.Wh);
-  const void* a_lo = bf ? static_cast<const void*>(p.Wlo) : static_cast<const void*>(p.Wh);
-  if (!encode_3d(&p.tmA_hi, dt, a_hi, K8, R, p.L, 64, 128, why)) return false;
-  if (!encode_3d(&p.tmA_lo, dt, a_lo, K8, R, p.L, 64, 128, why)) return false;
-  const uint64_t nu = p.units.size();
-  if (!encode_3d(&p.tmB_hi, dt, p.Bhi, K8, p.NB, nu, 64, p.NB, why)) return false;
-  if (!encode_3d(&p.tmB_lo, dt, p.Blo, K8, p.NB, nu, 64, p.NB, why)) return false;
-  return true;
-}
-
 template <int NB, bool SPLIT>
-static cudaError_t launch_tc_t(const Plan& p, cudaStream_t st) {
+static cudaError_t launch_tc_t(const ItemDev& one, const ItemDev* items, const TcSchedule& s, int* err,
+                               uint64_t timeout_ns, cudaStream_t st) {
   using Cfg = TcCfg<NB, SPLIT>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(contract_tc_kernel<NB, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)Cfg::SMEM);
+  cudaError_t e;
+  if (items) {
+    e = allow_max_smem(reinterpret_cast<const void*>(contract_tc_kernel<NB, SPLIT, true>));
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    contract_tc_kernel<NB, SPLIT, true><<<s.grid, 192, Cfg::SMEM, st>>>(one, items, s.d_tasks, s.d_cta_off, err,
+                                                                       timeout_ns);
+  } else {
+    e = allow_max_smem(reinterpret_cast<const void*>(contract_tc_kernel<NB, SPLIT, false>));
+    if (e != cudaSuccess) return e;
+    contract_tc_kernel<NB, SPLIT, false><<<s.grid, 192, Cfg::SMEM, st>>>(one, nullptr, s.d_tasks, s.d_cta_off, err,
+                                                                        timeout_ns);
   }
-  TcArgs a;
-  a.units = p.d_units;
-  a.n_tiles = (3 * p.M + 127) / 128;
-  a.ksplit = p.k_split;
-  a.nk = (8 * p.M + 63) / 64;
-  a.rows = 3 * p.M;
-  a.Fz = p.Fz;
-  a.F_pad = p.F_pad;
-  a.S_part = p.S_part;
-  a.err = p.d_err;
-  a.timeout_ns = p.timeout_ns;
-  const unsigned grid = (unsigned)(p.units.size() * a.n_tiles * a.ksplit);
-  contract_tc_kernel<NB, SPLIT><<<grid, 128, Cfg::SMEM, st>>>(p.tmA_hi, p.tmA_lo, p.tmB_hi, p.tmB_lo, a);
   return cudaGetLastError();
 }
 
 template <bool SPLIT>
-static cudaError_t launch_tc_nb(const Plan& p, cudaStream_t st) {
-  switch (p.NB) {
-    case 16: return launch_tc_t<16, SPLIT>(p, st);
-    case 32: return launch_tc_t<32, SPLIT>(p, st);
-    case 48: return launch_tc_t<48, SPLIT>(p, st);
-    case 64: return launch_tc_t<64, SPLIT>(p, st);
-    case 128: return launch_tc_t<128, SPLIT>(p, st);
-    case 256: return launch_tc_t<256, SPLIT>(p, st);
+static cudaError_t launch_tc_nb(int NB, const ItemDev& one, const ItemDev* items, const TcSchedule& s, int* err,
+                                uint64_t timeout_ns, cudaStream_t st) {
+  switch (NB) {
+    case 16: return launch_tc_t<16, SPLIT>(one, items, s, err, timeout_ns, st);
+    case 32: return launch_tc_t<32, SPLIT>(one, items, s, err, timeout_ns, st);
+    case 48: return launch_tc_t<48, SPLIT>(one, items, s, err, timeout_ns, st);
+    case 64: return launch_tc_t<64, SPLIT>(one, items, s, err, timeout_ns, st);
+    case 128: return launch_tc_t<128, SPLIT>(one, items, s, err, timeout_ns, st);
+    case 256: return launch_tc_t<256, SPLIT>(one, items, s, err, timeout_ns, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_contract_tc(const Plan& p, cudaStream_t st) {
-  if (p.units.empty()) return cudaSuccess;
-  return p.precision == SCW_PREC_SPLIT_BF16 ? launch_tc_nb<true>(p, st) : launch_tc_nb<false>(p, st);
+cudaError_t launch_contract_tc(const ItemDev& one, const ItemDev* items, const TcSchedule& s, int NB, bool bf16,
+                               int* err, uint64_t timeout_ns, cudaStream_t st) {
+  if (s.n_tasks == 0 || s.grid == 0) return cudaSuccess;
+  return bf16 ? launch_tc_nb<true>(NB, one, items, s, err, timeout_ns, st)
+              : launch_tc_nb<false>(NB, one, items, s, err, timeout_ns, st);
+}
+
+int tc_ctas_per_sm(int NB, bool bf16) {
+  switch (NB) {
+    case 16: return bf16 ? TcCfg<16, true>::CTAS_PER_SM : TcCfg<16, false>::CTAS_PER_SM;
+    case 32: return bf16 ? TcCfg<32, true>::CTAS_PER_SM : TcCfg<32, false>::CTAS_PER_SM;
+    case 48: return bf16 ? TcCfg<48, true>::CTAS_PER_SM : TcCfg<48, false>::CTAS_PER_SM;
+    case 64: return bf16 ? TcCfg<64, true>::CTAS_PER_SM : TcCfg<64, false>::CTAS_PER_SM;
+    case 128: return bf16 ? TcCfg<128, true>::CTAS_PER_SM : TcCfg<128, false>::CTAS_PER_SM;
+    default: return 1;
+  }
 }
 
 }  // namespace scw

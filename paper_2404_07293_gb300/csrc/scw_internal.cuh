@@ -18,13 +18,13 @@ namespace scw {
 enum : int {
   DEV_ERR_TIMEOUT_FULL = 1,    // consumer wait on a filled stage ran out
   DEV_ERR_TIMEOUT_EMPTY = 2,   // producer wait on a free stage ran out
-  DEV_ERR_TIMEOUT_ACCUM = 4,   // epilogue wait on the accumulator ran out
-  DEV_ERR_TIMEOUT_DRAIN = 8,   // wait for in-flight copies after an abort ran out
-  DEV_ERR_BAD_SHAPE = 16       // a kernel saw a launch shape it cannot handle
+  DEV_ERR_TIMEOUT_ACCUM = 4,   // wait on an accumulator buffer ran out
+  DEV_ERR_TIMEOUT_DRAIN = 8,   // wait for in-flight work after an abort ran out
+  DEV_ERR_TIMEOUT_DEP = 16     // wait on a cross-CTA dependency counter ran out
 };
 
 constexpr int kMaxFx = 4096;
-constexpr int kMaxM = 4096;         // U*V
+constexpr int kMaxM = 4096;              // U*V
 constexpr int kMaxPlanesPerLayer = 128;  // per contraction pass (N <= 256)
 
 // Plane slot of an active layer: which layer, where its planes start in the
@@ -36,6 +36,32 @@ struct LayerUnit {
   int pad;
 };
 
+// Everything a kernel needs to know about one synthesis item. Kernels take it
+// by value (__grid_constant__) for a single plan, or index a device array of
+// them for a batch.
+struct ItemDev {
+  const void* Ahi;         // tensor-core A = W: tile-major swizzled [L][tiles][nk][rows][64] (hi or FP16)
+  const void* Alo;         // low part (split-BF16 only)
+  const LayerUnit* units;
+  const double* zplanes;
+  const double* zbounds;
+  const double2* gamma;
+  const double2* alpha;
+  void* Bhi;               // [unit][nk][NB][64], same swizzled layout
+  void* Blo;
+  float2* S_part;          // [k_split][Fz][3M]
+  const int* nsplit;       // [Fz]
+  const float2* twx;       // [Up][Fx/8]   fold twiddles, order index p = ui + rotU (residue b fastest:
+                           //               the lanes of an x-pass warp take consecutive b)
+  const float2* twy;       // [Fy/8][Vp]
+  float2* T;               // [Fz][3][V][Fx] x-pass rows (plans only)
+  size_t split_stride;     // Fz * 3M
+  double inv_lam;
+  int M, U, V, Fx, Fy, Fz;
+  int F_pad, k_split, n_tiles, nk, n_units;
+  int rotU, rotV, Up, Vp;  // fold offsets (-(U/2)) & 7 and padded lengths roundup(U + rotU, 8)
+};
+
 struct Plan {
   // description
   int U = 0, V = 0, M = 0, L = 0, Fx = 0, Fy = 0, Fz = 0;
@@ -44,7 +70,6 @@ struct Plan {
   int precision = 0;
   unsigned flags = 0;
   std::vector<double> z_bounds, z_planes;
-  uint64_t timeout_ns = 2000000000ull;
 
   // plane assignment (host copies)
   std::vector<int> plane_region;  // -1 above, 0..L-1 layer, L below
@@ -55,7 +80,6 @@ struct Plan {
   int n_exterior = 0;
 
   // device tables
-  int* d_err = nullptr;
   LayerUnit* d_units = nullptr;
   double* d_zplanes = nullptr;
   double* d_zbounds = nullptr;     // [L+1]
@@ -64,8 +88,8 @@ struct Plan {
   int* d_ext_planes = nullptr;     // [n_exterior] plane indices outside the sample
   double2* d_sz_top = nullptr;     // [M]
   double2* d_sz_bot = nullptr;     // [M]
-  float2* d_twx = nullptr;         // [Fx/8][U]
-  float2* d_twy = nullptr;         // [Fy/8][V]
+  float2* d_twx = nullptr;         // [Up][Fx/8]
+  float2* d_twy = nullptr;         // [Fy/8][Vp]
 
   // attached inputs (not owned)
   const double2* gamma = nullptr;
@@ -76,13 +100,13 @@ struct Plan {
   bool layers_set = false;
 
   // converted W (owned)
-  __nv_bfloat16* Whi = nullptr;   // [L][3M][8M]
+  __nv_bfloat16* Whi = nullptr;   // tile-major swizzled, L * 3M * nk * 64 elements
   __nv_bfloat16* Wlo = nullptr;
-  __half* Wh = nullptr;           // [L][3M][8M]
+  __half* Wh = nullptr;           // same layout
   float2* Wt = nullptr;           // [L][4M][3M]
 
   // per-synthesis workspace (owned)
-  void* Bhi = nullptr;            // [unit][NB][8M] bf16 or fp16
+  void* Bhi = nullptr;            // [unit][nk][NB][64] bf16 or fp16 (swizzled)
   void* Blo = nullptr;
   float2* Cf = nullptr;           // [unit][4M][F_pad] (FP32 path)
   float2* S_part = nullptr;       // [k_split][Fz][3M]
@@ -95,40 +119,59 @@ struct Plan {
   double2* hio_p = nullptr;       // [3][3][M]: inc, ref, trn
   float2* hio_out = nullptr;
 
-  CUtensorMap tmA_hi, tmA_lo, tmB_hi, tmB_lo;
+  ItemDev item;                   // host copy of the kernels' view of this item
 
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the last W conversion
-  bool timing = false;
-  std::vector<cudaEvent_t> tev;   // 5 events per timed synthesize call
-  size_t tev_used = 0;
   bool convert_pending = false;
   size_t workspace_bytes = 0;
   double convert_ms = 0;
-  int kernels_per_synthesis = 0;
 };
+
+// Contraction schedule of a set of items: tasks (item, unit, row tile, split)
+// grouped per persistent CTA, longest first (LPT).
+struct TcSchedule {
+  int4* d_tasks = nullptr;
+  int* d_cta_off = nullptr;       // [grid + 1]
+  int grid = 0;
+  int n_tasks = 0;
+  double max_load = 0, mean_load = 0;  // in K-stages, for the autotuner's report
+};
+
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
+// once per (kernel, device): the attribute call is not repeated on the launch path.
+cudaError_t allow_max_smem(const void* kernel);
 
 // error reporting (thread-local message)
 scw_status set_error(scw_status s, const std::string& msg);
 scw_status cuda_error(cudaError_t e, const char* what);
 
 // launchers (host side), each returns cudaSuccess or the launch error
-cudaError_t launch_convert_split_bf16(const float2* W, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                                      size_t n_complex, cudaStream_t st);
-cudaError_t launch_convert_fp16(const float2* W, __half* h, size_t n_complex, cudaStream_t st);
-cudaError_t launch_transpose_layers(const float2* W, float2* Wt, int L, int rows, int cols,
-                                    cudaStream_t st);
-cudaError_t launch_phases_tc(const Plan& p, cudaStream_t st);
+cudaError_t launch_convert_tiled(const float2* W, void* hi, void* lo, int L, int M, bool bf16_split, cudaStream_t st);
+cudaError_t launch_transpose_layers(const float2* W, float2* Wt, int L, int rows, int cols, cudaStream_t st);
+
+// step (a): unit entries are (item, unit) pairs; items == nullptr means "the single item `one`"
+cudaError_t launch_phases_tc(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
+                             int max_M, int F_pad, bool bf16, cudaStream_t st);
 cudaError_t launch_phases_fp32(const Plan& p, cudaStream_t st);
 cudaError_t launch_exterior(const Plan& p, cudaStream_t st);
-cudaError_t launch_contract_tc(const Plan& p, cudaStream_t st);
-cudaError_t launch_contract_fp32(const Plan& p, cudaStream_t st);
-cudaError_t launch_recompose(const Plan& p, const float2* S_part, int S_splits_stride_planes,
-                             const int* d_nsplit, float2* out, cudaStream_t st);
-cudaError_t launch_gather_spectrum(const Plan& p, float2* S, cudaStream_t st);
-cudaError_t launch_xpass(const Plan& p, const float2* S_part, int split_stride_planes, const int* d_nsplit,
-                         cudaStream_t st);
-cudaError_t launch_ypass(const Plan& p, float2* out, cudaStream_t st);
 
-bool encode_tensor_maps(Plan& p, std::string& why);
+// step (b)
+cudaError_t launch_contract_tc(const ItemDev& one, const ItemDev* items, const TcSchedule& s, int NB, bool bf16,
+                               int* err, uint64_t timeout_ns, cudaStream_t st);
+cudaError_t launch_contract_fp32(const Plan& p, cudaStream_t st);
+int tc_ctas_per_sm(int NB, bool bf16);
+
+// step (c): plane entries are (item, plane) pairs; S_override / nsplit_override replace the
+// contraction's partial spectra with caller-given spectra
+size_t recompose_smem_bytes(int V, int Up, int Vp);
+cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_M,
+                         cudaStream_t st);
+cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_Qx,
+                         int max_V, float2* out_one, float2* const* d_outs, cudaStream_t st);
+cudaError_t launch_recompose(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_Qx,
+                             size_t smem, const float2* S_override, const int* nsplit_override, float2* out_one,
+                             float2* const* d_outs, cudaStream_t st);
+cudaError_t launch_gather_spectrum(const Plan& p, float2* S, cudaStream_t st);
+
 
 }  // namespace scw

@@ -1,15 +1,16 @@
-// scw_recompose_noalloc: the recompose step (x-pass + y-pass of scw_recompose)
-// for callers that cannot allocate device memory. Its scratch -- the twiddle
-// tables, a per-plane split count and the x-pass rows T -- lives in one
-// file-scope __device__ array instead of a plan's cudaMalloc'ed workspace.
-// The kernels are the library's own x-pass and y-pass, unchanged.
+// scw_recompose_noalloc: the recompose step of scw_recompose for callers that
+// cannot allocate device memory. Its scratch -- the fold twiddle tables, a
+// per-plane split count and the plane table -- lives in one file-scope
+// __device__ array instead of a plan's cudaMalloc'ed workspace. The kernel is
+// the library's own recompose kernel, unchanged.
+#include <cstring>
 #include <mutex>
 
 #include "scw_internal.cuh"
 
 namespace scw {
 
-constexpr size_t kNoAllocScratchBytes = size_t(64) << 20;  // SCW_NOALLOC_SCRATCH_BYTES in scw.h
+constexpr size_t kNoAllocScratchBytes = size_t(8) << 20;  // SCW_NOALLOC_SCRATCH_BYTES in scw.h
 
 // Shared by every call on a device; held by each device that loads the library until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -18,26 +19,38 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_addr[64] = {nullptr};
 
-// Twiddles exp(2 pi i (u b / F + u x0 / X)) with the argument reduced in FP64
-// (same tables a plan builds on the host) and the all-ones split count.
-__global__ void noalloc_setup_kernel(float2* twx, int U, int Fx, double x0_over_X, float2* twy, int V, int Fy,
-                                     double y0_over_Y, int* ones, int Fz) {
-  const int Qx = Fx / 8, Qy = Fy / 8;
-  const int nx = Qx * U, ny = Qy * V;
+// The fold twiddles exp(2 pi i (u b / F + u x0 / X)) in the padded layouts the
+// recompose kernels read (order u at index p = u + n/2 + rot, zeros elsewhere;
+// x table [p][b], y table [b][p]),
+// with the argument reduced in FP64 as a plan does on the host; the all-ones
+// split count; and the (item 0, plane f) entry table.
+__global__ void noalloc_setup_kernel(float2* twx, int U, int Up, int rotU, int Fx, double x0_over_X, float2* twy,
+                                     int V, int Vp, int rotV, int Fy, double y0_over_Y, int* ones, int2* entries,
+                                     int Fz) {
+  const int nx = (Fx / 8) * Up, ny = (Fy / 8) * Vp;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx + ny + Fz; i += gridDim.x * blockDim.x) {
     if (i < nx + ny) {
       const bool isx = i < nx;
       const int k = isx ? i : i - nx;
-      const int n = isx ? U : V;
-      const int b = k / n, idx = k - b * n;
-      const int u = idx - n / 2;
-      const double t = isx ? ((double)u * b / Fx + u * x0_over_X) : ((double)u * b / Fy + u * y0_over_Y);
-      const double r = t - rint(t);
-      double s, c;
-      sincospi(2.0 * r, &s, &c);
-      (isx ? twx : twy)[k] = make_float2((float)c, (float)s);
+      const int np = isx ? Up : Vp, n = isx ? U : V, rot = isx ? rotU : rotV;
+      // x table [p][b] (residue fastest), y table [b][p]
+      const int Qx = Fx / 8;
+      const int b = isx ? k % Qx : k / np;
+      const int idx = (isx ? k / Qx : k - b * np) - rot;
+      float2 w = make_float2(0.f, 0.f);
+      if (idx >= 0 && idx < n) {
+        const int u = idx - n / 2;
+        const double t = isx ? ((double)u * b / Fx + u * x0_over_X) : ((double)u * b / Fy + u * y0_over_Y);
+        const double r = t - rint(t);
+        double s, c;
+        sincospi(2.0 * r, &s, &c);
+        w = make_float2((float)c, (float)s);
+      }
+      (isx ? twx : twy)[k] = w;
     } else {
-      ones[i - nx - ny] = 1;
+      const int f = i - nx - ny;
+      ones[f] = 1;
+      entries[f] = make_int2(0, f);
     }
   }
 }
@@ -59,17 +72,19 @@ extern "C" scw_status scw_recompose_noalloc(int U, int V, double X, double Y, in
   if (Fz < 1 || Fz > 65535) return set_error(SCW_ERR_INVALID_ARGUMENT, "Fz must be in [1, 65535]");
   if ((reinterpret_cast<uintptr_t>(out) & 15u) != 0) return set_error(SCW_ERR_INVALID_ARGUMENT, "out must be 16-byte aligned");
 
-  // scratch layout: twx | twy | ones | T, each 256-byte aligned
-  const size_t b_twx = align256(sizeof(float2) * (size_t)(Fx / 8) * U);
-  const size_t b_twy = align256(sizeof(float2) * (size_t)(Fy / 8) * V);
+  // scratch layout: twx | twy | ones | entries, each 256-byte aligned
+  const int rotU = (8 - (U / 2) % 8) % 8, rotV = (8 - (V / 2) % 8) % 8;
+  const int Up = (U + rotU + 7) / 8 * 8, Vp = (V + rotV + 7) / 8 * 8;
+  const size_t b_twx = align256(sizeof(float2) * (size_t)(Fx / 8) * Up);
+  const size_t b_twy = align256(sizeof(float2) * (size_t)(Fy / 8) * Vp);
   const size_t b_one = align256(sizeof(int) * (size_t)Fz);
-  const size_t b_T = sizeof(float2) * (size_t)Fz * 3 * V * Fx;
-  const size_t need = b_twx + b_twy + b_one + b_T;
+  const size_t b_ent = align256(sizeof(int2) * (size_t)Fz);
+  const size_t need = b_twx + b_twy + b_one + b_ent;
   if (need > kNoAllocScratchBytes)
     return set_error(SCW_ERR_UNSUPPORTED, "scw_recompose_noalloc needs " + std::to_string(need) +
                                               " bytes of scratch, above its fixed " +
                                               std::to_string(kNoAllocScratchBytes) +
-                                              " (3 Fz V Fx complex64 plus tables); use scw_recompose with a plan");
+                                              " (twiddle and plane tables); use scw_recompose with a plan");
 
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -89,23 +104,27 @@ extern "C" scw_status scw_recompose_noalloc(int U, int V, double X, double Y, in
     base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
   }
 
-  Plan p;  // a stack descriptor of the sizes and scratch pointers; it owns nothing
-  p.U = U; p.V = V; p.M = U * V; p.Fx = Fx; p.Fy = Fy; p.Fz = Fz;
-  p.X = X; p.Y = Y; p.x0 = x0; p.y0 = y0;
-  p.d_twx = reinterpret_cast<float2*>(base);
-  p.d_twy = reinterpret_cast<float2*>(base + b_twx);
+  // the kernels' view of the sizes and scratch pointers, passed by value; it owns nothing
+  ItemDev it;
+  std::memset(&it, 0, sizeof(it));
+  it.M = U * V; it.U = U; it.V = V; it.Fx = Fx; it.Fy = Fy; it.Fz = Fz;
+  it.rotU = rotU; it.rotV = rotV; it.Up = Up; it.Vp = Vp;
+  it.split_stride = (size_t)Fz * 3 * U * V;
+  float2* twx = reinterpret_cast<float2*>(base);
+  float2* twy = reinterpret_cast<float2*>(base + b_twx);
   int* ones = reinterpret_cast<int*>(base + b_twx + b_twy);
-  p.T = reinterpret_cast<float2*>(base + b_twx + b_twy + b_one);
+  int2* entries = reinterpret_cast<int2*>(base + b_twx + b_twy + b_one);
+  it.twx = twx;
+  it.twy = twy;
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int n = (Fx / 8) * U + (Fy / 8) * V + Fz;
+  const int n = (Fx / 8) * Up + (Fy / 8) * Vp + Fz;
   noalloc_setup_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, st>>>(
-      p.d_twx, U, Fx, x0 / X, p.d_twy, V, Fy, y0 / Y, ones, Fz);
+      twx, U, Up, rotU, Fx, x0 / X, twy, V, Vp, rotV, Fy, y0 / Y, ones, entries, Fz);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "noalloc setup launch");
-  e = launch_xpass(p, static_cast<const float2*>(S), Fz, ones, st);
-  if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
-  e = launch_ypass(p, static_cast<float2*>(out), st);
-  if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
+  e = launch_recompose(it, nullptr, entries, Fz, Fx / 8, recompose_smem_bytes(V, Up, Vp),
+                       static_cast<const float2*>(S), ones, static_cast<float2*>(out), nullptr, st);
+  if (e != cudaSuccess) return cuda_error(e, "recompose launch");
   return SCW_OK;
 }

@@ -90,31 +90,50 @@ __device__ __forceinline__ ModeConst mode_const(double2 g, double2 al, double in
   return m;
 }
 
-// B operand of the tensor-core contraction, [unit][NB][8M] with NB = 2 F_pad:
-// row f holds (Re c_j, -Im c_j) at columns (2j, 2j+1), row F_pad + f holds
-// (Im c_j, Re c_j); with A = W viewed as interleaved reals this gives
-// [Re S | Im S] (the complex product as one real GEMM). hi = round(x),
-// lo = round(x - hi). One thread per mode j loops over the unit's planes.
-template <typename T>
-__global__ void __launch_bounds__(128) phases_tc_kernel(const LayerUnit* __restrict__ units,
-                                                        const double* __restrict__ zplanes,
-                                                        const double* __restrict__ zb,
-                                                        const double2* __restrict__ gamma,
-                                                        const double2* __restrict__ alpha, int M, int F_pad,
-                                                        double inv_lam, T* __restrict__ Bhi, T* __restrict__ Blo) {
+// Element offset of (row n, column k) in a tile-major operand with the
+// 128-byte swizzle of the tensor cores' K-major shared-memory layout: K is cut
+// into chunks of 64 16-bit elements; chunk kc holds `rows` rows of 128 bytes,
+// and the 16-byte group g of row n is stored at group g ^ (n mod 8). A chunk is
+// then one contiguous block that lands in shared memory as is.
+__device__ __forceinline__ size_t swz_offset(int n, int k, int rows) {
+  const int kc = k >> 6, e = k & 63;
+  const int g = e >> 3;
+  return (size_t)kc * rows * 64 + (size_t)n * 64 + (size_t)(((g ^ (n & 7)) << 3) | (e & 7));
+}
+
+// B operand of the tensor-core contraction, per work unit nk chunks of NB rows
+// (NB = 2 F_pad) in the layout above: row f holds (Re c_j, -Im c_j) at columns
+// (2j, 2j+1), row F_pad + f holds (Im c_j, Re c_j); with A = W viewed as
+// interleaved reals this gives [Re S | Im S] (the complex product as one real
+// GEMM). hi = round(x), lo = round(x - hi). One thread per mode j and group of
+// kPlaneGroup planes; blocks are (mode block, (item, unit) entry, plane group).
+constexpr int kPlaneGroup = 2;
+
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(128) phases_tc_kernel(const __grid_constant__ ItemDev one,
+                                                        const ItemDev* __restrict__ items,
+                                                        const int2* __restrict__ entries, int F_pad) {
   __shared__ PlaneOffsets off;
-  const LayerUnit u = units[blockIdx.y];
-  load_offsets(off, u, zplanes, zb);
+  const int2 e = entries[blockIdx.y];
+  const ItemDev& it = BATCH ? items[e.x] : one;
+  const LayerUnit u = it.units[e.y];
+  load_offsets(off, u, it.zplanes, it.zbounds);
   __syncthreads();
+  const int M = it.M;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int M4 = 4 * M;
   if (j >= M4) return;
-  const size_t K8 = (size_t)8 * M;
   const int NB = 2 * F_pad;
-  const ModeConst mc = mode_const(gamma[(size_t)u.layer * M4 + j], alpha[(size_t)u.layer * M4 + j], inv_lam);
+  const ModeConst mc = mode_const(it.gamma[(size_t)u.layer * M4 + j], it.alpha[(size_t)u.layer * M4 + j],
+                                  it.inv_lam);
   const bool fwd = j < 2 * M;
-  const size_t base = (size_t)blockIdx.y * NB * K8 + 2 * (size_t)j;  // B is per work unit
-  for (int f = 0; f < F_pad; ++f) {
+  const size_t base = (size_t)e.y * it.nk * NB * 64;  // B is per work unit
+  T* Bhi = static_cast<T*>(it.Bhi) + base;
+  T* Blo = static_cast<T*>(it.Blo) + base;
+  const int fb = blockIdx.z * kPlaneGroup;
+#pragma unroll
+  for (int q = 0; q < kPlaneGroup; ++q) {
+    const int f = fb + q;
     float2 cv = make_float2(0.f, 0.f);
     if (f < u.nf) {
       const float dh = fwd ? off.f_hi[f] : off.b_hi[f];
@@ -128,7 +147,7 @@ __global__ void __launch_bounds__(128) phases_tc_kernel(const LayerUnit* __restr
     l0.a = to_lp<T>(v0[0] - from_lp<T>(h0.a)); l0.b = to_lp<T>(v0[1] - from_lp<T>(h0.b));
     h1.a = to_lp<T>(v1[0]); h1.b = to_lp<T>(v1[1]);
     l1.a = to_lp<T>(v1[0] - from_lp<T>(h1.a)); l1.b = to_lp<T>(v1[1] - from_lp<T>(h1.b));
-    const size_t i0 = base + (size_t)f * K8, i1 = base + (size_t)(F_pad + f) * K8;
+    const size_t i0 = swz_offset(f, 2 * j, NB), i1 = swz_offset(F_pad + f, 2 * j, NB);
     *reinterpret_cast<Pair<T>*>(Bhi + i0) = h0;
     *reinterpret_cast<Pair<T>*>(Blo + i0) = l0;
     *reinterpret_cast<Pair<T>*>(Bhi + i1) = h1;
@@ -198,27 +217,44 @@ __global__ void exterior_kernel(const int* __restrict__ ext_planes, const double
 }
 
 // ---- one-off conversions of W (plan time) -----------------------------------
-__global__ void convert_split_bf16_kernel(const float4* __restrict__ W, uint2* __restrict__ hi,
-                                          uint2* __restrict__ lo, size_t n4) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
-    const float4 v = W[i];
-    const float x[4] = {v.x, v.y, v.z, v.w};
-    __nv_bfloat16 h[4], l[4];
+// W [L][R = 3M][K8 = 8M] reals (the complex64 layout) -> tile-major, swizzled
+// 16-bit copies for the tensor-core contraction: for layer l, row tile t
+// (rows 128 t .. 128 t + rt - 1, rt = min(128, R - 128 t)) and K chunk kc, one
+// contiguous block of rt x 64 elements (swz_offset layout; K beyond 8M is zero).
+// One thread per (l, row, kc, 16-byte group): 8 reals in, 8 (hi) + 8 (lo) out.
+template <typename T, bool SPLIT>
+__global__ void convert_tiled_kernel(const float* __restrict__ W, T* __restrict__ hi, T* __restrict__ lo, int L, int R,
+                                     int K8, int nk) {
+  const size_t total = (size_t)L * R * nk * 8;
+  for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
+    const int grp = (int)(g & 7);
+    const size_t q = g >> 3;
+    const int kc = (int)(q % nk);
+    const size_t q2 = q / nk;
+    const int row = (int)(q2 % R);
+    const int l = (int)(q2 / R);
+    const int k0 = kc * 64 + grp * 8;
+    float x[8];
+    if (k0 < K8) {
+      const float4* src = reinterpret_cast<const float4*>(W + ((size_t)l * R + row) * K8 + k0);
+      const float4 a = src[0], b = src[1];
+      x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w; x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+    } else {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      h[q] = __float2bfloat16_rn(x[q]);
-      l[q] = __float2bfloat16_rn(x[q] - __bfloat162float(h[q]));
+      for (int i = 0; i < 8; ++i) x[i] = 0.f;
     }
-    hi[i] = *reinterpret_cast<uint2*>(h);
-    lo[i] = *reinterpret_cast<uint2*>(l);
-  }
-}
-
-__global__ void convert_fp16_kernel(const float4* __restrict__ W, uint2* __restrict__ out, size_t n4) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
-    const float4 v = W[i];
-    __half h[4] = {__float2half_rn(v.x), __float2half_rn(v.y), __float2half_rn(v.z), __float2half_rn(v.w)};
-    out[i] = *reinterpret_cast<uint2*>(h);
+    const int t = row >> 7, n = row & 127;
+    const int rt = min(128, R - 128 * t);
+    const size_t off = (size_t)l * R * nk * 64 + (size_t)t * 128 * nk * 64 + (size_t)kc * rt * 64 + (size_t)n * 64 +
+                       (size_t)((grp ^ (n & 7)) << 3);
+    T h[8], lw[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      h[i] = to_lp<T>(x[i]);
+      if (SPLIT) lw[i] = to_lp<T>(x[i] - from_lp<T>(h[i]));
+    }
+    *reinterpret_cast<uint4*>(hi + off) = *reinterpret_cast<uint4*>(h);
+    if (SPLIT) *reinterpret_cast<uint4*>(lo + off) = *reinterpret_cast<uint4*>(lw);
   }
 }
 
@@ -246,19 +282,16 @@ static int grid_for(size_t n, int block) {
   return (int)g;
 }
 
-cudaError_t launch_convert_split_bf16(const float2* W, __nv_bfloat16* hi, __nv_bfloat16* lo,
-                                      size_t n_complex, cudaStream_t st) {
-  const size_t n4 = n_complex / 2;  // 2 complex = 4 floats; 4M columns keep this exact
-  convert_split_bf16_kernel<<<grid_for(n4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(W),
-                                                               reinterpret_cast<uint2*>(hi),
-                                                               reinterpret_cast<uint2*>(lo), n4);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_convert_fp16(const float2* W, __half* h, size_t n_complex, cudaStream_t st) {
-  const size_t n4 = n_complex / 2;
-  convert_fp16_kernel<<<grid_for(n4, 256), 256, 0, st>>>(reinterpret_cast<const float4*>(W),
-                                                         reinterpret_cast<uint2*>(h), n4);
+cudaError_t launch_convert_tiled(const float2* W, void* hi, void* lo, int L, int M, bool bf16_split, cudaStream_t st) {
+  const int R = 3 * M, K8 = 8 * M, nk = (K8 + 63) / 64;
+  const size_t total = (size_t)L * R * nk * 8;
+  const float* w = reinterpret_cast<const float*>(W);
+  if (bf16_split)
+    convert_tiled_kernel<__nv_bfloat16, true><<<grid_for(total, 256), 256, 0, st>>>(
+        w, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(lo), L, R, K8, nk);
+  else
+    convert_tiled_kernel<__half, false><<<grid_for(total, 256), 256, 0, st>>>(w, static_cast<__half*>(hi), nullptr,
+                                                                              L, R, K8, nk);
   return cudaGetLastError();
 }
 
@@ -268,20 +301,22 @@ cudaError_t launch_transpose_layers(const float2* W, float2* Wt, int L, int rows
   return cudaGetLastError();
 }
 
-cudaError_t launch_phases_tc(const Plan& p, cudaStream_t st) {
-  const int n_units = (int)p.units.size();
-  if (n_units == 0) return cudaSuccess;
-  dim3 grid((4 * p.M + 127) / 128, n_units);
-  const double inv_lam = 1.0 / p.lambda;
-  if (p.precision == SCW_PREC_SPLIT_BF16)
-    phases_tc_kernel<__nv_bfloat16><<<grid, 128, 0, st>>>(
-        p.d_units, p.d_zplanes, p.d_zbounds, p.gamma, p.alpha, p.M, p.F_pad, inv_lam,
-        static_cast<__nv_bfloat16*>(p.Bhi), static_cast<__nv_bfloat16*>(p.Blo));
+template <typename T>
+static cudaError_t launch_phases_tc_t(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
+                                      int max_M, int F_pad, cudaStream_t st) {
+  dim3 grid((4 * max_M + 127) / 128, n_entries, F_pad / kPlaneGroup);
+  if (items)
+    phases_tc_kernel<T, true><<<grid, 128, 0, st>>>(one, items, d_entries, F_pad);
   else
-    phases_tc_kernel<__half><<<grid, 128, 0, st>>>(p.d_units, p.d_zplanes, p.d_zbounds, p.gamma, p.alpha,
-                                                   p.M, p.F_pad, inv_lam, static_cast<__half*>(p.Bhi),
-                                                   static_cast<__half*>(p.Blo));
+    phases_tc_kernel<T, false><<<grid, 128, 0, st>>>(one, nullptr, d_entries, F_pad);
   return cudaGetLastError();
+}
+
+cudaError_t launch_phases_tc(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
+                             int max_M, int F_pad, bool bf16, cudaStream_t st) {
+  if (n_entries == 0) return cudaSuccess;
+  return bf16 ? launch_phases_tc_t<__nv_bfloat16>(one, items, d_entries, n_entries, max_M, F_pad, st)
+              : launch_phases_tc_t<__half>(one, items, d_entries, n_entries, max_M, F_pad, st);
 }
 
 cudaError_t launch_phases_fp32(const Plan& p, cudaStream_t st) {

@@ -7,14 +7,18 @@
 // index i = b + Q a (b < Q, a < 8), omega = exp(2 pi i / F):
 //   sum_u s_u omega^(u (b + Q a)) = sum_{r<8} e^(2 pi i r a / 8) F_b[r],
 //   F_b[r] = sum_{u = r mod 8} s_u omega^(u b).
-// So each thread folds the few non-zero inputs into 8 residue bins with one
-// table twiddle each (tw[b][u] = omega^(u b) times the origin phase
-// exp(2 pi i u x0 / X)), then finishes with an in-register radix-8 inverse
-// DFT and writes 8 outputs Q apart. Orders beyond the grid (|u| >= F/2) fold
-// exactly, as the sum is only evaluated at grid points.
+// The signed orders u are stored at index p = u + U/2 + rot with
+// rot = (-(U/2)) mod 8, so p mod 8 == u mod 8 and consecutive groups of 8
+// stored values land in residues 0..7 in order: the fold is a fully unrolled
+// loop over groups with independent loads (rows zero-padded to a multiple of
+// 8). Each table twiddle tw[b][p] = omega^(u b) exp(2 pi i u x0 / X) carries the
+// origin phase. An in-register radix-8 inverse DFT finishes the 8 outputs Q
+// apart. Orders beyond the grid (|u| >= F/2) fold exactly: the sum is only
+// evaluated at grid points.
 //
-//   x-pass: S[f][c][v][u]      -> T[f][c][v][x]   (V rows per plane)
-//   y-pass: T[f][c][v][x-block] -> out[c][f][y][x] (16-byte streaming stores)
+// Plans run the two directions as two kernels (x-pass rows T through L2, then
+// the y-pass with contiguous 512-byte warp stores); the allocation-free entry
+// point, which has no room for T, runs them fused in one kernel.
 #include "scw_internal.cuh"
 
 namespace scw {
@@ -57,80 +61,230 @@ __device__ __forceinline__ void idft8(float2 (&x)[8]) {
   }
 }
 
-// One CTA per (plane, component): sum the contraction's partial spectra into
-// shared memory, then V * Fx/8 fold+DFT tasks.
-__global__ void __launch_bounds__(256) xpass_kernel(const float2* __restrict__ S_part, size_t split_stride,
-                                                    const int* __restrict__ nsplit, const float2* __restrict__ twx,
-                                                    int U, int V, int Fx, float2* __restrict__ T) {
-  extern __shared__ float2 srow[];  // [M]
-  const int f = blockIdx.x, c = blockIdx.y;
-  const int M = U * V;
-  const int ns = nsplit[f];
-  const float2* src = S_part + (size_t)f * 3 * M + (size_t)c * M;
-  for (int m = threadIdx.x; m < M; m += blockDim.x) {
+// One CTA per (block of 8 column residues, item-plane, component). The CTA owns
+// the 64 output columns x = b + Qx a (b in its 8 residues, a < 8), which are
+// exactly the outputs of its residues' x-direction folds, so the x-pass rows
+// for its columns are computed once, straight into shared memory:
+//   1. the spectrum rows of component c (partial sums of the contraction added)
+//      -> srow[V][Up];
+//   2. x-direction fold + radix-8 inverse DFT per (row v, residue b)
+//      -> tcol[p = v + rotV][local column b_local + 8 a];
+//   3. y-direction fold + radix-8 inverse DFT per (column pair, y residue),
+//      16-byte streaming stores (each warp store: 8 runs of 8 contiguous columns).
+template <bool BATCH>
+__global__ void __launch_bounds__(256, 4) recompose_kernel(const __grid_constant__ ItemDev one,
+                                                           const ItemDev* __restrict__ items,
+                                                           const int2* __restrict__ entries,
+                                                           const float2* __restrict__ S_override,
+                                                           const int* __restrict__ nsplit_override,
+                                                           float2* out_one, float2* const* __restrict__ outs) {
+  extern __shared__ float4 sm4[];
+  const int2 e = entries[blockIdx.y];
+  const ItemDev& it = BATCH ? items[e.x] : one;
+  const int Qx = it.Fx >> 3;
+  const int b0 = blockIdx.x * 8;
+  if (b0 >= Qx) return;
+  const int nb = min(8, Qx - b0);
+  const int f = e.y, c = blockIdx.z;
+  const int U = it.U, V = it.V, M = it.M, Up = it.Up, Vp = it.Vp, rotU = it.rotU, rotV = it.rotV;
+  float4* tcol4 = sm4;                                  // [Vp][32] float4 = [Vp][64] complex
+  float2* tcol = reinterpret_cast<float2*>(sm4);
+  float2* srow = tcol + (size_t)Vp * 64;                // [V][Up]
+
+  // 1. spectrum rows of component c
+  const float2* src = (S_override ? S_override : it.S_part) + (size_t)f * 3 * M + (size_t)c * M;
+  const int ns = nsplit_override ? nsplit_override[f] : it.nsplit[f];
+  const size_t stride = it.split_stride;
+  for (int i = threadIdx.x; i < V * Up; i += blockDim.x) {
+    const int vi = i / Up, ui = i - vi * Up - rotU;
     float2 acc = make_float2(0.f, 0.f);
-    for (int s = 0; s < ns; ++s) acc = c_add(acc, src[(size_t)s * split_stride + m]);
-    srow[m] = acc;
+    if (ui >= 0 && ui < U) {
+      const float2* s = src + vi * U + ui;
+      for (int k = 0; k < ns; ++k) acc = c_add(acc, s[(size_t)k * stride]);
+    }
+    srow[i] = acc;
+  }
+  for (int i = threadIdx.x; i < Vp * 64; i += blockDim.x) {  // rows outside [rotV, rotV + V) stay zero
+    const int vi = (i >> 6) - rotV;
+    if (vi < 0 || vi >= V) tcol[i] = make_float2(0.f, 0.f);
   }
   __syncthreads();
-  const int Q = Fx >> 3;
-  const int h = U >> 1;
-  float2* dst = T + ((size_t)f * 3 + c) * V * Fx;
-  for (int task = threadIdx.x; task < V * Q; task += blockDim.x) {
-    const int vi = task / Q, b = task - vi * Q;
-    const float2* s = srow + vi * U;
-    const float2* tw = twx + (size_t)b * U;
-    float2 F[8];
+
+  // 2. x-direction: fold + DFT for (row vi, residue b0 + bl)
+  for (int t = threadIdx.x; t < V * 8; t += blockDim.x) {
+    const int vi = t >> 3, bl = t & 7;
+    float2 G[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      F[r] = make_float2(0.f, 0.f);
-      for (int ui = (r + h) & 7; ui < U; ui += 8) c_fma(F[r], s[ui], __ldg(tw + ui));
+    for (int q = 0; q < 8; ++q) G[q] = make_float2(0.f, 0.f);
+    if (bl < nb) {
+      const float2* s = srow + vi * Up;
+      const float2* tw = it.twx + b0 + bl;  // [p][b]
+      for (int p0 = 0; p0 < Up; p0 += 8) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) c_fma(G[q], s[p0 + q], __ldg(tw + (size_t)(p0 + q) * Qx));
+      }
+      idft8(G);
     }
-    idft8(F);
-    float2* o = dst + (size_t)vi * Fx + b;
+    float2* d = tcol + (size_t)(vi + rotV) * 64 + bl;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) o[a * Q] = F[a];
+    for (int a = 0; a < 8; ++a) d[8 * a] = G[a];
+  }
+  __syncthreads();
+
+  // 3. y-direction: lane l owns local columns (2l, 2l+1) = residues b0 + 2(l & 3) (+1), a = l >> 2
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int bl = 2 * (lane & 3);
+  const int x = b0 + bl + Qx * (lane >> 2);
+  const bool pair = bl + 1 < nb;
+  const bool v16 = pair && ((Qx & 1) == 0);  // x even: 16-byte aligned pair
+  const int Fx = it.Fx, Fy = it.Fy;
+  const int Qy = Fy >> 3;
+  float2* out = BATCH ? outs[e.x] : out_one;
+  float2* dst = out + (((size_t)c * it.Fz + f) * Fy) * Fx + x;
+  if (bl >= nb) return;  // no __syncthreads below
+  for (int b = w; b < Qy; b += 8) {
+    float2 G0[8], G1[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) G0[q] = G1[q] = make_float2(0.f, 0.f);
+    const float2* tw = it.twy + (size_t)b * Vp;
+    for (int p0 = 0; p0 < Vp; p0 += 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float2 t = __ldg(tw + p0 + q);
+        const float4 d = tcol4[(p0 + q) * 32 + lane];
+        c_fma(G0[q], make_float2(d.x, d.y), t);
+        c_fma(G1[q], make_float2(d.z, d.w), t);
+      }
+    }
+    idft8(G0);
+    idft8(G1);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      float2* o = dst + (size_t)(b + a * Qy) * Fx;
+      if (v16) {
+        __stcs(reinterpret_cast<float4*>(o), make_float4(G0[a].x, G0[a].y, G1[a].x, G1[a].y));
+      } else {
+        __stcs(o, G0[a]);
+        if (pair) __stcs(o + 1, G1[a]);
+      }
+    }
   }
 }
 
-// One CTA per (64-column block, plane, component); 8 warps, lane l owns the
+// ---- two-kernel form (plans): x-pass rows through L2, y-pass with 512-byte warp stores ----
+constexpr int kSplitUnroll = 8;  // split partials loaded together (more are added one by one)
+// Residue loops visit exactly the U (or V) stored orders: for residue r the
+// first stored index p >= rot with p = r (mod 8), then every 8th.
+
+// One CTA per (item-plane, component): V * Fx/8 tasks (row vi, residue b).
+template <bool BATCH>
+__global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ ItemDev one,
+                                                    const ItemDev* __restrict__ items,
+                                                    const int2* __restrict__ entries) {
+  extern __shared__ float2 xs_row[];  // [V][U]
+  const int2 e = entries[blockIdx.x];
+  const ItemDev& it = BATCH ? items[e.x] : one;
+  const int f = e.y, c = blockIdx.y;
+  const int U = it.U, V = it.V, M = it.M, Up = it.Up, rot = it.rotU, Fx = it.Fx;
+  const float2* src = it.S_part + (size_t)f * 3 * M + (size_t)c * M;
+  const int ns = it.nsplit[f];
+  const size_t stride = it.split_stride;
+  for (int m0 = 0; m0 < M; m0 += 2 * blockDim.x) {
+    // all split partials of two elements are requested before any is used
+    float2 v[2][kSplitUnroll];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = m0 + h * blockDim.x + threadIdx.x;
+#pragma unroll
+      for (int k = 0; k < kSplitUnroll; ++k)
+        v[h][k] = (m < M && k < ns) ? src[(size_t)k * stride + m] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = m0 + h * blockDim.x + threadIdx.x;
+      float2 acc = v[h][0];
+#pragma unroll
+      for (int k = 1; k < kSplitUnroll; ++k) acc = c_add(acc, v[h][k]);
+      for (int k = kSplitUnroll; k < ns; ++k) acc = c_add(acc, src[(size_t)k * stride + m]);
+      if (m < M) xs_row[m] = acc;
+    }
+  }
+  __syncthreads();
+  const int Q = Fx >> 3;
+  float2* dst = it.T + ((size_t)f * 3 + c) * V * Fx;
+  for (int t = threadIdx.x; t < V * Q; t += blockDim.x) {
+    const int vi = t / Q, b = t - vi * Q;
+    const float2* s = xs_row + vi * U - rot;  // indexed by stored position p
+    const float2* tw = it.twx + b;  // [p][b]: a warp's lanes read consecutive residues
+    float2 G[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      G[r] = make_float2(0.f, 0.f);
+      for (int p = rot + ((r - rot) & 7); p < rot + U; p += 8) c_fma(G[r], s[p], __ldg(tw + (size_t)p * Q));
+    }
+    idft8(G);
+    float2* o = dst + (size_t)vi * Fx + b;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) o[a * Q] = G[a];
+  }
+}
+
+// One CTA per (64-column block, item-plane, component); 8 warps, lane l owns the
 // column pair (2l, 2l+1) of the block and warp w the residues b = w, w+8, ...
-__global__ void __launch_bounds__(256) ypass_kernel(const float2* __restrict__ T, const float2* __restrict__ twy,
-                                                    int V, int Fx, int Fy, int Fz, float2* __restrict__ out) {
-  extern __shared__ float4 tcol4[];  // [V][32] float4 = [V][64] complex
-  float2* tcol = reinterpret_cast<float2*>(tcol4);
-  const int xb = blockIdx.x * 64, f = blockIdx.y, c = blockIdx.z;
-  const float2* src = T + ((size_t)f * 3 + c) * V * Fx;
-  for (int i = threadIdx.x; i < V * 64; i += blockDim.x) {
-    const int v = i >> 6, x = i & 63;
-    tcol[i] = (xb + x < Fx) ? src[(size_t)v * Fx + xb + x] : make_float2(0.f, 0.f);
+template <bool BATCH>
+__global__ void __launch_bounds__(256, 4) ypass_kernel(const __grid_constant__ ItemDev one,
+                                                       const ItemDev* __restrict__ items,
+                                                       const int2* __restrict__ entries, float2* out_one,
+                                                       float2* const* __restrict__ outs) {
+  extern __shared__ float4 ys_col4[];  // [V][32] float4 = [V][64] complex
+  float2* tcol = reinterpret_cast<float2*>(ys_col4);
+  const int2 e = entries[blockIdx.y];
+  const ItemDev& it = BATCH ? items[e.x] : one;
+  const int xb = blockIdx.x * 64;
+  if (xb >= it.Fx) return;
+  const int f = e.y, c = blockIdx.z;
+  const int V = it.V, Vp = it.Vp, rot = it.rotV, Fx = it.Fx, Fy = it.Fy;
+  const float2* src = it.T + ((size_t)f * 3 + c) * V * Fx;
+  {
+    // rows of the x-pass result for this column block, all requests in flight together
+    const int x = threadIdx.x & 63, v0 = threadIdx.x >> 6;
+    float2 tv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int v = v0 + 4 * k;
+      tv[k] = (v < V && xb + x < Fx) ? src[(size_t)v * Fx + xb + x] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (v0 + 4 * k < V) tcol[(v0 + 4 * k) * 64 + x] = tv[k];
+    for (int v = v0 + 32; v < V; v += 4) tcol[v * 64 + x] = (xb + x < Fx) ? src[(size_t)v * Fx + xb + x] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int x = xb + 2 * lane;
+  if (x >= Fx) return;  // Fx is a multiple of 8, so x + 1 < Fx as well
   const int Q = Fy >> 3;
-  const int h = V >> 1;
-  float2* dst = out + (((size_t)c * Fz + f) * Fy) * Fx + x;
+  float2* out = BATCH ? outs[e.x] : out_one;
+  float2* dst = out + (((size_t)c * it.Fz + f) * Fy) * Fx + x;
+  const float4* col = ys_col4 + lane - (size_t)rot * 32;  // indexed by stored position p
   for (int b = w; b < Q; b += 8) {
-    float2 F0[8], F1[8];
-    const float2* tw = twy + (size_t)b * V;
+    float2 G0[8], G1[8];
+    const float2* tw = it.twy + (size_t)b * Vp;
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
-      F0[r] = F1[r] = make_float2(0.f, 0.f);
-      for (int vi = (r + h) & 7; vi < V; vi += 8) {
-        const float2 t = __ldg(tw + vi);
-        const float4 d = tcol4[vi * 32 + lane];
-        c_fma(F0[r], make_float2(d.x, d.y), t);
-        c_fma(F1[r], make_float2(d.z, d.w), t);
+      G0[r] = G1[r] = make_float2(0.f, 0.f);
+      for (int p = rot + ((r - rot) & 7); p < rot + V; p += 8) {
+        const float2 t = __ldg(tw + p);
+        const float4 d = col[(size_t)p * 32];
+        c_fma(G0[r], make_float2(d.x, d.y), t);
+        c_fma(G1[r], make_float2(d.z, d.w), t);
       }
     }
-    idft8(F0);
-    idft8(F1);
-    if (x < Fx) {
+    idft8(G0);
+    idft8(G1);
 #pragma unroll
-      for (int a = 0; a < 8; ++a)
-        __stcs(reinterpret_cast<float4*>(dst + (size_t)(b + a * Q) * Fx), make_float4(F0[a].x, F0[a].y, F1[a].x, F1[a].y));
-    }
+    for (int a = 0; a < 8; ++a)
+      __stcs(reinterpret_cast<float4*>(dst + (size_t)(b + a * Q) * Fx), make_float4(G0[a].x, G0[a].y, G1[a].x, G1[a].y));
   }
 }
 
@@ -145,25 +299,61 @@ __global__ void gather_kernel(const float2* __restrict__ S_part, size_t split_st
   S[i] = acc;
 }
 
-cudaError_t launch_xpass(const Plan& p, const float2* S_part, int split_stride_planes, const int* d_nsplit,
+cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_M,
                          cudaStream_t st) {
-  const size_t split_stride = (size_t)split_stride_planes * 3 * p.M;
-  xpass_kernel<<<dim3(p.Fz, 3), 256, (size_t)p.M * sizeof(float2), st>>>(S_part, split_stride, d_nsplit, p.d_twx, p.U,
-                                                                        p.V, p.Fx, p.T);
+  if (n_entries == 0) return cudaSuccess;
+  const size_t xs = (size_t)max_M * sizeof(float2);
+  cudaError_t e;
+  if (items) {
+    e = allow_max_smem(reinterpret_cast<const void*>(xpass_kernel<true>));
+    if (e != cudaSuccess) return e;
+    xpass_kernel<true><<<dim3(n_entries, 3), 256, xs, st>>>(one, items, d_entries);
+  } else {
+    e = allow_max_smem(reinterpret_cast<const void*>(xpass_kernel<false>));
+    if (e != cudaSuccess) return e;
+    xpass_kernel<false><<<dim3(n_entries, 3), 256, xs, st>>>(one, nullptr, d_entries);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_ypass(const Plan& p, float2* out, cudaStream_t st) {
-  ypass_kernel<<<dim3((p.Fx + 63) / 64, p.Fz, 3), 256, (size_t)p.V * 64 * sizeof(float2), st>>>(p.T, p.d_twy, p.V, p.Fx,
-                                                                                               p.Fy, p.Fz, out);
+cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_Qx,
+                         int max_V, float2* out_one, float2* const* d_outs, cudaStream_t st) {
+  if (n_entries == 0) return cudaSuccess;
+  const size_t ys = (size_t)max_V * 64 * sizeof(float2);
+  const dim3 grid((max_Qx * 8 + 63) / 64, n_entries, 3);
+  cudaError_t e;
+  if (items) {
+    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<true>));
+    if (e != cudaSuccess) return e;
+    ypass_kernel<true><<<grid, 256, ys, st>>>(one, items, d_entries, nullptr, d_outs);
+  } else {
+    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<false>));
+    if (e != cudaSuccess) return e;
+    ypass_kernel<false><<<grid, 256, ys, st>>>(one, nullptr, d_entries, out_one, nullptr);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_recompose(const Plan& p, const float2* S_part, int split_stride_planes, const int* d_nsplit,
-                             float2* out, cudaStream_t st) {
-  cudaError_t e = launch_xpass(p, S_part, split_stride_planes, d_nsplit, st);
-  if (e != cudaSuccess) return e;
-  return launch_ypass(p, out, st);
+size_t recompose_smem_bytes(int V, int Up, int Vp) { return ((size_t)Vp * 64 + (size_t)V * Up) * sizeof(float2); }
+
+cudaError_t launch_recompose(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_Qx,
+                             size_t smem, const float2* S_override, const int* nsplit_override, float2* out_one,
+                             float2* const* d_outs, cudaStream_t st) {
+  if (n_entries == 0) return cudaSuccess;
+  dim3 grid((max_Qx + 7) / 8, n_entries, 3);
+  cudaError_t e;
+  if (items) {
+    e = allow_max_smem(reinterpret_cast<const void*>(recompose_kernel<true>));
+    if (e != cudaSuccess) return e;
+    recompose_kernel<true><<<grid, 256, smem, st>>>(one, items, d_entries, S_override, nsplit_override, nullptr,
+                                                    d_outs);
+  } else {
+    e = allow_max_smem(reinterpret_cast<const void*>(recompose_kernel<false>));
+    if (e != cudaSuccess) return e;
+    recompose_kernel<false><<<grid, 256, smem, st>>>(one, nullptr, d_entries, S_override, nsplit_override, out_one,
+                                                     nullptr);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gather_spectrum(const Plan& p, float2* S, cudaStream_t st) {

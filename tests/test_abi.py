@@ -99,7 +99,8 @@ def test_noalloc_rejects_sizes_above_its_scratch(lib):
     """The allocation-free recompose checks its fixed scratch size on the host,
     before looking at the device or launching anything."""
     dummy = ctypes.c_void_p(256)  # never dereferenced: the size check comes first
-    st = lib.scw_recompose_noalloc(21, 21, 16.0, 16.0, 4096, 4096, 100, 0.0, 0.0, dummy, dummy, None)
+    st = lib.scw_recompose_noalloc(4096, 1, 16.0, 16.0, 4096, 4096, 100, 0.0, 0.0, dummy, dummy, None)
     assert st == 2
     assert b"scratch" in lib.scw_last_error()
     assert lib.scw_recompose_noalloc(21, 21, 16.0, 16.0, 256, 256, 8, 0.0, 0.0, None, dummy, None) == 1
+    assert lib.scw_recompose_noalloc(21, 97, 16.0, 16.0, 256, 256, 8, 0.0, 0.0, dummy, dummy, None) == 1
