@@ -164,6 +164,16 @@ scw_status scw_synthesize_batched(scw_plan_t plan, void* const* outs, void* stre
 /* Human-readable record of the split choice (model and timed candidates). */
 const char* scw_plan_tune_report(scw_plan_t plan);
 
+/* Layer-group pipelining of a single tensor-core plan: the active layers are cut
+ * into `groups` contiguous groups; group g's recompose (step c) runs on a
+ * second, plan-owned stream while group g+1 is contracted (step b), whose
+ * persistent kernel then keeps one CTA per SM so both can share the SMs. The
+ * call returns after `stream` has all of it (the second stream joins it).
+ * groups = 1 (the default) keeps the serial order. Timed calls
+ * (scw_plan_enable_timing) always run serially so their kernel times are
+ * separable. Errors: UNSUPPORTED on batched or FP32 plans. */
+scw_status scw_plan_set_pipeline(scw_plan_t plan, int groups);
+
 /* Steps (a)+(b) only: the per-plane spectra.
  *   S  DEVICE complex64 [Fz][3][M] (S[z][c][m], Eq. 34 / Eq. 9). */
 scw_status scw_spectrum(scw_plan_t plan, void* S, void* stream);

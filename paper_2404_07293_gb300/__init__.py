@@ -161,6 +161,9 @@ class Plan:
         r = self._lib.scw_plan_tune_report(self._h)
         return r.decode() if r else ""
 
+    def set_pipeline(self, groups: int):
+        check(self._lib.scw_plan_set_pipeline(self._h, int(groups)), "scw_plan_set_pipeline")
+
     def close(self):
         if getattr(self, "_h", None):
             self._lib.scw_plan_destroy(self._h)

@@ -55,6 +55,7 @@ SIGNATURES = {
     "scw_plan_batched_set_layers": (c_int, [c_void_p, c_int] + [c_void_p] * 6 + [c_void_p]),
     "scw_synthesize_batched": (c_int, [c_void_p, POINTER(c_void_p), c_void_p]),
     "scw_plan_tune_report": (c_char_p, [c_void_p]),
+    "scw_plan_set_pipeline": (c_int, [c_void_p, c_int]),
     "scw_plan_check": (c_int, [c_void_p, c_void_p]),
     "scw_plan_set_timeout_ns": (c_int, [c_void_p, c_uint64]),
     "scw_plan_get_info": (c_int, [c_void_p, POINTER(ScwPlanInfo)]),

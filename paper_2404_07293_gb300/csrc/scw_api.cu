@@ -386,8 +386,9 @@ static void lpt(std::vector<TaskCost>& tasks, int G, std::vector<int>& cta_off, 
   cta_off[G] = (int)order.size();
 }
 
-static int schedule_grid(int n_tasks, int NB, bool bf16) {
-  return std::max(1, std::min(n_tasks, device_sms() * tc_ctas_per_sm(NB, bf16)));
+static int schedule_grid(int n_tasks, int NB, bool bf16, int ctas_per_sm = 0) {
+  const int cps = ctas_per_sm > 0 ? std::min(ctas_per_sm, tc_ctas_per_sm(NB, bf16)) : tc_ctas_per_sm(NB, bf16);
+  return std::max(1, std::min(n_tasks, device_sms() * cps));
 }
 
 // Makespan (in K-stages) of a set of per-item splits under LPT.
@@ -402,9 +403,18 @@ static double model_makespan(const std::vector<Plan*>& items, const std::vector<
   return mx;
 }
 
-static scw_status upload_schedule(const std::vector<Plan*>& items, int NB, bool bf16, TcSchedule& s) {
+// Schedule of the tasks of every item, or (unit_begin < unit_end) only of those
+// units of item 0; ctas_per_sm > 0 caps the persistent grid per SM.
+static scw_status upload_schedule(const std::vector<Plan*>& items, int NB, bool bf16, TcSchedule& s,
+                                  int ctas_per_sm = 0, int unit_begin = 0, int unit_end = 0) {
   std::vector<TaskCost> t;
   for (size_t i = 0; i < items.size(); ++i) item_tasks(items[i], (int)i, items[i]->k_split, t);
+  if (unit_begin < unit_end) {
+    std::vector<TaskCost> keep;
+    for (const auto& tc : t)
+      if (tc.t.y >= unit_begin && tc.t.y < unit_end) keep.push_back(tc);
+    t.swap(keep);
+  }
   if (s.d_tasks) cudaFree(s.d_tasks);
   if (s.d_cta_off) cudaFree(s.d_cta_off);
   s.d_tasks = nullptr;
@@ -414,7 +424,7 @@ static scw_status upload_schedule(const std::vector<Plan*>& items, int NB, bool 
     s.grid = 0;
     return SCW_OK;
   }
-  s.grid = schedule_grid(s.n_tasks, NB, bf16);
+  s.grid = schedule_grid(s.n_tasks, NB, bf16, ctas_per_sm);
   std::vector<int> off;
   std::vector<int4> order;
   lpt(t, s.grid, off, order, s.max_load, s.mean_load);
@@ -481,6 +491,14 @@ struct scw_plan_s {
   size_t tev_used = 0;
   int kernels_per_synthesis = 0;
   std::string tune_report;
+  // layer-group pipelining (single tensor-core plans): group g's recompose runs on
+  // st2 while group g+1 is contracted on the caller's stream
+  int groups = 1;
+  std::vector<TcSchedule> gsched;
+  std::vector<int> gplane;          // [groups + 1] offsets into the plane entries
+  cudaStream_t st2 = nullptr;
+  std::vector<cudaEvent_t> gev;     // contraction of group g done
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static void free_plan(scw_plan_t P) {
@@ -494,6 +512,14 @@ static void free_plan(scw_plan_t P) {
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->cap_stream) cudaStreamDestroy(P->cap_stream);
   for (cudaEvent_t ev : P->tev) cudaEventDestroy(ev);
+  for (auto& g : P->gsched) {
+    if (g.d_tasks) cudaFree(g.d_tasks);
+    if (g.d_cta_off) cudaFree(g.d_cta_off);
+  }
+  for (cudaEvent_t ev : P->gev) cudaEventDestroy(ev);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
+  if (P->st2) cudaStreamDestroy(P->st2);
   delete P;
 }
 
@@ -576,7 +602,53 @@ static scw_status enqueue_spectrum(scw_plan_t P, cudaStream_t st, bool marks, in
   return SCW_OK;
 }
 
+// Pipelined order: phases, then per group g the contraction of g on `st` and
+// the recompose of g on st2 once that contraction is done; st2 joins `st` at
+// the end. Groups cover disjoint units and plane ranges, so nothing is shared
+// between the overlapping kernels.
+static scw_status enqueue_pipelined(scw_plan_t P, float2* out_one, cudaStream_t st, int& n) {
+  n = 0;
+  cudaError_t e;
+  Plan* p = P->items[0];
+  const ItemDev& one = p->item;
+  e = launch_phases_tc(one, nullptr, P->d_unit_entries, P->n_unit_entries, P->max_M, P->F_pad, P->bf16, st);
+  if (e != cudaSuccess) return cuda_error(e, "phase kernel launch");
+  ++n;
+  if (p->n_exterior) {
+    e = launch_exterior(*p, st);
+    if (e != cudaSuccess) return cuda_error(e, "exterior kernel launch");
+    ++n;
+  }
+  e = cudaEventRecord(P->ev_fork, st);  // st2 must not start before the previous step ended on st
+  if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+  e = cudaStreamWaitEvent(P->st2, P->ev_fork, 0);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
+  for (int g = 0; g < P->groups; ++g) {
+    e = launch_contract_tc(one, nullptr, P->gsched[g], P->NB, P->bf16, P->d_err, P->timeout_ns, st);
+    if (e != cudaSuccess) return cuda_error(e, "contraction kernel launch");
+    if (P->gsched[g].n_tasks) ++n;
+    e = cudaEventRecord(P->gev[g], st);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+    e = cudaStreamWaitEvent(P->st2, P->gev[g], 0);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
+    const int nb = P->gplane[g + 1] - P->gplane[g];
+    if (nb == 0) continue;
+    const int2* ent = P->d_plane_entries + P->gplane[g];
+    e = launch_xpass(one, nullptr, ent, nb, P->max_M, P->st2);
+    if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
+    e = launch_ypass(one, nullptr, ent, nb, P->max_Qx, P->max_V, out_one, nullptr, P->st2);
+    if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
+    n += 2;
+  }
+  e = cudaEventRecord(P->ev_join, P->st2);
+  if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
+  e = cudaStreamWaitEvent(st, P->ev_join, 0);
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
+  return SCW_OK;
+}
+
 static scw_status enqueue_synthesis(scw_plan_t P, float2* out_one, cudaStream_t st, bool marks, int& n) {
+  if (P->groups > 1 && !marks) return enqueue_pipelined(P, out_one, st, n);
   n = 0;
   scw_status s = enqueue_spectrum(P, st, marks, n);
   if (s != SCW_OK) return s;
@@ -1128,5 +1200,48 @@ scw_status scw_plan_get_info(scw_plan_t P, scw_plan_info* info) {
 }
 
 const char* scw_plan_tune_report(scw_plan_t P) { return P ? P->tune_report.c_str() : ""; }
+
+scw_status scw_plan_set_pipeline(scw_plan_t P, int groups) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+  if (groups < 1) return set_error(SCW_ERR_INVALID_ARGUMENT, "groups must be >= 1");
+  if (groups > 1 && (P->batched || !P->tc))
+    return set_error(SCW_ERR_UNSUPPORTED, "pipelining is for single tensor-core plans");
+  Plan* p = P->items[0];
+  const int nu = (int)p->units.size();
+  groups = std::max(1, std::min(groups, nu));
+  for (auto& g : P->gsched) {
+    if (g.d_tasks) cudaFree(g.d_tasks);
+    if (g.d_cta_off) cudaFree(g.d_cta_off);
+  }
+  P->gsched.clear();
+  P->gplane.clear();
+  invalidate_graph(P);
+  P->groups = groups;
+  if (groups == 1) return SCW_OK;
+  cudaError_t e;
+  if (!P->st2) {
+    e = cudaStreamCreateWithFlags(&P->st2, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_error(e, "cudaStreamCreateWithFlags");
+    e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventCreate");
+  }
+  while ((int)P->gev.size() < groups) {
+    cudaEvent_t ev;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_error(e, "cudaEventCreate");
+    P->gev.push_back(ev);
+  }
+  // contiguous unit groups; group g's planes run up to the first plane of group g+1
+  P->gsched.resize(groups);
+  P->gplane.assign(groups + 1, 0);
+  for (int g = 0; g < groups; ++g) {
+    const int ub = (int)((long long)nu * g / groups), ue = (int)((long long)nu * (g + 1) / groups);
+    scw_status s = upload_schedule(P->items, P->NB, P->bf16, P->gsched[g], 1, ub, ue);
+    if (s != SCW_OK) return s;
+    P->gplane[g + 1] = (g + 1 < groups) ? p->units[ue].f0 : p->Fz;
+  }
+  return SCW_OK;
+}
 
 }  // extern "C"

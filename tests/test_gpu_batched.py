@@ -114,3 +114,29 @@ def test_single_plan_graph_replay_is_stable(cuda_device):
     plan.check()
     assert torch.equal(first, second) and torch.equal(second, third)
     assert plan.info()["kernels_per_synthesis"] == 4  # phases, contraction, x-pass, y-pass
+
+
+@pytest.mark.parametrize("groups", [2, 3, 5])
+def test_pipelined_plan_equals_serial(groups, cuda_device):
+    """Layer-group pipelining only reorders independent work: bit-identical field."""
+    import torch
+    import paper_2404_07293_gb300 as scw
+    W, g, a, pi, pr, pt = wl.random_layer_set(21, 9, 9, 7)
+    zb = np.linspace(0.0, 1.4, 8)
+    ls = layerset_from_arrays(1.0, 3.0, 3.0, 9, 9, zb, W, g, a, pi, pr, pt)
+    zp = np.concatenate([[-0.2], wl.cell_centred_planes(0.0, 1.4, 35), [1.6]])
+    kw = dict(U=9, V=9, L=7, lam=1.0, X=3.0, Y=3.0, z_bounds=zb, Fx=32, Fy=24, z_planes=zp, exterior=True)
+    dev = to_device(ls)
+    serial = scw.Plan(precision="split_bf16", **kw)
+    serial.set_layers(dev[0], dev[1], dev[2], *dev[3])
+    ref = serial.synthesize()
+    piped = scw.Plan(precision="split_bf16", **kw)
+    piped.set_pipeline(groups)
+    piped.set_layers(dev[0], dev[1], dev[2], *dev[3])
+    out = torch.empty_like(ref)
+    for _ in range(3):  # direct launch, capture, replay
+        piped.synthesize(out)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref)
+    piped.check()
+    serial.check()

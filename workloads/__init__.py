@@ -219,3 +219,44 @@ def config_surrogate_sample(seed: int) -> Problem:
     zb = np.arange(9) * d
     return Problem(f"surrogate_{seed}", 1.0, 32 * d, 32 * d, 15, 15, vol, zb,
                    plane_wave_image(32), Fx=64, Fy=64, z_planes=np.array([zb[-1] + 1e-9]))
+
+
+def random_layer_set_torch(seed: int, U: int, V: int, L: int, device="cuda", evanescent_frac: float = 0.05,
+                           backward_scale: float = 0.1):
+    """random_layer_set drawn with a seeded torch generator on ``device``.
+
+    Same distributions (and the same returned shapes and dtypes, as tensors);
+    used where the host draw would be too slow, e.g. the 25 GB of W of a
+    128-wavenumber sweep. The values differ from random_layer_set's.
+    """
+    import torch
+    M = U * V
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = dict(dtype=torch.float64, device=device, generator=g)
+    re = torch.rand((L, 2 * M), **f64) * 1.3 + 0.3
+    im = torch.empty((L, 2 * M), dtype=torch.float64, device=device).exponential_(1.0 / 0.01, generator=g)
+    ev = torch.rand((L, 2 * M), **f64) < evanescent_frac
+    re = torch.where(ev, torch.rand((L, 2 * M), **f64) * 0.05, re)
+    im = torch.where(ev, torch.rand((L, 2 * M), **f64) * 0.9 + 0.1, im)
+    gf = torch.complex(re, im)
+    gamma = torch.cat([gf, -gf], dim=1)
+    scale_w = 1.0 / math.sqrt(2 * 3 * M)
+    W = torch.randn((L, 3 * M, 4 * M), dtype=torch.complex64, device=device, generator=g) * (scale_w * math.sqrt(2))
+    sa = 1.0 / math.sqrt(2 * 2 * M)
+    af = torch.randn((L, 2 * M), dtype=torch.complex128, device=device, generator=g) * (sa * math.sqrt(2))
+    ab = torch.randn((L, 2 * M), dtype=torch.complex128, device=device, generator=g) * (sa * math.sqrt(2) * backward_scale)
+    alpha = torch.cat([af, ab], dim=1)
+    sp = 1.0 / math.sqrt(2 * M)
+    ext = [torch.randn((3, M), dtype=torch.complex128, device=device, generator=g) * (sp * math.sqrt(2))
+           for _ in range(3)]
+    return W, gamma, alpha, ext[0], ext[1], ext[2]
+
+
+def sweep_geometry(i: int, n_items: int = 128):
+    """Sizes of item i of the mid-IR sweep without building its sample volume:
+    (lam [um], U, X [um], z_bounds, z_planes, Fx, Fy) -- see config_sweep_item."""
+    nu = 1000.0 + 800.0 * i / (n_items - 1)
+    zb = np.arange(17) * 1.0
+    U = 9 + 2 * ((9 * i) // n_items)
+    return 1e4 / nu, U, 64.0, zb, cell_centred_planes(zb[0], zb[-1], 64), 128, 128
