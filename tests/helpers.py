@@ -27,3 +27,21 @@ def rel_l2(a, b, axis_c=True):
     a = np.asarray(a, dtype=np.complex128)
     b = np.asarray(b, dtype=np.complex128)
     return [float(np.linalg.norm(a[c] - b[c]) / max(np.linalg.norm(b[c]), 1e-300)) for c in range(a.shape[0])]
+
+
+def fno_init_groups(sh):
+    """(size, scale) per flat parameter group of the surrogate, in flat order."""
+    from oracle import fno
+    out = []
+    for name, shape, cplx in fno.param_layout(sh):
+        n = int(np.prod(shape)) * (2 if cplx else 1)
+        if name == "P":
+            sc = 1.0 / np.sqrt(sh.in_ch)
+        elif name.startswith("R"):
+            sc = 1.0 / sh.width
+        elif name.startswith("W") or name in ("Q", "e"):
+            sc = 1.0 / np.sqrt(sh.width)
+        else:
+            sc = 0.1
+        out.append((n, sc))
+    return out

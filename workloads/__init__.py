@@ -25,6 +25,7 @@ __all__ = [
     "sphere_volume", "ellipsoid_volume", "gaussian_beam_image", "plane_wave_image",
     "random_layer_set", "Problem", "config_tiny", "config_single_wavelength",
     "config_sweep_item", "config_surrogate_sample", "cell_centred_planes",
+    "phantom_batch", "random_flat",
 ]
 
 
@@ -260,3 +261,18 @@ def sweep_geometry(i: int, n_items: int = 128):
     zb = np.arange(17) * 1.0
     U = 9 + 2 * ((9 * i) // n_items)
     return 1e4 / nu, U, 64.0, zb, cell_centred_planes(zb[0], zb[-1], 64), 128, 128
+
+
+def phantom_batch(seed: int, B: int, nx: int = 32, ny: int = 32, nz: int = 8,
+                  semi_axes=(2.0, 8.0)) -> np.ndarray:
+    """B refractive-index phantoms n[B][nz][ny][nx] (complex128), sample b drawn
+    by ellipsoid_volume with seed ``seed + b`` (1..8 ellipsoids, semi-axes in
+    ``semi_axes`` voxels, n_re in [1.33, 1.6], kappa in [0, 0.05], background 1)."""
+    return np.stack([ellipsoid_volume(seed + b, nx, ny, nz, semi_axes=semi_axes) for b in range(B)])
+
+
+def random_flat(seed: int, groups) -> np.ndarray:
+    """Concatenated seeded draws: for each (size, scale) in ``groups``, ``size``
+    values uniform in [-scale, scale] (float64)."""
+    rng = np.random.default_rng(seed)
+    return np.concatenate([rng.uniform(-sc, sc, size=int(n)) for n, sc in groups])
