@@ -1,5 +1,6 @@
 """GB300-native volumetric field synthesis for the coupled-wave method of
-arXiv 2404.07293 (sCWatter): thin Python binding over libscw (include/scw.h).
+arXiv 2404.07293 (sCWatter): thin Python binding over libscw (include/scw.h,
+include/scw_fno.h for the learned surrogate).
 
 Every step of the hot path runs in the library's CUDA kernels; this module
 only checks tensor shapes/dtypes and passes pointers and the current torch
@@ -11,10 +12,10 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (FLAG_AUTOTUNE, FLAG_EXTERIOR, FLAG_HOST_IO, PRECISION, ScwDesc, ScwError, ScwKernelTimes,
-                   ScwPlanInfo, check, load)
+from ._lib import (FLAG_AUTOTUNE, FLAG_EXTERIOR, FLAG_HOST_IO, FNO_PRECISION, PRECISION, ScwDesc, ScwError,
+                   ScwFnoDesc, ScwKernelTimes, ScwPlanInfo, check, load)
 
-__all__ = ["Plan", "BatchedPlan", "ScwError", "load", "PRECISION"]
+__all__ = ["Plan", "BatchedPlan", "Surrogate", "ScwError", "load", "PRECISION"]
 
 
 def _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0, n_bot=1.0,
@@ -250,6 +251,114 @@ class BatchedPlan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.scw_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Surrogate:
+    """The learned surrogate (scw_surrogate_*): a Fourier neural operator from
+    refractive-index slices n [B][S][in][in] (complex64) to the exit-plane field
+    [B][3][N][N] (complex64), trained and evaluated by the library's kernels."""
+
+    def __init__(self, grid=64, modes=16, layers=4, slices=8, in_grid=32, batch_max=256, precision="bf16", seed=0,
+                 width=32):
+        self._lib = load()
+        self.grid, self.modes, self.layers, self.slices, self.in_grid = grid, modes, layers, slices, in_grid
+        self.batch_max = batch_max
+        d = ScwFnoDesc(width=int(width), grid=int(grid), modes=int(modes), layers=int(layers), slices=int(slices),
+                       in_grid=int(in_grid), batch_max=int(batch_max), precision=FNO_PRECISION[precision],
+                       seed=int(seed))
+        h = ctypes.c_void_p()
+        check(self._lib.scw_surrogate_create(ctypes.byref(d), ctypes.byref(h)), "scw_surrogate_create")
+        self._h = h
+        n = ctypes.c_size_t()
+        check(self._lib.scw_surrogate_param_count(self._h, ctypes.byref(n)), "scw_surrogate_param_count")
+        self.n_params = n.value
+
+    def _n_ptr(self, n, B):
+        import torch
+        return _dev_ptr(n, torch.complex64, (B, self.slices, self.in_grid, self.in_grid), "n")
+
+    def _f_ptr(self, t, B, name):
+        import torch
+        return _dev_ptr(t, torch.complex64, (B, 3, self.grid, self.grid), name)
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        check(self._lib.scw_surrogate_set_params(self._h, _host_ptr(a, np.float32, (self.n_params,), "flat"),
+                                                            self.n_params), "scw_surrogate_set_params")
+
+    def params(self) -> np.ndarray:
+        a = np.empty(self.n_params, dtype=np.float32)
+        check(self._lib.scw_surrogate_get_params(self._h, ctypes.c_void_p(a.ctypes.data), self.n_params),
+              "scw_surrogate_get_params")
+        return a
+
+    def grads(self) -> np.ndarray:
+        a = np.empty(self.n_params, dtype=np.float32)
+        check(self._lib.scw_surrogate_get_grads(self._h, ctypes.c_void_p(a.ctypes.data), self.n_params),
+              "scw_surrogate_get_grads")
+        return a
+
+    def forward_backward(self, n, target, read_loss=True, stream=None):
+        B = n.shape[0]
+        loss = np.zeros(3, dtype=np.float32)
+        check(self._lib.scw_surrogate_forward_backward(
+            self._h, self._n_ptr(n, B), self._f_ptr(target, B, "target"), B,
+            ctypes.c_void_p(loss.ctypes.data) if read_loss else None, _stream_handle(stream)),
+            "scw_surrogate_forward_backward")
+        return loss if read_loss else None
+
+    def train_step(self, n, target, lr=1e-3, read_loss=True, stream=None):
+        B = n.shape[0]
+        loss = np.zeros(3, dtype=np.float32)
+        check(self._lib.scw_surrogate_train_step(
+            self._h, self._n_ptr(n, B), self._f_ptr(target, B, "target"), B, float(lr),
+            ctypes.c_void_p(loss.ctypes.data) if read_loss else None, _stream_handle(stream)),
+            "scw_surrogate_train_step")
+        return loss if read_loss else None
+
+    def infer(self, n, threshold=5e-2, field=None, stream=None):
+        """(field, est_err, need_fallback) as device tensors."""
+        import torch
+        B = n.shape[0]
+        if field is None:
+            field = torch.empty((B, 3, self.grid, self.grid), dtype=torch.complex64, device=n.device)
+        est = torch.empty(B, dtype=torch.float32, device=n.device)
+        flag = torch.empty(B, dtype=torch.uint8, device=n.device)
+        check(self._lib.scw_surrogate_infer(
+            self._h, self._n_ptr(n, B), B, self._f_ptr(field, B, "field"), ctypes.c_void_p(est.data_ptr()),
+            ctypes.c_void_p(flag.data_ptr()), float(threshold), _stream_handle(stream)), "scw_surrogate_infer")
+        return field, est, flag
+
+    def calibrate(self, est, true_err, miss=0.01) -> float:
+        e = np.ascontiguousarray(est, dtype=np.float32)
+        t = np.ascontiguousarray(true_err, dtype=np.float32)
+        if e.shape != t.shape or e.ndim != 1:
+            raise ValueError("est and true_err must be 1-D arrays of one length")
+        q = ctypes.c_float()
+        check(self._lib.scw_surrogate_calibrate(self._h, ctypes.c_void_p(e.ctypes.data),
+                                                           ctypes.c_void_p(t.ctypes.data), len(e), float(miss),
+                                                           ctypes.byref(q)), "scw_surrogate_calibrate")
+        return q.value
+
+    def set_offset(self, q: float):
+        check(self._lib.scw_surrogate_set_offset(self._h, float(q)), "scw_surrogate_set_offset")
+
+    def launches(self) -> dict:
+        a, b = ctypes.c_int(), ctypes.c_int()
+        check(self._lib.scw_surrogate_launches(self._h, ctypes.byref(a), ctypes.byref(b)),
+              "scw_surrogate_launches")
+        return {"train_step": a.value, "infer": b.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.scw_surrogate_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -1,4 +1,4 @@
-"""ctypes declarations of the C ABI in include/scw.h (argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/scw.h and include/scw_fno.h (argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes
@@ -37,6 +37,14 @@ class ScwPlanInfo(ctypes.Structure):
                 ("schedule_mean_load", c_double)]
 
 
+class ScwFnoDesc(ctypes.Structure):
+    _fields_ = [("width", c_int), ("grid", c_int), ("modes", c_int), ("layers", c_int), ("slices", c_int),
+                ("in_grid", c_int), ("batch_max", c_int), ("precision", c_int), ("seed", ctypes.c_ulonglong)]
+
+
+FNO_PRECISION = {"bf16": 0, "fp32": 1}
+
+
 class ScwKernelTimes(ctypes.Structure):
     _fields_ = [("calls", c_int), ("phases_ms", c_double), ("contract_ms", c_double), ("recompose_ms", c_double),
                 ("xpass_ms", c_double), ("ypass_ms", c_double), ("total_ms", c_double)]
@@ -63,6 +71,19 @@ SIGNATURES = {
     "scw_plan_get_timings": (c_int, [c_void_p, POINTER(ScwKernelTimes)]),
     "scw_recompose_noalloc": (c_int, [c_int, c_int, c_double, c_double, c_int, c_int, c_int, c_double, c_double,
                                       c_void_p, c_void_p, c_void_p]),
+    "scw_surrogate_create": (c_int, [POINTER(ScwFnoDesc), POINTER(c_void_p)]),
+    "scw_surrogate_destroy": (c_int, [c_void_p]),
+    "scw_surrogate_param_count": (c_int, [c_void_p, POINTER(c_size_t)]),
+    "scw_surrogate_set_params": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "scw_surrogate_get_params": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "scw_surrogate_get_grads": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "scw_surrogate_forward_backward": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "scw_surrogate_train_step": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p]),
+    "scw_surrogate_infer": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p, ctypes.c_float,
+                                    c_void_p]),
+    "scw_surrogate_calibrate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p]),
+    "scw_surrogate_set_offset": (c_int, [c_void_p, ctypes.c_float]),
+    "scw_surrogate_launches": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
     "scw_status_string": (c_char_p, [c_int]),
     "scw_last_error": (c_char_p, []),
     "scw_version": (c_int, []),

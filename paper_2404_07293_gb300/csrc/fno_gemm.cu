@@ -1,0 +1,366 @@
+// The surrogate's dense contractions: D = A B^T over K with a fused epilogue.
+//
+// Tensor-core form (BF16 mode). A and B are K-major BF16 matrices read by TMA
+// (2D tensor maps, 64-element = 128-byte inner box, 128-byte swizzle, zero fill
+// out of bounds) into a ring of shared-memory stages; one thread issues
+// tcgen05.mma (kind::f16, M = 128, N = BN, K = 16) into an FP32 accumulator in
+// tensor memory; four epilogue warps read it back with tcgen05.ld (one TMEM lane
+// per thread = one row of D) and apply the epilogue 32 columns at a time.
+//   warp 0 lane 0   TMA producer (full/empty mbarriers per stage)
+//   warp 1 lane 0   MMA issuer; commits each stage back to the producer
+//   warps 2-5       epilogue
+// Every wait is bounded by a %globaltimer deadline; on timeout the CTA sets the
+// error word, lets issued copies and MMAs land, frees its tensor memory and exits.
+//
+// The products (N = pixels per sample, m = kept modes per axis, C = 32 channels):
+//   truncated DFT        Vh [B C][2 m^2]  = V_cf [B C][N^2] . D [2 m^2][N^2]^T     (EPI_ROWS_F32)
+//   inverse + 1x1 conv   Z^T [N^2][B C]   = E [N^2][Kp] . Wh [B C][Kp]^T, then
+//                        + W V + c and GELU in the epilogue                      (EPI_LAYER_FWD)
+//   backward of both     dV^T [N^2][B C]  = E . GVh^T, + W^T dZ, * GELU'(Z)     (EPI_LAYER_BWD)
+//   weight gradient      dW = sum_b dZ_b V_b^T over pixels, 4 samples per tile  (EPI_DW)
+// SIMT form (FP32 test mode): the same products and the same epilogue code on
+// FP32 operands, 128 rows x 32 columns per CTA.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "fno_internal.cuh"
+#include "scw_ptx.cuh"
+
+namespace scw {
+namespace fno {
+
+template <int BN>
+struct GemmCfg {
+  static constexpr uint32_t A_BYTES = 128u * 128u;            // 128 rows x 64 bf16
+  static constexpr uint32_t B_BYTES = (uint32_t)BN * 128u;     // BN rows x 64 bf16
+  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+  static constexpr int ST_RAW = (int)(100u * 1024u / STAGE);   // two CTAs per SM
+  static constexpr int STAGES = ST_RAW < 2 ? 2 : (ST_RAW > 6 ? 6 : ST_RAW);
+  static constexpr uint32_t SMEM = STAGES * STAGE + 1024u;
+  static constexpr uint32_t TMEM_COLS = BN < 32 ? 32u : (uint32_t)BN;
+};
+
+template <int BN, int EPI>
+__global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CUtensorMap mA,
+                                                      const __grid_constant__ CUtensorMap mB,
+                                                      const __grid_constant__ EpiArgs ea, int K, int kper, int* err,
+                                                      uint64_t timeout_ns) {
+  using Cfg = GemmCfg<BN>;
+  constexpr int STAGES = Cfg::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+  __shared__ __align__(16) float w_s[C * C];
+  __shared__ __align__(16) float b_s[C];
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * 128;
+  const int n0 = (EPI == EPI_DW) ? m0 : blockIdx.y * BN;
+  const int kb0 = blockIdx.z * kper;
+  const int nkb = max(0, min(K / 64 - kb0, kper));
+  const uint64_t deadline = ptx::globaltimer() + timeout_ns;
+
+  if constexpr (EPI == EPI_LAYER_FWD || EPI == EPI_LAYER_BWD) {
+    const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(ea.w);
+    const __nv_bfloat16* bias = static_cast<const __nv_bfloat16*>(ea.bias);
+    for (int i = threadIdx.x; i < C * C; i += blockDim.x) w_s[i] = __bfloat162float(w[i]);
+    if (threadIdx.x < C) b_s[threadIdx.x] = bias ? __bfloat162float(bias[threadIdx.x]) : 0.f;
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      ptx::mbar_init(ptx::smem_u32(&full_bar[i]), 1);
+      ptx::mbar_init(ptx::smem_u32(&empty_bar[i]), 1);
+    }
+    ptx::mbar_init(ptx::smem_u32(&acc_bar), 1);
+    ptx::mbar_init(ptx::smem_u32(&drain_bar), 1);
+    abort_s = 0;
+    ptx::fence_mbar_init();
+    ptx::prefetch_tensormap(&mA);
+    ptx::prefetch_tensormap(&mB);
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc(ptx::smem_u32(&tmem_base_s), Cfg::TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int st = 0, issued = 0;
+    uint32_t ph = 0;
+    for (int i = 0; i < nkb && !abort_s; ++i) {
+      if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[st]), ph ^ 1u, deadline)) {
+        atomicOr(err, DEV_ERR_TIMEOUT_EMPTY);
+        abort_s = 1;
+        break;
+      }
+      const uint32_t fb = ptx::smem_u32(&full_bar[st]);
+      ptx::mbar_arrive_expect_tx(fb, Cfg::STAGE);
+      const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE);
+      const int kc = (kb0 + i) * 64;
+      ptx::tma_load_2d(sa, &mA, kc, m0, fb);
+      ptx::tma_load_2d(sa + Cfg::A_BYTES, &mB, kc, n0, fb);
+      ++issued;
+      if (++st == STAGES) {
+        st = 0;
+        ph ^= 1u;
+      }
+    }
+    if (abort_s) {
+      const uint64_t d2 = ptx::globaltimer() + timeout_ns;
+      for (int back = 1; back <= STAGES && back <= issued; ++back) {
+        const int i = issued - back;
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[i % STAGES]), (uint32_t)(i / STAGES) & 1u, d2)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
+          break;
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- tcgen05.mma issuer ----------------
+    constexpr uint32_t idesc = ptx::idesc_f16(true, 128, BN);
+    int st = 0;
+    uint32_t ph = 0;
+    for (int i = 0; i < nkb && !abort_s; ++i) {
+      if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[st]), ph, deadline)) {
+        atomicOr(err, DEV_ERR_TIMEOUT_FULL);
+        abort_s = 1;
+        break;
+      }
+      ptx::tc_fence_after();
+      const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE);
+      const uint64_t da = ptx::sw128_desc(sa), db = ptx::sw128_desc(sa + Cfg::A_BYTES);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t o = (uint64_t)(2 * kk);  // 16 elements = 32 bytes, in 16-byte units
+        ptx::mma_f16(tmem, da + o, db + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      }
+      ptx::mma_commit(ptx::smem_u32(&empty_bar[st]));
+      if (++st == STAGES) {
+        st = 0;
+        ph ^= 1u;
+      }
+    }
+    if (!abort_s) {
+      ptx::mma_commit(ptx::smem_u32(&acc_bar));
+    } else {
+      ptx::mma_commit(ptx::smem_u32(&drain_bar));
+      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::globaltimer() + timeout_ns))
+        atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int grp = warp & 3;  // TMEM lanes 32 grp .. 32 grp + 31
+    bool ok = true;
+    for (;;) {
+      if (ptx::mbar_try_wait(ptx::smem_u32(&acc_bar), 0u)) break;
+      if (abort_s || ptx::globaltimer() > deadline) {
+        ok = false;
+        break;
+      }
+    }
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0 && !abort_s) atomicOr(err, DEV_ERR_TIMEOUT_ACCUM);
+      abort_s = 1;
+    } else {
+      ptx::tc_fence_after();
+      const int row = m0 + grp * 32 + lane;
+      const uint32_t lane_addr = tmem + ((uint32_t)(grp * 32) << 16);
+      const int col_end = (EPI == EPI_DW) ? n0 + 128 : ea.cols;
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        if (n0 + 32 * c >= col_end) break;  // warp-uniform
+        uint32_t r0[8], r1[8], r2[8], r3[8];
+        ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c), r0);
+        ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c + 8), r1);
+        ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c + 16), r2);
+        ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c + 24), r3);
+        ptx::tmem_wait_ld();
+        float acc[32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          acc[j] = nkb > 0 ? __uint_as_float(r0[j]) : 0.f;
+          acc[8 + j] = nkb > 0 ? __uint_as_float(r1[j]) : 0.f;
+          acc[16 + j] = nkb > 0 ? __uint_as_float(r2[j]) : 0.f;
+          acc[24 + j] = nkb > 0 ? __uint_as_float(r3[j]) : 0.f;
+        }
+        epilogue<EPI, __nv_bfloat16>(ea, w_s, b_s, row, n0 + 32 * c, blockIdx.z, acc);
+      }
+    }
+  }
+
+  // ---------------- teardown ----------------
+  __syncwarp();
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+  }
+}
+
+template <int EPI>
+__global__ void __launch_bounds__(128) gemm_simt_kernel(const float* __restrict__ A, long long lda,
+                                                        const float* __restrict__ Bm, long long ldb, EpiArgs ea,
+                                                        int a_rows, int NB_rows, int K, int kper) {
+  __shared__ float As[32][129];
+  __shared__ float Bs[32][33];
+  __shared__ __align__(16) float w_s[C * C];
+  __shared__ __align__(16) float b_s[C];
+  const int t = threadIdx.x;
+  if constexpr (EPI == EPI_LAYER_FWD || EPI == EPI_LAYER_BWD) {
+    const float* w = static_cast<const float*>(ea.w);
+    const float* bias = static_cast<const float*>(ea.bias);
+    for (int i = t; i < C * C; i += blockDim.x) w_s[i] = w[i];
+    if (t < C) b_s[t] = bias ? bias[t] : 0.f;
+  }
+  const int m0 = blockIdx.x * 128;
+  const int n0 = (EPI == EPI_DW) ? m0 + 32 * blockIdx.y : blockIdx.y * 32;
+  const int kbeg = blockIdx.z * kper * 64, kend = min(K, kbeg + kper * 64);
+  float acc[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) acc[j] = 0.f;
+  for (int kc = kbeg; kc < kend; kc += 32) {
+    const int k = kc + (t & 31);
+#pragma unroll 4
+    for (int r = t >> 5; r < 128; r += 4) {
+      const int row = m0 + r;
+      As[t & 31][r] = (row < a_rows && k < kend) ? A[(size_t)row * lda + k] : 0.f;
+    }
+#pragma unroll
+    for (int c = t >> 5; c < 32; c += 4) {
+      const int col = n0 + c;
+      Bs[t & 31][c] = (col < NB_rows && k < kend) ? Bm[(size_t)col * ldb + k] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) {
+      const float a = As[kk][t];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) acc[j] = fmaf(a, Bs[kk][j], acc[j]);
+    }
+    __syncthreads();
+  }
+  const int col_end = (EPI == EPI_DW) ? m0 + 128 : ea.cols;
+  if (n0 < col_end) epilogue<EPI, float>(ea, w_s, b_s, m0 + t, n0, blockIdx.z, acc);
+}
+
+// ---------------------------------------------------------------- host side ---
+template <int BN, int EPI>
+static cudaError_t launch_tc_t(const CUtensorMap& mA, const CUtensorMap& mB, const EpiArgs& ea, int M, int N, int K,
+                               int splits, int* err, uint64_t timeout_ns, cudaStream_t st) {
+  using Cfg = GemmCfg<BN>;
+  const void* fn = reinterpret_cast<const void*>(gemm_tc_kernel<BN, EPI>);
+  cudaError_t e = allow_max_smem(fn);
+  if (e != cudaSuccess) return e;
+  const int nkb = K / 64;
+  const int kper = (nkb + splits - 1) / splits;
+  const dim3 grid((M + 127) / 128, EPI == EPI_DW ? 1 : (N + BN - 1) / BN, splits);
+  gemm_tc_kernel<BN, EPI><<<grid, 192, Cfg::SMEM, st>>>(mA, mB, ea, K, kper, err, timeout_ns);
+  return cudaGetLastError();
+}
+
+template <int EPI>
+static cudaError_t launch_tc_bn(int BN, const CUtensorMap& mA, const CUtensorMap& mB, const EpiArgs& ea, int M,
+                                int N, int K, int splits, int* err, uint64_t timeout_ns, cudaStream_t st) {
+  switch (BN) {
+    case 32: return launch_tc_t<32, EPI>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
+    case 64: return launch_tc_t<64, EPI>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
+    case 128: return launch_tc_t<128, EPI>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
+    case 256: return launch_tc_t<256, EPI>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtensorMap& mB, const EpiArgs& ea, int M,
+                           int N, int K, int splits, int* err, uint64_t timeout_ns, cudaStream_t st) {
+  if (K % 64 != 0 || splits < 1) return cudaErrorInvalidValue;
+  if ((epi == EPI_LAYER_FWD || epi == EPI_LAYER_BWD) && splits != 1) return cudaErrorInvalidValue;
+  switch (epi) {
+    case EPI_ROWS_F32: return launch_tc_bn<EPI_ROWS_F32>(BN, mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
+    case EPI_LAYER_FWD: return launch_tc_bn<EPI_LAYER_FWD>(BN, mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
+    case EPI_LAYER_BWD: return launch_tc_bn<EPI_LAYER_BWD>(BN, mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
+    case EPI_DW:
+      return BN == 128 ? launch_tc_t<128, EPI_DW>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st)
+                       : cudaErrorInvalidValue;
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int gemm_tc_ctas_per_sm(int BN) {
+  const uint32_t smem = BN == 32    ? GemmCfg<32>::SMEM
+                        : BN == 64  ? GemmCfg<64>::SMEM
+                        : BN == 128 ? GemmCfg<128>::SMEM
+                                    : GemmCfg<256>::SMEM;
+  return smem <= 110u * 1024u ? 2 : 1;
+}
+
+template <int EPI>
+static cudaError_t launch_simt_t(const float* A, long long lda, const float* B, long long ldb, const EpiArgs& ea, int M,
+                                 int N, int K, int splits, cudaStream_t st) {
+  const int nkb = (K + 63) / 64;
+  const int kper = (nkb + splits - 1) / splits;
+  const dim3 grid((M + 127) / 128, EPI == EPI_DW ? 4 : (N + 31) / 32, splits);
+  // rows of A and B that exist (EPI_DW tiles cover whole 4-sample groups; A and B hold B*C rows)
+  const int a_rows = EPI == EPI_DW ? ea.rows : M;
+  const int nb_rows = EPI == EPI_DW ? ea.rows : N;
+  gemm_simt_kernel<EPI><<<grid, 128, 0, st>>>(A, lda, B, ldb, ea, a_rows, nb_rows, K, kper);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_simt(int epi, const float* A, long long lda, const float* B, long long ldb, const EpiArgs& ea,
+                             int M, int N, int K, int splits, cudaStream_t st) {
+  if (splits < 1) return cudaErrorInvalidValue;
+  if ((epi == EPI_LAYER_FWD || epi == EPI_LAYER_BWD) && splits != 1) return cudaErrorInvalidValue;
+  switch (epi) {
+    case EPI_ROWS_F32: return launch_simt_t<EPI_ROWS_F32>(A, lda, B, ldb, ea, M, N, K, splits, st);
+    case EPI_LAYER_FWD: return launch_simt_t<EPI_LAYER_FWD>(A, lda, B, ldb, ea, M, N, K, splits, st);
+    case EPI_LAYER_BWD: return launch_simt_t<EPI_LAYER_BWD>(A, lda, B, ldb, ea, M, N, K, splits, st);
+    case EPI_DW: return launch_simt_t<EPI_DW>(A, lda, B, ldb, ea, M, N, K, splits, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+scw_status make_map_bf16(CUtensorMap* m, const void* base, long long cols, long long rows, long long pitch,
+                         int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return set_error(SCW_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) || (pitch * 2) % 16 || box_rows < 1 || box_rows > 256)
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "tensor map: base, pitch or box out of range");
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(SCW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return SCW_OK;
+}
+
+}  // namespace fno
+}  // namespace scw

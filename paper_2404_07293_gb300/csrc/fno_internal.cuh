@@ -1,0 +1,253 @@
+// Internal declarations of the surrogate (Fourier neural operator) kernels.
+// The network, its loss and the flat parameter order are defined in
+// include/scw_fno.h; this header holds the device-side views of them.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "scw_internal.cuh"
+
+namespace scw {
+namespace fno {
+
+constexpr int C = 32;    // channels (width)
+constexpr int OUT = 6;   // Re/Im of E_x, E_y, E_z
+constexpr int PIX_BLOCK = 256;  // pixels per block of the per-pixel kernels (N*N is a multiple)
+
+// GEMM epilogues. Rows / columns are those of the GEMM's D = A B^T.
+enum Epi : int {
+  EPI_ROWS_F32 = 0,   // D[row][col] * alpha -> FP32 out (+ split offset): truncated DFTs
+  EPI_LAYER_FWD = 1,  // rows = pixels, columns = (sample, channel): Z = alpha D + c + W V; V' = GELU(Z)
+  EPI_LAYER_BWD = 2,  // rows = pixels, columns = (sample, channel): dV = D + W^T dZ; dZ' = dV GELU'(Z)
+  EPI_DW = 3          // rows = (sample, o), columns = (sample, i) of 4 samples: keep the diagonal blocks
+};
+
+struct EpiArgs {
+  float alpha;
+  int rows;            // valid rows of D
+  int cols;            // valid columns of D
+  int P;               // pixels per sample
+  int B;               // valid samples
+  float* out;          // EPI_ROWS_F32: [split][rows][ld]; EPI_DW: [group][split][4][C][C]
+  long long ld;
+  long long split_stride;
+  int splits;          // EPI_DW: K splits per group
+  const void* w;       // EPI_LAYER_*: W [C][C] (row = output channel), element type T
+  const void* bias;    // EPI_LAYER_FWD: c [C] (T), may be null
+  const void* x_cl;    // FWD: V_l channel-last [B][P][C]; BWD: dZ_l channel-last
+  const void* z_in;    // BWD: Z_{l-1} channel-last (GELU'), null for l = 0
+  void* z_out;         // FWD: Z_l channel-last, null when not needed
+  void* out_cf;        // FWD: V_{l+1} [B][C][P]; BWD: dZ_{l-1} (or dV_0) [B][C][P]
+  void* out_cl;        // FWD: V_{l+1} [B][P][C]; BWD: dZ_{l-1} [B][P][C] or null
+  int gelu;            // FWD: apply GELU
+};
+
+// ---- element access (T = float or __nv_bfloat16) ----------------------------------------
+template <typename T>
+__device__ __forceinline__ float to_f(T x);
+template <>
+__device__ __forceinline__ float to_f<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename T>
+__device__ __forceinline__ T from_f(float x);
+template <>
+__device__ __forceinline__ float from_f<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+// 32 contiguous elements <-> float[32] with 16-byte accesses (p 16-byte aligned)
+template <typename T>
+__device__ __forceinline__ void ld32(const T* p, float (&v)[32]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const float4 t = q[j];
+      v[4 * j] = t.x;
+      v[4 * j + 1] = t.y;
+      v[4 * j + 2] = t.z;
+      v[4 * j + 3] = t.w;
+    }
+  } else {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint4 t = q[j];
+      const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        v[8 * j + 2 * h] = __uint_as_float(w[h] << 16);
+        v[8 * j + 2 * h + 1] = __uint_as_float(w[h] & 0xffff0000u);
+      }
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void st32(T* p, const float (&v)[32]) {
+  if constexpr (sizeof(T) == 4) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) q[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+  } else {
+    uint4* q = reinterpret_cast<uint4*>(p);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t w[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(v[8 * j + 2 * h], v[8 * j + 2 * h + 1]);
+        w[h] = *reinterpret_cast<const uint32_t*>(&b);
+      }
+      q[j] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+  }
+}
+
+// GELU(z) = z Phi(z) and its derivative Phi(z) + z phi(z), Phi the standard normal CDF
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+// ---- epilogues, shared by the tensor-core and the SIMT GEMM ------------------------------
+// Called once per (row, 32-column chunk starting at col0) with that chunk's accumulators.
+// w_s: W as FP32 [C][C] in shared memory; b_s: bias [C] (zeros if none).
+template <int EPI, typename T>
+__device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, const float* b_s, int row, int col0,
+                                         int split, const float (&acc)[32]) {
+  if constexpr (EPI == EPI_ROWS_F32) {
+    if (row >= a.rows) return;
+    float* o = a.out + (size_t)split * a.split_stride + (size_t)row * a.ld + col0;
+    if (col0 + 32 <= a.cols) {
+#pragma unroll
+      for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4*>(o + j) =
+            make_float4(a.alpha * acc[j], a.alpha * acc[j + 1], a.alpha * acc[j + 2], a.alpha * acc[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (col0 + j < a.cols) o[j] = a.alpha * acc[j];
+    }
+  } else if constexpr (EPI == EPI_LAYER_FWD) {
+    const int p = row, b = col0 / C;
+    if (p >= a.P || b >= a.B) return;
+    const size_t cl = ((size_t)b * a.P + p) * C;
+    float x[32], z[32];
+    ld32(static_cast<const T*>(a.x_cl) + cl, x);
+#pragma unroll
+    for (int o = 0; o < C; ++o) {
+      float s = a.alpha * acc[o] + b_s[o];
+#pragma unroll
+      for (int i = 0; i < C; ++i) s = fmaf(w_s[o * C + i], x[i], s);
+      z[o] = s;
+    }
+    if (a.z_out) st32(static_cast<T*>(a.z_out) + cl, z);
+    if (a.gelu) {
+#pragma unroll
+      for (int o = 0; o < C; ++o) z[o] = gelu_f(z[o]);
+    }
+    st32(static_cast<T*>(a.out_cl) + cl, z);
+    T* cf = static_cast<T*>(a.out_cf) + (size_t)b * C * a.P + p;
+#pragma unroll
+    for (int o = 0; o < C; ++o) cf[(size_t)o * a.P] = from_f<T>(z[o]);
+  } else if constexpr (EPI == EPI_LAYER_BWD) {
+    const int p = row, b = col0 / C;
+    if (p >= a.P || b >= a.B) return;
+    const size_t cl = ((size_t)b * a.P + p) * C;
+    float x[32], d[32];
+    ld32(static_cast<const T*>(a.x_cl) + cl, x);
+#pragma unroll
+    for (int i = 0; i < C; ++i) {
+      float s = acc[i];
+#pragma unroll
+      for (int o = 0; o < C; ++o) s = fmaf(w_s[o * C + i], x[o], s);
+      d[i] = s;
+    }
+    if (a.z_in) {
+      float z[32];
+      ld32(static_cast<const T*>(a.z_in) + cl, z);
+#pragma unroll
+      for (int i = 0; i < C; ++i) d[i] *= gelu_grad_f(z[i]);
+    }
+    if (a.out_cl) st32(static_cast<T*>(a.out_cl) + cl, d);
+    T* cf = static_cast<T*>(a.out_cf) + (size_t)b * C * a.P + p;
+#pragma unroll
+    for (int i = 0; i < C; ++i) cf[(size_t)i * a.P] = from_f<T>(d[i]);
+  } else {  // EPI_DW: row = 32 s + o of group g = row / 128; chunk c = (col0 % 128) / 32
+    const int g = row / 128, s = (row % 128) / C, o = row % C, c = (col0 % 128) / C;
+    if (c != s) return;
+    float* dst = a.out + ((((size_t)g * a.splits + split) * 4 + s) * C + o) * C;
+    const bool valid = g * 4 + s < a.B;
+#pragma unroll
+    for (int j = 0; j < 32; j += 4)
+      *reinterpret_cast<float4*>(dst + j) = valid ? make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3])
+                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// ---- launchers ---------------------------------------------------------------------------
+// Tensor-core GEMM D = A B^T over K (bf16, K-major, TMA maps with 128-byte swizzle and
+// a 64-element inner box): A rows in boxes of 128, B rows in boxes of BN (32..256).
+// grid = (ceil(M/128), ceil(N/BN), splits); EPI_DW uses grid.x = groups and the same row
+// offset for A and B. Each split covers kper 64-wide K blocks.
+cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtensorMap& mB, const EpiArgs& ea,
+                           int M, int N, int K, int splits, int* err, uint64_t timeout_ns, cudaStream_t st);
+// FP32 SIMT GEMM with the same semantics (A [M][lda], B [N][ldb] row-major FP32; for EPI_DW
+// rows of B are offset like rows of A).
+cudaError_t launch_gemm_simt(int epi, const float* A, long long lda, const float* B, long long ldb,
+                             const EpiArgs& ea, int M, int N, int K, int splits, cudaStream_t st);
+int gemm_tc_ctas_per_sm(int BN);
+
+// encode a 2D bf16 tensor map: `rows` rows of `cols` elements (row pitch `pitch` elements),
+// box {64, box_rows}, 128-byte swizzle, out-of-bounds elements read as zero
+scw_status make_map_bf16(CUtensorMap* m, const void* base, long long cols, long long rows, long long pitch,
+                         int box_rows);
+
+template <typename T>
+cudaError_t launch_tables(T* D, T* E, int N, int m, int Kp, cudaStream_t st);
+template <typename T>
+cudaError_t launch_lift(const float2* n, const T* params, T* Vcf, T* Vcl, int B, int S, int in_grid, int N,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t launch_mix_fwd(const float* Vh, int splits, long long split_stride, const T* R, T* Wh, int B, int m,
+                           int Kc, int Kp, cudaStream_t st);
+template <typename T>
+cudaError_t launch_mix_bwd(const float* G, const float* Vh, int splits, long long split_stride, const T* R, T* GVh,
+                           float* part, int sample_blocks, int B, int m, int Kc, int Kp, int N, cudaStream_t st);
+cudaError_t launch_target_norm(const float2* target, float* part, int B, int P, cudaStream_t st);
+template <typename T>
+cudaError_t launch_project_train(const T* Vcl, const float2* target, const T* params_q, const float* part_tn,
+                                 float* dF, T* dZcf, T* dZcl, float* part_err, float* part_pool, int B, int P,
+                                 cudaStream_t st);
+template <typename T>
+cudaError_t launch_project_reduce(const T* Vcf, const float* dF, float* part, int B, int P, cudaStream_t st);
+template <typename T>
+cudaError_t launch_head(const float* part_tn, const float* part_err, const float* part_pool, const T* params_e,
+                        float* grad_e, float* loss, float* h_out, float* rel2_out, int B, int P, int with_loss,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t launch_lift_bwd(const T* dV0cf, const float2* n, float* part, int B, int S, int in_grid, int N,
+                            cudaStream_t st);
+cudaError_t launch_reduce_rows_ex(const float* part, int rows, int width, long long pitch, float scale, float* out,
+                                  float* scratch, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adam(float* master, const float* grad, float* m, float* v, T* copy, long long n, float lr,
+                        float bc1, float bc2, cudaStream_t st);
+template <typename T>
+cudaError_t launch_copy_params(const float* master, T* copy, long long n, cudaStream_t st);
+template <typename T>
+cudaError_t launch_project_infer(const T* Vcl, const T* params_q, float2* field, float* part_pool, int B, int P,
+                                 cudaStream_t st);
+template <typename T>
+cudaError_t launch_head_infer(const float* part_pool, const T* params_e, float q, float threshold, float* h_out,
+                              float* est, unsigned char* flag, int B, int P, cudaStream_t st);
+
+}  // namespace fno
+}  // namespace scw

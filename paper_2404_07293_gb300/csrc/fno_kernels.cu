@@ -1,0 +1,702 @@
+// The surrogate's SIMT kernels: DFT tables, lift, per-mode complex mixing
+// (forward and backward), projection + loss, error head, lift backward,
+// deterministic partial-sum reduction and Adam. Element type T is BF16 in the
+// training mode and FP32 in the test mode; accumulations are FP32 throughout.
+// Definitions of every quantity are in include/scw_fno.h.
+#include "fno_internal.cuh"
+
+namespace scw {
+namespace fno {
+
+// ---- DFT tables: D[2k + r][p] = cos(theta) (r = 0) or -sin(theta) (r = 1), E = D^T (pads zero)
+// theta = 2 pi ((kx x + ky y) mod N) / N, reduced exactly in integers, evaluated in FP64.
+template <typename T>
+__global__ void tables_kernel(T* __restrict__ D, T* __restrict__ E, int N, int m, int Kp) {
+  const int P = N * N, Kc = 2 * m * m;
+  const long long total = (long long)Kc * P;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx / P), p = (int)(idx % P);
+    const int k = q >> 1;
+    const int ky = k / m - m / 2, kx = k % m - m / 2;
+    const int y = p / N, x = p % N;
+    const int r = (((kx * x + ky * y) % N) + N) % N;
+    double s, c;
+    sincospi(2.0 * r / N, &s, &c);
+    const float v = (q & 1) ? (float)-s : (float)c;
+    D[(size_t)q * P + p] = from_f<T>(v);
+    E[(size_t)p * Kp + q] = from_f<T>(v);
+  }
+}
+
+// ---- lift: V_0 = P a + p, a = (Re n - 1, Im n) per slice, nearest upsampling
+template <typename T>
+__global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n, const T* __restrict__ prm,
+                                                   T* __restrict__ Vcf, T* __restrict__ Vcl, int B, int S,
+                                                   int in_grid, int N) {
+  __shared__ float Ps[C * 32];
+  __shared__ float ps[C];
+  const int cin = 2 * S;
+  for (int i = threadIdx.x; i < C * cin; i += blockDim.x) Ps[i] = to_f(prm[i]);
+  if (threadIdx.x < C) ps[threadIdx.x] = to_f(prm[C * cin + threadIdx.x]);
+  __syncthreads();
+  const int P = N * N;
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)B * P) return;
+  const int b = (int)(idx / P), p = (int)(idx % P);
+  const int r = N / in_grid;
+  const int yi = (p / N) / r, xi = (p % N) / r;
+  float a[32];
+  for (int s = 0; s < S; ++s) {
+    const float2 v = n[(((size_t)b * S + s) * in_grid + yi) * in_grid + xi];
+    a[2 * s] = v.x - 1.0f;
+    a[2 * s + 1] = v.y;
+  }
+  float o[32];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    float t = ps[c];
+    for (int i = 0; i < cin; ++i) t = fmaf(Ps[c * cin + i], a[i], t);
+    o[c] = t;
+  }
+  st32(Vcl + ((size_t)b * P + p) * C, o);
+  T* cf = Vcf + (size_t)b * C * P + p;
+#pragma unroll
+  for (int c = 0; c < C; ++c) cf[(size_t)c * P] = from_f<T>(o[c]);
+}
+
+// ---- mixing, forward: Wh[b][o][k] = sum_i R[k][o][i] Vh[b][i][k]; 4 modes x 8 samples per CTA
+template <typename T>
+__global__ void __launch_bounds__(256) mix_fwd_kernel(const float* __restrict__ Vh, int splits,
+                                                      long long split_stride, const T* __restrict__ R,
+                                                      T* __restrict__ Wh, int B, int Kc, int Kp) {
+  __shared__ float2 Rs[4][C][C];  // [kk][i][o]
+  __shared__ float2 Vs[8][C][4];  // [s][i][kk]
+  const int k0 = blockIdx.x * 4, b0 = blockIdx.y * 8;
+  for (int idx = threadIdx.x; idx < 4 * C * C; idx += blockDim.x) {
+    const int kk = idx / (C * C), o = (idx / C) % C, i = idx % C;
+    const T* src = R + (((size_t)(k0 + kk) * C + o) * C + i) * 2;
+    Rs[kk][i][o] = make_float2(to_f(src[0]), to_f(src[1]));
+  }
+  for (int idx = threadIdx.x; idx < 8 * C * 4; idx += blockDim.x) {
+    const int s = idx / (C * 4), i = (idx / 4) % C, kk = idx % 4;
+    const int b = b0 + s;
+    float2 v = make_float2(0.f, 0.f);
+    if (b < B) {
+      const float* src = Vh + ((size_t)b * C + i) * Kc + 2 * (k0 + kk);
+      for (int z = 0; z < splits; ++z) {
+        v.x += src[(size_t)z * split_stride];
+        v.y += src[(size_t)z * split_stride + 1];
+      }
+    }
+    Vs[s][i][kk] = v;
+  }
+  __syncthreads();
+  const int s = threadIdx.x >> 5, o = threadIdx.x & 31;
+  const int b = b0 + s;
+  float out[8];
+#pragma unroll
+  for (int kk = 0; kk < 4; ++kk) {
+    float re = 0.f, im = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < C; ++i) {
+      const float2 r = Rs[kk][i][o], v = Vs[s][i][kk];
+      re = fmaf(r.x, v.x, fmaf(-r.y, v.y, re));
+      im = fmaf(r.x, v.y, fmaf(r.y, v.x, im));
+    }
+    out[2 * kk] = re;
+    out[2 * kk + 1] = im;
+  }
+  if (b < B) {
+    T* dst = Wh + ((size_t)b * C + o) * Kp + 2 * k0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) dst[j] = from_f<T>(out[j]);
+  }
+}
+
+// ---- mixing, backward (G = dL/dRe + i dL/dIm convention):
+//   GVh[b][i][k] = sum_o conj(R[k][o][i]) G[b][o][k]
+//   part dR[k][o][i] = sum_b G[b][o][k] conj(Vh[b][i][k])   (over this CTA's samples)
+//   part dc[o] = N^2 sum_b Re G[b][o][k_dc]                   (the DC mode carries sum_x dZ / N^2)
+// part row layout: [m^2][C][C][2] then [C]
+template <typename T>
+__global__ void __launch_bounds__(256) mix_bwd_kernel(const float* __restrict__ G, const float* __restrict__ Vh,
+                                                      int splits, long long split_stride, const T* __restrict__ R,
+                                                      T* __restrict__ GVh, float* __restrict__ part, int B, int m,
+                                                      int Kc, int Kp, int N) {
+  extern __shared__ float2 mb_smem[];
+  float2(*Rs)[C][C] = reinterpret_cast<float2(*)[C][C]>(mb_smem);                 // [4][o][i]
+  float2(*Gs)[C][4] = reinterpret_cast<float2(*)[C][4]>(mb_smem + 4 * C * C);     // [8][o][kk]
+  float2(*Vs)[C][4] = reinterpret_cast<float2(*)[C][4]>(mb_smem + 4 * C * C + 8 * C * 4);  // [8][i][kk]
+  const int k0 = blockIdx.x * 4;
+  const int chunk = (B + gridDim.y - 1) / gridDim.y;
+  const int bs = blockIdx.y * chunk, be = min(B, bs + chunk);
+  const int kdc = (m / 2) * m + m / 2;
+  const bool has_dc = kdc >= k0 && kdc < k0 + 4;
+  for (int idx = threadIdx.x; idx < 4 * C * C; idx += blockDim.x) {
+    const int kk = idx / (C * C), o = (idx / C) % C, i = idx % C;
+    const T* src = R + (((size_t)(k0 + kk) * C + o) * C + i) * 2;
+    Rs[kk][o][i] = make_float2(to_f(src[0]), to_f(src[1]));
+  }
+  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+  float2 acc[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) acc[j][kk] = make_float2(0.f, 0.f);
+  float dc = 0.f;
+  for (int sb = bs; sb < be; sb += 8) {
+    __syncthreads();
+    for (int idx = t; idx < 8 * C * 4; idx += blockDim.x) {
+      const int s = idx / (C * 4), c = (idx / 4) % C, kk = idx % 4;
+      const int b = sb + s;
+      float2 g = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
+      if (b < be) {
+        const size_t off = ((size_t)b * C + c) * Kc + 2 * (k0 + kk);
+        for (int z = 0; z < splits; ++z) {
+          g.x += G[off + (size_t)z * split_stride];
+          g.y += G[off + (size_t)z * split_stride + 1];
+          v.x += Vh[off + (size_t)z * split_stride];
+          v.y += Vh[off + (size_t)z * split_stride + 1];
+        }
+      }
+      Gs[s][c][kk] = g;
+      Vs[s][c][kk] = v;
+    }
+    __syncthreads();
+    {  // GVh: thread (s = warp, i = lane)
+      const int s = wp, i = lane, b = sb + s;
+      float out[8];
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        float re = 0.f, im = 0.f;
+#pragma unroll 8
+        for (int o = 0; o < C; ++o) {
+          const float2 r = Rs[kk][o][i], g = Gs[s][o][kk];  // conj(r) g
+          re = fmaf(r.x, g.x, fmaf(r.y, g.y, re));
+          im = fmaf(r.x, g.y, fmaf(-r.y, g.x, im));
+        }
+        out[2 * kk] = re;
+        out[2 * kk + 1] = im;
+      }
+      if (b < be) {
+        T* dst = GVh + ((size_t)b * C + i) * Kp + 2 * k0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) dst[j] = from_f<T>(out[j]);
+      }
+    }
+    // dR: thread (o = warp + 8 j, i = lane)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = wp + 8 * j;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        float2 a = acc[j][kk];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+          const float2 g = Gs[s][o][kk], v = Vs[s][lane][kk];  // g conj(v)
+          a.x = fmaf(g.x, v.x, fmaf(g.y, v.y, a.x));
+          a.y = fmaf(g.y, v.x, fmaf(-g.x, v.y, a.y));
+        }
+        acc[j][kk] = a;
+      }
+    }
+    if (has_dc && t < C) {
+#pragma unroll
+      for (int s = 0; s < 8; ++s) dc += Gs[s][t][kdc - k0].x;
+    }
+  }
+  const size_t row = (size_t)blockIdx.y * ((size_t)m * m * C * C * 2 + C);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int o = wp + 8 * j;
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      float* dst = part + row + (((size_t)(k0 + kk) * C + o) * C + lane) * 2;
+      dst[0] = acc[j][kk].x;
+      dst[1] = acc[j][kk].y;
+    }
+  }
+  if (has_dc && t < C) part[row + (size_t)m * m * C * C * 2 + t] = dc * (float)N * (float)N;
+}
+
+// ---- projection, loss and their gradient (training) ----------------------------------------
+// part_tn[b][blk] = sum over the block's pixels of |T|^2
+__global__ void __launch_bounds__(256) target_norm_kernel(const float2* __restrict__ target, float* __restrict__ part,
+                                                          int P) {
+  __shared__ float red[8];
+  const int b = blockIdx.y, p = blockIdx.x * PIX_BLOCK + threadIdx.x;
+  float s = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float2 v = target[((size_t)b * 3 + c) * P + p];
+    s += v.x * v.x + v.y * v.y;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part[(size_t)b * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// F = Q v + q; d = F - T; dF = 2 d / (B ||T_b||^2); dV_L = Q^T dF (= dZ of the last layer)
+template <typename T>
+__global__ void __launch_bounds__(256) project_train_kernel(const T* __restrict__ Vcl, const float2* __restrict__ target,
+                                                            const T* __restrict__ prm_q,
+                                                            const float* __restrict__ part_tn, float* __restrict__ dF,
+                                                            T* __restrict__ dZcf, T* __restrict__ dZcl,
+                                                            float* __restrict__ part_err, float* __restrict__ part_pool,
+                                                            int B, int P) {
+  __shared__ float Qs[OUT * C + OUT];
+  __shared__ float pool_s[PIX_BLOCK][C + 1];
+  __shared__ float red[8];
+  __shared__ float tn_s;
+  const int nblk = gridDim.x, b = blockIdx.y, p = blockIdx.x * PIX_BLOCK + threadIdx.x;
+  for (int i = threadIdx.x; i < OUT * C + OUT; i += blockDim.x) Qs[i] = to_f(prm_q[i]);
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int j = 0; j < nblk; ++j) s += part_tn[(size_t)b * nblk + j];
+    tn_s = s;
+  }
+  __syncthreads();
+  float v[32];
+  ld32(Vcl + ((size_t)b * P + p) * C, v);
+#pragma unroll
+  for (int o = 0; o < C; ++o) pool_s[threadIdx.x][o] = v[o];
+  float d[OUT];
+#pragma unroll
+  for (int j = 0; j < OUT; ++j) {
+    float f = Qs[OUT * C + j];
+#pragma unroll
+    for (int o = 0; o < C; ++o) f = fmaf(Qs[j * C + o], v[o], f);
+    const float2 tv = target[((size_t)b * 3 + j / 2) * P + p];
+    d[j] = f - ((j & 1) ? tv.y : tv.x);
+  }
+  float e2 = 0.f;
+  const float sc = 2.0f / ((float)B * tn_s);
+#pragma unroll
+  for (int j = 0; j < OUT; ++j) {
+    e2 = fmaf(d[j], d[j], e2);
+    d[j] *= sc;
+    dF[((size_t)b * OUT + j) * P + p] = d[j];
+  }
+  float g[32];
+#pragma unroll
+  for (int o = 0; o < C; ++o) {
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < OUT; ++j) s = fmaf(Qs[j * C + o], d[j], s);
+    g[o] = s;
+  }
+  st32(dZcl + ((size_t)b * P + p) * C, g);
+  T* cf = dZcf + (size_t)b * C * P + p;
+#pragma unroll
+  for (int o = 0; o < C; ++o) cf[(size_t)o * P] = from_f<T>(g[o]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    part_err[(size_t)b * nblk + blockIdx.x] = t;
+  }
+  if (threadIdx.x < C) {
+    float s = 0.f;
+    for (int r = 0; r < PIX_BLOCK; ++r) s += pool_s[r][threadIdx.x];
+    part_pool[((size_t)b * nblk + blockIdx.x) * C + threadIdx.x] = s;
+  }
+}
+
+// part row [6 C + 6]: dQ[j][o] = sum_p dF[j][p] V[o][p], dq[j] = sum_p dF[j][p] over the block's pixels
+template <typename T>
+__global__ void __launch_bounds__(256) project_reduce_kernel(const T* __restrict__ Vcf, const float* __restrict__ dF,
+                                                             float* __restrict__ part, int P) {
+  __shared__ float Vs[C][PIX_BLOCK + 1];
+  __shared__ float Fs[OUT][PIX_BLOCK];
+  const int b = blockIdx.y, p0 = blockIdx.x * PIX_BLOCK, t = threadIdx.x;
+  for (int o = 0; o < C; ++o) Vs[o][t] = to_f(Vcf[((size_t)b * C + o) * P + p0 + t]);
+  for (int j = 0; j < OUT; ++j) Fs[j][t] = dF[((size_t)b * OUT + j) * P + p0 + t];
+  __syncthreads();
+  float* dst = part + ((size_t)b * gridDim.x + blockIdx.x) * (OUT * C + OUT);
+  if (t < OUT * C) {
+    const int j = t / C, o = t % C;
+    float s = 0.f;
+    for (int p = 0; p < PIX_BLOCK; ++p) s = fmaf(Fs[j][p], Vs[o][p], s);
+    dst[t] = s;
+  } else if (t < OUT * C + OUT) {
+    const int j = t - OUT * C;
+    float s = 0.f;
+    for (int p = 0; p < PIX_BLOCK; ++p) s += Fs[j][p];
+    dst[t] = s;
+  }
+}
+
+// error head and the loss (one CTA): h = e . pool + e0, rel2 = ||F - T||^2 / ||T||^2,
+// L_field = mean rel2, L_head = mean (h - log(rel2 + 1e-12)/2)^2; grad_e gets de[C], de0
+template <typename T>
+__global__ void __launch_bounds__(256) head_kernel(const float* __restrict__ part_tn, const float* __restrict__ part_err,
+                                                   const float* __restrict__ part_pool, const T* __restrict__ prm_e,
+                                                   float* __restrict__ grad_e, float* __restrict__ loss,
+                                                   float* __restrict__ h_out, float* __restrict__ rel2_out, int B,
+                                                   int nblk, int P) {
+  __shared__ float es[C + 1];
+  __shared__ float red[8][C + 3];
+  if (threadIdx.x <= C) es[threadIdx.x] = to_f(prm_e[threadIdx.x]);
+  __syncthreads();
+  float de[C + 1], lf = 0.f, lh = 0.f;
+#pragma unroll
+  for (int o = 0; o <= C; ++o) de[o] = 0.f;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    float tn = 0.f, e2 = 0.f;
+    for (int j = 0; j < nblk; ++j) {
+      tn += part_tn[(size_t)b * nblk + j];
+      e2 += part_err[(size_t)b * nblk + j];
+    }
+    float pool[C];
+#pragma unroll
+    for (int o = 0; o < C; ++o) pool[o] = 0.f;
+    for (int j = 0; j < nblk; ++j) {
+      const float* pp = part_pool + ((size_t)b * nblk + j) * C;
+#pragma unroll
+      for (int o = 0; o < C; ++o) pool[o] += pp[o];
+    }
+    float h = es[C];
+#pragma unroll
+    for (int o = 0; o < C; ++o) {
+      pool[o] /= (float)P;
+      h = fmaf(es[o], pool[o], h);
+    }
+    const float rel2 = e2 / tn;
+    const float tgt = 0.5f * logf(rel2 + 1e-12f);
+    const float dh = 2.0f * (h - tgt) / (float)B;
+    lf += rel2 / (float)B;
+    lh += (h - tgt) * (h - tgt) / (float)B;
+#pragma unroll
+    for (int o = 0; o < C; ++o) de[o] = fmaf(dh, pool[o], de[o]);
+    de[C] += dh;
+    if (h_out) h_out[b] = h;
+    if (rel2_out) rel2_out[b] = rel2;
+  }
+  // block reduction of (de[0..C], lf, lh)
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 0; o <= C; ++o) {
+    float v = de[o];
+#pragma unroll
+    for (int s = 16; s; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
+    if (lane == 0) red[wp][o] = v;
+  }
+#pragma unroll
+  for (int s = 16; s; s >>= 1) {
+    lf += __shfl_xor_sync(0xffffffffu, lf, s);
+    lh += __shfl_xor_sync(0xffffffffu, lh, s);
+  }
+  if (lane == 0) {
+    red[wp][C + 1] = lf;
+    red[wp][C + 2] = lh;
+  }
+  __syncthreads();
+  if (threadIdx.x < C + 3) {
+    float v = 0.f;
+    for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
+    if (threadIdx.x <= C) {
+      grad_e[threadIdx.x] += v;
+    } else if (loss) {
+      loss[threadIdx.x - C] = v;  // 1: L_field, 2: L_head
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && loss) loss[0] = loss[1] + loss[2];
+}
+
+// ---- lift backward: part row [C][2S] then [C]: dP[o][c] = sum dV0[o] a[c], dp[o] = sum dV0[o]
+// (dV0 summed over each input pixel's r x r block first: a is constant there)
+template <typename T>
+__global__ void __launch_bounds__(128) lift_bwd_kernel(const T* __restrict__ dV0cf, const float2* __restrict__ n,
+                                                       float* __restrict__ part, int B, int S, int in_grid, int N) {
+  __shared__ float dv_s[128][C + 1];
+  __shared__ float a_s[128][33];
+  const int cin = 2 * S, P = N * N, Pi = in_grid * in_grid, r = N / in_grid;
+  const long long idx = blockIdx.x * 128LL + threadIdx.x;
+  const bool valid = idx < (long long)B * Pi;
+  if (valid) {
+    const int b = (int)(idx / Pi), pi = (int)(idx % Pi);
+    const int yi = pi / in_grid, xi = pi % in_grid;
+    for (int o = 0; o < C; ++o) {
+      const T* src = dV0cf + ((size_t)b * C + o) * P;
+      float s = 0.f;
+      for (int dy = 0; dy < r; ++dy)
+        for (int dx = 0; dx < r; ++dx) s += to_f(src[(size_t)(yi * r + dy) * N + xi * r + dx]);
+      dv_s[threadIdx.x][o] = s;
+    }
+    for (int s = 0; s < S; ++s) {
+      const float2 v = n[(((size_t)b * S + s) * in_grid + yi) * in_grid + xi];
+      a_s[threadIdx.x][2 * s] = v.x - 1.0f;
+      a_s[threadIdx.x][2 * s + 1] = v.y;
+    }
+  } else {
+    for (int o = 0; o < C; ++o) dv_s[threadIdx.x][o] = 0.f;
+    for (int c = 0; c < cin; ++c) a_s[threadIdx.x][c] = 0.f;
+  }
+  __syncthreads();
+  const int width = C * cin + C;
+  float* dst = part + (size_t)blockIdx.x * width;
+  for (int q = threadIdx.x; q < width; q += 128) {
+    float s = 0.f;
+    if (q < C * cin) {
+      const int o = q / cin, c = q % cin;
+      for (int j = 0; j < 128; ++j) s = fmaf(dv_s[j][o], a_s[j][c], s);
+    } else {
+      const int o = q - C * cin;
+      for (int j = 0; j < 128; ++j) s += dv_s[j][o];
+    }
+    dst[q] = s;
+  }
+}
+
+// ---- deterministic column sums: block (32, 8) per 32 columns and a chunk of rows
+__global__ void __launch_bounds__(256) reduce_rows_kernel(const float* __restrict__ part, int rows, int width,
+                                                          long long pitch, int chunk, float scale,
+                                                          float* __restrict__ out, float* __restrict__ scratch) {
+  __shared__ float red[8][33];
+  const int col = blockIdx.x * 32 + threadIdx.x;
+  const int r0 = blockIdx.y * chunk, r1 = min(rows, r0 + chunk);
+  float s = 0.f;
+  if (col < width)
+    for (int r = r0 + threadIdx.y; r < r1; r += 8) s += part[(size_t)r * pitch + col];
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && col < width) {
+    float t = 0.f;
+    for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+    if (scratch)
+      scratch[(size_t)blockIdx.y * width + col] = t;
+    else
+      out[col] += scale * t;
+  }
+}
+
+// ---- Adam (bias-corrected), refreshes the kernels' copy of the parameters
+template <typename T>
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, T* __restrict__ copy, long long n, float lr, float bc1, float bc2) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / bc1) / (sqrtf(vi / bc2) + 1e-8f);
+    w[i] = wi;
+    copy[i] = from_f<T>(wi);
+  }
+}
+
+template <typename T>
+__global__ void copy_params_kernel(const float* __restrict__ w, T* __restrict__ copy, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    copy[i] = from_f<T>(w[i]);
+}
+
+// ---- inference: field and the head's estimate --------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) project_infer_kernel(const T* __restrict__ Vcl, const T* __restrict__ prm_q,
+                                                            float2* __restrict__ field, float* __restrict__ part_pool,
+                                                            int P) {
+  __shared__ float Qs[OUT * C + OUT];
+  __shared__ float pool_s[PIX_BLOCK][C + 1];
+  const int nblk = gridDim.x, b = blockIdx.y, p = blockIdx.x * PIX_BLOCK + threadIdx.x;
+  for (int i = threadIdx.x; i < OUT * C + OUT; i += blockDim.x) Qs[i] = to_f(prm_q[i]);
+  __syncthreads();
+  float v[32];
+  ld32(Vcl + ((size_t)b * P + p) * C, v);
+#pragma unroll
+  for (int o = 0; o < C; ++o) pool_s[threadIdx.x][o] = v[o];
+  float f[OUT];
+#pragma unroll
+  for (int j = 0; j < OUT; ++j) {
+    float s = Qs[OUT * C + j];
+#pragma unroll
+    for (int o = 0; o < C; ++o) s = fmaf(Qs[j * C + o], v[o], s);
+    f[j] = s;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) field[((size_t)b * 3 + c) * P + p] = make_float2(f[2 * c], f[2 * c + 1]);
+  __syncthreads();
+  if (threadIdx.x < C) {
+    float s = 0.f;
+    for (int r = 0; r < PIX_BLOCK; ++r) s += pool_s[r][threadIdx.x];
+    part_pool[((size_t)b * nblk + blockIdx.x) * C + threadIdx.x] = s;
+  }
+}
+
+template <typename T>
+__global__ void head_infer_kernel(const float* __restrict__ part_pool, const T* __restrict__ prm_e, float q,
+                                  float threshold, float* __restrict__ h_out, float* __restrict__ est,
+                                  unsigned char* __restrict__ flag, int B, int nblk, int P) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  float h = to_f(prm_e[C]);
+  for (int o = 0; o < C; ++o) {
+    float s = 0.f;
+    for (int j = 0; j < nblk; ++j) s += part_pool[((size_t)b * nblk + j) * C + o];
+    h = fmaf(to_f(prm_e[o]), s / (float)P, h);
+  }
+  if (h_out) h_out[b] = h;
+  const float e = expf(h + q);
+  if (est) est[b] = e;
+  if (flag) flag[b] = e > threshold ? 1 : 0;
+}
+
+// ---------------------------------------------------------------- launchers ---
+static int blocks_for(long long n, int threads, int cap = 152 * 16) {
+  const long long b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <typename T>
+cudaError_t launch_tables(T* D, T* E, int N, int m, int Kp, cudaStream_t st) {
+  const long long n = 2LL * m * m * N * N;
+  tables_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(D, E, N, m, Kp);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lift(const float2* n, const T* params, T* Vcf, T* Vcl, int B, int S, int in_grid, int N,
+                        cudaStream_t st) {
+  const long long total = (long long)B * N * N;
+  lift_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, params, Vcf, Vcl, B, S, in_grid, N);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mix_fwd(const float* Vh, int splits, long long split_stride, const T* R, T* Wh, int B, int m,
+                           int Kc, int Kp, cudaStream_t st) {
+  const dim3 grid(m * m / 4, (B + 7) / 8);
+  mix_fwd_kernel<T><<<grid, 256, 0, st>>>(Vh, splits, split_stride, R, Wh, B, Kc, Kp);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mix_bwd(const float* G, const float* Vh, int splits, long long split_stride, const T* R, T* GVh,
+                           float* part, int sample_blocks, int B, int m, int Kc, int Kp, int N, cudaStream_t st) {
+  const size_t smem = (4 * C * C + 2 * 8 * C * 4) * sizeof(float2);
+  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(mix_bwd_kernel<T>));
+  if (e != cudaSuccess) return e;
+  const dim3 grid(m * m / 4, sample_blocks);
+  mix_bwd_kernel<T><<<grid, 256, smem, st>>>(G, Vh, splits, split_stride, R, GVh, part, B, m, Kc, Kp, N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_target_norm(const float2* target, float* part, int B, int P, cudaStream_t st) {
+  target_norm_kernel<<<dim3(P / PIX_BLOCK, B), PIX_BLOCK, 0, st>>>(target, part, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_project_train(const T* Vcl, const float2* target, const T* params_q, const float* part_tn, float* dF,
+                                 T* dZcf, T* dZcl, float* part_err, float* part_pool, int B, int P, cudaStream_t st) {
+  project_train_kernel<T><<<dim3(P / PIX_BLOCK, B), PIX_BLOCK, 0, st>>>(Vcl, target, params_q, part_tn, dF, dZcf, dZcl,
+                                                                       part_err, part_pool, B, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_project_reduce(const T* Vcf, const float* dF, float* part, int B, int P, cudaStream_t st) {
+  project_reduce_kernel<T><<<dim3(P / PIX_BLOCK, B), PIX_BLOCK, 0, st>>>(Vcf, dF, part, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_head(const float* part_tn, const float* part_err, const float* part_pool, const T* params_e,
+                        float* grad_e, float* loss, float* h_out, float* rel2_out, int B, int P, int with_loss,
+                        cudaStream_t st) {
+  head_kernel<T><<<1, 256, 0, st>>>(part_tn, part_err, part_pool, params_e, grad_e, with_loss ? loss : nullptr, h_out,
+                                    rel2_out, B, P / PIX_BLOCK, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lift_bwd(const T* dV0cf, const float2* n, float* part, int B, int S, int in_grid, int N,
+                            cudaStream_t st) {
+  const long long total = (long long)B * in_grid * in_grid;
+  lift_bwd_kernel<T><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(dV0cf, n, part, B, S, in_grid, N);
+  return cudaGetLastError();
+}
+
+// out[j] += scale * sum_r part[r pitch + j]; rows above 256 go through `scratch`
+// (64 rows of `width`) in a second pass so that no thread sums more than ~32 rows.
+cudaError_t launch_reduce_rows_ex(const float* part, int rows, int width, long long pitch, float scale, float* out,
+                                  float* scratch, cudaStream_t st) {
+  if (rows <= 0 || width <= 0) return cudaSuccess;
+  const dim3 block(32, 8);
+  const unsigned gx = (unsigned)((width + 31) / 32);
+  if (rows <= 256 || !scratch) {
+    reduce_rows_kernel<<<dim3(gx, 1), block, 0, st>>>(part, rows, width, pitch, rows, scale, out, nullptr);
+    return cudaGetLastError();
+  }
+  const int ry = std::min(64, (rows + 255) / 256);
+  const int chunk = (rows + ry - 1) / ry;
+  reduce_rows_kernel<<<dim3(gx, ry), block, 0, st>>>(part, rows, width, pitch, chunk, scale, out, scratch);
+  reduce_rows_kernel<<<dim3(gx, 1), block, 0, st>>>(scratch, ry, width, width, ry, scale, out, nullptr);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_adam(float* master, const float* grad, float* m, float* v, T* copy, long long n, float lr,
+                        float bc1, float bc2, cudaStream_t st) {
+  adam_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(master, grad, m, v, copy, n, lr, bc1, bc2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_copy_params(const float* master, T* copy, long long n, cudaStream_t st) {
+  copy_params_kernel<T><<<blocks_for(n, 256), 256, 0, st>>>(master, copy, n);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_project_infer(const T* Vcl, const T* params_q, float2* field, float* part_pool, int B, int P,
+                                 cudaStream_t st) {
+  project_infer_kernel<T><<<dim3(P / PIX_BLOCK, B), PIX_BLOCK, 0, st>>>(Vcl, params_q, field, part_pool, P);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_head_infer(const float* part_pool, const T* params_e, float q, float threshold, float* h_out,
+                              float* est, unsigned char* flag, int B, int P, cudaStream_t st) {
+  head_infer_kernel<T><<<(B + 127) / 128, 128, 0, st>>>(part_pool, params_e, q, threshold, h_out, est, flag, B,
+                                                        P / PIX_BLOCK, P);
+  return cudaGetLastError();
+}
+
+#define SCW_FNO_INSTANTIATE(T)                                                                                       \
+  template cudaError_t launch_tables<T>(T*, T*, int, int, int, cudaStream_t);                                      \
+  template cudaError_t launch_lift<T>(const float2*, const T*, T*, T*, int, int, int, int, cudaStream_t);          \
+  template cudaError_t launch_mix_fwd<T>(const float*, int, long long, const T*, T*, int, int, int, int,           \
+                                         cudaStream_t);                                                             \
+  template cudaError_t launch_mix_bwd<T>(const float*, const float*, int, long long, const T*, T*, float*, int,   \
+                                         int, int, int, int, int, cudaStream_t);                                    \
+  template cudaError_t launch_project_train<T>(const T*, const float2*, const T*, const float*, float*, T*, T*,   \
+                                               float*, float*, int, int, cudaStream_t);                            \
+  template cudaError_t launch_project_reduce<T>(const T*, const float*, float*, int, int, cudaStream_t);          \
+  template cudaError_t launch_head<T>(const float*, const float*, const float*, const T*, float*, float*, float*, \
+                                      float*, int, int, int, cudaStream_t);                                         \
+  template cudaError_t launch_lift_bwd<T>(const T*, const float2*, float*, int, int, int, int, cudaStream_t);      \
+  template cudaError_t launch_adam<T>(float*, const float*, float*, float*, T*, long long, float, float, float,   \
+                                      cudaStream_t);                                                                \
+  template cudaError_t launch_copy_params<T>(const float*, T*, long long, cudaStream_t);                          \
+  template cudaError_t launch_project_infer<T>(const T*, const T*, float2*, float*, int, int, cudaStream_t);      \
+  template cudaError_t launch_head_infer<T>(const float*, const T*, float, float, float*, float*, unsigned char*,  \
+                                            int, int, cudaStream_t);
+
+SCW_FNO_INSTANTIATE(float)
+SCW_FNO_INSTANTIATE(__nv_bfloat16)
+
+}  // namespace fno
+}  // namespace scw

@@ -132,7 +132,7 @@ static scw_status validate_desc(const scw_desc* d) {
   return SCW_OK;
 }
 
-static scw_status check_device() {
+scw_status check_device() {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_error(e, "cudaGetDevice");

@@ -144,6 +144,7 @@ cudaError_t allow_max_smem(const void* kernel);
 // error reporting (thread-local message)
 scw_status set_error(scw_status s, const std::string& msg);
 scw_status cuda_error(cudaError_t e, const char* what);
+scw_status check_device();  // SCW_OK on an sm_103 device
 
 // launchers (host side), each returns cudaSuccess or the launch error
 cudaError_t launch_convert_tiled(const float2* W, void* hi, void* lo, int L, int M, bool bf16_split, cudaStream_t st);

@@ -1,4 +1,4 @@
-// Thin inline-PTX wrappers for sm_103a: mbarrier, TMA bulk tensor copies and
+// Thin inline-PTX wrappers for sm_103a: mbarrier, TMA bulk and tensor copies and
 // the tcgen05 tensor-core / tensor-memory instructions. Every wait is bounded
 // by a %globaltimer deadline and reports failure instead of spinning forever.
 #pragma once
@@ -56,15 +56,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
   }
 }
 
-// 3D tiled TMA load global -> shared, completion signalled on `bar`.
-// c0 is the innermost (contiguous) coordinate; callers keep c0 * elem_size a
-// multiple of 16 bytes.
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
-                                            uint32_t bar) {
+// 2D tiled TMA load global -> shared (box of the tensor map), completion
+// signalled on `bar`. c0 is the innermost (contiguous) coordinate; callers keep
+// c0 * element size a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int c0, int c1, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
       : "memory");
 }
 
