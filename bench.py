@@ -46,6 +46,14 @@ def peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+def bf16_sustained():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops_sustained"])
+    except Exception:
+        return 1700.0
+
+
 def geometry():
     zb = np.arange(L_LAYERS + 1) * DZ
     Fz = L_LAYERS * PLANES_PER_LAYER
@@ -235,6 +243,72 @@ def run_sweep(args, dev, world, peaks_hbm):
     return res
 
 
+def run_surrogate(args, dev, bf16_peaks):
+    """Learned surrogate at its full size: 4 Fourier layers of width 32, 16x16
+    kept modes on a 64x64 grid, inputs 8 slices of 32x32 complex n (seeded
+    ellipsoid phantoms), targets complex exit-plane fields [3][64][64] (random
+    values of that shape: throughput does not depend on them). Times one Adam
+    training step and one inference call per batch through the C ABI."""
+    import torch
+    import paper_2404_07293_gb300 as scw
+    import workloads as wl
+    B = args.fno_batch
+    n = torch.from_numpy(wl.phantom_batch(77, B).astype(np.complex64)).to(dev)
+    g = torch.Generator(device=dev)
+    g.manual_seed(5)
+    target = torch.randn((B, 3, 64, 64), dtype=torch.complex64, device=dev, generator=g)
+    s = scw.Surrogate(grid=64, modes=16, layers=4, slices=8, in_grid=32, batch_max=B, precision="bf16", seed=1)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(3, args.warmup)):
+        s.train_step(n, target, lr=1e-4, read_loss=False)
+    steps = max(3, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        s.train_step(n, target, lr=1e-4, read_loss=False)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    train_ms = e0.elapsed_time(e1) / steps
+    loss = s.train_step(n, target, lr=1e-4)
+    field = torch.empty((B, 3, 64, 64), dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        s.infer(n, field=field)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for _ in range(steps):
+        s.infer(n, field=field)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    infer_ms = e0.elapsed_time(e1) / steps
+    launches = s.launches()
+    # per-family breakdown of the training step (events between launches)
+    s.enable_timing(True)
+    for _ in range(3):
+        s.train_step(n, target, lr=1e-4, read_loss=False)
+    t = s.timings()
+    s.enable_timing(False)
+    calls = max(1, t["calls"])
+    fam = {k: t[k + "_ms"] / calls for k in ("dft", "layer", "dw", "mix", "other")}
+    tf = {k: (t[k + "_flops"] / calls) / (fam[k] * 1e-3) / 1e12 for k in ("dft", "layer", "dw") if fam[k] > 0}
+    dom = max(("dft", "layer"), key=lambda k: fam[k])
+    peak = bf16_peaks[1]
+    s.close()
+    return {
+        "workload": "fno_4_layers_width_32_modes_16x16_grid_64x64_from_8x32x32", "batch": B,
+        "train_samples_per_s": B / (train_ms * 1e-3), "train_ms_per_step": train_ms,
+        "infer_samples_per_s": B / (infer_ms * 1e-3), "infer_ms_per_batch": infer_ms,
+        "loss_after": [float(x) for x in loss],
+        "kernel_ms_per_train_step": fam, "tflops": tf,
+        "roofline": {"kernel": "gemm_tc_kernel (" + {"dft": "truncated DFT", "layer": "inverse DFT + 1x1 conv"}[dom]
+                     + ")", "bound": "tensor", "achieved": tf[dom], "peak": peak, "unit": "TFLOP/s",
+                     "frac": tf[dom] / peak, "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured; fallback 1700 if absent)"},
+        "gpu_launches": {"train_step": launches["train_step"], "infer": launches["infer"]},
+        "dtype": "bf16 activations and weights, fp32 accumulation and master weights",
+    }
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2404_07293_gb300 as scw
@@ -398,6 +472,11 @@ def run_ours(args, world, rank, local):
         torch.cuda.empty_cache()
         sweep = run_sweep(args, dev, world, hbm)
 
+    surrogate = None
+    if not args.no_surrogate:
+        torch.cuda.empty_cache()
+        surrogate = run_surrogate(args, dev, (bf16_tf, bf16_sustained()))
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         rate, n, dt = oracle_sample_rate(W.astype(np.complex128), g, a, zb, zp, seconds=args.cpu_seconds)
@@ -434,6 +513,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu,
             "variants": variants or None,
             "sweep": sweep,
+            "surrogate": surrogate,
         }
         print(json.dumps(line), flush=True)
     plan.close()
@@ -456,6 +536,8 @@ def main():
     ap.add_argument("--compare", action="store_true", help="also time the other contraction precisions")
     ap.add_argument("--no-sweep", action="store_true", help="skip the batched spectroscopic sweep")
     ap.add_argument("--sweep-items", type=int, default=128)
+    ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate block")
+    ap.add_argument("--fno-batch", type=int, default=256)
     ap.add_argument("--layers", type=int, default=32)
     ap.add_argument("--pipeline", type=int, default=1, help="layer groups overlapped in graph replay")
     ap.add_argument("--planes-per-layer", type=int, default=8)

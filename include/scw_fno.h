@@ -108,6 +108,22 @@ scw_status scw_surrogate_calibrate(scw_fno_t fno, const float* est, const float*
                                    float* q_out);
 scw_status scw_surrogate_set_offset(scw_fno_t fno, float q);
 
+/* Per-kernel timing: while on, every call records a CUDA event after each of its
+ * launches and synchronises its stream at the end; times (ms, summed since the
+ * last enable) and algorithmic FLOPs accumulate per kernel family:
+ *   dft    truncated-DFT GEMMs (tensor cores in BF16 mode), forward and backward
+ *   layer  inverse-DFT + 1x1-convolution GEMMs with their fused epilogues
+ *   dw     weight-gradient GEMMs
+ *   mix    per-mode complex mixing, forward and backward
+ *   other  lift, projection, loss, head, reductions, Adam */
+typedef struct {
+  int calls;
+  double dft_ms, layer_ms, dw_ms, mix_ms, other_ms, total_ms;
+  double dft_flops, layer_flops, dw_flops, mix_flops;
+} scw_fno_times;
+scw_status scw_surrogate_enable_timing(scw_fno_t fno, int on);
+scw_status scw_surrogate_get_timings(scw_fno_t fno, scw_fno_times* out);
+
 /* Kernel launches of one train_step / infer call at batch B (for accounting). */
 scw_status scw_surrogate_launches(scw_fno_t fno, int* train_step, int* infer);
 

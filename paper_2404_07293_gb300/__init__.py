@@ -13,7 +13,7 @@ import ctypes
 import numpy as np
 
 from ._lib import (FLAG_AUTOTUNE, FLAG_EXTERIOR, FLAG_HOST_IO, FNO_PRECISION, PRECISION, ScwDesc, ScwError,
-                   ScwFnoDesc, ScwKernelTimes, ScwPlanInfo, check, load)
+                   ScwFnoDesc, ScwFnoTimes, ScwKernelTimes, ScwPlanInfo, check, load)
 
 __all__ = ["Plan", "BatchedPlan", "Surrogate", "ScwError", "load", "PRECISION"]
 
@@ -349,6 +349,14 @@ class Surrogate:
 
     def set_offset(self, q: float):
         check(self._lib.scw_surrogate_set_offset(self._h, float(q)), "scw_surrogate_set_offset")
+
+    def enable_timing(self, on=True):
+        check(self._lib.scw_surrogate_enable_timing(self._h, 1 if on else 0), "scw_surrogate_enable_timing")
+
+    def timings(self) -> dict:
+        t = ScwFnoTimes()
+        check(self._lib.scw_surrogate_get_timings(self._h, ctypes.byref(t)), "scw_surrogate_get_timings")
+        return {k: getattr(t, k) for k, _ in ScwFnoTimes._fields_}
 
     def launches(self) -> dict:
         a, b = ctypes.c_int(), ctypes.c_int()

@@ -45,6 +45,12 @@ class ScwFnoDesc(ctypes.Structure):
 FNO_PRECISION = {"bf16": 0, "fp32": 1}
 
 
+class ScwFnoTimes(ctypes.Structure):
+    _fields_ = [("calls", c_int), ("dft_ms", c_double), ("layer_ms", c_double), ("dw_ms", c_double),
+                ("mix_ms", c_double), ("other_ms", c_double), ("total_ms", c_double), ("dft_flops", c_double),
+                ("layer_flops", c_double), ("dw_flops", c_double), ("mix_flops", c_double)]
+
+
 class ScwKernelTimes(ctypes.Structure):
     _fields_ = [("calls", c_int), ("phases_ms", c_double), ("contract_ms", c_double), ("recompose_ms", c_double),
                 ("xpass_ms", c_double), ("ypass_ms", c_double), ("total_ms", c_double)]
@@ -84,6 +90,8 @@ SIGNATURES = {
     "scw_surrogate_calibrate": (c_int, [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p]),
     "scw_surrogate_set_offset": (c_int, [c_void_p, ctypes.c_float]),
     "scw_surrogate_launches": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
+    "scw_surrogate_enable_timing": (c_int, [c_void_p, c_int]),
+    "scw_surrogate_get_timings": (c_int, [c_void_p, POINTER(ScwFnoTimes)]),
     "scw_status_string": (c_char_p, [c_int]),
     "scw_last_error": (c_char_p, []),
     "scw_version": (c_int, []),

@@ -35,8 +35,9 @@ struct scw_fno_s {
   void* Vcf[9] = {};        // [Bmax][C][P]
   void* Vcl[9] = {};        // [Bmax][P][C]
   void* Zcl[8] = {};        // [Bmax][P][C]
-  float* Vh[8] = {};        // [kMaxSplit][Bmax C][Kc]
+  float* Vh[8] = {};        // complex [kMaxSplit][Kc/2][Bmax C] (mode-major)
   float* GWh = nullptr;     // same shape as one Vh
+  void* WT = nullptr;       // [L][C][C]: W_l transposed (tensor-core operand of the backward 1x1)
   void* Wh = nullptr;       // [Bmax C][Kp]
   void* GVh = nullptr;
   void* dZcf[2] = {};
@@ -49,15 +50,26 @@ struct scw_fno_s {
   uint64_t timeout_ns = 2000000000ull;
 
   CUtensorMap map_Vcf[9], map_dZcf[2], map_D, map_E, map_Wh, map_GVh;
+  CUtensorMap map_Vcl[8], map_dZcl[2], map_W[8], map_WT[8];  // 1x1-convolution operands (64-byte swizzle)
 
   std::vector<void*> allocs;
   size_t bytes = 0;
   int launches_train = 0, launches_infer = 0;
   int counter = 0;  // launches of the current call
+
+  // per-kernel timing (scw_surrogate_enable_timing): one event after every launch
+  bool timing = false;
+  std::vector<cudaEvent_t> events;
+  std::vector<int> cats;
+  std::vector<double> flops;
+  cudaStream_t tstream = nullptr;
+  double acc_ms[5] = {}, acc_flops[5] = {};
+  int timed_calls = 0;
 };
 
+enum { CAT_DFT = 0, CAT_LAYER = 1, CAT_DW = 2, CAT_MIX = 3, CAT_OTHER = 4 };
+
 static constexpr int kMaxSplit = 8;
-static constexpr int kMixBlocks = 8;
 
 static cudaError_t falloc(scw_fno_s* f, void** p, size_t bytes) {
   *p = nullptr;
@@ -73,6 +85,8 @@ static cudaError_t falloc(scw_fno_s* f, void** p, size_t bytes) {
 static void free_all(scw_fno_s* f) {
   for (void* p : f->allocs) cudaFree(p);
   f->allocs.clear();
+  for (cudaEvent_t ev : f->events) cudaEventDestroy(ev);
+  f->events.clear();
 }
 
 // splitmix64 (Steele, Lea and Flood 2014): counter-based uniform draws
@@ -102,9 +116,54 @@ static int dw_splits(const scw_fno_s* f, int B) {
 
 static int dft_bn(const scw_fno_s* f) { return f->Kc >= 256 ? 256 : (f->Kc >= 128 ? 128 : (f->Kc >= 64 ? 64 : 32)); }
 
-static scw_status launch_ok(scw_fno_s* f, cudaError_t e, const char* what) {
+// record timing event i (created on first use)
+static cudaError_t mark(scw_fno_s* f, size_t i) {
+  while (i >= f->events.size()) {
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreate(&ev);
+    if (e != cudaSuccess) return e;
+    f->events.push_back(ev);
+  }
+  return cudaEventRecord(f->events[i], f->tstream);
+}
+
+static scw_status launch_ok(scw_fno_s* f, cudaError_t e, const char* what, int cat = CAT_OTHER, double flops = 0) {
+  if (e != cudaSuccess) return cuda_error(e, what);
   ++f->counter;
-  return e == cudaSuccess ? SCW_OK : cuda_error(e, what);
+  if (f->timing) {
+    f->cats.push_back(cat);
+    f->flops.push_back(flops);
+    e = mark(f, f->cats.size());
+    if (e != cudaSuccess) return cuda_error(e, "timing event");
+  }
+  return SCW_OK;
+}
+
+static scw_status begin_call(scw_fno_s* f, cudaStream_t st) {
+  f->counter = 0;
+  if (!f->timing) return SCW_OK;
+  f->tstream = st;
+  f->cats.clear();
+  f->flops.clear();
+  // event 0 marks the start; timed launch i ends at event i + 1
+  cudaError_t e = mark(f, 0);
+  if (e != cudaSuccess) return cuda_error(e, "timing event");
+  return SCW_OK;
+}
+
+static scw_status end_call(scw_fno_s* f) {
+  if (!f->timing) return SCW_OK;
+  cudaError_t e = cudaEventSynchronize(f->events[f->cats.size()]);
+  if (e != cudaSuccess) return cuda_error(e, "timing sync");
+  for (size_t i = 0; i < f->cats.size(); ++i) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, f->events[i], f->events[i + 1]);
+    if (e != cudaSuccess) return cuda_error(e, "timing read");
+    f->acc_ms[f->cats[i]] += ms;
+    f->acc_flops[f->cats[i]] += f->flops[i];
+  }
+  ++f->timed_calls;
+  return SCW_OK;
 }
 
 #define FNO_TRY(expr)              \
@@ -118,6 +177,14 @@ static T* at(void* base, long long off) {
   return static_cast<T*>(base) + off;
 }
 
+// W^T copies for the backward 1x1 convolution on the tensor cores (BF16 mode)
+static cudaError_t refresh_wt(scw_fno_s* f, cudaStream_t st) {
+  if (!f->bf16) return cudaSuccess;
+  const long long stride = f->L > 1 ? f->off_W[1] - f->off_W[0] : 0;
+  return launch_transpose_w<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(f->wcopy), f->off_W[0], stride,
+                                           static_cast<__nv_bfloat16*>(f->WT), f->L, st);
+}
+
 // ---------------------------------------------------------------- forward ---
 template <typename T>
 static scw_status forward(scw_fno_s* f, const float2* n, int B, bool keep_z, cudaStream_t st) {
@@ -125,7 +192,9 @@ static scw_status forward(scw_fno_s* f, const float2* n, int B, bool keep_z, cud
   FNO_TRY(launch_ok(f, launch_lift<T>(n, at<T>(f->wcopy, f->off_P), static_cast<T*>(f->Vcf[0]),
                                       static_cast<T*>(f->Vcl[0]), B, f->S, f->in_grid, f->N, st),
                     "lift"));
-  const long long vstride = (long long)f->Bmax * C * f->Kc;
+  const long long ld = (long long)f->Bmax * C;                // complex elements per mode
+  const long long vstride = ld * (f->Kc / 2);                 // complex elements per split
+  const float inv_n2 = 1.f / ((float)f->N * (float)f->N);
   for (int l = 0; l < f->L; ++l) {
     const int bn = dft_bn(f);
     const int ks = dft_splits(f, B, bn);
@@ -134,18 +203,20 @@ static scw_status forward(scw_fno_s* f, const float2* n, int B, bool keep_z, cud
     ea.rows = BC;
     ea.cols = f->Kc;
     ea.out = f->Vh[l];
-    ea.ld = f->Kc;
+    ea.ld = ld;
     ea.split_stride = vstride;
-    cudaError_t e = f->bf16 ? launch_gemm_tc(EPI_ROWS_F32, bn, f->map_Vcf[l], f->map_D, ea, BC, f->Kc, f->P, ks,
-                                             f->d_err, f->timeout_ns, st)
-                            : launch_gemm_simt(EPI_ROWS_F32, static_cast<const float*>(f->Vcf[l]), f->P,
+    cudaError_t e = f->bf16 ? launch_gemm_tc(EPI_MODES, bn, f->map_Vcf[l], f->map_D, f->map_D, f->map_D, ea, BC,
+                                             f->Kc, f->P, ks, f->d_err, f->timeout_ns, st)
+                            : launch_gemm_simt(EPI_MODES, static_cast<const float*>(f->Vcf[l]), f->P,
                                                static_cast<const float*>(f->D), f->P, ea, BC, f->Kc, f->P, ks, st);
-    FNO_TRY(launch_ok(f, e, "truncated DFT"));
-    FNO_TRY(launch_ok(f, launch_mix_fwd<T>(f->Vh[l], ks, vstride, at<T>(f->wcopy, f->off_R[l]),
-                                           static_cast<T*>(f->Wh), B, f->m, f->Kc, f->Kp, st),
-                      "mode mixing"));
+    FNO_TRY(launch_ok(f, e, "truncated DFT", CAT_DFT, 2.0 * BC * f->Kc * f->P));
+    // Wh carries the inverse transform's 1/N^2 so that the 1x1 convolution can share its accumulator
+    FNO_TRY(launch_ok(f, launch_mix_fwd<T>(reinterpret_cast<const float2*>(f->Vh[l]), ks, vstride, ld,
+                                           at<T>(f->wcopy, f->off_R[l]), static_cast<T*>(f->Wh), inv_n2, B, f->m,
+                                           f->Kp, st),
+                      "mode mixing", CAT_MIX, 8.0 * f->m * f->m * C * C * B));
     EpiArgs eb{};
-    eb.alpha = 1.f / ((float)f->N * (float)f->N);
+    eb.alpha = 1.f;
     eb.rows = f->P;
     eb.cols = BC;
     eb.P = f->P;
@@ -157,11 +228,11 @@ static scw_status forward(scw_fno_s* f, const float2* n, int B, bool keep_z, cud
     eb.out_cf = f->Vcf[l + 1];
     eb.out_cl = f->Vcl[l + 1];
     eb.gelu = l < f->L - 1 ? 1 : 0;
-    e = f->bf16 ? launch_gemm_tc(EPI_LAYER_FWD, 256, f->map_E, f->map_Wh, eb, f->P, BC, f->Kp, 1, f->d_err,
-                                 f->timeout_ns, st)
+    e = f->bf16 ? launch_gemm_tc(EPI_LAYER_FWD, 256, f->map_E, f->map_Wh, f->map_Vcl[l], f->map_W[l], eb, f->P, BC,
+                                 f->Kp, 1, f->d_err, f->timeout_ns, st)
                 : launch_gemm_simt(EPI_LAYER_FWD, static_cast<const float*>(f->E), f->Kp,
                                    static_cast<const float*>(f->Wh), f->Kp, eb, f->P, BC, f->Kp, 1, st);
-    FNO_TRY(launch_ok(f, e, "inverse DFT + 1x1 convolution"));
+    FNO_TRY(launch_ok(f, e, "inverse DFT + 1x1 convolution", CAT_LAYER, 2.0 * f->P * BC * (f->Kc + C)));
   }
   return SCW_OK;
 }
@@ -192,7 +263,8 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
   FNO_TRY(launch_ok(f, launch_head<T>(f->part_tn, f->part_err, f->part_pool, at<T>(f->wcopy, f->off_e),
                                       f->grad + f->off_e, f->loss_d, f->h_d, f->rel2_d, B, P, 1, st),
                     "error head"));
-  const long long vstride = (long long)f->Bmax * C * f->Kc;
+  const long long ld = (long long)f->Bmax * C;
+  const long long vstride = ld * (f->Kc / 2);
   const long long mix_w = (long long)f->m * f->m * C * C * 2;
   int cur = 0;
   for (int l = f->L - 1; l >= 0; --l) {
@@ -203,13 +275,13 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     ea.rows = BC;
     ea.cols = f->Kc;
     ea.out = f->GWh;
-    ea.ld = f->Kc;
+    ea.ld = ld;
     ea.split_stride = vstride;
-    e = f->bf16 ? launch_gemm_tc(EPI_ROWS_F32, bn, f->map_dZcf[cur], f->map_D, ea, BC, f->Kc, P, ks, f->d_err,
-                                 f->timeout_ns, st)
-                : launch_gemm_simt(EPI_ROWS_F32, static_cast<const float*>(f->dZcf[cur]), P,
+    e = f->bf16 ? launch_gemm_tc(EPI_MODES, bn, f->map_dZcf[cur], f->map_D, f->map_D, f->map_D, ea, BC, f->Kc, P, ks,
+                                 f->d_err, f->timeout_ns, st)
+                : launch_gemm_simt(EPI_MODES, static_cast<const float*>(f->dZcf[cur]), P,
                                    static_cast<const float*>(f->D), P, ea, BC, f->Kc, P, ks, st);
-    FNO_TRY(launch_ok(f, e, "truncated DFT of dZ"));
+    FNO_TRY(launch_ok(f, e, "truncated DFT of dZ", CAT_DFT, 2.0 * BC * f->Kc * P));
     // dW_l = sum_b dZ_b V_b^T
     const int kw = dw_splits(f, B);
     const int groups = (B + 3) / 4;
@@ -218,17 +290,19 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     ew.B = B;
     ew.out = f->part_dw;
     ew.splits = kw;
-    e = f->bf16 ? launch_gemm_tc(EPI_DW, 128, f->map_dZcf[cur], f->map_Vcf[l], ew, groups * 128, groups * 128, P, kw,
-                                 f->d_err, f->timeout_ns, st)
+    e = f->bf16 ? launch_gemm_tc(EPI_DW, 128, f->map_dZcf[cur], f->map_Vcf[l], f->map_D, f->map_D, ew, groups * 128,
+                                 groups * 128, P, kw, f->d_err, f->timeout_ns, st)
                 : launch_gemm_simt(EPI_DW, static_cast<const float*>(f->dZcf[cur]), P,
                                    static_cast<const float*>(f->Vcf[l]), P, ew, groups * 128, groups * 128, P, kw, st);
-    FNO_TRY(launch_ok(f, e, "weight gradient"));
+    FNO_TRY(launch_ok(f, e, "weight gradient", CAT_DW, 2.0 * BC * C * P));
     FNO_TRY(reduce_into(f, f->part_dw, groups * kw * 4, C * C, C * C, f->grad + f->off_W[l], st));
     // mixing backward
-    const int sb = std::min(kMixBlocks, std::max(1, (B + 31) / 32));
-    FNO_TRY(launch_ok(f, launch_mix_bwd<T>(f->GWh, f->Vh[l], ks, vstride, at<T>(f->wcopy, f->off_R[l]),
-                                           static_cast<T*>(f->GVh), f->part_mix, sb, B, f->m, f->Kc, f->Kp, f->N, st),
-                      "mode mixing backward"));
+    const int sb = mix_sample_blocks(B);
+    FNO_TRY(launch_ok(f, launch_mix_bwd<T>(reinterpret_cast<const float2*>(f->GWh),
+                                           reinterpret_cast<const float2*>(f->Vh[l]), ks, vstride, ld,
+                                           at<T>(f->wcopy, f->off_R[l]), static_cast<T*>(f->GVh), f->part_mix, B,
+                                           f->m, f->Kp, f->N, st),
+                      "mode mixing backward", CAT_MIX, 16.0 * f->m * f->m * C * C * B));
     FNO_TRY(reduce_into(f, f->part_mix, sb, (int)mix_w, mix_w + C, f->grad + f->off_R[l], st));
     FNO_TRY(reduce_into(f, f->part_mix + mix_w, sb, C, mix_w + C, f->grad + f->off_c[l], st));
     // dV_l = Re IDFT(GVh) + W^T dZ, times GELU'(Z_{l-1})
@@ -243,11 +317,11 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     eb.z_in = l > 0 ? f->Zcl[l - 1] : nullptr;
     eb.out_cf = f->dZcf[1 - cur];
     eb.out_cl = l > 0 ? f->dZcl[1 - cur] : nullptr;
-    e = f->bf16 ? launch_gemm_tc(EPI_LAYER_BWD, 256, f->map_E, f->map_GVh, eb, P, BC, f->Kp, 1, f->d_err,
-                                 f->timeout_ns, st)
+    e = f->bf16 ? launch_gemm_tc(EPI_LAYER_BWD, 256, f->map_E, f->map_GVh, f->map_dZcl[cur], f->map_WT[l], eb, P, BC,
+                                 f->Kp, 1, f->d_err, f->timeout_ns, st)
                 : launch_gemm_simt(EPI_LAYER_BWD, static_cast<const float*>(f->E), f->Kp,
                                    static_cast<const float*>(f->GVh), f->Kp, eb, P, BC, f->Kp, 1, st);
-    FNO_TRY(launch_ok(f, e, "layer backward"));
+    FNO_TRY(launch_ok(f, e, "layer backward", CAT_LAYER, 2.0 * P * BC * (f->Kc + C)));
     cur = 1 - cur;
   }
   FNO_TRY(launch_ok(f, launch_lift_bwd<T>(static_cast<const T*>(f->dZcf[cur]), n, f->part_lift, B, f->S, f->in_grid,
@@ -374,7 +448,8 @@ scw_status scw_surrogate_create(const scw_fno_desc* d, scw_fno_t* out) {
   A((void**)&f->part_err, Bm * f->nblk * 4);
   A((void**)&f->part_pool, Bm * f->nblk * C * 4);
   A((void**)&f->part_proj, Bm * f->nblk * (OUT * C + OUT) * 4);
-  A((void**)&f->part_mix, (size_t)kMixBlocks * ((size_t)f->m * f->m * C * C * 2 + C) * 4);
+  A((void**)&f->part_mix, (size_t)mix_sample_blocks(f->Bmax) * ((size_t)f->m * f->m * C * C * 2 + C) * 4);
+  A(&f->WT, (size_t)f->L * C * C * esz);
   A((void**)&f->part_dw, ((Bm + 3) / 4) * kMaxSplit * 4 * C * C * 4);
   A((void**)&f->part_lift, ((Bm * f->in_grid * f->in_grid + 127) / 128) * (C * 2 * f->S + C) * 4);
   A((void**)&f->scratch, (size_t)64 * 4096 * 4);
@@ -416,6 +491,7 @@ scw_status scw_surrogate_create(const scw_fno_desc* d, scw_fno_t* out) {
   if (e == cudaSuccess)
     e = f->bf16 ? launch_copy_params<__nv_bfloat16>(f->master, static_cast<__nv_bfloat16*>(f->wcopy), f->n_params, st)
                 : launch_copy_params<float>(f->master, static_cast<float*>(f->wcopy), f->n_params, st);
+  if (e == cudaSuccess) e = refresh_wt(f, st);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_all(f);
@@ -430,6 +506,15 @@ scw_status scw_surrogate_create(const scw_fno_desc* d, scw_fno_t* out) {
     if (s == SCW_OK) s = make_map_bf16(&f->map_GVh, f->GVh, f->Kp, BCm, f->Kp, 256);
     for (int l = 0; l <= f->L && s == SCW_OK; ++l) s = make_map_bf16(&f->map_Vcf[l], f->Vcf[l], f->P, BCm, f->P, 128);
     for (int i = 0; i < 2 && s == SCW_OK; ++i) s = make_map_bf16(&f->map_dZcf[i], f->dZcf[i], f->P, BCm, f->P, 128);
+    const long long BPm = (long long)f->Bmax * f->P;
+    for (int l = 0; l < f->L && s == SCW_OK; ++l) {
+      s = make_map_bf16(&f->map_Vcl[l], f->Vcl[l], C, BPm, C, 128, 32);
+      if (s == SCW_OK)
+        s = make_map_bf16(&f->map_W[l], static_cast<__nv_bfloat16*>(f->wcopy) + f->off_W[l], C, C, C, C, 32);
+      if (s == SCW_OK)
+        s = make_map_bf16(&f->map_WT[l], static_cast<__nv_bfloat16*>(f->WT) + (size_t)l * C * C, C, C, C, C, 32);
+    }
+    for (int i = 0; i < 2 && s == SCW_OK; ++i) s = make_map_bf16(&f->map_dZcl[i], f->dZcl[i], C, BPm, C, 128, 32);
     if (s != SCW_OK) {
       free_all(f);
       delete f;
@@ -462,6 +547,7 @@ scw_status scw_surrogate_set_params(scw_fno_t f, const float* host, size_t count
   if (e == cudaSuccess)
     e = f->bf16 ? launch_copy_params<__nv_bfloat16>(f->master, static_cast<__nv_bfloat16*>(f->wcopy), f->n_params, 0)
                 : launch_copy_params<float>(f->master, static_cast<float*>(f->wcopy), f->n_params, 0);
+  if (e == cudaSuccess) e = refresh_wt(f, 0);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_error(e, "set_params");
   f->step = 0;
@@ -491,13 +577,14 @@ scw_status scw_surrogate_forward_backward(scw_fno_t f, const void* n, const void
   FNO_TRY(check_batch(f, n, B));
   if (!target) return set_error(SCW_ERR_INVALID_ARGUMENT, "target is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  f->counter = 0;
+  FNO_TRY(begin_call(f, st));
   scw_status s = f->bf16 ? forward_backward<__nv_bfloat16>(f, static_cast<const float2*>(n),
                                                           static_cast<const float2*>(target), B, st)
                          : forward_backward<float>(f, static_cast<const float2*>(n), static_cast<const float2*>(target),
                                                    B, st);
   f->launches_train = f->counter;
   if (s != SCW_OK) return s;
+  FNO_TRY(end_call(f));
   return read_loss(f, loss, st);
 }
 
@@ -507,7 +594,7 @@ scw_status scw_surrogate_train_step(scw_fno_t f, const void* n, const void* targ
   if (!target) return set_error(SCW_ERR_INVALID_ARGUMENT, "target is NULL");
   if (!(lr >= 0.f)) return set_error(SCW_ERR_INVALID_ARGUMENT, "lr must be >= 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  f->counter = 0;
+  FNO_TRY(begin_call(f, st));
   scw_status s = f->bf16 ? forward_backward<__nv_bfloat16>(f, static_cast<const float2*>(n),
                                                           static_cast<const float2*>(target), B, st)
                          : forward_backward<float>(f, static_cast<const float2*>(n), static_cast<const float2*>(target),
@@ -521,7 +608,9 @@ scw_status scw_surrogate_train_step(scw_fno_t f, const void* n, const void* targ
                           : launch_adam<float>(f->master, f->grad, f->adam_m, f->adam_v, static_cast<float*>(f->wcopy),
                                                f->n_params, lr, bc1, bc2, st);
   FNO_TRY(launch_ok(f, e, "Adam"));
+  if (f->bf16) FNO_TRY(launch_ok(f, refresh_wt(f, st), "W transpose"));
   f->launches_train = f->counter;
+  FNO_TRY(end_call(f));
   return read_loss(f, loss, st);
 }
 
@@ -531,13 +620,14 @@ scw_status scw_surrogate_infer(scw_fno_t f, const void* n, int B, void* field, f
   if (!field) return set_error(SCW_ERR_INVALID_ARGUMENT, "field is NULL");
   if ((reinterpret_cast<uintptr_t>(field) & 7u) != 0) return set_error(SCW_ERR_INVALID_ARGUMENT, "field must be 8-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  f->counter = 0;
+  FNO_TRY(begin_call(f, st));
   scw_status s = f->bf16 ? infer_t<__nv_bfloat16>(f, static_cast<const float2*>(n), B, static_cast<float2*>(field),
                                                  est_err, need_fallback, threshold, st)
                          : infer_t<float>(f, static_cast<const float2*>(n), B, static_cast<float2*>(field), est_err,
                                           need_fallback, threshold, st);
   f->launches_infer = f->counter;
-  return s;
+  if (s != SCW_OK) return s;
+  return end_call(f);
 }
 
 scw_status scw_surrogate_calibrate(scw_fno_t f, const float* est, const float* true_err, int count, float miss,
@@ -561,6 +651,31 @@ scw_status scw_surrogate_calibrate(scw_fno_t f, const float* est, const float* t
 scw_status scw_surrogate_set_offset(scw_fno_t f, float q) {
   if (!f) return set_error(SCW_ERR_INVALID_ARGUMENT, "handle is NULL");
   f->q_cal = q;
+  return SCW_OK;
+}
+
+scw_status scw_surrogate_enable_timing(scw_fno_t f, int on) {
+  if (!f) return set_error(SCW_ERR_INVALID_ARGUMENT, "handle is NULL");
+  f->timing = on != 0;
+  for (int c = 0; c < 5; ++c) f->acc_ms[c] = f->acc_flops[c] = 0;
+  f->timed_calls = 0;
+  return SCW_OK;
+}
+
+scw_status scw_surrogate_get_timings(scw_fno_t f, scw_fno_times* out) {
+  if (!f || !out) return set_error(SCW_ERR_INVALID_ARGUMENT, "handle and out are required");
+  out->calls = f->timed_calls;
+  out->dft_ms = f->acc_ms[CAT_DFT];
+  out->layer_ms = f->acc_ms[CAT_LAYER];
+  out->dw_ms = f->acc_ms[CAT_DW];
+  out->mix_ms = f->acc_ms[CAT_MIX];
+  out->other_ms = f->acc_ms[CAT_OTHER];
+  out->total_ms = 0;
+  for (int c = 0; c < 5; ++c) out->total_ms += f->acc_ms[c];
+  out->dft_flops = f->acc_flops[CAT_DFT];
+  out->layer_flops = f->acc_flops[CAT_LAYER];
+  out->dw_flops = f->acc_flops[CAT_DW];
+  out->mix_flops = f->acc_flops[CAT_MIX];
   return SCW_OK;
 }
 

@@ -4,19 +4,25 @@
 // (2D tensor maps, 64-element = 128-byte inner box, 128-byte swizzle, zero fill
 // out of bounds) into a ring of shared-memory stages; one thread issues
 // tcgen05.mma (kind::f16, M = 128, N = BN, K = 16) into an FP32 accumulator in
-// tensor memory; four epilogue warps read it back with tcgen05.ld (one TMEM lane
-// per thread = one row of D) and apply the epilogue 32 columns at a time.
+// tensor memory; eight epilogue warps read it back with tcgen05.ld (one TMEM lane
+// per thread = one row of D; two warps per 32-lane quadrant split the columns)
+// and apply the epilogue 32 columns at a time.
 //   warp 0 lane 0   TMA producer (full/empty mbarriers per stage)
 //   warp 1 lane 0   MMA issuer; commits each stage back to the producer
-//   warps 2-5       epilogue
+//   warps 2-9       epilogue
+// The layer products add the 1x1 convolution as a second K segment: for each
+// sample s of the tile, D[:, 32 s .. 32 s + 32) += X_s W^T (X_s = that sample's
+// channel-last activations of the tile's 128 pixels, K = 32, 64-byte swizzle,
+// N = 32 MMAs into the sample's own accumulator columns).
 // Every wait is bounded by a %globaltimer deadline; on timeout the CTA sets the
 // error word, lets issued copies and MMAs land, frees its tensor memory and exits.
 //
 // The products (N = pixels per sample, m = kept modes per axis, C = 32 channels):
-//   truncated DFT        Vh [B C][2 m^2]  = V_cf [B C][N^2] . D [2 m^2][N^2]^T     (EPI_ROWS_F32)
-//   inverse + 1x1 conv   Z^T [N^2][B C]   = E [N^2][Kp] . Wh [B C][Kp]^T, then
-//                        + W V + c and GELU in the epilogue                      (EPI_LAYER_FWD)
-//   backward of both     dV^T [N^2][B C]  = E . GVh^T, + W^T dZ, * GELU'(Z)     (EPI_LAYER_BWD)
+//   truncated DFT        Vh [B C][2 m^2]  = V_cf [B C][N^2] . D [2 m^2][N^2]^T, stored
+//                        mode-major as complex Vh[mode][B C]                     (EPI_MODES)
+//   inverse + 1x1 conv   Z^T [N^2][B C]   = E [N^2][Kp] . Wh [B C][Kp]^T + V_cl W^T,
+//                        then + c and GELU in the epilogue                       (EPI_LAYER_FWD)
+//   backward of both     dV^T [N^2][B C]  = E . GVh^T + dZ_cl W, * GELU'(Z)      (EPI_LAYER_BWD)
 //   weight gradient      dW = sum_b dZ_b V_b^T over pixels, 4 samples per tile  (EPI_DW)
 // SIMT form (FP32 test mode): the same products and the same epilogue code on
 // FP32 operands, 128 rows x 32 columns per CTA.
@@ -41,13 +47,19 @@ struct GemmCfg {
   static constexpr uint32_t TMEM_COLS = BN < 32 ? 32u : (uint32_t)BN;
 };
 
+constexpr int kGemmThreads = 320;
+constexpr uint32_t kSeg2Bytes = 128u * 64u + 32u * 64u;  // X_s tile + W tile (64-byte rows)
+
 template <int BN, int EPI>
-__global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CUtensorMap mA,
-                                                      const __grid_constant__ CUtensorMap mB,
-                                                      const __grid_constant__ EpiArgs ea, int K, int kper, int* err,
-                                                      uint64_t timeout_ns) {
+__global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_constant__ CUtensorMap mA,
+                                                                  const __grid_constant__ CUtensorMap mB,
+                                                                  const __grid_constant__ CUtensorMap mA2,
+                                                                  const __grid_constant__ CUtensorMap mW,
+                                                                  const __grid_constant__ EpiArgs ea, int K, int kper,
+                                                                  int* err, uint64_t timeout_ns) {
   using Cfg = GemmCfg<BN>;
   constexpr int STAGES = Cfg::STAGES;
+  constexpr bool SEG2 = (EPI == EPI_LAYER_FWD || EPI == EPI_LAYER_BWD);
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -64,12 +76,15 @@ __global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CU
   const int n0 = (EPI == EPI_DW) ? m0 : blockIdx.y * BN;
   const int kb0 = blockIdx.z * kper;
   const int nkb = max(0, min(K / 64 - kb0, kper));
+  // samples of this tile whose 1x1 convolution runs as a second K segment
+  const int nseg = SEG2 ? max(0, min(BN / C, ea.B - n0 / C)) : 0;
+  const int total = nkb + nseg;
   const uint64_t deadline = ptx::globaltimer() + timeout_ns;
 
-  if constexpr (EPI == EPI_LAYER_FWD || EPI == EPI_LAYER_BWD) {
+  if constexpr (SEG2) {
     const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(ea.w);
     const __nv_bfloat16* bias = static_cast<const __nv_bfloat16*>(ea.bias);
-    for (int i = threadIdx.x; i < C * C; i += blockDim.x) w_s[i] = __bfloat162float(w[i]);
+    (void)w;
     if (threadIdx.x < C) b_s[threadIdx.x] = bias ? __bfloat162float(bias[threadIdx.x]) : 0.f;
   }
   if (threadIdx.x == 0) {
@@ -83,6 +98,10 @@ __global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CU
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&mA);
     ptx::prefetch_tensormap(&mB);
+    if (SEG2 && nseg > 0) {
+      ptx::prefetch_tensormap(&mA2);
+      ptx::prefetch_tensormap(&mW);
+    }
   }
   if (warp == 0) {
     ptx::tmem_alloc(ptx::smem_u32(&tmem_base_s), Cfg::TMEM_COLS);
@@ -97,18 +116,26 @@ __global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CU
     // ---------------- TMA producer ----------------
     int st = 0, issued = 0;
     uint32_t ph = 0;
-    for (int i = 0; i < nkb && !abort_s; ++i) {
+    for (int i = 0; i < total && !abort_s; ++i) {
       if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[st]), ph ^ 1u, deadline)) {
         atomicOr(err, DEV_ERR_TIMEOUT_EMPTY);
         abort_s = 1;
         break;
       }
       const uint32_t fb = ptx::smem_u32(&full_bar[st]);
-      ptx::mbar_arrive_expect_tx(fb, Cfg::STAGE);
       const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE);
-      const int kc = (kb0 + i) * 64;
-      ptx::tma_load_2d(sa, &mA, kc, m0, fb);
-      ptx::tma_load_2d(sa + Cfg::A_BYTES, &mB, kc, n0, fb);
+      if (i < nkb) {
+        ptx::mbar_arrive_expect_tx(fb, Cfg::STAGE);
+        const int kc = (kb0 + i) * 64;
+        ptx::tma_load_2d(sa, &mA, kc, m0, fb);
+        ptx::tma_load_2d(sa + Cfg::A_BYTES, &mB, kc, n0, fb);
+      } else {
+        // X_s: rows (sample n0/C + s, pixels m0 .. m0 + 127) of the channel-last activations
+        const int smp = n0 / C + (i - nkb);
+        ptx::mbar_arrive_expect_tx(fb, kSeg2Bytes);
+        ptx::tma_load_2d(sa, &mA2, 0, smp * ea.P + m0, fb);
+        ptx::tma_load_2d(sa + Cfg::A_BYTES, &mW, 0, 0, fb);
+      }
       ++issued;
       if (++st == STAGES) {
         st = 0;
@@ -128,9 +155,10 @@ __global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CU
   } else if (warp == 1 && lane == 0) {
     // ---------------- tcgen05.mma issuer ----------------
     constexpr uint32_t idesc = ptx::idesc_f16(true, 128, BN);
+    constexpr uint32_t idesc32 = ptx::idesc_f16(true, 128, 32);
     int st = 0;
     uint32_t ph = 0;
-    for (int i = 0; i < nkb && !abort_s; ++i) {
+    for (int i = 0; i < total && !abort_s; ++i) {
       if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[st]), ph, deadline)) {
         atomicOr(err, DEV_ERR_TIMEOUT_FULL);
         abort_s = 1;
@@ -138,11 +166,21 @@ __global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CU
       }
       ptx::tc_fence_after();
       const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE);
-      const uint64_t da = ptx::sw128_desc(sa), db = ptx::sw128_desc(sa + Cfg::A_BYTES);
+      if (i < nkb) {
+        const uint64_t da = ptx::sw128_desc(sa), db = ptx::sw128_desc(sa + Cfg::A_BYTES);
 #pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        const uint64_t o = (uint64_t)(2 * kk);  // 16 elements = 32 bytes, in 16-byte units
-        ptx::mma_f16(tmem, da + o, db + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t o = (uint64_t)(2 * kk);  // 16 elements = 32 bytes, in 16-byte units
+          ptx::mma_f16(tmem, da + o, db + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        }
+      } else {
+        const uint64_t da = ptx::sw64_desc(sa), db = ptx::sw64_desc(sa + Cfg::A_BYTES);
+        const uint32_t d = tmem + (uint32_t)(C * (i - nkb));
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          const uint64_t o = (uint64_t)(2 * kk);
+          ptx::mma_f16(d, da + o, db + o, idesc32, (nkb > 0 || kk > 0) ? 1u : 0u);
+        }
       }
       ptx::mma_commit(ptx::smem_u32(&empty_bar[st]));
       if (++st == STAGES) {
@@ -159,7 +197,8 @@ __global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CU
     }
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int grp = warp & 3;  // TMEM lanes 32 grp .. 32 grp + 31
+    const int grp = warp & 3;         // TMEM lanes 32 grp .. 32 grp + 31
+    const int half = (warp - 2) >> 2;  // column chunks half, half + 2, ...
     bool ok = true;
     for (;;) {
       if (ptx::mbar_try_wait(ptx::smem_u32(&acc_bar), 0u)) break;
@@ -177,7 +216,7 @@ __global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CU
       const uint32_t lane_addr = tmem + ((uint32_t)(grp * 32) << 16);
       const int col_end = (EPI == EPI_DW) ? n0 + 128 : ea.cols;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = half; c < BN / 32; c += 2) {
         if (n0 + 32 * c >= col_end) break;  // warp-uniform
         uint32_t r0[8], r1[8], r2[8], r3[8];
         ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c), r0);
@@ -188,12 +227,12 @@ __global__ void __launch_bounds__(192) gemm_tc_kernel(const __grid_constant__ CU
         float acc[32];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          acc[j] = nkb > 0 ? __uint_as_float(r0[j]) : 0.f;
-          acc[8 + j] = nkb > 0 ? __uint_as_float(r1[j]) : 0.f;
-          acc[16 + j] = nkb > 0 ? __uint_as_float(r2[j]) : 0.f;
-          acc[24 + j] = nkb > 0 ? __uint_as_float(r3[j]) : 0.f;
+          acc[j] = total > 0 ? __uint_as_float(r0[j]) : 0.f;
+          acc[8 + j] = total > 0 ? __uint_as_float(r1[j]) : 0.f;
+          acc[16 + j] = total > 0 ? __uint_as_float(r2[j]) : 0.f;
+          acc[24 + j] = total > 0 ? __uint_as_float(r3[j]) : 0.f;
         }
-        epilogue<EPI, __nv_bfloat16>(ea, w_s, b_s, row, n0 + 32 * c, blockIdx.z, acc);
+        epilogue<EPI, __nv_bfloat16, SEG2>(ea, w_s, b_s, row, n0 + 32 * c, blockIdx.z, acc);
       }
     }
   }
@@ -251,13 +290,14 @@ __global__ void __launch_bounds__(128) gemm_simt_kernel(const float* __restrict_
     __syncthreads();
   }
   const int col_end = (EPI == EPI_DW) ? m0 + 128 : ea.cols;
-  if (n0 < col_end) epilogue<EPI, float>(ea, w_s, b_s, m0 + t, n0, blockIdx.z, acc);
+  if (n0 < col_end) epilogue<EPI, float, false>(ea, w_s, b_s, m0 + t, n0, blockIdx.z, acc);
 }
 
 // ---------------------------------------------------------------- host side ---
 template <int BN, int EPI>
-static cudaError_t launch_tc_t(const CUtensorMap& mA, const CUtensorMap& mB, const EpiArgs& ea, int M, int N, int K,
-                               int splits, int* err, uint64_t timeout_ns, cudaStream_t st) {
+static cudaError_t launch_tc_t(const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
+                               const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int splits, int* err,
+                               uint64_t timeout_ns, cudaStream_t st) {
   using Cfg = GemmCfg<BN>;
   const void* fn = reinterpret_cast<const void*>(gemm_tc_kernel<BN, EPI>);
   cudaError_t e = allow_max_smem(fn);
@@ -265,32 +305,38 @@ static cudaError_t launch_tc_t(const CUtensorMap& mA, const CUtensorMap& mB, con
   const int nkb = K / 64;
   const int kper = (nkb + splits - 1) / splits;
   const dim3 grid((M + 127) / 128, EPI == EPI_DW ? 1 : (N + BN - 1) / BN, splits);
-  gemm_tc_kernel<BN, EPI><<<grid, 192, Cfg::SMEM, st>>>(mA, mB, ea, K, kper, err, timeout_ns);
+  gemm_tc_kernel<BN, EPI><<<grid, kGemmThreads, Cfg::SMEM, st>>>(mA, mB, mA2, mW, ea, K, kper, err, timeout_ns);
   return cudaGetLastError();
 }
 
 template <int EPI>
-static cudaError_t launch_tc_bn(int BN, const CUtensorMap& mA, const CUtensorMap& mB, const EpiArgs& ea, int M,
-                                int N, int K, int splits, int* err, uint64_t timeout_ns, cudaStream_t st) {
+static cudaError_t launch_tc_bn(int BN, const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
+                                const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int splits, int* err,
+                                uint64_t timeout_ns, cudaStream_t st) {
   switch (BN) {
-    case 32: return launch_tc_t<32, EPI>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
-    case 64: return launch_tc_t<64, EPI>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
-    case 128: return launch_tc_t<128, EPI>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
-    case 256: return launch_tc_t<256, EPI>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
+    case 32: return launch_tc_t<32, EPI>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
+    case 64: return launch_tc_t<64, EPI>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
+    case 128: return launch_tc_t<128, EPI>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
+    case 256: return launch_tc_t<256, EPI>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtensorMap& mB, const EpiArgs& ea, int M,
-                           int N, int K, int splits, int* err, uint64_t timeout_ns, cudaStream_t st) {
+cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
+                           const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int splits, int* err,
+                           uint64_t timeout_ns, cudaStream_t st) {
   if (K % 64 != 0 || splits < 1) return cudaErrorInvalidValue;
-  if ((epi == EPI_LAYER_FWD || epi == EPI_LAYER_BWD) && splits != 1) return cudaErrorInvalidValue;
+  const bool layer = epi == EPI_LAYER_FWD || epi == EPI_LAYER_BWD;
+  // the 1x1 segment shares the accumulator: the DFT part must come pre-scaled (alpha 1)
+  if (layer && (splits != 1 || BN != 256 || ea.alpha != 1.0f)) return cudaErrorInvalidValue;
   switch (epi) {
-    case EPI_ROWS_F32: return launch_tc_bn<EPI_ROWS_F32>(BN, mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
-    case EPI_LAYER_FWD: return launch_tc_bn<EPI_LAYER_FWD>(BN, mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
-    case EPI_LAYER_BWD: return launch_tc_bn<EPI_LAYER_BWD>(BN, mA, mB, ea, M, N, K, splits, err, timeout_ns, st);
+    case EPI_MODES: return launch_tc_bn<EPI_MODES>(BN, mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
+    case EPI_LAYER_FWD:
+      return launch_tc_t<256, EPI_LAYER_FWD>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
+    case EPI_LAYER_BWD:
+      return launch_tc_t<256, EPI_LAYER_BWD>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
     case EPI_DW:
-      return BN == 128 ? launch_tc_t<128, EPI_DW>(mA, mB, ea, M, N, K, splits, err, timeout_ns, st)
+      return BN == 128 ? launch_tc_t<128, EPI_DW>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st)
                        : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
@@ -322,7 +368,7 @@ cudaError_t launch_gemm_simt(int epi, const float* A, long long lda, const float
   if (splits < 1) return cudaErrorInvalidValue;
   if ((epi == EPI_LAYER_FWD || epi == EPI_LAYER_BWD) && splits != 1) return cudaErrorInvalidValue;
   switch (epi) {
-    case EPI_ROWS_F32: return launch_simt_t<EPI_ROWS_F32>(A, lda, B, ldb, ea, M, N, K, splits, st);
+    case EPI_MODES: return launch_simt_t<EPI_MODES>(A, lda, B, ldb, ea, M, N, K, splits, st);
     case EPI_LAYER_FWD: return launch_simt_t<EPI_LAYER_FWD>(A, lda, B, ldb, ea, M, N, K, splits, st);
     case EPI_LAYER_BWD: return launch_simt_t<EPI_LAYER_BWD>(A, lda, B, ldb, ea, M, N, K, splits, st);
     case EPI_DW: return launch_simt_t<EPI_DW>(A, lda, B, ldb, ea, M, N, K, splits, st);
@@ -346,18 +392,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 scw_status make_map_bf16(CUtensorMap* m, const void* base, long long cols, long long rows, long long pitch,
-                         int box_rows) {
+                         int box_rows, int box_cols) {
   auto fn = encode_fn();
   if (!fn) return set_error(SCW_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  if ((reinterpret_cast<uintptr_t>(base) & 15u) || (pitch * 2) % 16 || box_rows < 1 || box_rows > 256)
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) || (pitch * 2) % 16 || box_rows < 1 || box_rows > 256 ||
+      (box_cols != 64 && box_cols != 32))
     return set_error(SCW_ERR_INVALID_ARGUMENT, "tensor map: base, pitch or box out of range");
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(pitch * 2)};
-  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1u, 1u};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                  CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(SCW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return SCW_OK;
 }

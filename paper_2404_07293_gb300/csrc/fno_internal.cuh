@@ -20,7 +20,8 @@ constexpr int PIX_BLOCK = 256;  // pixels per block of the per-pixel kernels (N*
 
 // GEMM epilogues. Rows / columns are those of the GEMM's D = A B^T.
 enum Epi : int {
-  EPI_ROWS_F32 = 0,   // D[row][col] * alpha -> FP32 out (+ split offset): truncated DFTs
+  EPI_MODES = 0,      // rows = (sample, channel), columns = (mode, re/im): alpha D -> mode-major complex
+                      // out[split][mode][row] (truncated DFTs)
   EPI_LAYER_FWD = 1,  // rows = pixels, columns = (sample, channel): Z = alpha D + c + W V; V' = GELU(Z)
   EPI_LAYER_BWD = 2,  // rows = pixels, columns = (sample, channel): dV = D + W^T dZ; dZ' = dV GELU'(Z)
   EPI_DW = 3          // rows = (sample, o), columns = (sample, i) of 4 samples: keep the diagonal blocks
@@ -32,9 +33,9 @@ struct EpiArgs {
   int cols;            // valid columns of D
   int P;               // pixels per sample
   int B;               // valid samples
-  float* out;          // EPI_ROWS_F32: [split][rows][ld]; EPI_DW: [group][split][4][C][C]
-  long long ld;
-  long long split_stride;
+  float* out;          // EPI_MODES: complex [split][cols/2][ld]; EPI_DW: [group][split][4][C][C]
+  long long ld;        // EPI_MODES: row capacity per mode (complex elements)
+  long long split_stride;  // EPI_MODES: complex elements per split
   int splits;          // EPI_DW: K splits per group
   const void* w;       // EPI_LAYER_*: W [C][C] (row = output channel), element type T
   const void* bias;    // EPI_LAYER_FWD: c [C] (T), may be null
@@ -118,35 +119,36 @@ __device__ __forceinline__ float gelu_grad_f(float z) {
 
 // ---- epilogues, shared by the tensor-core and the SIMT GEMM ------------------------------
 // Called once per (row, 32-column chunk starting at col0) with that chunk's accumulators.
-// w_s: W as FP32 [C][C] in shared memory; b_s: bias [C] (zeros if none).
-template <int EPI, typename T>
+// w_s: W as FP32 [C][C] in shared memory; b_s: bias [C] (zeros if none). WACC: the 1x1
+// convolution is already in the accumulator (tensor-core path); otherwise it is applied here.
+template <int EPI, typename T, bool WACC>
 __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, const float* b_s, int row, int col0,
                                          int split, const float (&acc)[32]) {
-  if constexpr (EPI == EPI_ROWS_F32) {
+  if constexpr (EPI == EPI_MODES) {
     if (row >= a.rows) return;
-    float* o = a.out + (size_t)split * a.split_stride + (size_t)row * a.ld + col0;
-    if (col0 + 32 <= a.cols) {
+    float2* o = reinterpret_cast<float2*>(a.out) + (size_t)split * a.split_stride + row;
 #pragma unroll
-      for (int j = 0; j < 32; j += 4)
-        *reinterpret_cast<float4*>(o + j) =
-            make_float4(a.alpha * acc[j], a.alpha * acc[j + 1], a.alpha * acc[j + 2], a.alpha * acc[j + 3]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j)
-        if (col0 + j < a.cols) o[j] = a.alpha * acc[j];
+    for (int j = 0; j < 16; ++j) {
+      const int k = col0 / 2 + j;
+      if (2 * k < a.cols) o[(size_t)k * a.ld] = make_float2(a.alpha * acc[2 * j], a.alpha * acc[2 * j + 1]);
     }
   } else if constexpr (EPI == EPI_LAYER_FWD) {
     const int p = row, b = col0 / C;
     if (p >= a.P || b >= a.B) return;
     const size_t cl = ((size_t)b * a.P + p) * C;
-    float x[32], z[32];
-    ld32(static_cast<const T*>(a.x_cl) + cl, x);
+    float z[32];
 #pragma unroll
-    for (int o = 0; o < C; ++o) {
-      float s = a.alpha * acc[o] + b_s[o];
+    for (int o = 0; o < C; ++o) z[o] = a.alpha * acc[o] + b_s[o];
+    if constexpr (!WACC) {
+      float x[32];
+      ld32(static_cast<const T*>(a.x_cl) + cl, x);
 #pragma unroll
-      for (int i = 0; i < C; ++i) s = fmaf(w_s[o * C + i], x[i], s);
-      z[o] = s;
+      for (int o = 0; o < C; ++o) {
+        float s = z[o];
+#pragma unroll
+        for (int i = 0; i < C; ++i) s = fmaf(w_s[o * C + i], x[i], s);
+        z[o] = s;
+      }
     }
     if (a.z_out) st32(static_cast<T*>(a.z_out) + cl, z);
     if (a.gelu) {
@@ -161,14 +163,19 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
     const int p = row, b = col0 / C;
     if (p >= a.P || b >= a.B) return;
     const size_t cl = ((size_t)b * a.P + p) * C;
-    float x[32], d[32];
-    ld32(static_cast<const T*>(a.x_cl) + cl, x);
+    float d[32];
 #pragma unroll
-    for (int i = 0; i < C; ++i) {
-      float s = acc[i];
+    for (int i = 0; i < C; ++i) d[i] = a.alpha * acc[i];
+    if constexpr (!WACC) {
+      float x[32];
+      ld32(static_cast<const T*>(a.x_cl) + cl, x);
 #pragma unroll
-      for (int o = 0; o < C; ++o) s = fmaf(w_s[o * C + i], x[o], s);
-      d[i] = s;
+      for (int i = 0; i < C; ++i) {
+        float s = d[i];
+#pragma unroll
+        for (int o = 0; o < C; ++o) s = fmaf(w_s[o * C + i], x[o], s);
+        d[i] = s;
+      }
     }
     if (a.z_in) {
       float z[32];
@@ -197,8 +204,12 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
 // a 64-element inner box): A rows in boxes of 128, B rows in boxes of BN (32..256).
 // grid = (ceil(M/128), ceil(N/BN), splits); EPI_DW uses grid.x = groups and the same row
 // offset for A and B. Each split covers kper 64-wide K blocks.
-cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtensorMap& mB, const EpiArgs& ea,
-                           int M, int N, int K, int splits, int* err, uint64_t timeout_ns, cudaStream_t st);
+// EPI_LAYER_*: mA2 / mW are the 1x1-convolution operands (channel-last activations [B P][C]
+// and W or W^T [C][C], 64-byte swizzle, boxes {32, 128} and {32, 32}); they run on the tensor
+// cores as one extra K = 32 segment per sample of the tile, into that sample's 32 columns.
+cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
+                           const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int splits, int* err,
+                           uint64_t timeout_ns, cudaStream_t st);
 // FP32 SIMT GEMM with the same semantics (A [M][lda], B [N][ldb] row-major FP32; for EPI_DW
 // rows of B are offset like rows of A).
 cudaError_t launch_gemm_simt(int epi, const float* A, long long lda, const float* B, long long ldb,
@@ -206,21 +217,27 @@ cudaError_t launch_gemm_simt(int epi, const float* A, long long lda, const float
 int gemm_tc_ctas_per_sm(int BN);
 
 // encode a 2D bf16 tensor map: `rows` rows of `cols` elements (row pitch `pitch` elements),
-// box {64, box_rows}, 128-byte swizzle, out-of-bounds elements read as zero
+// box {box_cols, box_rows} with box_cols 64 (128-byte swizzle) or 32 (64-byte swizzle),
+// out-of-bounds elements read as zero
 scw_status make_map_bf16(CUtensorMap* m, const void* base, long long cols, long long rows, long long pitch,
-                         int box_rows);
+                         int box_rows, int box_cols = 64);
 
 template <typename T>
 cudaError_t launch_tables(T* D, T* E, int N, int m, int Kp, cudaStream_t st);
 template <typename T>
 cudaError_t launch_lift(const float2* n, const T* params, T* Vcf, T* Vcl, int B, int S, int in_grid, int N,
                         cudaStream_t st);
+// mode-major spectra: Vh[split][mode][ld] complex, row b C + i
 template <typename T>
-cudaError_t launch_mix_fwd(const float* Vh, int splits, long long split_stride, const T* R, T* Wh, int B, int m,
-                           int Kc, int Kp, cudaStream_t st);
+cudaError_t launch_mix_fwd(const float2* Vh, int splits, long long split_stride, long long ld, const T* R, T* Wh,
+                           float scale, int B, int m, int Kp, cudaStream_t st);
 template <typename T>
-cudaError_t launch_mix_bwd(const float* G, const float* Vh, int splits, long long split_stride, const T* R, T* GVh,
-                           float* part, int sample_blocks, int B, int m, int Kc, int Kp, int N, cudaStream_t st);
+cudaError_t launch_mix_bwd(const float2* G, const float2* Vh, int splits, long long split_stride, long long ld,
+                           const T* R, T* GVh, float* part, int B, int m, int Kp, int N, cudaStream_t st);
+int mix_sample_blocks(int B);
+template <typename T>
+cudaError_t launch_transpose_w(const T* wcopy, long long off_W0, long long layer_stride, T* WT, int L,
+                               cudaStream_t st);
 cudaError_t launch_target_norm(const float2* target, float* part, int B, int P, cudaStream_t st);
 template <typename T>
 cudaError_t launch_project_train(const T* Vcl, const float2* target, const T* params_q, const float* part_tn,

@@ -65,159 +65,169 @@ __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n,
   for (int c = 0; c < C; ++c) cf[(size_t)c * P] = from_f<T>(o[c]);
 }
 
-// ---- mixing, forward: Wh[b][o][k] = sum_i R[k][o][i] Vh[b][i][k]; 4 modes x 8 samples per CTA
+// ---- mixing (per kept mode k, complex C x C), spectra mode-major Vh[split][k][b C + i] ------
+// forward: Wh[b][o][k] = scale sum_i R[k][o][i] Vh[b][i][k]; CTA = 8 modes x 32 samples,
+// so that each (b, o) row of Wh receives 16 contiguous values (32 bytes in BF16).
+constexpr int MIX_MODES = 8;
+constexpr int MIX_SAMPLES = 32;
+
 template <typename T>
-__global__ void __launch_bounds__(256) mix_fwd_kernel(const float* __restrict__ Vh, int splits,
-                                                      long long split_stride, const T* __restrict__ R,
-                                                      T* __restrict__ Wh, int B, int Kc, int Kp) {
-  __shared__ float2 Rs[4][C][C];  // [kk][i][o]
-  __shared__ float2 Vs[8][C][4];  // [s][i][kk]
-  const int k0 = blockIdx.x * 4, b0 = blockIdx.y * 8;
-  for (int idx = threadIdx.x; idx < 4 * C * C; idx += blockDim.x) {
-    const int kk = idx / (C * C), o = (idx / C) % C, i = idx % C;
-    const T* src = R + (((size_t)(k0 + kk) * C + o) * C + i) * 2;
-    Rs[kk][i][o] = make_float2(to_f(src[0]), to_f(src[1]));
-  }
-  for (int idx = threadIdx.x; idx < 8 * C * 4; idx += blockDim.x) {
-    const int s = idx / (C * 4), i = (idx / 4) % C, kk = idx % 4;
-    const int b = b0 + s;
-    float2 v = make_float2(0.f, 0.f);
-    if (b < B) {
-      const float* src = Vh + ((size_t)b * C + i) * Kc + 2 * (k0 + kk);
-      for (int z = 0; z < splits; ++z) {
-        v.x += src[(size_t)z * split_stride];
-        v.y += src[(size_t)z * split_stride + 1];
-      }
-    }
-    Vs[s][i][kk] = v;
-  }
-  __syncthreads();
-  const int s = threadIdx.x >> 5, o = threadIdx.x & 31;
-  const int b = b0 + s;
-  float out[8];
+__global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__ Vh, int splits,
+                                                      long long split_stride, long long ld, const T* __restrict__ R,
+                                                      T* __restrict__ Wh, float scale, int B, int Kp) {
+  __shared__ float2 Rs[C][C + 1];            // [i][o]
+  __shared__ float2 Vs[MIX_SAMPLES][C + 1];  // [s][i]
+  const int k0 = blockIdx.x * MIX_MODES, b0 = blockIdx.y * MIX_SAMPLES;
+  const int t = threadIdx.x, o = t & 31, w = t >> 5;
+  float2 acc[MIX_MODES][4];
 #pragma unroll
-  for (int kk = 0; kk < 4; ++kk) {
-    float re = 0.f, im = 0.f;
-#pragma unroll 8
-    for (int i = 0; i < C; ++i) {
-      const float2 r = Rs[kk][i][o], v = Vs[s][i][kk];
-      re = fmaf(r.x, v.x, fmaf(-r.y, v.y, re));
-      im = fmaf(r.x, v.y, fmaf(r.y, v.x, im));
+  for (int kk = 0; kk < MIX_MODES; ++kk) {
+    const int k = k0 + kk;
+    __syncthreads();
+    for (int idx = t; idx < C * C; idx += blockDim.x) {
+      const int oo = idx / C, i = idx % C;
+      const T* src = R + (((size_t)k * C + oo) * C + i) * 2;
+      Rs[i][oo] = make_float2(to_f(src[0]), to_f(src[1]));
     }
-    out[2 * kk] = re;
-    out[2 * kk + 1] = im;
+    for (int idx = t; idx < MIX_SAMPLES * C; idx += blockDim.x) {
+      const int s = idx / C, i = idx % C, b = b0 + s;
+      float2 v = make_float2(0.f, 0.f);
+      if (b < B) {
+        const float2* src = Vh + (size_t)k * ld + (size_t)b * C + i;
+        for (int z = 0; z < splits; ++z) {
+          const float2 u = src[(size_t)z * split_stride];
+          v.x += u.x;
+          v.y += u.y;
+        }
+      }
+      Vs[s][i] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int s = w + 8 * j;
+      float re = 0.f, im = 0.f;
+#pragma unroll 8
+      for (int i = 0; i < C; ++i) {
+        const float2 r = Rs[i][o], v = Vs[s][i];
+        re = fmaf(r.x, v.x, fmaf(-r.y, v.y, re));
+        im = fmaf(r.x, v.y, fmaf(r.y, v.x, im));
+      }
+      acc[kk][j] = make_float2(scale * re, scale * im);
+    }
   }
-  if (b < B) {
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int b = b0 + w + 8 * j;
+    if (b >= B) continue;
     T* dst = Wh + ((size_t)b * C + o) * Kp + 2 * k0;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) dst[j] = from_f<T>(out[j]);
+    for (int kk = 0; kk < MIX_MODES; ++kk) {
+      dst[2 * kk] = from_f<T>(acc[kk][j].x);
+      dst[2 * kk + 1] = from_f<T>(acc[kk][j].y);
+    }
   }
 }
 
-// ---- mixing, backward (G = dL/dRe + i dL/dIm convention):
+// backward (G = dL/dRe + i dL/dIm convention), per CTA = 8 modes x 32 samples:
 //   GVh[b][i][k] = sum_o conj(R[k][o][i]) G[b][o][k]
-//   part dR[k][o][i] = sum_b G[b][o][k] conj(Vh[b][i][k])   (over this CTA's samples)
+//   part dR[k][o][i] = sum_b G[b][o][k] conj(Vh[b][i][k])   (this CTA's samples)
 //   part dc[o] = N^2 sum_b Re G[b][o][k_dc]                   (the DC mode carries sum_x dZ / N^2)
-// part row layout: [m^2][C][C][2] then [C]
+// part row (one per sample block): [m^2][C][C][2] then [C]
 template <typename T>
-__global__ void __launch_bounds__(256) mix_bwd_kernel(const float* __restrict__ G, const float* __restrict__ Vh,
-                                                      int splits, long long split_stride, const T* __restrict__ R,
-                                                      T* __restrict__ GVh, float* __restrict__ part, int B, int m,
-                                                      int Kc, int Kp, int N) {
-  extern __shared__ float2 mb_smem[];
-  float2(*Rs)[C][C] = reinterpret_cast<float2(*)[C][C]>(mb_smem);                 // [4][o][i]
-  float2(*Gs)[C][4] = reinterpret_cast<float2(*)[C][4]>(mb_smem + 4 * C * C);     // [8][o][kk]
-  float2(*Vs)[C][4] = reinterpret_cast<float2(*)[C][4]>(mb_smem + 4 * C * C + 8 * C * 4);  // [8][i][kk]
-  const int k0 = blockIdx.x * 4;
-  const int chunk = (B + gridDim.y - 1) / gridDim.y;
-  const int bs = blockIdx.y * chunk, be = min(B, bs + chunk);
+__global__ void __launch_bounds__(256) mix_bwd_kernel(const float2* __restrict__ G, const float2* __restrict__ Vh,
+                                                      int splits, long long split_stride, long long ld,
+                                                      const T* __restrict__ R, T* __restrict__ GVh,
+                                                      float* __restrict__ part, int B, int m, int Kp, int N) {
+  __shared__ float2 Rs[C][C + 1];            // [o][i]
+  __shared__ float2 Gs[MIX_SAMPLES][C + 1];  // [s][o]
+  __shared__ float2 Vs[MIX_SAMPLES][C + 1];  // [s][i]
+  const int k0 = blockIdx.x * MIX_MODES, b0 = blockIdx.y * MIX_SAMPLES;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int kdc = (m / 2) * m + m / 2;
-  const bool has_dc = kdc >= k0 && kdc < k0 + 4;
-  for (int idx = threadIdx.x; idx < 4 * C * C; idx += blockDim.x) {
-    const int kk = idx / (C * C), o = (idx / C) % C, i = idx % C;
-    const T* src = R + (((size_t)(k0 + kk) * C + o) * C + i) * 2;
-    Rs[kk][o][i] = make_float2(to_f(src[0]), to_f(src[1]));
-  }
-  const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
-  float2 acc[4][4];
+  const size_t row = (size_t)blockIdx.y * ((size_t)m * m * C * C * 2 + C);
+  float2 gv[MIX_MODES][4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) acc[j][kk] = make_float2(0.f, 0.f);
-  float dc = 0.f;
-  for (int sb = bs; sb < be; sb += 8) {
+  for (int kk = 0; kk < MIX_MODES; ++kk) {
+    const int k = k0 + kk;
     __syncthreads();
-    for (int idx = t; idx < 8 * C * 4; idx += blockDim.x) {
-      const int s = idx / (C * 4), c = (idx / 4) % C, kk = idx % 4;
-      const int b = sb + s;
+    for (int idx = t; idx < C * C; idx += blockDim.x) {
+      const int o = idx / C, i = idx % C;
+      const T* src = R + (((size_t)k * C + o) * C + i) * 2;
+      Rs[o][i] = make_float2(to_f(src[0]), to_f(src[1]));
+    }
+    for (int idx = t; idx < MIX_SAMPLES * C; idx += blockDim.x) {
+      const int s = idx / C, c = idx % C, b = b0 + s;
       float2 g = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
-      if (b < be) {
-        const size_t off = ((size_t)b * C + c) * Kc + 2 * (k0 + kk);
+      if (b < B) {
+        const size_t off = (size_t)k * ld + (size_t)b * C + c;
         for (int z = 0; z < splits; ++z) {
-          g.x += G[off + (size_t)z * split_stride];
-          g.y += G[off + (size_t)z * split_stride + 1];
-          v.x += Vh[off + (size_t)z * split_stride];
-          v.y += Vh[off + (size_t)z * split_stride + 1];
+          const float2 gu = G[off + (size_t)z * split_stride], vu = Vh[off + (size_t)z * split_stride];
+          g.x += gu.x;
+          g.y += gu.y;
+          v.x += vu.x;
+          v.y += vu.y;
         }
       }
-      Gs[s][c][kk] = g;
-      Vs[s][c][kk] = v;
+      Gs[s][c] = g;
+      Vs[s][c] = v;
     }
     __syncthreads();
-    {  // GVh: thread (s = warp, i = lane)
-      const int s = wp, i = lane, b = sb + s;
-      float out[8];
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        float re = 0.f, im = 0.f;
-#pragma unroll 8
-        for (int o = 0; o < C; ++o) {
-          const float2 r = Rs[kk][o][i], g = Gs[s][o][kk];  // conj(r) g
-          re = fmaf(r.x, g.x, fmaf(r.y, g.y, re));
-          im = fmaf(r.x, g.y, fmaf(-r.y, g.x, im));
-        }
-        out[2 * kk] = re;
-        out[2 * kk + 1] = im;
-      }
-      if (b < be) {
-        T* dst = GVh + ((size_t)b * C + i) * Kp + 2 * k0;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) dst[j] = from_f<T>(out[j]);
-      }
-    }
-    // dR: thread (o = warp + 8 j, i = lane)
+    // GVh: thread (s = w + 8 j, i = lane)
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const int o = wp + 8 * j;
-#pragma unroll
-      for (int kk = 0; kk < 4; ++kk) {
-        float2 a = acc[j][kk];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-          const float2 g = Gs[s][o][kk], v = Vs[s][lane][kk];  // g conj(v)
-          a.x = fmaf(g.x, v.x, fmaf(g.y, v.y, a.x));
-          a.y = fmaf(g.y, v.x, fmaf(-g.x, v.y, a.y));
-        }
-        acc[j][kk] = a;
+      const int s = w + 8 * j;
+      float re = 0.f, im = 0.f;
+#pragma unroll 8
+      for (int o = 0; o < C; ++o) {
+        const float2 r = Rs[o][lane], g = Gs[s][o];  // conj(r) g
+        re = fmaf(r.x, g.x, fmaf(r.y, g.y, re));
+        im = fmaf(r.x, g.y, fmaf(-r.y, g.x, im));
       }
+      gv[kk][j] = make_float2(re, im);
     }
-    if (has_dc && t < C) {
+    // dR: thread (o = w + 8 j, i = lane), summed over the block's samples
 #pragma unroll
-      for (int s = 0; s < 8; ++s) dc += Gs[s][t][kdc - k0].x;
+    for (int j = 0; j < 4; ++j) {
+      const int o = w + 8 * j;
+      float re = 0.f, im = 0.f;
+#pragma unroll 8
+      for (int s = 0; s < MIX_SAMPLES; ++s) {
+        const float2 g = Gs[s][o], v = Vs[s][lane];  // g conj(v)
+        re = fmaf(g.x, v.x, fmaf(g.y, v.y, re));
+        im = fmaf(g.y, v.x, fmaf(-g.x, v.y, im));
+      }
+      float* dst = part + row + (((size_t)k * C + o) * C + lane) * 2;
+      dst[0] = re;
+      dst[1] = im;
+    }
+    if (k == kdc && t < C) {
+      float d = 0.f;
+      for (int s = 0; s < MIX_SAMPLES; ++s) d += Gs[s][t].x;
+      part[row + (size_t)m * m * C * C * 2 + t] = d * (float)N * (float)N;
     }
   }
-  const size_t row = (size_t)blockIdx.y * ((size_t)m * m * C * C * 2 + C);
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int o = wp + 8 * j;
+    const int b = b0 + w + 8 * j;
+    if (b >= B) continue;
+    T* dst = GVh + ((size_t)b * C + lane) * Kp + 2 * k0;
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-      float* dst = part + row + (((size_t)(k0 + kk) * C + o) * C + lane) * 2;
-      dst[0] = acc[j][kk].x;
-      dst[1] = acc[j][kk].y;
+    for (int kk = 0; kk < MIX_MODES; ++kk) {
+      dst[2 * kk] = from_f<T>(gv[kk][j].x);
+      dst[2 * kk + 1] = from_f<T>(gv[kk][j].y);
     }
   }
-  if (has_dc && t < C) part[row + (size_t)m * m * C * C * 2 + t] = dc * (float)N * (float)N;
+}
+
+// W^T of every layer (the backward 1x1 convolution's tensor-core operand): WT[l][i][o] = W_l[o][i]
+template <typename T>
+__global__ void transpose_w_kernel(const T* __restrict__ wcopy, long long off_W0, long long layer_stride,
+                                   T* __restrict__ WT, int L) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= L * C * C) return;
+  const int l = idx / (C * C), i = (idx / C) % C, o = idx % C;
+  WT[idx] = wcopy[off_W0 + (long long)l * layer_stride + o * C + i];
 }
 
 // ---- projection, loss and their gradient (training) ----------------------------------------
@@ -575,21 +585,27 @@ cudaError_t launch_lift(const float2* n, const T* params, T* Vcf, T* Vcl, int B,
 }
 
 template <typename T>
-cudaError_t launch_mix_fwd(const float* Vh, int splits, long long split_stride, const T* R, T* Wh, int B, int m,
-                           int Kc, int Kp, cudaStream_t st) {
-  const dim3 grid(m * m / 4, (B + 7) / 8);
-  mix_fwd_kernel<T><<<grid, 256, 0, st>>>(Vh, splits, split_stride, R, Wh, B, Kc, Kp);
+cudaError_t launch_mix_fwd(const float2* Vh, int splits, long long split_stride, long long ld, const T* R, T* Wh,
+                           float scale, int B, int m, int Kp, cudaStream_t st) {
+  const dim3 grid(m * m / MIX_MODES, (B + MIX_SAMPLES - 1) / MIX_SAMPLES);
+  mix_fwd_kernel<T><<<grid, 256, 0, st>>>(Vh, splits, split_stride, ld, R, Wh, scale, B, Kp);
+  return cudaGetLastError();
+}
+
+int mix_sample_blocks(int B) { return (B + MIX_SAMPLES - 1) / MIX_SAMPLES; }
+
+template <typename T>
+cudaError_t launch_mix_bwd(const float2* G, const float2* Vh, int splits, long long split_stride, long long ld,
+                           const T* R, T* GVh, float* part, int B, int m, int Kp, int N, cudaStream_t st) {
+  const dim3 grid(m * m / MIX_MODES, mix_sample_blocks(B));
+  mix_bwd_kernel<T><<<grid, 256, 0, st>>>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_mix_bwd(const float* G, const float* Vh, int splits, long long split_stride, const T* R, T* GVh,
-                           float* part, int sample_blocks, int B, int m, int Kc, int Kp, int N, cudaStream_t st) {
-  const size_t smem = (4 * C * C + 2 * 8 * C * 4) * sizeof(float2);
-  cudaError_t e = allow_max_smem(reinterpret_cast<const void*>(mix_bwd_kernel<T>));
-  if (e != cudaSuccess) return e;
-  const dim3 grid(m * m / 4, sample_blocks);
-  mix_bwd_kernel<T><<<grid, 256, smem, st>>>(G, Vh, splits, split_stride, R, GVh, part, B, m, Kc, Kp, N);
+cudaError_t launch_transpose_w(const T* wcopy, long long off_W0, long long layer_stride, T* WT, int L,
+                               cudaStream_t st) {
+  transpose_w_kernel<T><<<(L * C * C + 255) / 256, 256, 0, st>>>(wcopy, off_W0, layer_stride, WT, L);
   return cudaGetLastError();
 }
 
@@ -678,10 +694,11 @@ cudaError_t launch_head_infer(const float* part_pool, const T* params_e, float q
 #define SCW_FNO_INSTANTIATE(T)                                                                                       \
   template cudaError_t launch_tables<T>(T*, T*, int, int, int, cudaStream_t);                                      \
   template cudaError_t launch_lift<T>(const float2*, const T*, T*, T*, int, int, int, int, cudaStream_t);          \
-  template cudaError_t launch_mix_fwd<T>(const float*, int, long long, const T*, T*, int, int, int, int,           \
-                                         cudaStream_t);                                                             \
-  template cudaError_t launch_mix_bwd<T>(const float*, const float*, int, long long, const T*, T*, float*, int,   \
-                                         int, int, int, int, int, cudaStream_t);                                    \
+  template cudaError_t launch_mix_fwd<T>(const float2*, int, long long, long long, const T*, T*, float, int, int, \
+                                         int, cudaStream_t);                                                        \
+  template cudaError_t launch_mix_bwd<T>(const float2*, const float2*, int, long long, long long, const T*, T*,   \
+                                         float*, int, int, int, int, cudaStream_t);                                 \
+  template cudaError_t launch_transpose_w<T>(const T*, long long, long long, T*, int, cudaStream_t);              \
   template cudaError_t launch_project_train<T>(const T*, const float2*, const T*, const float*, float*, T*, T*,   \
                                                float*, float*, int, int, cudaStream_t);                            \
   template cudaError_t launch_project_reduce<T>(const T*, const float*, float*, int, int, cudaStream_t);          \

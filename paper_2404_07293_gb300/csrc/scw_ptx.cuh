@@ -160,6 +160,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t smem_addr) {
   return d;
 }
 
+// The same for a K-major tile with 64-byte swizzling: rows of 64 bytes (32 16-bit
+// elements), 8-row groups 512 bytes apart, swizzle mode 4 (64 B) in [61,64).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t smem_addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1u << 16;
+  d |= (uint64_t)(512u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)4u << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16: D format F32 (bits [4,6) = 1), A and B
 // format in bits [7,10) and [10,13) (0 = F16, 1 = BF16), both K-major (bits 15,
 // 16 = 0), N >> 3 in bits [17,23), M >> 4 in bits [24,29).
