@@ -46,6 +46,22 @@ def peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu record (profiles/traffic.json), or None
+    when the kernel's source changed since the capture or the workload differs."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except Exception:
+        return None
+    if not sha.startswith(rec["source_sha256_prefix"]) or rec["workload"] != workload:
+        return None
+    return rec["traffic_bytes_per_launch"]
+
+
 def bf16_sustained():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -407,7 +423,8 @@ def run_ours(args, world, rank, local):
     dominant = max(kernels, key=lambda k: kernels[k]["launch_ms"])
     d = kernels[dominant]
     roof = {"kernel": d["kernel"], "bound": "hbm", "achieved": d["gbs"], "peak": hbm, "unit": "GB/s",
-            "frac": d["frac"], "traffic": None, "algorithmic_bytes": d["algorithmic_bytes"],
+            "frac": d["frac"], "traffic": recorded_traffic(d["kernel"], workload_name()),
+            "algorithmic_bytes": d["algorithmic_bytes"],
             "launch_ms": d["launch_ms"], "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_kind})"}
     whole_bytes = w_bytes + out_bytes
     step_roofline_ms = whole_bytes / (hbm * 1e9) * 1e3
