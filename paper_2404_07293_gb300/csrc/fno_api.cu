@@ -42,9 +42,8 @@ struct scw_fno_s {
   void* GVh = nullptr;
   void* dZcf[2] = {};
   void* dZcl[2] = {};
-  float* dF = nullptr;      // [Bmax][6][P]
   float* part_tn = nullptr, *part_err = nullptr, *part_pool = nullptr, *part_proj = nullptr;
-  float* part_mix = nullptr, *part_dw = nullptr, *part_lift = nullptr, *scratch = nullptr;
+  float* part_mix = nullptr, *part_dw = nullptr, *part_lift = nullptr, *part_head = nullptr, *scratch = nullptr;
   float* loss_d = nullptr, *h_d = nullptr, *rel2_d = nullptr;
   int* d_err = nullptr;
   uint64_t timeout_ns = 2000000000ull;
@@ -254,15 +253,18 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
   const int BC = B * C, P = f->P, nblk = f->nblk;
   FNO_TRY(launch_ok(f, launch_target_norm(target, f->part_tn, B, P, st), "target norm"));
   FNO_TRY(launch_ok(f, launch_project_train<T>(static_cast<const T*>(f->Vcl[f->L]), target, at<T>(f->wcopy, f->off_Q),
-                                               f->part_tn, f->dF, static_cast<T*>(f->dZcf[0]),
-                                               static_cast<T*>(f->dZcl[0]), f->part_err, f->part_pool, B, P, st),
+                                               f->part_tn, static_cast<T*>(f->dZcf[0]),
+                                               static_cast<T*>(f->dZcl[0]), f->part_err, f->part_pool, f->part_proj, B,
+                                               P, st),
                     "projection"));
-  FNO_TRY(launch_ok(f, launch_project_reduce<T>(static_cast<const T*>(f->Vcf[f->L]), f->dF, f->part_proj, B, P, st),
-                    "projection gradient"));
   FNO_TRY(reduce_into(f, f->part_proj, B * nblk, OUT * C + OUT, OUT * C + OUT, f->grad + f->off_Q, st));
-  FNO_TRY(launch_ok(f, launch_head<T>(f->part_tn, f->part_err, f->part_pool, at<T>(f->wcopy, f->off_e),
-                                      f->grad + f->off_e, f->loss_d, f->h_d, f->rel2_d, B, P, 1, st),
+  FNO_TRY(launch_ok(f, launch_head<T>(f->part_tn, f->part_err, f->part_pool, at<T>(f->wcopy, f->off_e), f->part_head,
+                                      f->h_d, f->rel2_d, B, P, st),
                     "error head"));
+  e = cudaMemsetAsync(f->loss_d, 0, 4 * sizeof(float), st);
+  if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
+  FNO_TRY(reduce_into(f, f->part_head, B, C + 1, C + 3, f->grad + f->off_e, st));
+  FNO_TRY(reduce_into(f, f->part_head + C + 1, B, 2, C + 3, f->loss_d + 1, st));
   const long long ld = (long long)f->Bmax * C;
   const long long vstride = ld * (f->Kc / 2);
   const long long mix_w = (long long)f->m * f->m * C * C * 2;
@@ -315,8 +317,8 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     eb.w = at<T>(f->wcopy, f->off_W[l]);
     eb.x_cl = f->dZcl[cur];
     eb.z_in = l > 0 ? f->Zcl[l - 1] : nullptr;
-    eb.out_cf = f->dZcf[1 - cur];
-    eb.out_cl = l > 0 ? f->dZcl[1 - cur] : nullptr;
+    eb.out_cf = l > 0 ? f->dZcf[1 - cur] : nullptr;  // dV_0 is consumed channel-last only
+    eb.out_cl = f->dZcl[1 - cur];
     e = f->bf16 ? launch_gemm_tc(EPI_LAYER_BWD, 256, f->map_E, f->map_GVh, f->map_dZcl[cur], f->map_WT[l], eb, P, BC,
                                  f->Kp, 1, f->d_err, f->timeout_ns, st)
                 : launch_gemm_simt(EPI_LAYER_BWD, static_cast<const float*>(f->E), f->Kp,
@@ -324,7 +326,7 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     FNO_TRY(launch_ok(f, e, "layer backward", CAT_LAYER, 2.0 * P * BC * (f->Kc + C)));
     cur = 1 - cur;
   }
-  FNO_TRY(launch_ok(f, launch_lift_bwd<T>(static_cast<const T*>(f->dZcf[cur]), n, f->part_lift, B, f->S, f->in_grid,
+  FNO_TRY(launch_ok(f, launch_lift_bwd<T>(static_cast<const T*>(f->dZcl[cur]), n, f->part_lift, B, f->S, f->in_grid,
                                           f->N, st),
                     "lift backward"));
   const int lift_rows = (B * f->in_grid * f->in_grid + 127) / 128;
@@ -350,6 +352,7 @@ static scw_status read_loss(scw_fno_s* f, float* loss, cudaStream_t st) {
   cudaError_t e = cudaMemcpyAsync(loss, f->loss_d, 3 * sizeof(float), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_error(e, "loss read-back");
+  loss[0] = loss[1] + loss[2];
   int err = 0;
   e = cudaMemcpy(&err, f->d_err, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_error(e, "error word read-back");
@@ -443,7 +446,7 @@ scw_status scw_surrogate_create(const scw_fno_desc* d, scw_fno_t* out) {
     A(&f->dZcf[i], act);
     A(&f->dZcl[i], act);
   }
-  A((void**)&f->dF, Bm * OUT * P * 4);
+  A((void**)&f->part_head, Bm * (C + 3) * 4);
   A((void**)&f->part_tn, Bm * f->nblk * 4);
   A((void**)&f->part_err, Bm * f->nblk * 4);
   A((void**)&f->part_pool, Bm * f->nblk * C * 4);

@@ -42,8 +42,8 @@ struct EpiArgs {
   const void* x_cl;    // FWD: V_l channel-last [B][P][C]; BWD: dZ_l channel-last
   const void* z_in;    // BWD: Z_{l-1} channel-last (GELU'), null for l = 0
   void* z_out;         // FWD: Z_l channel-last, null when not needed
-  void* out_cf;        // FWD: V_{l+1} [B][C][P]; BWD: dZ_{l-1} (or dV_0) [B][C][P]
-  void* out_cl;        // FWD: V_{l+1} [B][P][C]; BWD: dZ_{l-1} [B][P][C] or null
+  void* out_cf;        // FWD: V_{l+1} [B][C][P]; BWD: dZ_{l-1} [B][C][P], null for l = 0
+  void* out_cl;        // FWD: V_{l+1} [B][P][C]; BWD: dZ_{l-1} (or dV_0 for l = 0) [B][P][C]
   int gelu;            // FWD: apply GELU
 };
 
@@ -184,9 +184,11 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
       for (int i = 0; i < C; ++i) d[i] *= gelu_grad_f(z[i]);
     }
     if (a.out_cl) st32(static_cast<T*>(a.out_cl) + cl, d);
-    T* cf = static_cast<T*>(a.out_cf) + (size_t)b * C * a.P + p;
+    if (a.out_cf) {
+      T* cf = static_cast<T*>(a.out_cf) + (size_t)b * C * a.P + p;
 #pragma unroll
-    for (int i = 0; i < C; ++i) cf[(size_t)i * a.P] = from_f<T>(d[i]);
+      for (int i = 0; i < C; ++i) cf[(size_t)i * a.P] = from_f<T>(d[i]);
+    }
   } else {  // EPI_DW: row = 32 s + o of group g = row / 128; chunk c = (col0 % 128) / 32
     const int g = row / 128, s = (row % 128) / C, o = row % C, c = (col0 % 128) / C;
     if (c != s) return;
@@ -240,17 +242,14 @@ cudaError_t launch_transpose_w(const T* wcopy, long long off_W0, long long layer
                                cudaStream_t st);
 cudaError_t launch_target_norm(const float2* target, float* part, int B, int P, cudaStream_t st);
 template <typename T>
-cudaError_t launch_project_train(const T* Vcl, const float2* target, const T* params_q, const float* part_tn,
-                                 float* dF, T* dZcf, T* dZcl, float* part_err, float* part_pool, int B, int P,
+cudaError_t launch_project_train(const T* Vcl, const float2* target, const T* params_q, const float* part_tn, T* dZcf,
+                                 T* dZcl, float* part_err, float* part_pool, float* part_proj, int B, int P,
                                  cudaStream_t st);
 template <typename T>
-cudaError_t launch_project_reduce(const T* Vcf, const float* dF, float* part, int B, int P, cudaStream_t st);
-template <typename T>
 cudaError_t launch_head(const float* part_tn, const float* part_err, const float* part_pool, const T* params_e,
-                        float* grad_e, float* loss, float* h_out, float* rel2_out, int B, int P, int with_loss,
-                        cudaStream_t st);
+                        float* part_head, float* h_out, float* rel2_out, int B, int P, cudaStream_t st);
 template <typename T>
-cudaError_t launch_lift_bwd(const T* dV0cf, const float2* n, float* part, int B, int S, int in_grid, int N,
+cudaError_t launch_lift_bwd(const T* dV0cl, const float2* n, float* part, int B, int S, int in_grid, int N,
                             cudaStream_t st);
 cudaError_t launch_reduce_rows_ex(const float* part, int rows, int width, long long pitch, float scale, float* out,
                                   float* scratch, cudaStream_t st);

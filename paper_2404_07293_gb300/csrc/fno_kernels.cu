@@ -30,14 +30,18 @@ __global__ void tables_kernel(T* __restrict__ D, T* __restrict__ E, int N, int m
 }
 
 // ---- lift: V_0 = P a + p, a = (Re n - 1, Im n) per slice, nearest upsampling
+// (features beyond the 2S inputs are zero, so the channel loop has a fixed trip count)
 template <typename T>
 __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n, const T* __restrict__ prm,
                                                    T* __restrict__ Vcf, T* __restrict__ Vcl, int B, int S,
                                                    int in_grid, int N) {
-  __shared__ float Ps[C * 32];
+  __shared__ float Ps[C * 32];  // [c][32], zero-padded past 2S
   __shared__ float ps[C];
   const int cin = 2 * S;
-  for (int i = threadIdx.x; i < C * cin; i += blockDim.x) Ps[i] = to_f(prm[i]);
+  for (int i = threadIdx.x; i < C * 32; i += blockDim.x) {
+    const int c = i / 32, j = i % 32;
+    Ps[i] = j < cin ? to_f(prm[c * cin + j]) : 0.f;
+  }
   if (threadIdx.x < C) ps[threadIdx.x] = to_f(prm[C * cin + threadIdx.x]);
   __syncthreads();
   const int P = N * N;
@@ -47,8 +51,10 @@ __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n,
   const int r = N / in_grid;
   const int yi = (p / N) / r, xi = (p % N) / r;
   float a[32];
-  for (int s = 0; s < S; ++s) {
-    const float2 v = n[(((size_t)b * S + s) * in_grid + yi) * in_grid + xi];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    float2 v = make_float2(1.f, 0.f);
+    if (s < S) v = n[(((size_t)b * S + s) * in_grid + yi) * in_grid + xi];
     a[2 * s] = v.x - 1.0f;
     a[2 * s + 1] = v.y;
   }
@@ -56,7 +62,8 @@ __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n,
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     float t = ps[c];
-    for (int i = 0; i < cin; ++i) t = fmaf(Ps[c * cin + i], a[i], t);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) t = fmaf(Ps[c * 32 + i], a[i], t);
     o[c] = t;
   }
   st32(Vcl + ((size_t)b * P + p) * C, o);
@@ -66,70 +73,79 @@ __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n,
 }
 
 // ---- mixing (per kept mode k, complex C x C), spectra mode-major Vh[split][k][b C + i] ------
-// forward: Wh[b][o][k] = scale sum_i R[k][o][i] Vh[b][i][k]; CTA = 8 modes x 32 samples,
-// so that each (b, o) row of Wh receives 16 contiguous values (32 bytes in BF16).
-constexpr int MIX_MODES = 8;
+// One CTA per (mode, block of 32 samples), 256 threads: thread (warp w, lane) handles
+// samples w + 8 j (j < 4) and channel `lane`. Many small CTAs keep enough warps in flight
+// to hide the global-load latency of the per-mode operands.
 constexpr int MIX_SAMPLES = 32;
 
+template <typename T>
+__device__ __forceinline__ float2 ld_pair(const T* base, size_t pair);
+template <>
+__device__ __forceinline__ float2 ld_pair<float>(const float* base, size_t pair) {
+  return reinterpret_cast<const float2*>(base)[pair];
+}
+template <>
+__device__ __forceinline__ float2 ld_pair<__nv_bfloat16>(const __nv_bfloat16* base, size_t pair) {
+  const uint32_t w = reinterpret_cast<const uint32_t*>(base)[pair];
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
+template <typename T>
+__device__ __forceinline__ void st_pair(T* base, size_t pair, float2 v);
+template <>
+__device__ __forceinline__ void st_pair<float>(float* base, size_t pair, float2 v) {
+  reinterpret_cast<float2*>(base)[pair] = v;
+}
+template <>
+__device__ __forceinline__ void st_pair<__nv_bfloat16>(__nv_bfloat16* base, size_t pair, float2 v) {
+  reinterpret_cast<__nv_bfloat162*>(base)[pair] = __floats2bfloat162_rn(v.x, v.y);
+}
+
+// split-summed complex value of a mode-major spectrum
+__device__ __forceinline__ float2 ld_spec(const float2* __restrict__ X, size_t off, int splits,
+                                          long long split_stride) {
+  float2 v = X[off];
+  for (int z = 1; z < splits; ++z) {
+    const float2 u = X[off + (size_t)z * split_stride];
+    v.x += u.x;
+    v.y += u.y;
+  }
+  return v;
+}
+
+// forward: Wh[b][o][k] = scale sum_i R[k][o][i] Vh[b][i][k]
 template <typename T>
 __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__ Vh, int splits,
                                                       long long split_stride, long long ld, const T* __restrict__ R,
                                                       T* __restrict__ Wh, float scale, int B, int Kp) {
   __shared__ float2 Rs[C][C + 1];            // [i][o]
   __shared__ float2 Vs[MIX_SAMPLES][C + 1];  // [s][i]
-  const int k0 = blockIdx.x * MIX_MODES, b0 = blockIdx.y * MIX_SAMPLES;
-  const int t = threadIdx.x, o = t & 31, w = t >> 5;
-  float2 acc[MIX_MODES][4];
+  const int k = blockIdx.x, b0 = blockIdx.y * MIX_SAMPLES;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
 #pragma unroll
-  for (int kk = 0; kk < MIX_MODES; ++kk) {
-    const int k = k0 + kk;
-    __syncthreads();
-    for (int idx = t; idx < C * C; idx += blockDim.x) {
-      const int oo = idx / C, i = idx % C;
-      const T* src = R + (((size_t)k * C + oo) * C + i) * 2;
-      Rs[i][oo] = make_float2(to_f(src[0]), to_f(src[1]));
-    }
-    for (int idx = t; idx < MIX_SAMPLES * C; idx += blockDim.x) {
-      const int s = idx / C, i = idx % C, b = b0 + s;
-      float2 v = make_float2(0.f, 0.f);
-      if (b < B) {
-        const float2* src = Vh + (size_t)k * ld + (size_t)b * C + i;
-        for (int z = 0; z < splits; ++z) {
-          const float2 u = src[(size_t)z * split_stride];
-          v.x += u.x;
-          v.y += u.y;
-        }
-      }
-      Vs[s][i] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int s = w + 8 * j;
-      float re = 0.f, im = 0.f;
-#pragma unroll 8
-      for (int i = 0; i < C; ++i) {
-        const float2 r = Rs[i][o], v = Vs[s][i];
-        re = fmaf(r.x, v.x, fmaf(-r.y, v.y, re));
-        im = fmaf(r.x, v.y, fmaf(r.y, v.x, im));
-      }
-      acc[kk][j] = make_float2(scale * re, scale * im);
-    }
+  for (int q = 0; q < 4; ++q) {
+    const int idx = t + 256 * q, row = idx / C, col = idx % C;
+    Rs[col][row] = ld_pair(R, ((size_t)k * C + row) * C + col);
+    const int b = b0 + row;
+    Vs[row][col] = b < B ? ld_spec(Vh, (size_t)k * ld + (size_t)b * C + col, splits, split_stride)
+                         : make_float2(0.f, 0.f);
   }
+  __syncthreads();
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int b = b0 + w + 8 * j;
-    if (b >= B) continue;
-    T* dst = Wh + ((size_t)b * C + o) * Kp + 2 * k0;
-#pragma unroll
-    for (int kk = 0; kk < MIX_MODES; ++kk) {
-      dst[2 * kk] = from_f<T>(acc[kk][j].x);
-      dst[2 * kk + 1] = from_f<T>(acc[kk][j].y);
+    const int s = w + 8 * j, b = b0 + s;
+    float re = 0.f, im = 0.f;
+#pragma unroll 8
+    for (int i = 0; i < C; ++i) {
+      const float2 r = Rs[i][lane], v = Vs[s][i];
+      re = fmaf(r.x, v.x, fmaf(-r.y, v.y, re));
+      im = fmaf(r.x, v.y, fmaf(r.y, v.x, im));
     }
+    if (b < B) st_pair(Wh, (((size_t)b * C + lane) * Kp) / 2 + k, make_float2(scale * re, scale * im));
   }
 }
 
-// backward (G = dL/dRe + i dL/dIm convention), per CTA = 8 modes x 32 samples:
+// backward (G = dL/dRe + i dL/dIm convention):
 //   GVh[b][i][k] = sum_o conj(R[k][o][i]) G[b][o][k]
 //   part dR[k][o][i] = sum_b G[b][o][k] conj(Vh[b][i][k])   (this CTA's samples)
 //   part dc[o] = N^2 sum_b Re G[b][o][k_dc]                   (the DC mode carries sum_x dZ / N^2)
@@ -142,81 +158,50 @@ __global__ void __launch_bounds__(256) mix_bwd_kernel(const float2* __restrict__
   __shared__ float2 Rs[C][C + 1];            // [o][i]
   __shared__ float2 Gs[MIX_SAMPLES][C + 1];  // [s][o]
   __shared__ float2 Vs[MIX_SAMPLES][C + 1];  // [s][i]
-  const int k0 = blockIdx.x * MIX_MODES, b0 = blockIdx.y * MIX_SAMPLES;
+  const int k = blockIdx.x, b0 = blockIdx.y * MIX_SAMPLES;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int kdc = (m / 2) * m + m / 2;
-  const size_t row = (size_t)blockIdx.y * ((size_t)m * m * C * C * 2 + C);
-  float2 gv[MIX_MODES][4];
+  const size_t row0 = (size_t)blockIdx.y * ((size_t)m * m * C * C * 2 + C);
 #pragma unroll
-  for (int kk = 0; kk < MIX_MODES; ++kk) {
-    const int k = k0 + kk;
-    __syncthreads();
-    for (int idx = t; idx < C * C; idx += blockDim.x) {
-      const int o = idx / C, i = idx % C;
-      const T* src = R + (((size_t)k * C + o) * C + i) * 2;
-      Rs[o][i] = make_float2(to_f(src[0]), to_f(src[1]));
-    }
-    for (int idx = t; idx < MIX_SAMPLES * C; idx += blockDim.x) {
-      const int s = idx / C, c = idx % C, b = b0 + s;
-      float2 g = make_float2(0.f, 0.f), v = make_float2(0.f, 0.f);
-      if (b < B) {
-        const size_t off = (size_t)k * ld + (size_t)b * C + c;
-        for (int z = 0; z < splits; ++z) {
-          const float2 gu = G[off + (size_t)z * split_stride], vu = Vh[off + (size_t)z * split_stride];
-          g.x += gu.x;
-          g.y += gu.y;
-          v.x += vu.x;
-          v.y += vu.y;
-        }
-      }
-      Gs[s][c] = g;
-      Vs[s][c] = v;
-    }
-    __syncthreads();
-    // GVh: thread (s = w + 8 j, i = lane)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int s = w + 8 * j;
-      float re = 0.f, im = 0.f;
-#pragma unroll 8
-      for (int o = 0; o < C; ++o) {
-        const float2 r = Rs[o][lane], g = Gs[s][o];  // conj(r) g
-        re = fmaf(r.x, g.x, fmaf(r.y, g.y, re));
-        im = fmaf(r.x, g.y, fmaf(-r.y, g.x, im));
-      }
-      gv[kk][j] = make_float2(re, im);
-    }
-    // dR: thread (o = w + 8 j, i = lane), summed over the block's samples
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int o = w + 8 * j;
-      float re = 0.f, im = 0.f;
-#pragma unroll 8
-      for (int s = 0; s < MIX_SAMPLES; ++s) {
-        const float2 g = Gs[s][o], v = Vs[s][lane];  // g conj(v)
-        re = fmaf(g.x, v.x, fmaf(g.y, v.y, re));
-        im = fmaf(g.y, v.x, fmaf(-g.x, v.y, im));
-      }
-      float* dst = part + row + (((size_t)k * C + o) * C + lane) * 2;
-      dst[0] = re;
-      dst[1] = im;
-    }
-    if (k == kdc && t < C) {
-      float d = 0.f;
-      for (int s = 0; s < MIX_SAMPLES; ++s) d += Gs[s][t].x;
-      part[row + (size_t)m * m * C * C * 2 + t] = d * (float)N * (float)N;
-    }
+  for (int q = 0; q < 4; ++q) {
+    const int idx = t + 256 * q, row = idx / C, col = idx % C;
+    Rs[row][col] = ld_pair(R, ((size_t)k * C + row) * C + col);
+    const int b = b0 + row;
+    const size_t off = (size_t)k * ld + (size_t)b * C + col;
+    Gs[row][col] = b < B ? ld_spec(G, off, splits, split_stride) : make_float2(0.f, 0.f);
+    Vs[row][col] = b < B ? ld_spec(Vh, off, splits, split_stride) : make_float2(0.f, 0.f);
   }
+  __syncthreads();
+  // GVh: thread (s = w + 8 j, i = lane)
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int b = b0 + w + 8 * j;
-    if (b >= B) continue;
-    T* dst = GVh + ((size_t)b * C + lane) * Kp + 2 * k0;
-#pragma unroll
-    for (int kk = 0; kk < MIX_MODES; ++kk) {
-      dst[2 * kk] = from_f<T>(gv[kk][j].x);
-      dst[2 * kk + 1] = from_f<T>(gv[kk][j].y);
+    const int s = w + 8 * j, b = b0 + s;
+    float re = 0.f, im = 0.f;
+#pragma unroll 8
+    for (int o = 0; o < C; ++o) {
+      const float2 r = Rs[o][lane], g = Gs[s][o];  // conj(r) g
+      re = fmaf(r.x, g.x, fmaf(r.y, g.y, re));
+      im = fmaf(r.x, g.y, fmaf(-r.y, g.x, im));
     }
+    if (b < B) st_pair(GVh, (((size_t)b * C + lane) * Kp) / 2 + k, make_float2(re, im));
+  }
+  // dR: thread (o = w + 8 j, i = lane), summed over the block's samples
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int o = w + 8 * j;
+    float re = 0.f, im = 0.f;
+#pragma unroll 8
+    for (int s = 0; s < MIX_SAMPLES; ++s) {
+      const float2 g = Gs[s][o], v = Vs[s][lane];  // g conj(v)
+      re = fmaf(g.x, v.x, fmaf(g.y, v.y, re));
+      im = fmaf(g.y, v.x, fmaf(-g.x, v.y, im));
+    }
+    reinterpret_cast<float2*>(part + row0)[((size_t)k * C + o) * C + lane] = make_float2(re, im);
+  }
+  if (k == kdc && t < C) {
+    float d = 0.f;
+    for (int s = 0; s < MIX_SAMPLES; ++s) d += Gs[s][t].x;
+    part[row0 + (size_t)m * m * C * C * 2 + t] = d * (float)N * (float)N;
   }
 }
 
@@ -253,21 +238,27 @@ __global__ void __launch_bounds__(256) target_norm_kernel(const float2* __restri
   }
 }
 
-// F = Q v + q; d = F - T; dF = 2 d / (B ||T_b||^2); dV_L = Q^T dF (= dZ of the last layer)
+// F = Q v + q; d = F - T; dF = 2 d / (B ||T_b||^2); dV_L = Q^T dF (= dZ of the last layer).
+// Per block of 256 pixels of one sample it also writes the partial sums
+//   part_proj row [6 C + 6]: dQ[j][o] = sum_p dF[j][p] V[o][p], dq[j] = sum_p dF[j][p]
+//   part_err = sum_p |d|^2, part_pool[C] = sum_p V[o][p]
 template <typename T>
-__global__ void __launch_bounds__(256) project_train_kernel(const T* __restrict__ Vcl, const float2* __restrict__ target,
-                                                            const T* __restrict__ prm_q,
-                                                            const float* __restrict__ part_tn, float* __restrict__ dF,
-                                                            T* __restrict__ dZcf, T* __restrict__ dZcl,
-                                                            float* __restrict__ part_err, float* __restrict__ part_pool,
-                                                            int B, int P) {
+__global__ void __launch_bounds__(256) project_train_kernel(const T* __restrict__ Vcl,
+                                                               const float2* __restrict__ target,
+                                                               const T* __restrict__ prm_q,
+                                                               const float* __restrict__ part_tn,
+                                                               T* __restrict__ dZcf, T* __restrict__ dZcl,
+                                                               float* __restrict__ part_err,
+                                                               float* __restrict__ part_pool,
+                                                               float* __restrict__ part_proj, int B, int P) {
   __shared__ float Qs[OUT * C + OUT];
-  __shared__ float pool_s[PIX_BLOCK][C + 1];
+  __shared__ float Vs[PIX_BLOCK][C + 1];
+  __shared__ float Fs[OUT][PIX_BLOCK];
   __shared__ float red[8];
   __shared__ float tn_s;
-  const int nblk = gridDim.x, b = blockIdx.y, p = blockIdx.x * PIX_BLOCK + threadIdx.x;
-  for (int i = threadIdx.x; i < OUT * C + OUT; i += blockDim.x) Qs[i] = to_f(prm_q[i]);
-  if (threadIdx.x == 0) {
+  const int nblk = gridDim.x, b = blockIdx.y, t = threadIdx.x, p = blockIdx.x * PIX_BLOCK + t;
+  for (int i = t; i < OUT * C + OUT; i += blockDim.x) Qs[i] = to_f(prm_q[i]);
+  if (t == 0) {
     float s = 0.f;
     for (int j = 0; j < nblk; ++j) s += part_tn[(size_t)b * nblk + j];
     tn_s = s;
@@ -276,7 +267,7 @@ __global__ void __launch_bounds__(256) project_train_kernel(const T* __restrict_
   float v[32];
   ld32(Vcl + ((size_t)b * P + p) * C, v);
 #pragma unroll
-  for (int o = 0; o < C; ++o) pool_s[threadIdx.x][o] = v[o];
+  for (int o = 0; o < C; ++o) Vs[t][o] = v[o];
   float d[OUT];
 #pragma unroll
   for (int j = 0; j < OUT; ++j) {
@@ -292,167 +283,120 @@ __global__ void __launch_bounds__(256) project_train_kernel(const T* __restrict_
   for (int j = 0; j < OUT; ++j) {
     e2 = fmaf(d[j], d[j], e2);
     d[j] *= sc;
-    dF[((size_t)b * OUT + j) * P + p] = d[j];
+    Fs[j][t] = d[j];
   }
-  float g[32];
 #pragma unroll
   for (int o = 0; o < C; ++o) {
     float s = 0.f;
 #pragma unroll
     for (int j = 0; j < OUT; ++j) s = fmaf(Qs[j * C + o], d[j], s);
-    g[o] = s;
+    v[o] = s;  // v now holds dV_L
   }
-  st32(dZcl + ((size_t)b * P + p) * C, g);
+  st32(dZcl + ((size_t)b * P + p) * C, v);
   T* cf = dZcf + (size_t)b * C * P + p;
 #pragma unroll
-  for (int o = 0; o < C; ++o) cf[(size_t)o * P] = from_f<T>(g[o]);
+  for (int o = 0; o < C; ++o) cf[(size_t)o * P] = from_f<T>(v[o]);
 #pragma unroll
   for (int o = 16; o; o >>= 1) e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e2;
+  if ((t & 31) == 0) red[t >> 5] = e2;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    float t = 0.f;
-    for (int w = 0; w < 8; ++w) t += red[w];
-    part_err[(size_t)b * nblk + blockIdx.x] = t;
-  }
-  if (threadIdx.x < C) {
+  const size_t blk = (size_t)b * nblk + blockIdx.x;
+  if (t == 0) {
     float s = 0.f;
-    for (int r = 0; r < PIX_BLOCK; ++r) s += pool_s[r][threadIdx.x];
-    part_pool[((size_t)b * nblk + blockIdx.x) * C + threadIdx.x] = s;
+    for (int w = 0; w < 8; ++w) s += red[w];
+    part_err[blk] = s;
   }
-}
-
-// part row [6 C + 6]: dQ[j][o] = sum_p dF[j][p] V[o][p], dq[j] = sum_p dF[j][p] over the block's pixels
-template <typename T>
-__global__ void __launch_bounds__(256) project_reduce_kernel(const T* __restrict__ Vcf, const float* __restrict__ dF,
-                                                             float* __restrict__ part, int P) {
-  __shared__ float Vs[C][PIX_BLOCK + 1];
-  __shared__ float Fs[OUT][PIX_BLOCK];
-  const int b = blockIdx.y, p0 = blockIdx.x * PIX_BLOCK, t = threadIdx.x;
-  for (int o = 0; o < C; ++o) Vs[o][t] = to_f(Vcf[((size_t)b * C + o) * P + p0 + t]);
-  for (int j = 0; j < OUT; ++j) Fs[j][t] = dF[((size_t)b * OUT + j) * P + p0 + t];
-  __syncthreads();
-  float* dst = part + ((size_t)b * gridDim.x + blockIdx.x) * (OUT * C + OUT);
   if (t < OUT * C) {
     const int j = t / C, o = t % C;
     float s = 0.f;
-    for (int p = 0; p < PIX_BLOCK; ++p) s = fmaf(Fs[j][p], Vs[o][p], s);
-    dst[t] = s;
+    for (int q = 0; q < PIX_BLOCK; ++q) s = fmaf(Fs[j][q], Vs[q][o], s);
+    part_proj[blk * (OUT * C + OUT) + t] = s;
   } else if (t < OUT * C + OUT) {
     const int j = t - OUT * C;
     float s = 0.f;
-    for (int p = 0; p < PIX_BLOCK; ++p) s += Fs[j][p];
-    dst[t] = s;
+    for (int q = 0; q < PIX_BLOCK; ++q) s += Fs[j][q];
+    part_proj[blk * (OUT * C + OUT) + t] = s;
+  } else if (t >= 224) {
+    const int o = t - 224;
+    float s = 0.f;
+    for (int q = 0; q < PIX_BLOCK; ++q) s += Vs[q][o];
+    part_pool[blk * C + o] = s;
   }
 }
 
-// error head and the loss (one CTA): h = e . pool + e0, rel2 = ||F - T||^2 / ||T||^2,
-// L_field = mean rel2, L_head = mean (h - log(rel2 + 1e-12)/2)^2; grad_e gets de[C], de0
+// error head and the loss, one warp per sample (lane = channel): h = e . pool + e0,
+// rel2 = ||F - T||^2 / ||T||^2, tgt = log(rel2 + 1e-12) / 2, dh = 2 (h - tgt) / B.
+// part_head row [C + 3]: dh pool[0..C), dh, rel2 / B, (h - tgt)^2 / B, summed over samples
+// into (grad e, grad e0) and (L_field, L_head) by the caller.
 template <typename T>
 __global__ void __launch_bounds__(256) head_kernel(const float* __restrict__ part_tn, const float* __restrict__ part_err,
                                                    const float* __restrict__ part_pool, const T* __restrict__ prm_e,
-                                                   float* __restrict__ grad_e, float* __restrict__ loss,
-                                                   float* __restrict__ h_out, float* __restrict__ rel2_out, int B,
-                                                   int nblk, int P) {
-  __shared__ float es[C + 1];
-  __shared__ float red[8][C + 3];
-  if (threadIdx.x <= C) es[threadIdx.x] = to_f(prm_e[threadIdx.x]);
-  __syncthreads();
-  float de[C + 1], lf = 0.f, lh = 0.f;
+                                                   float* __restrict__ part_head, float* __restrict__ h_out,
+                                                   float* __restrict__ rel2_out, int B, int nblk, int P) {
+  const int lane = threadIdx.x & 31, b = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (b >= B) return;
+  float pool = 0.f, tn = 0.f, e2 = 0.f;
+  for (int j = 0; j < nblk; ++j) pool += part_pool[((size_t)b * nblk + j) * C + lane];
+  pool /= (float)P;
+  for (int j = lane; j < nblk; j += 32) {
+    tn += part_tn[(size_t)b * nblk + j];
+    e2 += part_err[(size_t)b * nblk + j];
+  }
+  float h = to_f(prm_e[lane]) * pool;
 #pragma unroll
-  for (int o = 0; o <= C; ++o) de[o] = 0.f;
-  for (int b = threadIdx.x; b < B; b += blockDim.x) {
-    float tn = 0.f, e2 = 0.f;
-    for (int j = 0; j < nblk; ++j) {
-      tn += part_tn[(size_t)b * nblk + j];
-      e2 += part_err[(size_t)b * nblk + j];
-    }
-    float pool[C];
-#pragma unroll
-    for (int o = 0; o < C; ++o) pool[o] = 0.f;
-    for (int j = 0; j < nblk; ++j) {
-      const float* pp = part_pool + ((size_t)b * nblk + j) * C;
-#pragma unroll
-      for (int o = 0; o < C; ++o) pool[o] += pp[o];
-    }
-    float h = es[C];
-#pragma unroll
-    for (int o = 0; o < C; ++o) {
-      pool[o] /= (float)P;
-      h = fmaf(es[o], pool[o], h);
-    }
-    const float rel2 = e2 / tn;
-    const float tgt = 0.5f * logf(rel2 + 1e-12f);
-    const float dh = 2.0f * (h - tgt) / (float)B;
-    lf += rel2 / (float)B;
-    lh += (h - tgt) * (h - tgt) / (float)B;
-#pragma unroll
-    for (int o = 0; o < C; ++o) de[o] = fmaf(dh, pool[o], de[o]);
-    de[C] += dh;
+  for (int o = 16; o; o >>= 1) {
+    h += __shfl_xor_sync(0xffffffffu, h, o);
+    tn += __shfl_xor_sync(0xffffffffu, tn, o);
+    e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+  }
+  h += to_f(prm_e[C]);
+  const float rel2 = e2 / tn;
+  const float tgt = 0.5f * logf(rel2 + 1e-12f);
+  const float dh = 2.0f * (h - tgt) / (float)B;
+  float* row = part_head + (size_t)b * (C + 3);
+  row[lane] = dh * pool;
+  if (lane == 0) {
+    row[C] = dh;
+    row[C + 1] = rel2 / (float)B;
+    row[C + 2] = (h - tgt) * (h - tgt) / (float)B;
     if (h_out) h_out[b] = h;
     if (rel2_out) rel2_out[b] = rel2;
   }
-  // block reduction of (de[0..C], lf, lh)
-  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 0; o <= C; ++o) {
-    float v = de[o];
-#pragma unroll
-    for (int s = 16; s; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
-    if (lane == 0) red[wp][o] = v;
-  }
-#pragma unroll
-  for (int s = 16; s; s >>= 1) {
-    lf += __shfl_xor_sync(0xffffffffu, lf, s);
-    lh += __shfl_xor_sync(0xffffffffu, lh, s);
-  }
-  if (lane == 0) {
-    red[wp][C + 1] = lf;
-    red[wp][C + 2] = lh;
-  }
-  __syncthreads();
-  if (threadIdx.x < C + 3) {
-    float v = 0.f;
-    for (int w = 0; w < 8; ++w) v += red[w][threadIdx.x];
-    if (threadIdx.x <= C) {
-      grad_e[threadIdx.x] += v;
-    } else if (loss) {
-      loss[threadIdx.x - C] = v;  // 1: L_field, 2: L_head
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && loss) loss[0] = loss[1] + loss[2];
 }
 
 // ---- lift backward: part row [C][2S] then [C]: dP[o][c] = sum dV0[o] a[c], dp[o] = sum dV0[o]
-// (dV0 summed over each input pixel's r x r block first: a is constant there)
+// (dV0, channel-last, is summed over each input pixel's r x r block first: a is constant there)
 template <typename T>
-__global__ void __launch_bounds__(128) lift_bwd_kernel(const T* __restrict__ dV0cf, const float2* __restrict__ n,
+__global__ void __launch_bounds__(128) lift_bwd_kernel(const T* __restrict__ dV0cl, const float2* __restrict__ n,
                                                        float* __restrict__ part, int B, int S, int in_grid, int N) {
   __shared__ float dv_s[128][C + 1];
   __shared__ float a_s[128][33];
   const int cin = 2 * S, P = N * N, Pi = in_grid * in_grid, r = N / in_grid;
   const long long idx = blockIdx.x * 128LL + threadIdx.x;
   const bool valid = idx < (long long)B * Pi;
+  float dv[32];
+#pragma unroll
+  for (int o = 0; o < C; ++o) dv[o] = 0.f;
   if (valid) {
     const int b = (int)(idx / Pi), pi = (int)(idx % Pi);
     const int yi = pi / in_grid, xi = pi % in_grid;
-    for (int o = 0; o < C; ++o) {
-      const T* src = dV0cf + ((size_t)b * C + o) * P;
-      float s = 0.f;
-      for (int dy = 0; dy < r; ++dy)
-        for (int dx = 0; dx < r; ++dx) s += to_f(src[(size_t)(yi * r + dy) * N + xi * r + dx]);
-      dv_s[threadIdx.x][o] = s;
-    }
+    for (int dy = 0; dy < r; ++dy)
+      for (int dx = 0; dx < r; ++dx) {
+        float x[32];
+        ld32(dV0cl + ((size_t)b * P + (size_t)(yi * r + dy) * N + xi * r + dx) * C, x);
+#pragma unroll
+        for (int o = 0; o < C; ++o) dv[o] += x[o];
+      }
     for (int s = 0; s < S; ++s) {
       const float2 v = n[(((size_t)b * S + s) * in_grid + yi) * in_grid + xi];
       a_s[threadIdx.x][2 * s] = v.x - 1.0f;
       a_s[threadIdx.x][2 * s + 1] = v.y;
     }
   } else {
-    for (int o = 0; o < C; ++o) dv_s[threadIdx.x][o] = 0.f;
     for (int c = 0; c < cin; ++c) a_s[threadIdx.x][c] = 0.f;
   }
+#pragma unroll
+  for (int o = 0; o < C; ++o) dv_s[threadIdx.x][o] = dv[o];
   __syncthreads();
   const int width = C * cin + C;
   float* dst = part + (size_t)blockIdx.x * width;
@@ -587,7 +531,7 @@ cudaError_t launch_lift(const float2* n, const T* params, T* Vcf, T* Vcl, int B,
 template <typename T>
 cudaError_t launch_mix_fwd(const float2* Vh, int splits, long long split_stride, long long ld, const T* R, T* Wh,
                            float scale, int B, int m, int Kp, cudaStream_t st) {
-  const dim3 grid(m * m / MIX_MODES, (B + MIX_SAMPLES - 1) / MIX_SAMPLES);
+  const dim3 grid(m * m, (B + MIX_SAMPLES - 1) / MIX_SAMPLES);
   mix_fwd_kernel<T><<<grid, 256, 0, st>>>(Vh, splits, split_stride, ld, R, Wh, scale, B, Kp);
   return cudaGetLastError();
 }
@@ -597,7 +541,7 @@ int mix_sample_blocks(int B) { return (B + MIX_SAMPLES - 1) / MIX_SAMPLES; }
 template <typename T>
 cudaError_t launch_mix_bwd(const float2* G, const float2* Vh, int splits, long long split_stride, long long ld,
                            const T* R, T* GVh, float* part, int B, int m, int Kp, int N, cudaStream_t st) {
-  const dim3 grid(m * m / MIX_MODES, mix_sample_blocks(B));
+  const dim3 grid(m * m, mix_sample_blocks(B));
   mix_bwd_kernel<T><<<grid, 256, 0, st>>>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N);
   return cudaGetLastError();
 }
@@ -615,33 +559,27 @@ cudaError_t launch_target_norm(const float2* target, float* part, int B, int P, 
 }
 
 template <typename T>
-cudaError_t launch_project_train(const T* Vcl, const float2* target, const T* params_q, const float* part_tn, float* dF,
-                                 T* dZcf, T* dZcl, float* part_err, float* part_pool, int B, int P, cudaStream_t st) {
-  project_train_kernel<T><<<dim3(P / PIX_BLOCK, B), PIX_BLOCK, 0, st>>>(Vcl, target, params_q, part_tn, dF, dZcf, dZcl,
-                                                                       part_err, part_pool, B, P);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t launch_project_reduce(const T* Vcf, const float* dF, float* part, int B, int P, cudaStream_t st) {
-  project_reduce_kernel<T><<<dim3(P / PIX_BLOCK, B), PIX_BLOCK, 0, st>>>(Vcf, dF, part, P);
+cudaError_t launch_project_train(const T* Vcl, const float2* target, const T* params_q, const float* part_tn, T* dZcf,
+                                 T* dZcl, float* part_err, float* part_pool, float* part_proj, int B, int P,
+                                 cudaStream_t st) {
+  project_train_kernel<T><<<dim3(P / PIX_BLOCK, B), PIX_BLOCK, 0, st>>>(Vcl, target, params_q, part_tn, dZcf, dZcl,
+                                                                       part_err, part_pool, part_proj, B, P);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_head(const float* part_tn, const float* part_err, const float* part_pool, const T* params_e,
-                        float* grad_e, float* loss, float* h_out, float* rel2_out, int B, int P, int with_loss,
-                        cudaStream_t st) {
-  head_kernel<T><<<1, 256, 0, st>>>(part_tn, part_err, part_pool, params_e, grad_e, with_loss ? loss : nullptr, h_out,
-                                    rel2_out, B, P / PIX_BLOCK, P);
+                        float* part_head, float* h_out, float* rel2_out, int B, int P, cudaStream_t st) {
+  head_kernel<T><<<(B + 7) / 8, 256, 0, st>>>(part_tn, part_err, part_pool, params_e, part_head, h_out, rel2_out, B,
+                                              P / PIX_BLOCK, P);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_lift_bwd(const T* dV0cf, const float2* n, float* part, int B, int S, int in_grid, int N,
+cudaError_t launch_lift_bwd(const T* dV0cl, const float2* n, float* part, int B, int S, int in_grid, int N,
                             cudaStream_t st) {
   const long long total = (long long)B * in_grid * in_grid;
-  lift_bwd_kernel<T><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(dV0cf, n, part, B, S, in_grid, N);
+  lift_bwd_kernel<T><<<(unsigned)((total + 127) / 128), 128, 0, st>>>(dV0cl, n, part, B, S, in_grid, N);
   return cudaGetLastError();
 }
 
@@ -699,11 +637,10 @@ cudaError_t launch_head_infer(const float* part_pool, const T* params_e, float q
   template cudaError_t launch_mix_bwd<T>(const float2*, const float2*, int, long long, long long, const T*, T*,   \
                                          float*, int, int, int, int, cudaStream_t);                                 \
   template cudaError_t launch_transpose_w<T>(const T*, long long, long long, T*, int, cudaStream_t);              \
-  template cudaError_t launch_project_train<T>(const T*, const float2*, const T*, const float*, float*, T*, T*,   \
+  template cudaError_t launch_project_train<T>(const T*, const float2*, const T*, const float*, T*, T*, float*,   \
                                                float*, float*, int, int, cudaStream_t);                            \
-  template cudaError_t launch_project_reduce<T>(const T*, const float*, float*, int, int, cudaStream_t);          \
-  template cudaError_t launch_head<T>(const float*, const float*, const float*, const T*, float*, float*, float*, \
-                                      float*, int, int, int, cudaStream_t);                                         \
+  template cudaError_t launch_head<T>(const float*, const float*, const float*, const T*, float*, float*, float*,  \
+                                      int, int, cudaStream_t);                                                      \
   template cudaError_t launch_lift_bwd<T>(const T*, const float2*, float*, int, int, int, int, cudaStream_t);      \
   template cudaError_t launch_adam<T>(float*, const float*, float*, float*, T*, long long, float, float, float,   \
                                       cudaStream_t);                                                                \
