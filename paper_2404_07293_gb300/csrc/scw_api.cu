@@ -197,24 +197,22 @@ static scw_status build_item(Plan* p, const std::vector<int>& ext) {
     szt[m] = make_double2(a.real(), a.imag());
     szb[m] = make_double2(b.real(), b.imag());
   }
-  // fold tables: order u at index p = u + U/2 + rot, rot = (-(U/2)) mod 8, rows padded to a multiple of 8
+  // fold tables: order u at position u mod Up (fold_pos), rows padded to a multiple of 8
   ItemDev& it = p->item;
   std::memset(&it, 0, sizeof(it));
-  it.rotU = (8 - (p->U / 2) % 8) % 8;
-  it.rotV = (8 - (p->V / 2) % 8) % 8;
-  it.Up = (p->U + it.rotU + 7) / 8 * 8;
-  it.Vp = (p->V + it.rotV + 7) / 8 * 8;
+  it.Up = fold_np(p->U);
+  it.Vp = fold_np(p->V);
   const int Qx = p->Fx / 8, Qy = p->Fy / 8;
   std::vector<float2> twx((size_t)Qx * it.Up, make_float2(0.f, 0.f)), twy((size_t)Qy * it.Vp, make_float2(0.f, 0.f));
   for (int b = 0; b < Qx; ++b)
     for (int ui = 0; ui < p->U; ++ui) {
       const int u = ui - p->U / 2;
-      twx[(size_t)(ui + it.rotU) * Qx + b] = cis_cycles((double)u * b / p->Fx + u * p->x0 / p->X);  // [p][b]
+      twx[(size_t)fold_pos(ui, p->U, it.Up) * Qx + b] = cis_cycles((double)u * b / p->Fx + u * p->x0 / p->X);
     }
   for (int b = 0; b < Qy; ++b)
     for (int vi = 0; vi < p->V; ++vi) {
       const int v = vi - p->V / 2;
-      twy[(size_t)b * it.Vp + vi + it.rotV] = cis_cycles((double)v * b / p->Fy + v * p->y0 / p->Y);
+      twy[(size_t)b * it.Vp + fold_pos(vi, p->V, it.Vp)] = cis_cycles((double)v * b / p->Fy + v * p->y0 / p->Y);
     }
   std::vector<int> ones(p->Fz, 1);
   size_t& tot = p->workspace_bytes;
@@ -473,12 +471,13 @@ struct scw_plan_s {
   ItemDev* d_items = nullptr;      // batched plans only
   int2* d_unit_entries = nullptr;
   int n_unit_entries = 0;
-  int2* d_plane_entries = nullptr;
+  int2* d_plane_entries = nullptr;  // y-pass-pair class first (ypass_pairs), then the rest
   int n_plane_entries = 0;
+  int n_pair_entries = 0;
   TcSchedule sched;
   float2** d_outs = nullptr;
   float2** h_outs = nullptr;       // pinned
-  int max_M = 0, max_Qx = 0, max_V = 0;
+  int max_M = 0, max_Qx = 0, max_V = 0, max_VUp = 0, max_Vp = 0;
   size_t rec_smem = 0;
   // graph replay
   cudaStream_t cap_stream = nullptr;
@@ -634,11 +633,13 @@ static scw_status enqueue_pipelined(scw_plan_t P, float2* out_one, cudaStream_t 
     const int nb = P->gplane[g + 1] - P->gplane[g];
     if (nb == 0) continue;
     const int2* ent = P->d_plane_entries + P->gplane[g];
-    e = launch_xpass(one, nullptr, ent, nb, P->max_M, P->st2);
+    e = launch_xpass(one, nullptr, ent, nb, P->max_VUp, P->st2);
     if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
-    e = launch_ypass(one, nullptr, ent, nb, P->max_Qx, P->max_V, out_one, nullptr, P->st2);
+    int ny = 0;
+    e = launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, out_one, nullptr,
+                     P->st2, &ny);
     if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
-    n += 2;
+    n += 1 + ny;
   }
   e = cudaEventRecord(P->ev_join, P->st2);
   if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
@@ -655,13 +656,15 @@ static scw_status enqueue_synthesis(scw_plan_t P, float2* out_one, cudaStream_t 
   const ItemDev& one = P->items[0]->item;
   const ItemDev* items = P->batched ? P->d_items : nullptr;
   mark(P, 2, st, marks);
-  cudaError_t e = launch_xpass(one, items, P->d_plane_entries, P->n_plane_entries, P->max_M, st);
+  cudaError_t e = launch_xpass(one, items, P->d_plane_entries, P->n_plane_entries, P->max_VUp, st);
   if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
   mark(P, 3, st, marks);
-  e = launch_ypass(one, items, P->d_plane_entries, P->n_plane_entries, P->max_Qx, P->max_V, out_one, P->d_outs, st);
+  int ny = 0;
+  e = launch_ypass(one, items, P->d_plane_entries, P->n_plane_entries, P->n_pair_entries, P->max_Qx, P->max_Vp,
+                   out_one, P->d_outs, st, &ny);
   if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
   mark(P, 4, st, marks);
-  n += 2;
+  n += 1 + ny;
   if (marks && P->timing && P->tev_used + kMarks <= P->tev.size()) P->tev_used += kMarks;
   return SCW_OK;
 }
@@ -825,8 +828,15 @@ static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, boo
     P->max_M = std::max(P->max_M, p->M);
     P->max_Qx = std::max(P->max_Qx, p->Fx / 8);
     P->max_V = std::max(P->max_V, p->V);
+    P->max_VUp = std::max(P->max_VUp, p->V * p->item.Up);
+    P->max_Vp = std::max(P->max_Vp, p->item.Vp);
     P->rec_smem = std::max(P->rec_smem, recompose_smem_bytes(p->V, p->item.Up, p->item.Vp));
   }
+  // plane entries of items with long y folds first: they run the two-residue y-pass
+  std::stable_partition(pe.begin(), pe.end(),
+                        [&](const int2& en) { return ypass_pairs(P->items[en.x]->item.Vp); });
+  P->n_pair_entries = 0;
+  for (const int2& en : pe) P->n_pair_entries += ypass_pairs(P->items[en.x]->item.Vp) ? 1 : 0;
   P->n_unit_entries = (int)ue.size();
   P->n_plane_entries = (int)pe.size();
   SCW_TRY(upload(&P->d_unit_entries, ue, tot));

@@ -51,15 +51,15 @@ struct ItemDev {
   void* Blo;
   float2* S_part;          // [k_split][Fz][3M]
   const int* nsplit;       // [Fz]
-  const float2* twx;       // [Up][Fx/8]   fold twiddles, order index p = ui + rotU (residue b fastest:
-                           //               the lanes of an x-pass warp take consecutive b)
+  const float2* twx;       // [Up][Fx/8]   fold twiddles at wrapped positions (fold_pos; residue b
+                           //               fastest: the lanes of an x-pass warp take consecutive b)
   const float2* twy;       // [Fy/8][Vp]
   float2* T;               // [Fz][3][V][Fx] x-pass rows (plans only)
   size_t split_stride;     // Fz * 3M
   double inv_lam;
   int M, U, V, Fx, Fy, Fz;
   int F_pad, k_split, n_tiles, nk, n_units;
-  int rotU, rotV, Up, Vp;  // fold offsets (-(U/2)) & 7 and padded lengths roundup(U + rotU, 8)
+  int Up, Vp;              // padded fold lengths roundup(U, 8), roundup(V, 8)
 };
 
 struct Plan {
@@ -137,6 +137,24 @@ struct TcSchedule {
   double max_load = 0, mean_load = 0;  // in K-stages, for the autotuner's report
 };
 
+// Fold layout of the recomposition: the signed order u of an axis with n orders
+// (u in [-floor(n/2), n - 1 - floor(n/2)]) sits at position u mod np, np = roundup(n, 8),
+// so that position mod 8 = u mod 8 and a fold over residues walks whole groups of 8
+// positions; the positions between the largest positive and the smallest wrapped
+// negative order hold zeros.
+__host__ __device__ __forceinline__ int fold_np(int n) { return (n + 7) / 8 * 8; }
+__host__ __device__ __forceinline__ int fold_pos(int ui, int n, int np) {
+  const int u = ui - n / 2;
+  return u >= 0 ? u : u + np;
+}
+// order index ui at position pos, or -1 for a zero position
+__host__ __device__ __forceinline__ int fold_order(int pos, int n, int np) {
+  const int h = n / 2;
+  if (pos <= n - 1 - h) return pos + h;
+  if (pos >= np - h) return pos - np + h;
+  return -1;
+}
+
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,
 // once per (kernel, device): the attribute call is not repeated on the launch path.
 cudaError_t allow_max_smem(const void* kernel);
@@ -165,10 +183,14 @@ int tc_ctas_per_sm(int NB, bool bf16);
 // step (c): plane entries are (item, plane) pairs; S_override / nsplit_override replace the
 // contraction's partial spectra with caller-given spectra
 size_t recompose_smem_bytes(int V, int Up, int Vp);
-cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_M,
+cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_VUp,
                          cudaStream_t st);
-cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_Qx,
-                         int max_V, float2* out_one, float2* const* d_outs, cudaStream_t st);
+// entries [0, n_pair) run the two-residue y-pass (long folds, ypass_pairs(Vp)), the rest the
+// one-residue y-pass; *launches receives the number of kernels launched (0, 1 or 2)
+bool ypass_pairs(int Vp);
+cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int n_pair,
+                         int max_Qx, int max_Vp, float2* out_one, float2* const* d_outs, cudaStream_t st,
+                         int* launches);
 cudaError_t launch_recompose(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_Qx,
                              size_t smem, const float2* S_override, const int* nsplit_override, float2* out_one,
                              float2* const* d_outs, cudaStream_t st);

@@ -20,25 +20,24 @@ static std::mutex g_noalloc_mu;
 static void* g_noalloc_addr[64] = {nullptr};
 
 // The fold twiddles exp(2 pi i (u b / F + u x0 / X)) in the padded layouts the
-// recompose kernels read (order u at index p = u + n/2 + rot, zeros elsewhere;
+// recompose kernels read (order u at position u mod np, fold_pos; zeros elsewhere;
 // x table [p][b], y table [b][p]),
 // with the argument reduced in FP64 as a plan does on the host; the all-ones
 // split count; and the (item 0, plane f) entry table.
-__global__ void noalloc_setup_kernel(float2* twx, int U, int Up, int rotU, int Fx, double x0_over_X, float2* twy,
-                                     int V, int Vp, int rotV, int Fy, double y0_over_Y, int* ones, int2* entries,
-                                     int Fz) {
+__global__ void noalloc_setup_kernel(float2* twx, int U, int Up, int Fx, double x0_over_X, float2* twy, int V,
+                                     int Vp, int Fy, double y0_over_Y, int* ones, int2* entries, int Fz) {
   const int nx = (Fx / 8) * Up, ny = (Fy / 8) * Vp;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nx + ny + Fz; i += gridDim.x * blockDim.x) {
     if (i < nx + ny) {
       const bool isx = i < nx;
       const int k = isx ? i : i - nx;
-      const int np = isx ? Up : Vp, n = isx ? U : V, rot = isx ? rotU : rotV;
+      const int np = isx ? Up : Vp, n = isx ? U : V;
       // x table [p][b] (residue fastest), y table [b][p]
       const int Qx = Fx / 8;
       const int b = isx ? k % Qx : k / np;
-      const int idx = (isx ? k / Qx : k - b * np) - rot;
+      const int idx = fold_order(isx ? k / Qx : k - b * np, n, np);
       float2 w = make_float2(0.f, 0.f);
-      if (idx >= 0 && idx < n) {
+      if (idx >= 0) {
         const int u = idx - n / 2;
         const double t = isx ? ((double)u * b / Fx + u * x0_over_X) : ((double)u * b / Fy + u * y0_over_Y);
         const double r = t - rint(t);
@@ -73,8 +72,7 @@ extern "C" scw_status scw_recompose_noalloc(int U, int V, double X, double Y, in
   if ((reinterpret_cast<uintptr_t>(out) & 15u) != 0) return set_error(SCW_ERR_INVALID_ARGUMENT, "out must be 16-byte aligned");
 
   // scratch layout: twx | twy | ones | entries, each 256-byte aligned
-  const int rotU = (8 - (U / 2) % 8) % 8, rotV = (8 - (V / 2) % 8) % 8;
-  const int Up = (U + rotU + 7) / 8 * 8, Vp = (V + rotV + 7) / 8 * 8;
+  const int Up = fold_np(U), Vp = fold_np(V);
   const size_t b_twx = align256(sizeof(float2) * (size_t)(Fx / 8) * Up);
   const size_t b_twy = align256(sizeof(float2) * (size_t)(Fy / 8) * Vp);
   const size_t b_one = align256(sizeof(int) * (size_t)Fz);
@@ -108,7 +106,8 @@ extern "C" scw_status scw_recompose_noalloc(int U, int V, double X, double Y, in
   ItemDev it;
   std::memset(&it, 0, sizeof(it));
   it.M = U * V; it.U = U; it.V = V; it.Fx = Fx; it.Fy = Fy; it.Fz = Fz;
-  it.rotU = rotU; it.rotV = rotV; it.Up = Up; it.Vp = Vp;
+  it.Up = Up;
+  it.Vp = Vp;
   it.split_stride = (size_t)Fz * 3 * U * V;
   float2* twx = reinterpret_cast<float2*>(base);
   float2* twy = reinterpret_cast<float2*>(base + b_twx);
@@ -120,7 +119,7 @@ extern "C" scw_status scw_recompose_noalloc(int U, int V, double X, double Y, in
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int n = (Fx / 8) * Up + (Fy / 8) * Vp + Fz;
   noalloc_setup_kernel<<<(n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024, 256, 0, st>>>(
-      twx, U, Up, rotU, Fx, x0 / X, twy, V, Vp, rotV, Fy, y0 / Y, ones, entries, Fz);
+      twx, U, Up, Fx, x0 / X, twy, V, Vp, Fy, y0 / Y, ones, entries, Fz);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "noalloc setup launch");
   e = launch_recompose(it, nullptr, entries, Fz, Fx / 8, recompose_smem_bytes(V, Up, Vp),

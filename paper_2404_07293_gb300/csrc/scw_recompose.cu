@@ -7,11 +7,11 @@
 // index i = b + Q a (b < Q, a < 8), omega = exp(2 pi i / F):
 //   sum_u s_u omega^(u (b + Q a)) = sum_{r<8} e^(2 pi i r a / 8) F_b[r],
 //   F_b[r] = sum_{u = r mod 8} s_u omega^(u b).
-// The signed orders u are stored at index p = u + U/2 + rot with
-// rot = (-(U/2)) mod 8, so p mod 8 == u mod 8 and consecutive groups of 8
-// stored values land in residues 0..7 in order: the fold is a fully unrolled
-// loop over groups with independent loads (rows zero-padded to a multiple of
-// 8). Each table twiddle tw[b][p] = omega^(u b) exp(2 pi i u x0 / X) carries the
+// The signed orders u are stored at position u mod Up (Up = U rounded up to a
+// multiple of 8; fold_pos), so position mod 8 == u mod 8 and consecutive groups
+// of 8 stored values land in residues 0..7 in order: every fold is a fully
+// unrolled loop over whole groups with independent loads, and at most 7 of the
+// Up positions are zero padding. Each table twiddle tw[b][p] = omega^(u b) exp(2 pi i u x0 / X) carries the
 // origin phase. An in-register radix-8 inverse DFT finishes the 8 outputs Q
 // apart. Orders beyond the grid (|u| >= F/2) fold exactly: the sum is only
 // evaluated at grid points.
@@ -68,7 +68,7 @@ __device__ __forceinline__ void idft8(float2 (&x)[8]) {
 //   1. the spectrum rows of component c (partial sums of the contraction added)
 //      -> srow[V][Up];
 //   2. x-direction fold + radix-8 inverse DFT per (row v, residue b)
-//      -> tcol[p = v + rotV][local column b_local + 8 a];
+//      -> tcol[p = fold position of v][local column b_local + 8 a];
 //   3. y-direction fold + radix-8 inverse DFT per (column pair, y residue),
 //      16-byte streaming stores (each warp store: 8 runs of 8 contiguous columns).
 template <bool BATCH>
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(256, 4) recompose_kernel(const __grid_constant
   if (b0 >= Qx) return;
   const int nb = min(8, Qx - b0);
   const int f = e.y, c = blockIdx.z;
-  const int U = it.U, V = it.V, M = it.M, Up = it.Up, Vp = it.Vp, rotU = it.rotU, rotV = it.rotV;
+  const int U = it.U, V = it.V, M = it.M, Up = it.Up, Vp = it.Vp;
   float4* tcol4 = sm4;                                  // [Vp][32] float4 = [Vp][64] complex
   float2* tcol = reinterpret_cast<float2*>(sm4);
   float2* srow = tcol + (size_t)Vp * 64;                // [V][Up]
@@ -96,18 +96,16 @@ __global__ void __launch_bounds__(256, 4) recompose_kernel(const __grid_constant
   const int ns = nsplit_override ? nsplit_override[f] : it.nsplit[f];
   const size_t stride = it.split_stride;
   for (int i = threadIdx.x; i < V * Up; i += blockDim.x) {
-    const int vi = i / Up, ui = i - vi * Up - rotU;
+    const int vi = i / Up, ui = fold_order(i - vi * Up, U, Up);
     float2 acc = make_float2(0.f, 0.f);
-    if (ui >= 0 && ui < U) {
+    if (ui >= 0) {
       const float2* s = src + vi * U + ui;
       for (int k = 0; k < ns; ++k) acc = c_add(acc, s[(size_t)k * stride]);
     }
     srow[i] = acc;
   }
-  for (int i = threadIdx.x; i < Vp * 64; i += blockDim.x) {  // rows outside [rotV, rotV + V) stay zero
-    const int vi = (i >> 6) - rotV;
-    if (vi < 0 || vi >= V) tcol[i] = make_float2(0.f, 0.f);
-  }
+  for (int i = threadIdx.x; i < Vp * 64; i += blockDim.x)  // padding rows stay zero
+    if (fold_order(i >> 6, V, Vp) < 0) tcol[i] = make_float2(0.f, 0.f);
   __syncthreads();
 
   // 2. x-direction: fold + DFT for (row vi, residue b0 + bl)
@@ -125,7 +123,7 @@ __global__ void __launch_bounds__(256, 4) recompose_kernel(const __grid_constant
       }
       idft8(G);
     }
-    float2* d = tcol + (size_t)(vi + rotV) * 64 + bl;
+    float2* d = tcol + (size_t)fold_pos(vi, V, Vp) * 64 + bl;
 #pragma unroll
     for (int a = 0; a < 8; ++a) d[8 * a] = G[a];
   }
@@ -177,36 +175,42 @@ constexpr int kSplitUnroll = 8;  // split partials loaded together (more are add
 // first stored index p >= rot with p = r (mod 8), then every 8th.
 
 // One CTA per (item-plane, component): V * Fx/8 tasks (row vi, residue b).
+// The spectrum of component c (split partials summed) is laid out [V][Up] in
+// shared memory at the fold positions, padding zero.
 template <bool BATCH>
 __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ ItemDev one,
                                                     const ItemDev* __restrict__ items,
                                                     const int2* __restrict__ entries) {
-  extern __shared__ float2 xs_row[];  // [V][U]
+  extern __shared__ float2 xs_row[];  // [V][Up]
   const int2 e = entries[blockIdx.x];
   const ItemDev& it = BATCH ? items[e.x] : one;
   const int f = e.y, c = blockIdx.y;
-  const int U = it.U, V = it.V, M = it.M, Up = it.Up, rot = it.rotU, Fx = it.Fx;
+  const int U = it.U, V = it.V, M = it.M, Up = it.Up, Fx = it.Fx;
   const float2* src = it.S_part + (size_t)f * 3 * M + (size_t)c * M;
   const int ns = it.nsplit[f];
   const size_t stride = it.split_stride;
-  for (int m0 = 0; m0 < M; m0 += 2 * blockDim.x) {
+  for (int i0 = 0; i0 < V * Up; i0 += 2 * blockDim.x) {
     // all split partials of two elements are requested before any is used
     float2 v[2][kSplitUnroll];
+    int off[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int m = m0 + h * blockDim.x + threadIdx.x;
+      const int i = i0 + h * blockDim.x + threadIdx.x;
+      const int vi = i / Up, ui = i < V * Up ? fold_order(i - vi * Up, U, Up) : -1;
+      off[h] = ui >= 0 ? vi * U + ui : -1;
 #pragma unroll
       for (int k = 0; k < kSplitUnroll; ++k)
-        v[h][k] = (m < M && k < ns) ? src[(size_t)k * stride + m] : make_float2(0.f, 0.f);
+        v[h][k] = (off[h] >= 0 && k < ns) ? src[(size_t)k * stride + off[h]] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-      const int m = m0 + h * blockDim.x + threadIdx.x;
+      const int i = i0 + h * blockDim.x + threadIdx.x;
       float2 acc = v[h][0];
 #pragma unroll
       for (int k = 1; k < kSplitUnroll; ++k) acc = c_add(acc, v[h][k]);
-      for (int k = kSplitUnroll; k < ns; ++k) acc = c_add(acc, src[(size_t)k * stride + m]);
-      if (m < M) xs_row[m] = acc;
+      if (off[h] >= 0)
+        for (int k = kSplitUnroll; k < ns; ++k) acc = c_add(acc, src[(size_t)k * stride + off[h]]);
+      if (i < V * Up) xs_row[i] = acc;
     }
   }
   __syncthreads();
@@ -214,13 +218,14 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
   float2* dst = it.T + ((size_t)f * 3 + c) * V * Fx;
   for (int t = threadIdx.x; t < V * Q; t += blockDim.x) {
     const int vi = t / Q, b = t - vi * Q;
-    const float2* s = xs_row + vi * U - rot;  // indexed by stored position p
+    const float2* s = xs_row + vi * Up;
     const float2* tw = it.twx + b;  // [p][b]: a warp's lanes read consecutive residues
     float2 G[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      G[r] = make_float2(0.f, 0.f);
-      for (int p = rot + ((r - rot) & 7); p < rot + U; p += 8) c_fma(G[r], s[p], __ldg(tw + (size_t)p * Q));
+    for (int r = 0; r < 8; ++r) G[r] = make_float2(0.f, 0.f);
+    for (int p0 = 0; p0 < Up; p0 += 8) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) c_fma(G[r], s[p0 + r], __ldg(tw + (size_t)(p0 + r) * Q));
     }
     idft8(G);
     float2* o = dst + (size_t)vi * Fx + b;
@@ -229,35 +234,41 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
   }
 }
 
-// One CTA per (64-column block, item-plane, component); 8 warps, lane l owns the
-// column pair (2l, 2l+1) of the block and warp w the residues b = w, w+8, ...
-template <bool BATCH>
-__global__ void __launch_bounds__(256, 4) ypass_kernel(const __grid_constant__ ItemDev one,
+// One CTA per (64-column block, item-plane, component); 8 warps. The x-pass rows of
+// the block sit at their fold positions in shared memory ([Vp][64], padding rows zero).
+// Lane l owns the column pair (2l, 2l+1). PAIR: warp w takes the residue pairs
+// (b, b + 8), b = w, w + 16, ..., so each shared-memory load feeds four complex FMAs
+// (long folds); otherwise one residue b = w, w + 8, ... at a time and twice the
+// resident warps (short folds, where latency dominates).
+template <bool BATCH, bool PAIR>
+__global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_constant__ ItemDev one,
                                                        const ItemDev* __restrict__ items,
                                                        const int2* __restrict__ entries, float2* out_one,
                                                        float2* const* __restrict__ outs) {
-  extern __shared__ float4 ys_col4[];  // [V][32] float4 = [V][64] complex
+  extern __shared__ float4 ys_col4[];  // [Vp][32] float4 = [Vp][64] complex
   float2* tcol = reinterpret_cast<float2*>(ys_col4);
   const int2 e = entries[blockIdx.y];
   const ItemDev& it = BATCH ? items[e.x] : one;
   const int xb = blockIdx.x * 64;
   if (xb >= it.Fx) return;
   const int f = e.y, c = blockIdx.z;
-  const int V = it.V, Vp = it.Vp, rot = it.rotV, Fx = it.Fx, Fy = it.Fy;
+  const int V = it.V, Vp = it.Vp, Fx = it.Fx, Fy = it.Fy;
   const float2* src = it.T + ((size_t)f * 3 + c) * V * Fx;
   {
-    // rows of the x-pass result for this column block, all requests in flight together
-    const int x = threadIdx.x & 63, v0 = threadIdx.x >> 6;
-    float2 tv[8];
+    // rows of the x-pass result for this column block, 8 requests in flight per thread
+    const int x = threadIdx.x & 63, r0 = threadIdx.x >> 6;
+    for (int p0 = r0; p0 < Vp; p0 += 32) {
+      float2 tv[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const int v = v0 + 4 * k;
-      tv[k] = (v < V && xb + x < Fx) ? src[(size_t)v * Fx + xb + x] : make_float2(0.f, 0.f);
+      for (int k = 0; k < 8; ++k) {
+        const int pos = p0 + 4 * k;
+        const int v = pos < Vp ? fold_order(pos, V, Vp) : -1;
+        tv[k] = (v >= 0 && xb + x < Fx) ? src[(size_t)v * Fx + xb + x] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (p0 + 4 * k < Vp) tcol[(p0 + 4 * k) * 64 + x] = tv[k];
     }
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (v0 + 4 * k < V) tcol[(v0 + 4 * k) * 64 + x] = tv[k];
-    for (int v = v0 + 32; v < V; v += 4) tcol[v * 64 + x] = (xb + x < Fx) ? src[(size_t)v * Fx + xb + x] : make_float2(0.f, 0.f);
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -266,25 +277,63 @@ __global__ void __launch_bounds__(256, 4) ypass_kernel(const __grid_constant__ I
   const int Q = Fy >> 3;
   float2* out = BATCH ? outs[e.x] : out_one;
   float2* dst = out + (((size_t)c * it.Fz + f) * Fy) * Fx + x;
-  const float4* col = ys_col4 + lane - (size_t)rot * 32;  // indexed by stored position p
-  for (int b = w; b < Q; b += 8) {
-    float2 G0[8], G1[8];
-    const float2* tw = it.twy + (size_t)b * Vp;
+  const float4* col = ys_col4 + lane;
+  if constexpr (!PAIR) {
+    for (int b = w; b < Q; b += 8) {
+      const float2* tw = it.twy + (size_t)b * Vp;
+      float2 G0[8], G1[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      G0[r] = G1[r] = make_float2(0.f, 0.f);
-      for (int p = rot + ((r - rot) & 7); p < rot + V; p += 8) {
-        const float2 t = __ldg(tw + p);
-        const float4 d = col[(size_t)p * 32];
-        c_fma(G0[r], make_float2(d.x, d.y), t);
-        c_fma(G1[r], make_float2(d.z, d.w), t);
+      for (int r = 0; r < 8; ++r) G0[r] = G1[r] = make_float2(0.f, 0.f);
+      for (int p0 = 0; p0 < Vp; p0 += 8) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const float4 d = col[(size_t)(p0 + r) * 32];
+          const float2 t = __ldg(tw + p0 + r);
+          c_fma(G0[r], make_float2(d.x, d.y), t);
+          c_fma(G1[r], make_float2(d.z, d.w), t);
+        }
+      }
+      idft8(G0);
+      idft8(G1);
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        __stcs(reinterpret_cast<float4*>(dst + (size_t)(b + a * Q) * Fx),
+               make_float4(G0[a].x, G0[a].y, G1[a].x, G1[a].y));
+    }
+    return;
+  }
+  for (int b = w; b < Q; b += 16) {
+    const bool two = b + 8 < Q;
+    const float2* twA = it.twy + (size_t)b * Vp;
+    const float2* twB = two ? twA + (size_t)8 * Vp : twA;
+    float2 A0[8], A1[8], B0[8], B1[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) A0[r] = A1[r] = B0[r] = B1[r] = make_float2(0.f, 0.f);
+    for (int p0 = 0; p0 < Vp; p0 += 8) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const float4 d = col[(size_t)(p0 + r) * 32];
+        const float2 ta = __ldg(twA + p0 + r), tb = __ldg(twB + p0 + r);
+        const float2 d0 = make_float2(d.x, d.y), d1 = make_float2(d.z, d.w);
+        c_fma(A0[r], d0, ta);
+        c_fma(A1[r], d1, ta);
+        c_fma(B0[r], d0, tb);
+        c_fma(B1[r], d1, tb);
       }
     }
-    idft8(G0);
-    idft8(G1);
+    idft8(A0);
+    idft8(A1);
 #pragma unroll
     for (int a = 0; a < 8; ++a)
-      __stcs(reinterpret_cast<float4*>(dst + (size_t)(b + a * Q) * Fx), make_float4(G0[a].x, G0[a].y, G1[a].x, G1[a].y));
+      __stcs(reinterpret_cast<float4*>(dst + (size_t)(b + a * Q) * Fx), make_float4(A0[a].x, A0[a].y, A1[a].x, A1[a].y));
+    if (two) {
+      idft8(B0);
+      idft8(B1);
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+        __stcs(reinterpret_cast<float4*>(dst + (size_t)(b + 8 + a * Q) * Fx),
+               make_float4(B0[a].x, B0[a].y, B1[a].x, B1[a].y));
+    }
   }
 }
 
@@ -299,10 +348,10 @@ __global__ void gather_kernel(const float2* __restrict__ S_part, size_t split_st
   S[i] = acc;
 }
 
-cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_M,
+cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_VUp,
                          cudaStream_t st) {
   if (n_entries == 0) return cudaSuccess;
-  const size_t xs = (size_t)max_M * sizeof(float2);
+  const size_t xs = (size_t)max_VUp * sizeof(float2);
   cudaError_t e;
   if (items) {
     e = allow_max_smem(reinterpret_cast<const void*>(xpass_kernel<true>));
@@ -316,22 +365,41 @@ cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d
   return cudaGetLastError();
 }
 
-cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_Qx,
-                         int max_V, float2* out_one, float2* const* d_outs, cudaStream_t st) {
-  if (n_entries == 0) return cudaSuccess;
-  const size_t ys = (size_t)max_V * 64 * sizeof(float2);
+template <bool PAIR>
+static cudaError_t launch_ypass_t(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
+                                  int max_Qx, size_t ys, float2* out_one, float2* const* d_outs, cudaStream_t st) {
   const dim3 grid((max_Qx * 8 + 63) / 64, n_entries, 3);
   cudaError_t e;
   if (items) {
-    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<true>));
+    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<true, PAIR>));
     if (e != cudaSuccess) return e;
-    ypass_kernel<true><<<grid, 256, ys, st>>>(one, items, d_entries, nullptr, d_outs);
+    ypass_kernel<true, PAIR><<<grid, 256, ys, st>>>(one, items, d_entries, nullptr, d_outs);
   } else {
-    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<false>));
+    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<false, PAIR>));
     if (e != cudaSuccess) return e;
-    ypass_kernel<false><<<grid, 256, ys, st>>>(one, nullptr, d_entries, out_one, nullptr);
+    ypass_kernel<false, PAIR><<<grid, 256, ys, st>>>(one, nullptr, d_entries, out_one, nullptr);
   }
   return cudaGetLastError();
+}
+
+bool ypass_pairs(int Vp) { return Vp >= 24; }
+
+cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int n_pair,
+                         int max_Qx, int max_Vp, float2* out_one, float2* const* d_outs, cudaStream_t st,
+                         int* launches) {
+  const size_t ys = (size_t)max_Vp * 64 * sizeof(float2);
+  int n = 0;
+  cudaError_t e = cudaSuccess;
+  if (n_pair > 0) {
+    e = launch_ypass_t<true>(one, items, d_entries, n_pair, max_Qx, ys, out_one, d_outs, st);
+    ++n;
+  }
+  if (e == cudaSuccess && n_entries > n_pair) {
+    e = launch_ypass_t<false>(one, items, d_entries + n_pair, n_entries - n_pair, max_Qx, ys, out_one, d_outs, st);
+    ++n;
+  }
+  if (launches) *launches = n;
+  return e;
 }
 
 size_t recompose_smem_bytes(int V, int Up, int Vp) { return ((size_t)Vp * 64 + (size_t)V * Up) * sizeof(float2); }
