@@ -139,6 +139,31 @@ def dist_setup():
     return world, rank, local
 
 
+# ---- replicas: every rank synthesises its own volume; no data-path collective ----
+def replica_seed(rank: int) -> int:
+    """Seed of a rank's synthetic layer set (independent replicas)."""
+    return rank
+
+
+def reduce_over_ranks(x: float, op: str, device) -> float:
+    """MAX or SUM of a host scalar over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX if op == "max" else tdist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def replica_throughput(units_local: float, seconds_local: float, device):
+    """Whole-job throughput of independent replicas: the units all ranks processed
+    over the slowest rank's time. Returns (value, max_seconds)."""
+    total = reduce_over_ranks(units_local, "sum", device)
+    slowest = reduce_over_ranks(seconds_local, "max", device)
+    return total / slowest, slowest
+
+
 def oracle_sample_rate(W, g, a, zb, zp, seconds=12.0, max_planes=None):
     """Voxels/s of the FP64 oracle (spectrum + direct sum) on whole planes of
     the same workload, planes taken in order until ~`seconds` elapse or
@@ -246,7 +271,7 @@ def run_sweep(args, dev, world, peaks_hbm):
     info = bp.info()
     roof_ms = (w_bytes + out_bytes) / (peaks_hbm * 1e9) * 1e3
     res = {"workload": f"sweep_{n}_wavenumbers_orders_9_to_25_16_layers_128x128x64", "items": n,
-           "voxels_per_sweep": voxels, "ms_per_sweep": ms, "value": world * voxels / (ms * 1e-3),
+           "voxels_per_sweep": voxels, "ms_per_sweep": ms, "value": replica_throughput(voxels, ms * 1e-3, dev)[0],
            "unit": "voxels/s", "steps": steps, "graph": True,
            "algorithmic_bytes": w_bytes + out_bytes, "hbm_roofline_ms": roof_ms, "roofline_frac": roof_ms / ms,
            "contract_gbs": w_bytes / (kt["contract_ms"] * 1e-3) / 1e9,
@@ -341,7 +366,7 @@ def run_ours(args, world, rank, local):
     Fz = len(zp)
     voxels = F_XY * F_XY * Fz
 
-    W, g, a, *_ = wl.random_layer_set(rank, U_ORD, U_ORD, L_LAYERS)
+    W, g, a, *_ = wl.random_layer_set(replica_seed(rank), U_ORD, U_ORD, L_LAYERS)
     Wd = torch.from_numpy(W).to(dev)
     gd = torch.from_numpy(g).to(dev)
     ad = torch.from_numpy(a).to(dev)
@@ -396,11 +421,8 @@ def run_ours(args, world, rank, local):
     plan.enable_timing(False)
     plan.check()
     direct_ms = d0.elapsed_time(d1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * voxels * args.steps / (ms * 1e-3)
+    value, seconds = replica_throughput(voxels * args.steps, ms * 1e-3, dev)
+    ms = seconds * 1e3
     info = plan.info()
 
     # roofline of the dominant kernel: algorithmic bytes per launch / live launch time
@@ -471,12 +493,9 @@ def run_ours(args, world, rank, local):
         for _ in range(n_e2e):
             hplan.synthesize_host(Wh, gh, ah, out=oh)
         t_e2e = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([t_e2e], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        e2e_value, t_e2e = replica_throughput(voxels * n_e2e, t_e2e, dev)
         hplan.check()
-        e2e = {"value": world * voxels * n_e2e / t_e2e, "unit": "voxels/s",
+        e2e = {"value": e2e_value, "unit": "voxels/s",
                "h2d_bytes_per_step": W.nbytes + g.nbytes + a.nbytes, "d2h_bytes_per_step": oh.nbytes,
                "steps": n_e2e, "ms_per_step": 1e3 * t_e2e / n_e2e,
                "includes": "H2D of W, gamma, alpha; W conversion; synthesis; D2H of the field"}
@@ -555,6 +574,8 @@ def main():
     ap.add_argument("--sweep-items", type=int, default=128)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate block")
     ap.add_argument("--fno-batch", type=int, default=256)
+    ap.add_argument("--only-surrogate", action="store_true",
+                    help="run only the learned-surrogate block and print its JSON (a profiling aid, not the bench line)")
     ap.add_argument("--layers", type=int, default=32)
     ap.add_argument("--pipeline", type=int, default=1, help="layer groups overlapped in graph replay")
     ap.add_argument("--planes-per-layer", type=int, default=8)
@@ -566,6 +587,12 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         return run_reference(args, world, rank)
+    if args.only_surrogate:
+        import torch
+        dev = torch.device("cuda", local)
+        torch.cuda.set_device(dev)
+        print(json.dumps({"surrogate": run_surrogate(args, dev, (peaks()[1], bf16_sustained()))}), flush=True)
+        return 0
     return run_ours(args, world, rank, local)
 
 
