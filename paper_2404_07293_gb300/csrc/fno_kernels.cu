@@ -29,13 +29,27 @@ __global__ void tables_kernel(T* __restrict__ D, T* __restrict__ E, int N, int m
   }
 }
 
-// ---- lift: V_0 = P a + p, a = (Re n - 1, Im n) per slice, nearest upsampling
-// (features beyond the 2S inputs are zero, so the channel loop has a fixed trip count)
+// ---- lift: V_0 = P a + p, a = (Re n - 1, Im n) per slice, nearest upsampling.
+// One thread per input pixel: the r x r output pixels it covers share one value,
+// written channel-last (32 contiguous values each) and channel-first (pairs of
+// horizontally adjacent pixels in one store when r is even). Features beyond the
+// 2S inputs are zero, so the channel loop has a fixed trip count.
+template <typename T>
+__device__ __forceinline__ void st_same_pair(T* p, float v);
+template <>
+__device__ __forceinline__ void st_same_pair<float>(float* p, float v) {
+  *reinterpret_cast<float2*>(p) = make_float2(v, v);
+}
+template <>
+__device__ __forceinline__ void st_same_pair<__nv_bfloat16>(__nv_bfloat16* p, float v) {
+  *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v, v);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n, const T* __restrict__ prm,
                                                    T* __restrict__ Vcf, T* __restrict__ Vcl, int B, int S,
                                                    int in_grid, int N) {
-  __shared__ float Ps[C * 32];  // [c][32], zero-padded past 2S
+  __shared__ __align__(16) float Ps[C * 32];  // [c][32], zero-padded past 2S
   __shared__ float ps[C];
   const int cin = 2 * S;
   for (int i = threadIdx.x; i < C * 32; i += blockDim.x) {
@@ -44,12 +58,11 @@ __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n,
   }
   if (threadIdx.x < C) ps[threadIdx.x] = to_f(prm[C * cin + threadIdx.x]);
   __syncthreads();
-  const int P = N * N;
+  const int P = N * N, Pi = in_grid * in_grid, r = N / in_grid;
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)B * P) return;
-  const int b = (int)(idx / P), p = (int)(idx % P);
-  const int r = N / in_grid;
-  const int yi = (p / N) / r, xi = (p % N) / r;
+  if (idx >= (long long)B * Pi) return;
+  const int b = (int)(idx / Pi), pi = (int)(idx % Pi);
+  const int yi = pi / in_grid, xi = pi % in_grid;
   float a[32];
 #pragma unroll
   for (int s = 0; s < 16; ++s) {
@@ -58,18 +71,34 @@ __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n,
     a[2 * s] = v.x - 1.0f;
     a[2 * s + 1] = v.y;
   }
+  const float4* P4 = reinterpret_cast<const float4*>(Ps);
   float o[32];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
     float t = ps[c];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) t = fmaf(Ps[c * 32 + i], a[i], t);
+    for (int i = 0; i < 8; ++i) {
+      const float4 w = P4[c * 8 + i];
+      t = fmaf(w.x, a[4 * i], fmaf(w.y, a[4 * i + 1], fmaf(w.z, a[4 * i + 2], fmaf(w.w, a[4 * i + 3], t))));
+    }
     o[c] = t;
   }
-  st32(Vcl + ((size_t)b * P + p) * C, o);
-  T* cf = Vcf + (size_t)b * C * P + p;
+  for (int dy = 0; dy < r; ++dy) {
+    const int row = (yi * r + dy) * N + xi * r;
+    for (int dx = 0; dx < r; ++dx) st32(Vcl + ((size_t)b * P + row + dx) * C, o);
+    T* cf = Vcf + (size_t)b * C * P + row;
+    if ((r & 1) == 0) {
+      for (int dx = 0; dx < r; dx += 2) {
 #pragma unroll
-  for (int c = 0; c < C; ++c) cf[(size_t)c * P] = from_f<T>(o[c]);
+        for (int c = 0; c < C; ++c) st_same_pair(cf + (size_t)c * P + dx, o[c]);
+      }
+    } else {
+      for (int dx = 0; dx < r; ++dx) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) cf[(size_t)c * P + dx] = from_f<T>(o[c]);
+      }
+    }
+  }
 }
 
 // ---- mixing (per kept mode k, complex C x C), spectra mode-major Vh[split][k][b C + i] ------
@@ -243,7 +272,7 @@ __global__ void __launch_bounds__(256) target_norm_kernel(const float2* __restri
 //   part_proj row [6 C + 6]: dQ[j][o] = sum_p dF[j][p] V[o][p], dq[j] = sum_p dF[j][p]
 //   part_err = sum_p |d|^2, part_pool[C] = sum_p V[o][p]
 template <typename T>
-__global__ void __launch_bounds__(256) project_train_kernel(const T* __restrict__ Vcl,
+__global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restrict__ Vcl,
                                                                const float2* __restrict__ target,
                                                                const T* __restrict__ prm_q,
                                                                const float* __restrict__ part_tn,
@@ -251,7 +280,7 @@ __global__ void __launch_bounds__(256) project_train_kernel(const T* __restrict_
                                                                float* __restrict__ part_err,
                                                                float* __restrict__ part_pool,
                                                                float* __restrict__ part_proj, int B, int P) {
-  __shared__ float Qs[OUT * C + OUT];
+  __shared__ __align__(16) float Qs[OUT * C + OUT];
   __shared__ float Vs[PIX_BLOCK][C + 1];
   __shared__ float Fs[OUT][PIX_BLOCK];
   __shared__ float red[8];
@@ -268,12 +297,16 @@ __global__ void __launch_bounds__(256) project_train_kernel(const T* __restrict_
   ld32(Vcl + ((size_t)b * P + p) * C, v);
 #pragma unroll
   for (int o = 0; o < C; ++o) Vs[t][o] = v[o];
+  const float4* Q4 = reinterpret_cast<const float4*>(Qs);  // row j: Q4[8 j .. 8 j + 8)
   float d[OUT];
 #pragma unroll
   for (int j = 0; j < OUT; ++j) {
     float f = Qs[OUT * C + j];
 #pragma unroll
-    for (int o = 0; o < C; ++o) f = fmaf(Qs[j * C + o], v[o], f);
+    for (int i = 0; i < 8; ++i) {
+      const float4 q = Q4[8 * j + i];
+      f = fmaf(q.x, v[4 * i], fmaf(q.y, v[4 * i + 1], fmaf(q.z, v[4 * i + 2], fmaf(q.w, v[4 * i + 3], f))));
+    }
     const float2 tv = target[((size_t)b * 3 + j / 2) * P + p];
     d[j] = f - ((j & 1) ? tv.y : tv.x);
   }
@@ -285,12 +318,22 @@ __global__ void __launch_bounds__(256) project_train_kernel(const T* __restrict_
     d[j] *= sc;
     Fs[j][t] = d[j];
   }
+  __syncwarp();  // Q is re-read from shared memory below rather than held in registers across both products
 #pragma unroll
-  for (int o = 0; o < C; ++o) {
-    float s = 0.f;
+  for (int i = 0; i < 8; ++i) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < OUT; ++j) s = fmaf(Qs[j * C + o], d[j], s);
-    v[o] = s;  // v now holds dV_L
+    for (int j = 0; j < OUT; ++j) {
+      const float4 q = Q4[8 * j + i];
+      acc.x = fmaf(q.x, d[j], acc.x);
+      acc.y = fmaf(q.y, d[j], acc.y);
+      acc.z = fmaf(q.z, d[j], acc.z);
+      acc.w = fmaf(q.w, d[j], acc.w);
+    }
+    v[4 * i] = acc.x;  // v now holds dV_L
+    v[4 * i + 1] = acc.y;
+    v[4 * i + 2] = acc.z;
+    v[4 * i + 3] = acc.w;
   }
   st32(dZcl + ((size_t)b * P + p) * C, v);
   T* cf = dZcf + (size_t)b * C * P + p;
@@ -523,7 +566,7 @@ cudaError_t launch_tables(T* D, T* E, int N, int m, int Kp, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_lift(const float2* n, const T* params, T* Vcf, T* Vcl, int B, int S, int in_grid, int N,
                         cudaStream_t st) {
-  const long long total = (long long)B * N * N;
+  const long long total = (long long)B * in_grid * in_grid;
   lift_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(n, params, Vcf, Vcl, B, S, in_grid, N);
   return cudaGetLastError();
 }
