@@ -477,7 +477,8 @@ struct scw_plan_s {
   TcSchedule sched;
   float2** d_outs = nullptr;
   float2** h_outs = nullptr;       // pinned
-  int max_M = 0, max_Qx = 0, max_V = 0, max_VUp = 0, max_Vp = 0;
+  int max_M = 0, max_Qx = 0, max_V = 0, max_Vp = 0;
+  size_t xpass_smem = 0;
   size_t rec_smem = 0;
   // graph replay
   cudaStream_t cap_stream = nullptr;
@@ -633,7 +634,7 @@ static scw_status enqueue_pipelined(scw_plan_t P, float2* out_one, cudaStream_t 
     const int nb = P->gplane[g + 1] - P->gplane[g];
     if (nb == 0) continue;
     const int2* ent = P->d_plane_entries + P->gplane[g];
-    e = launch_xpass(one, nullptr, ent, nb, P->max_VUp, P->st2);
+    e = launch_xpass(one, nullptr, ent, nb, P->xpass_smem, P->st2);
     if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
     int ny = 0;
     e = launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, out_one, nullptr,
@@ -656,7 +657,7 @@ static scw_status enqueue_synthesis(scw_plan_t P, float2* out_one, cudaStream_t 
   const ItemDev& one = P->items[0]->item;
   const ItemDev* items = P->batched ? P->d_items : nullptr;
   mark(P, 2, st, marks);
-  cudaError_t e = launch_xpass(one, items, P->d_plane_entries, P->n_plane_entries, P->max_VUp, st);
+  cudaError_t e = launch_xpass(one, items, P->d_plane_entries, P->n_plane_entries, P->xpass_smem, st);
   if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
   mark(P, 3, st, marks);
   int ny = 0;
@@ -828,7 +829,7 @@ static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, boo
     P->max_M = std::max(P->max_M, p->M);
     P->max_Qx = std::max(P->max_Qx, p->Fx / 8);
     P->max_V = std::max(P->max_V, p->V);
-    P->max_VUp = std::max(P->max_VUp, p->V * p->item.Up);
+    P->xpass_smem = std::max(P->xpass_smem, xpass_smem_bytes(p->V, p->item.Up, p->Fx));
     P->max_Vp = std::max(P->max_Vp, p->item.Vp);
     P->rec_smem = std::max(P->rec_smem, recompose_smem_bytes(p->V, p->item.Up, p->item.Vp));
   }

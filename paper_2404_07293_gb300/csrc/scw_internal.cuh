@@ -183,8 +183,10 @@ int tc_ctas_per_sm(int NB, bool bf16);
 // step (c): plane entries are (item, plane) pairs; S_override / nsplit_override replace the
 // contraction's partial spectra with caller-given spectra
 size_t recompose_smem_bytes(int V, int Up, int Vp);
-cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_VUp,
-                         cudaStream_t st);
+// smem_bytes: the largest xpass_smem_bytes of the items
+size_t xpass_smem_bytes(int V, int Up, int Fx);
+cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
+                         size_t smem_bytes, cudaStream_t st);
 // entries [0, n_pair) run the two-residue y-pass (long folds, ypass_pairs(Vp)), the rest the
 // one-residue y-pass; *launches receives the number of kernels launched (0, 1 or 2)
 bool ypass_pairs(int Vp);

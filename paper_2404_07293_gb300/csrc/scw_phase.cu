@@ -105,10 +105,9 @@ __device__ __forceinline__ size_t swz_offset(int n, int k, int rows) {
 // (NB = 2 F_pad) in the layout above: row f holds (Re c_j, -Im c_j) at columns
 // (2j, 2j+1), row F_pad + f holds (Im c_j, Re c_j); with A = W viewed as
 // interleaved reals this gives [Re S | Im S] (the complex product as one real
-// GEMM). hi = round(x), lo = round(x - hi). One thread per mode j and group of
-// kPlaneGroup planes; blocks are (mode block, (item, unit) entry, plane group).
-constexpr int kPlaneGroup = 2;
-
+// GEMM). hi = round(x), lo = round(x - hi). One thread per mode j and all planes
+// of its unit (the mode's constants are loaded and reduced once); blocks are
+// (mode block, (item, unit) entry).
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(128) phases_tc_kernel(const __grid_constant__ ItemDev one,
                                                         const ItemDev* __restrict__ items,
@@ -117,23 +116,25 @@ __global__ void __launch_bounds__(128) phases_tc_kernel(const __grid_constant__ 
   const int2 e = entries[blockIdx.y];
   const ItemDev& it = BATCH ? items[e.x] : one;
   const LayerUnit u = it.units[e.y];
-  load_offsets(off, u, it.zplanes, it.zbounds);
-  __syncthreads();
   const int M = it.M;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int M4 = 4 * M;
+  // the mode's constants are requested before the block waits for the plane offsets
+  double2 g = make_double2(0.0, 0.0), al = make_double2(0.0, 0.0);
+  if (j < M4) {
+    g = it.gamma[(size_t)u.layer * M4 + j];
+    al = it.alpha[(size_t)u.layer * M4 + j];
+  }
+  load_offsets(off, u, it.zplanes, it.zbounds);
+  __syncthreads();
   if (j >= M4) return;
   const int NB = 2 * F_pad;
-  const ModeConst mc = mode_const(it.gamma[(size_t)u.layer * M4 + j], it.alpha[(size_t)u.layer * M4 + j],
-                                  it.inv_lam);
+  const ModeConst mc = mode_const(g, al, it.inv_lam);
   const bool fwd = j < 2 * M;
   const size_t base = (size_t)e.y * it.nk * NB * 64;  // B is per work unit
   T* Bhi = static_cast<T*>(it.Bhi) + base;
   T* Blo = static_cast<T*>(it.Blo) + base;
-  const int fb = blockIdx.z * kPlaneGroup;
-#pragma unroll
-  for (int q = 0; q < kPlaneGroup; ++q) {
-    const int f = fb + q;
+  for (int f = 0; f < F_pad; ++f) {
     float2 cv = make_float2(0.f, 0.f);
     if (f < u.nf) {
       const float dh = fwd ? off.f_hi[f] : off.b_hi[f];
@@ -304,7 +305,7 @@ cudaError_t launch_transpose_layers(const float2* W, float2* Wt, int L, int rows
 template <typename T>
 static cudaError_t launch_phases_tc_t(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
                                       int max_M, int F_pad, cudaStream_t st) {
-  dim3 grid((4 * max_M + 127) / 128, n_entries, F_pad / kPlaneGroup);
+  dim3 grid((4 * max_M + 127) / 128, n_entries);
   if (items)
     phases_tc_kernel<T, true><<<grid, 128, 0, st>>>(one, items, d_entries, F_pad);
   else

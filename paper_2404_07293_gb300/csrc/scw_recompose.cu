@@ -176,16 +176,28 @@ constexpr int kSplitUnroll = 8;  // split partials loaded together (more are add
 
 // One CTA per (item-plane, component): V * Fx/8 tasks (row vi, residue b).
 // The spectrum of component c (split partials summed) is laid out [V][Up] in
-// shared memory at the fold positions, padding zero.
+// shared memory at the fold positions, padding zero; the fold twiddles [Up][Fx/8]
+// follow it when they fit (xpass_twiddles_staged), else they are read through L1.
+constexpr size_t kXpassTwBytes = 32 * 1024;
+
+__host__ __device__ __forceinline__ bool xpass_twiddles_staged(int Up, int Fx) {
+  return (size_t)Up * (Fx / 8) * sizeof(float2) <= kXpassTwBytes;
+}
+
 template <bool BATCH>
 __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ ItemDev one,
                                                     const ItemDev* __restrict__ items,
                                                     const int2* __restrict__ entries) {
-  extern __shared__ float2 xs_row[];  // [V][Up]
+  extern __shared__ float2 xs_row[];  // [V][Up], then the staged twiddles [Up][Fx/8]
   const int2 e = entries[blockIdx.x];
   const ItemDev& it = BATCH ? items[e.x] : one;
   const int f = e.y, c = blockIdx.y;
   const int U = it.U, V = it.V, M = it.M, Up = it.Up, Fx = it.Fx;
+  const int Q = Fx >> 3;
+  const bool staged = xpass_twiddles_staged(Up, Fx);
+  float2* tw_s = xs_row + V * Up;
+  if (staged)
+    for (int i = threadIdx.x; i < Up * Q; i += blockDim.x) tw_s[i] = __ldg(it.twx + i);
   const float2* src = it.S_part + (size_t)f * 3 * M + (size_t)c * M;
   const int ns = it.nsplit[f];
   const size_t stride = it.split_stride;
@@ -214,18 +226,19 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
     }
   }
   __syncthreads();
-  const int Q = Fx >> 3;
   float2* dst = it.T + ((size_t)f * 3 + c) * V * Fx;
+  const float2* twb = staged ? tw_s : it.twx;  // [p][b]: a warp's lanes read consecutive residues
   for (int t = threadIdx.x; t < V * Q; t += blockDim.x) {
     const int vi = t / Q, b = t - vi * Q;
     const float2* s = xs_row + vi * Up;
-    const float2* tw = it.twx + b;  // [p][b]: a warp's lanes read consecutive residues
+    const float2* tw = twb + b;
     float2 G[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) G[r] = make_float2(0.f, 0.f);
+#pragma unroll 2
     for (int p0 = 0; p0 < Up; p0 += 8) {
 #pragma unroll
-      for (int r = 0; r < 8; ++r) c_fma(G[r], s[p0 + r], __ldg(tw + (size_t)(p0 + r) * Q));
+      for (int r = 0; r < 8; ++r) c_fma(G[r], s[p0 + r], tw[(size_t)(p0 + r) * Q]);
     }
     idft8(G);
     float2* o = dst + (size_t)vi * Fx + b;
@@ -348,10 +361,14 @@ __global__ void gather_kernel(const float2* __restrict__ S_part, size_t split_st
   S[i] = acc;
 }
 
-cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_VUp,
-                         cudaStream_t st) {
+size_t xpass_smem_bytes(int V, int Up, int Fx) {
+  return ((size_t)V * Up + (xpass_twiddles_staged(Up, Fx) ? (size_t)Up * (Fx / 8) : 0)) * sizeof(float2);
+}
+
+cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
+                         size_t smem_bytes, cudaStream_t st) {
   if (n_entries == 0) return cudaSuccess;
-  const size_t xs = (size_t)max_VUp * sizeof(float2);
+  const size_t xs = smem_bytes;
   cudaError_t e;
   if (items) {
     e = allow_max_smem(reinterpret_cast<const void*>(xpass_kernel<true>));
