@@ -190,6 +190,9 @@ def blas_threads():
         from threadpoolctl import threadpool_info
         return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
     except Exception:
+        for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+            if os.environ.get(k, "").isdigit():
+                return min(int(os.environ[k]), os.cpu_count() or 1)
         return os.cpu_count() or 1
 
 
