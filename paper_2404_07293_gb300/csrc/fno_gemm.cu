@@ -28,6 +28,7 @@
 // FP32 operands, 128 rows x 32 columns per CTA.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "fno_internal.cuh"
@@ -247,6 +248,230 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
   }
 }
 
+// Persistent form of the layer products (EPI_LAYER_FWD / EPI_LAYER_BWD, BN = 256): one
+// CTA per SM walks the output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (pixel
+// tile fastest, so CTAs in flight share their Wh / GVh tile through L2). Four operand
+// stages; two 256-column TMEM accumulators, so the epilogue of one tile runs while the
+// MMAs of the next one are issued (acc_full / acc_empty barriers, as in the contraction).
+constexpr int kLayerStages = 4;
+constexpr uint32_t kLayerStage = GemmCfg<256>::STAGE;
+constexpr uint32_t kLayerSmem = kLayerStages * kLayerStage + 1024u;
+
+template <int EPI>
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_layer_persistent(const __grid_constant__ CUtensorMap mA,
+                                                                         const __grid_constant__ CUtensorMap mB,
+                                                                         const __grid_constant__ CUtensorMap mA2,
+                                                                         const __grid_constant__ CUtensorMap mW,
+                                                                         const __grid_constant__ EpiArgs ea, int K,
+                                                                         int m_tiles, int n_tiles, int* err,
+                                                                         uint64_t timeout_ns) {
+  constexpr int BN = 256;
+  constexpr int STAGES = kLayerStages;
+  constexpr uint32_t A_BYTES = GemmCfg<256>::A_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar[2];
+  __shared__ __align__(8) uint64_t acce_bar[2];
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+  __shared__ __align__(16) float w_s[C * C];
+  __shared__ __align__(16) float b_s[C];
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tasks = m_tiles * n_tiles;
+  const int nkb = K / 64;
+  const uint64_t deadline = ptx::globaltimer() + timeout_ns;
+  auto tile_nseg = [&](int n0) { return max(0, min(BN / C, ea.B - n0 / C)); };
+
+  if (threadIdx.x < C) {
+    const __nv_bfloat16* bias = static_cast<const __nv_bfloat16*>(ea.bias);
+    b_s[threadIdx.x] = bias ? __bfloat162float(bias[threadIdx.x]) : 0.f;
+  }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      ptx::mbar_init(ptx::smem_u32(&full_bar[i]), 1);
+      ptx::mbar_init(ptx::smem_u32(&empty_bar[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(ptx::smem_u32(&accf_bar[i]), 1);
+      ptx::mbar_init(ptx::smem_u32(&acce_bar[i]), 8);  // one arrival per epilogue warp
+    }
+    ptx::mbar_init(ptx::smem_u32(&drain_bar), 1);
+    abort_s = 0;
+    ptx::fence_mbar_init();
+    ptx::prefetch_tensormap(&mA);
+    ptx::prefetch_tensormap(&mB);
+    ptx::prefetch_tensormap(&mA2);
+    ptx::prefetch_tensormap(&mW);
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc(ptx::smem_u32(&tmem_base_s), 2 * BN);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int st = 0, issued = 0;
+    uint32_t ph = 0;
+    for (int t = blockIdx.x; t < n_tasks && !abort_s; t += gridDim.x) {
+      const int m0 = (t % m_tiles) * 128, n0 = (t / m_tiles) * BN;
+      const int total = nkb + tile_nseg(n0);
+      for (int i = 0; i < total && !abort_s; ++i) {
+        if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[st]), ph ^ 1u, deadline)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_EMPTY);
+          abort_s = 1;
+          break;
+        }
+        const uint32_t fb = ptx::smem_u32(&full_bar[st]);
+        const uint32_t sa = ptx::smem_u32(smem + (size_t)st * kLayerStage);
+        if (i < nkb) {
+          ptx::mbar_arrive_expect_tx(fb, kLayerStage);
+          ptx::tma_load_2d(sa, &mA, i * 64, m0, fb);
+          ptx::tma_load_2d(sa + A_BYTES, &mB, i * 64, n0, fb);
+        } else {
+          const int smp = n0 / C + (i - nkb);
+          ptx::mbar_arrive_expect_tx(fb, kSeg2Bytes);
+          ptx::tma_load_2d(sa, &mA2, 0, smp * ea.P + m0, fb);
+          ptx::tma_load_2d(sa + A_BYTES, &mW, 0, 0, fb);
+        }
+        ++issued;
+        if (++st == STAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    if (abort_s) {
+      const uint64_t d2 = ptx::globaltimer() + timeout_ns;
+      for (int back = 1; back <= STAGES && back <= issued; ++back) {
+        const int i = issued - back;
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[i % STAGES]), (uint32_t)(i / STAGES) & 1u, d2)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
+          break;
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- tcgen05.mma issuer ----------------
+    constexpr uint32_t idesc = ptx::idesc_f16(true, 128, BN);
+    constexpr uint32_t idesc32 = ptx::idesc_f16(true, 128, 32);
+    int st = 0, lt = 0;
+    uint32_t ph = 0;
+    for (int t = blockIdx.x; t < n_tasks && !abort_s; t += gridDim.x, ++lt) {
+      const int n0 = (t / m_tiles) * BN;
+      const int total = nkb + tile_nseg(n0);
+      const int acc = lt & 1;
+      if (!ptx::mbar_wait(ptx::smem_u32(&acce_bar[acc]), ((uint32_t)(lt >> 1) & 1u) ^ 1u, deadline)) {
+        atomicOr(err, DEV_ERR_TIMEOUT_ACCUM);
+        abort_s = 1;
+        break;
+      }
+      ptx::tc_fence_after();
+      const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
+      for (int i = 0; i < total; ++i) {
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[st]), ph, deadline)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_FULL);
+          abort_s = 1;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t sa = ptx::smem_u32(smem + (size_t)st * kLayerStage);
+        if (i < nkb) {
+          const uint64_t da = ptx::sw128_desc(sa), db = ptx::sw128_desc(sa + A_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t o = (uint64_t)(2 * kk);
+            ptx::mma_f16(d_tmem, da + o, db + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
+          }
+        } else {
+          const uint64_t da = ptx::sw64_desc(sa), db = ptx::sw64_desc(sa + A_BYTES);
+          const uint32_t d = d_tmem + (uint32_t)(C * (i - nkb));
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t o = (uint64_t)(2 * kk);
+            ptx::mma_f16(d, da + o, db + o, idesc32, 1u);
+          }
+        }
+        ptx::mma_commit(ptx::smem_u32(&empty_bar[st]));
+        if (++st == STAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+      if (abort_s) break;
+      ptx::mma_commit(ptx::smem_u32(&accf_bar[acc]));
+    }
+    if (abort_s) {
+      ptx::mma_commit(ptx::smem_u32(&drain_bar));
+      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::globaltimer() + timeout_ns))
+        atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int grp = warp & 3;          // TMEM lanes 32 grp .. 32 grp + 31
+    const int half = (warp - 2) >> 2;  // column chunks half, half + 2, ...
+    int lt = 0;
+    for (int t = blockIdx.x; t < n_tasks; t += gridDim.x, ++lt) {
+      const int m0 = (t % m_tiles) * 128, n0 = (t / m_tiles) * BN;
+      const int acc = lt & 1;
+      bool ok = true;
+      for (;;) {
+        if (ptx::mbar_try_wait(ptx::smem_u32(&accf_bar[acc]), (uint32_t)(lt >> 1) & 1u)) break;
+        if (abort_s || ptx::globaltimer() > deadline) {
+          ok = false;
+          break;
+        }
+      }
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0 && !abort_s) atomicOr(err, DEV_ERR_TIMEOUT_ACCUM);
+        abort_s = 1;
+        break;
+      }
+      ptx::tc_fence_after();
+      const int row = m0 + grp * 32 + lane;
+      const uint32_t lane_addr = tmem + (uint32_t)(acc * BN) + ((uint32_t)(grp * 32) << 16);
+#pragma unroll 1
+      for (int c = half; c < BN / 32; c += 2) {
+        if (n0 + 32 * c >= ea.cols) break;  // warp-uniform
+        uint32_t r0[8], r1[8], r2[8], r3[8];
+        ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c), r0);
+        ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c + 8), r1);
+        ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c + 16), r2);
+        ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c + 24), r3);
+        ptx::tmem_wait_ld();
+        float a[32];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          a[j] = __uint_as_float(r0[j]);
+          a[8 + j] = __uint_as_float(r1[j]);
+          a[16 + j] = __uint_as_float(r2[j]);
+          a[24 + j] = __uint_as_float(r3[j]);
+        }
+        epilogue<EPI, __nv_bfloat16, true>(ea, w_s, b_s, row, n0 + 32 * c, 0, a);
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&acce_bar[acc]));
+    }
+  }
+
+  // ---------------- teardown ----------------
+  __syncwarp();
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 2 * BN);
+  }
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(128) gemm_simt_kernel(const float* __restrict__ A, long long lda,
                                                         const float* __restrict__ Bm, long long ldb, EpiArgs ea,
@@ -310,6 +535,22 @@ static cudaError_t launch_tc_t(const CUtensorMap& mA, const CUtensorMap& mB, con
 }
 
 template <int EPI>
+static cudaError_t launch_layer_persistent(const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
+                                           const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int* err,
+                                           uint64_t timeout_ns, cudaStream_t st) {
+  const void* fn = reinterpret_cast<const void*>(gemm_layer_persistent<EPI>);
+  cudaError_t e = allow_max_smem(fn);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int m_tiles = (M + 127) / 128, n_tiles = (N + 255) / 256;
+  const int grid = std::max(1, std::min(m_tiles * n_tiles, sms));
+  gemm_layer_persistent<EPI><<<grid, kGemmThreads, kLayerSmem, st>>>(mA, mB, mA2, mW, ea, K, m_tiles, n_tiles, err,
+                                                                     timeout_ns);
+  return cudaGetLastError();
+}
+
+template <int EPI>
 static cudaError_t launch_tc_bn(int BN, const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
                                 const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int splits, int* err,
                                 uint64_t timeout_ns, cudaStream_t st) {
@@ -332,9 +573,9 @@ cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtenso
   switch (epi) {
     case EPI_MODES: return launch_tc_bn<EPI_MODES>(BN, mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
     case EPI_LAYER_FWD:
-      return launch_tc_t<256, EPI_LAYER_FWD>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
+      return launch_layer_persistent<EPI_LAYER_FWD>(mA, mB, mA2, mW, ea, M, N, K, err, timeout_ns, st);
     case EPI_LAYER_BWD:
-      return launch_tc_t<256, EPI_LAYER_BWD>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
+      return launch_layer_persistent<EPI_LAYER_BWD>(mA, mB, mA2, mW, ea, M, N, K, err, timeout_ns, st);
     case EPI_DW:
       return BN == 128 ? launch_tc_t<128, EPI_DW>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st)
                        : cudaErrorInvalidValue;
