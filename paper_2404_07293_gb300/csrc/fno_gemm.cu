@@ -253,12 +253,15 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
 // tile fastest, so CTAs in flight share their Wh / GVh tile through L2). Four operand
 // stages; two 256-column TMEM accumulators, so the epilogue of one tile runs while the
 // MMAs of the next one are issued (acc_full / acc_empty barriers, as in the contraction).
+// Twelve epilogue warps (three per TMEM lane quadrant) share the 8 column chunks.
 constexpr int kLayerStages = 4;
 constexpr uint32_t kLayerStage = GemmCfg<256>::STAGE;
 constexpr uint32_t kLayerSmem = kLayerStages * kLayerStage + 1024u;
+constexpr int kLayerEpiWarps = 12;  // three per 32-lane TMEM quadrant
+constexpr int kLayerThreads = 32 * (2 + kLayerEpiWarps);
 
 template <int EPI>
-__global__ void __launch_bounds__(kGemmThreads, 1) gemm_layer_persistent(const __grid_constant__ CUtensorMap mA,
+__global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const __grid_constant__ CUtensorMap mA,
                                                                          const __grid_constant__ CUtensorMap mB,
                                                                          const __grid_constant__ CUtensorMap mA2,
                                                                          const __grid_constant__ CUtensorMap mW,
@@ -297,7 +300,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_layer_persistent(const _
     }
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(ptx::smem_u32(&accf_bar[i]), 1);
-      ptx::mbar_init(ptx::smem_u32(&acce_bar[i]), 8);  // one arrival per epilogue warp
+      ptx::mbar_init(ptx::smem_u32(&acce_bar[i]), kLayerEpiWarps);  // one arrival per epilogue warp
     }
     ptx::mbar_init(ptx::smem_u32(&drain_bar), 1);
     abort_s = 0;
@@ -415,8 +418,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_layer_persistent(const _
     }
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int grp = warp & 3;          // TMEM lanes 32 grp .. 32 grp + 31
-    const int half = (warp - 2) >> 2;  // column chunks half, half + 2, ...
+    const int grp = warp & 3;           // TMEM lanes 32 grp .. 32 grp + 31
+    const int third = (warp - 2) >> 2;  // column chunks third, third + 3, ...
     int lt = 0;
     for (int t = blockIdx.x; t < n_tasks; t += gridDim.x, ++lt) {
       const int m0 = (t % m_tiles) * 128, n0 = (t / m_tiles) * BN;
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_layer_persistent(const _
       const int row = m0 + grp * 32 + lane;
       const uint32_t lane_addr = tmem + (uint32_t)(acc * BN) + ((uint32_t)(grp * 32) << 16);
 #pragma unroll 1
-      for (int c = half; c < BN / 32; c += 2) {
+      for (int c = third; c < BN / 32; c += 3) {
         if (n0 + 32 * c >= ea.cols) break;  // warp-uniform
         uint32_t r0[8], r1[8], r2[8], r3[8];
         ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c), r0);
@@ -545,8 +548,8 @@ static cudaError_t launch_layer_persistent(const CUtensorMap& mA, const CUtensor
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int m_tiles = (M + 127) / 128, n_tiles = (N + 255) / 256;
   const int grid = std::max(1, std::min(m_tiles * n_tiles, sms));
-  gemm_layer_persistent<EPI><<<grid, kGemmThreads, kLayerSmem, st>>>(mA, mB, mA2, mW, ea, K, m_tiles, n_tiles, err,
-                                                                     timeout_ns);
+  gemm_layer_persistent<EPI><<<grid, kLayerThreads, kLayerSmem, st>>>(mA, mB, mA2, mW, ea, K, m_tiles, n_tiles, err,
+                                                                      timeout_ns);
   return cudaGetLastError();
 }
 
