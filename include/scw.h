@@ -197,6 +197,14 @@ scw_status scw_plan_check(scw_plan_t plan, void* stream);
 /* Device-side wait limit in nanoseconds for the plan's kernels (default 2 s). */
 scw_status scw_plan_set_timeout_ns(scw_plan_t plan, uint64_t ns);
 
+/* Failure injection for tests of the timeout path (on != 0): the first CTA of the
+ * tensor-core contraction leaves its first operand stage unfilled, so its bounded
+ * waits run out after the plan's timeout; it then lets its issued copies and MMAs
+ * land, frees its tensor memory and returns, and the next scw_plan_check reports
+ * SCW_ERR_TIMEOUT (the field of that call is invalid). Nothing faults or hangs.
+ * UNSUPPORTED for FP32 plans. Drops the graph. */
+scw_status scw_plan_inject_stall(scw_plan_t plan, int on);
+
 scw_status scw_plan_get_info(scw_plan_t plan, scw_plan_info* info);
 
 /* Per-step kernel durations, measured with CUDA events recorded on the

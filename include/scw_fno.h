@@ -108,6 +108,16 @@ scw_status scw_surrogate_calibrate(scw_fno_t fno, const float* est, const float*
                                    float* q_out);
 scw_status scw_surrogate_set_offset(scw_fno_t fno, float q);
 
+/* Checkpoint / resume of the whole training state: FP32 master parameters, both
+ * Adam moments, the Adam step count and the calibration offset q, as one HOST
+ * byte blob (a 32-byte header, then three arrays of param_count floats).
+ * Loading refreshes the kernels' parameter copies, so the next train_step after
+ * a load gives bit-identical parameters to the one the saved handle would have
+ * taken. INVALID_ARGUMENT on a size, magic or parameter-count mismatch. */
+scw_status scw_surrogate_state_bytes(scw_fno_t fno, size_t* bytes);
+scw_status scw_surrogate_save_state(scw_fno_t fno, void* host, size_t bytes);
+scw_status scw_surrogate_load_state(scw_fno_t fno, const void* host, size_t bytes);
+
 /* Per-kernel timing: while on, every call records a CUDA event after each of its
  * launches and synchronises its stream at the end; times (ms, summed since the
  * last enable) and algorithmic FLOPs accumulate per kernel family:

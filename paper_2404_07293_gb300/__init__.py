@@ -145,6 +145,10 @@ class Plan:
     def set_timeout_ns(self, ns):
         check(self._lib.scw_plan_set_timeout_ns(self._h, int(ns)), "scw_plan_set_timeout_ns")
 
+    def inject_stall(self, on=True):
+        """Failure injection: the next synthesis's contraction waits run out (see scw_plan_inject_stall)."""
+        check(self._lib.scw_plan_inject_stall(self._h, 1 if on else 0), "scw_plan_inject_stall")
+
     def enable_timing(self, on=True):
         check(self._lib.scw_plan_enable_timing(self._h, 1 if on else 0), "scw_plan_enable_timing")
 
@@ -349,6 +353,29 @@ class Surrogate:
 
     def set_offset(self, q: float):
         check(self._lib.scw_surrogate_set_offset(self._h, float(q)), "scw_surrogate_set_offset")
+
+    def state(self) -> np.ndarray:
+        """The whole training state (parameters, Adam moments, step, calibration) as host bytes."""
+        n = ctypes.c_size_t()
+        check(self._lib.scw_surrogate_state_bytes(self._h, ctypes.byref(n)), "scw_surrogate_state_bytes")
+        buf = np.empty(n.value, dtype=np.uint8)
+        check(self._lib.scw_surrogate_save_state(self._h, ctypes.c_void_p(buf.ctypes.data), n.value),
+              "scw_surrogate_save_state")
+        return buf
+
+    def load_state(self, buf):
+        b = np.ascontiguousarray(buf, dtype=np.uint8)
+        check(self._lib.scw_surrogate_load_state(self._h, ctypes.c_void_p(b.ctypes.data), b.size),
+              "scw_surrogate_load_state")
+
+    def save(self, path):
+        """torch.save of the training state as a host tensor."""
+        import torch
+        torch.save({"scw_surrogate_state": torch.from_numpy(self.state())}, path)
+
+    def load(self, path):
+        import torch
+        self.load_state(torch.load(path)["scw_surrogate_state"].numpy())
 
     def enable_timing(self, on=True):
         check(self._lib.scw_surrogate_enable_timing(self._h, 1 if on else 0), "scw_surrogate_enable_timing")

@@ -72,6 +72,7 @@ SIGNATURES = {
     "scw_plan_set_pipeline": (c_int, [c_void_p, c_int]),
     "scw_plan_check": (c_int, [c_void_p, c_void_p]),
     "scw_plan_set_timeout_ns": (c_int, [c_void_p, c_uint64]),
+    "scw_plan_inject_stall": (c_int, [c_void_p, c_int]),
     "scw_plan_get_info": (c_int, [c_void_p, POINTER(ScwPlanInfo)]),
     "scw_plan_enable_timing": (c_int, [c_void_p, c_int]),
     "scw_plan_get_timings": (c_int, [c_void_p, POINTER(ScwKernelTimes)]),
@@ -91,6 +92,9 @@ SIGNATURES = {
     "scw_surrogate_set_offset": (c_int, [c_void_p, ctypes.c_float]),
     "scw_surrogate_launches": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
     "scw_surrogate_enable_timing": (c_int, [c_void_p, c_int]),
+    "scw_surrogate_state_bytes": (c_int, [c_void_p, POINTER(c_size_t)]),
+    "scw_surrogate_save_state": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "scw_surrogate_load_state": (c_int, [c_void_p, c_void_p, c_size_t]),
     "scw_surrogate_get_timings": (c_int, [c_void_p, POINTER(ScwFnoTimes)]),
     "scw_status_string": (c_char_p, [c_int]),
     "scw_last_error": (c_char_p, []),

@@ -657,6 +657,64 @@ scw_status scw_surrogate_set_offset(scw_fno_t f, float q) {
   return SCW_OK;
 }
 
+// checkpoint blob: header, then master, m, v (FP32, param_count each)
+struct StateHeader {
+  uint32_t magic;    // 'SCWF'
+  uint32_t version;  // 1
+  uint64_t n_params;
+  int32_t step;
+  float q_cal;
+  uint64_t reserved;
+};
+static_assert(sizeof(StateHeader) == 32, "checkpoint header is 32 bytes");
+static constexpr uint32_t kStateMagic = 0x46574353u;
+
+scw_status scw_surrogate_state_bytes(scw_fno_t f, size_t* bytes) {
+  if (!f || !bytes) return set_error(SCW_ERR_INVALID_ARGUMENT, "handle and bytes are required");
+  *bytes = sizeof(StateHeader) + 3 * (size_t)f->n_params * sizeof(float);
+  return SCW_OK;
+}
+
+scw_status scw_surrogate_save_state(scw_fno_t f, void* host, size_t bytes) {
+  if (!f || !host) return set_error(SCW_ERR_INVALID_ARGUMENT, "handle and host are required");
+  const size_t n = (size_t)f->n_params;
+  if (bytes != sizeof(StateHeader) + 3 * n * sizeof(float))
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "bytes differs from scw_surrogate_state_bytes");
+  StateHeader h{kStateMagic, 1u, (uint64_t)n, f->step, f->q_cal, 0};
+  std::memcpy(host, &h, sizeof(h));
+  float* dst = reinterpret_cast<float*>(static_cast<uint8_t*>(host) + sizeof(h));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(dst, f->master, n * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(dst + n, f->adam_m, n * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(dst + 2 * n, f->adam_v, n * 4, cudaMemcpyDeviceToHost);
+  return e == cudaSuccess ? SCW_OK : cuda_error(e, "save_state");
+}
+
+scw_status scw_surrogate_load_state(scw_fno_t f, const void* host, size_t bytes) {
+  if (!f || !host) return set_error(SCW_ERR_INVALID_ARGUMENT, "handle and host are required");
+  const size_t n = (size_t)f->n_params;
+  if (bytes != sizeof(StateHeader) + 3 * n * sizeof(float))
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "bytes differs from scw_surrogate_state_bytes");
+  StateHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  if (h.magic != kStateMagic || h.version != 1u || h.n_params != (uint64_t)n || h.step < 0)
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "not a checkpoint of this surrogate shape");
+  const float* src = reinterpret_cast<const float*>(static_cast<const uint8_t*>(host) + sizeof(h));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(f->master, src, n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(f->adam_m, src + n, n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(f->adam_v, src + 2 * n, n * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = f->bf16 ? launch_copy_params<__nv_bfloat16>(f->master, static_cast<__nv_bfloat16*>(f->wcopy), f->n_params, 0)
+                : launch_copy_params<float>(f->master, static_cast<float*>(f->wcopy), f->n_params, 0);
+  if (e == cudaSuccess) e = refresh_wt(f, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_error(e, "load_state");
+  f->step = h.step;
+  f->q_cal = h.q_cal;
+  return SCW_OK;
+}
+
 scw_status scw_surrogate_enable_timing(scw_fno_t f, int on) {
   if (!f) return set_error(SCW_ERR_INVALID_ARGUMENT, "handle is NULL");
   f->timing = on != 0;

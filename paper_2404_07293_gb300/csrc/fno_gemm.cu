@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
       }
     }
     if (abort_s) {
-      const uint64_t d2 = ptx::globaltimer() + timeout_ns;
+      const uint64_t d2 = ptx::drain_deadline(timeout_ns);
       for (int back = 1; back <= STAGES && back <= issued; ++back) {
         const int i = issued - back;
         if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[i % STAGES]), (uint32_t)(i / STAGES) & 1u, d2)) {
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
       ptx::mma_commit(ptx::smem_u32(&acc_bar));
     } else {
       ptx::mma_commit(ptx::smem_u32(&drain_bar));
-      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::globaltimer() + timeout_ns))
+      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::drain_deadline(timeout_ns)))
         atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
     }
   } else if (warp >= 2) {
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
       }
     }
     if (abort_s) {
-      const uint64_t d2 = ptx::globaltimer() + timeout_ns;
+      const uint64_t d2 = ptx::drain_deadline(timeout_ns);
       for (int back = 1; back <= STAGES && back <= issued; ++back) {
         const int i = issued - back;
         if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[i % STAGES]), (uint32_t)(i / STAGES) & 1u, d2)) {
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
     }
     if (abort_s) {
       ptx::mma_commit(ptx::smem_u32(&drain_bar));
-      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::globaltimer() + timeout_ns))
+      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::drain_deadline(timeout_ns)))
         atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
     }
   } else if (warp >= 2) {

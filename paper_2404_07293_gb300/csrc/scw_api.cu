@@ -474,6 +474,7 @@ struct scw_plan_s {
   int2* d_plane_entries = nullptr;  // y-pass-pair class first (ypass_pairs), then the rest
   int n_plane_entries = 0;
   int n_pair_entries = 0;
+  int inject_stall = 0;            // scw_plan_inject_stall (tests of the timeout path)
   TcSchedule sched;
   float2** d_outs = nullptr;
   float2** h_outs = nullptr;       // pinned
@@ -588,7 +589,7 @@ static scw_status enqueue_spectrum(scw_plan_t P, cudaStream_t st, bool marks, in
     }
   mark(P, 1, st, marks);
   if (P->tc) {
-    e = launch_contract_tc(one, items, P->sched, P->NB, P->bf16, P->d_err, P->timeout_ns, st);
+    e = launch_contract_tc(one, items, P->sched, P->NB, P->bf16, P->d_err, P->timeout_ns, P->inject_stall, st);
     if (e != cudaSuccess) return cuda_error(e, "contraction kernel launch");
     if (P->sched.n_tasks) ++n;
   } else {
@@ -624,7 +625,7 @@ static scw_status enqueue_pipelined(scw_plan_t P, float2* out_one, cudaStream_t 
   e = cudaStreamWaitEvent(P->st2, P->ev_fork, 0);
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamWaitEvent");
   for (int g = 0; g < P->groups; ++g) {
-    e = launch_contract_tc(one, nullptr, P->gsched[g], P->NB, P->bf16, P->d_err, P->timeout_ns, st);
+    e = launch_contract_tc(one, nullptr, P->gsched[g], P->NB, P->bf16, P->d_err, P->timeout_ns, P->inject_stall, st);
     if (e != cudaSuccess) return cuda_error(e, "contraction kernel launch");
     if (P->gsched[g].n_tasks) ++n;
     e = cudaEventRecord(P->gev[g], st);
@@ -781,10 +782,10 @@ static scw_status choose_splits(scw_plan_t P, bool timed, const std::vector<int>
         s = upload_schedule(P->items, P->NB, P->bf16, P->sched);
         if (s != SCW_OK) return s;
         const ItemDev* items = P->batched ? P->d_items : nullptr;
-        launch_contract_tc(P->items[0]->item, items, P->sched, P->NB, P->bf16, P->d_err, P->timeout_ns, ts);
+        launch_contract_tc(P->items[0]->item, items, P->sched, P->NB, P->bf16, P->d_err, P->timeout_ns, 0, ts);
         cudaEventRecord(a, ts);
         for (int r = 0; r < 3; ++r)
-          launch_contract_tc(P->items[0]->item, items, P->sched, P->NB, P->bf16, P->d_err, P->timeout_ns, ts);
+          launch_contract_tc(P->items[0]->item, items, P->sched, P->NB, P->bf16, P->d_err, P->timeout_ns, 0, ts);
         cudaEventRecord(b, ts);
         cudaError_t e = cudaEventSynchronize(b);
         if (e != cudaSuccess) return cuda_error(e, "autotune timing");
@@ -1138,6 +1139,14 @@ scw_status scw_plan_set_timeout_ns(scw_plan_t P, uint64_t ns) {
   if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
   if (ns == 0) return set_error(SCW_ERR_INVALID_ARGUMENT, "timeout must be positive");
   P->timeout_ns = ns;
+  invalidate_graph(P);
+  return SCW_OK;
+}
+
+scw_status scw_plan_inject_stall(scw_plan_t P, int on) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+  if (!P->tc) return set_error(SCW_ERR_UNSUPPORTED, "stall injection exists in the tensor-core contraction only");
+  P->inject_stall = on ? 1 : 0;
   invalidate_graph(P);
   return SCW_OK;
 }

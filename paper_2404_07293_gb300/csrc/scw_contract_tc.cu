@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
                                                           const ItemDev* __restrict__ items,
                                                           const int4* __restrict__ tasks,
                                                           const int* __restrict__ cta_off, int* err,
-                                                          uint64_t timeout_ns) {
+                                                          uint64_t timeout_ns, int inject_stall) {
   using Cfg = TcCfg<NB, SPLIT>;
   constexpr int STAGES = Cfg::STAGES;
   constexpr int FP = NB / 2;  // plane slots
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
     const uint64_t pol_a = ptx::policy_evict_first(), pol_b = ptx::policy_evict_last();
     int st = 0;
     uint32_t ph = 0;
-    int issued = 0;
+    int issued = 0, skipped = -1;
     for (int t = t_begin; t < t_end && !abort_s; ++t) {
       const int4 tk = tasks[t];
       const ItemDev& it = BATCH ? items[tk.x] : one;
@@ -135,16 +135,20 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
           break;
         }
         const uint32_t fb = ptx::smem_u32(&full_bar[st]);
-        ptx::mbar_arrive_expect_tx(fb, tx);
-        const int kc = g.kb + i;
-        const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
-        const size_t ao = a0 + (size_t)kc * g.rt * 64;
-        ptx::bulk_load(sa, Ah + ao, a_bytes, fb, pol_a);
-        if (SPLIT) ptx::bulk_load(sa + Cfg::A_BYTES, Al + ao, a_bytes, fb, pol_a);
-        const uint32_t sb = sa + Cfg::NA * Cfg::A_BYTES;
-        const size_t bo = b0 + (size_t)kc * NB * 64;
-        ptx::bulk_load(sb, Bh + bo, Cfg::B_BYTES, fb, pol_b);
-        ptx::bulk_load(sb + Cfg::B_BYTES, Bl + bo, Cfg::B_BYTES, fb, pol_b);
+        if (inject_stall && blockIdx.x == 0 && issued == 0) {
+          skipped = 0;  // failure injection (scw_plan_inject_stall): this stage is never filled
+        } else {
+          ptx::mbar_arrive_expect_tx(fb, tx);
+          const int kc = g.kb + i;
+          const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE_BYTES);
+          const size_t ao = a0 + (size_t)kc * g.rt * 64;
+          ptx::bulk_load(sa, Ah + ao, a_bytes, fb, pol_a);
+          if (SPLIT) ptx::bulk_load(sa + Cfg::A_BYTES, Al + ao, a_bytes, fb, pol_a);
+          const uint32_t sb = sa + Cfg::NA * Cfg::A_BYTES;
+          const size_t bo = b0 + (size_t)kc * NB * 64;
+          ptx::bulk_load(sb, Bh + bo, Cfg::B_BYTES, fb, pol_b);
+          ptx::bulk_load(sb + Cfg::B_BYTES, Bl + bo, Cfg::B_BYTES, fb, pol_b);
+        }
         ++issued;
         if (++st == STAGES) {
           st = 0;
@@ -154,9 +158,10 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
     }
     if (abort_s) {
       // let the last issued copies land before the CTA's shared memory goes away
-      const uint64_t d2 = ptx::globaltimer() + timeout_ns;
+      const uint64_t d2 = ptx::drain_deadline(timeout_ns);
       for (int back = 1; back <= STAGES && back <= issued; ++back) {
         const int i = issued - back;
+        if (i == skipped) continue;  // nothing was sent to that stage
         if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[i % STAGES]), (uint32_t)(i / STAGES) & 1u, d2)) {
           atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
           break;
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
     if (abort_s) {
       // issued MMAs must finish before the tensor memory is released
       ptx::mma_commit(ptx::smem_u32(&drain_bar));
-      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::globaltimer() + timeout_ns))
+      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::drain_deadline(timeout_ns)))
         atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
     }
   } else if (warp >= 2) {
@@ -276,42 +281,42 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
 // ---------------------------------------------------------------- host side ---
 template <int NB, bool SPLIT>
 static cudaError_t launch_tc_t(const ItemDev& one, const ItemDev* items, const TcSchedule& s, int* err,
-                               uint64_t timeout_ns, cudaStream_t st) {
+                               uint64_t timeout_ns, int inject, cudaStream_t st) {
   using Cfg = TcCfg<NB, SPLIT>;
   cudaError_t e;
   if (items) {
     e = allow_max_smem(reinterpret_cast<const void*>(contract_tc_kernel<NB, SPLIT, true>));
     if (e != cudaSuccess) return e;
     contract_tc_kernel<NB, SPLIT, true><<<s.grid, 192, Cfg::SMEM, st>>>(one, items, s.d_tasks, s.d_cta_off, err,
-                                                                       timeout_ns);
+                                                                       timeout_ns, inject);
   } else {
     e = allow_max_smem(reinterpret_cast<const void*>(contract_tc_kernel<NB, SPLIT, false>));
     if (e != cudaSuccess) return e;
     contract_tc_kernel<NB, SPLIT, false><<<s.grid, 192, Cfg::SMEM, st>>>(one, nullptr, s.d_tasks, s.d_cta_off, err,
-                                                                        timeout_ns);
+                                                                        timeout_ns, inject);
   }
   return cudaGetLastError();
 }
 
 template <bool SPLIT>
 static cudaError_t launch_tc_nb(int NB, const ItemDev& one, const ItemDev* items, const TcSchedule& s, int* err,
-                                uint64_t timeout_ns, cudaStream_t st) {
+                                uint64_t timeout_ns, int inject, cudaStream_t st) {
   switch (NB) {
-    case 16: return launch_tc_t<16, SPLIT>(one, items, s, err, timeout_ns, st);
-    case 32: return launch_tc_t<32, SPLIT>(one, items, s, err, timeout_ns, st);
-    case 48: return launch_tc_t<48, SPLIT>(one, items, s, err, timeout_ns, st);
-    case 64: return launch_tc_t<64, SPLIT>(one, items, s, err, timeout_ns, st);
-    case 128: return launch_tc_t<128, SPLIT>(one, items, s, err, timeout_ns, st);
-    case 256: return launch_tc_t<256, SPLIT>(one, items, s, err, timeout_ns, st);
+    case 16: return launch_tc_t<16, SPLIT>(one, items, s, err, timeout_ns, inject, st);
+    case 32: return launch_tc_t<32, SPLIT>(one, items, s, err, timeout_ns, inject, st);
+    case 48: return launch_tc_t<48, SPLIT>(one, items, s, err, timeout_ns, inject, st);
+    case 64: return launch_tc_t<64, SPLIT>(one, items, s, err, timeout_ns, inject, st);
+    case 128: return launch_tc_t<128, SPLIT>(one, items, s, err, timeout_ns, inject, st);
+    case 256: return launch_tc_t<256, SPLIT>(one, items, s, err, timeout_ns, inject, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_contract_tc(const ItemDev& one, const ItemDev* items, const TcSchedule& s, int NB, bool bf16,
-                               int* err, uint64_t timeout_ns, cudaStream_t st) {
+                               int* err, uint64_t timeout_ns, int inject, cudaStream_t st) {
   if (s.n_tasks == 0 || s.grid == 0) return cudaSuccess;
-  return bf16 ? launch_tc_nb<true>(NB, one, items, s, err, timeout_ns, st)
-              : launch_tc_nb<false>(NB, one, items, s, err, timeout_ns, st);
+  return bf16 ? launch_tc_nb<true>(NB, one, items, s, err, timeout_ns, inject, st)
+              : launch_tc_nb<false>(NB, one, items, s, err, timeout_ns, inject, st);
 }
 
 int tc_ctas_per_sm(int NB, bool bf16) {

@@ -175,8 +175,10 @@ cudaError_t launch_phases_fp32(const Plan& p, cudaStream_t st);
 cudaError_t launch_exterior(const Plan& p, cudaStream_t st);
 
 // step (b)
+// inject: failure injection for tests; the first CTA leaves its first operand stage
+// unfilled, so its bounded waits run out and it reports DEV_ERR_TIMEOUT_* (0 in production)
 cudaError_t launch_contract_tc(const ItemDev& one, const ItemDev* items, const TcSchedule& s, int NB, bool bf16,
-                               int* err, uint64_t timeout_ns, cudaStream_t st);
+                               int* err, uint64_t timeout_ns, int inject, cudaStream_t st);
 cudaError_t launch_contract_fp32(const Plan& p, cudaStream_t st);
 int tc_ctas_per_sm(int NB, bool bf16);
 

@@ -56,6 +56,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
   }
 }
 
+// Deadline of the waits after an abort (issued copies and MMAs landing before the
+// CTA's shared and tensor memory go away): never shorter than one second, whatever
+// the caller's timeout, because these always complete.
+__device__ __forceinline__ uint64_t drain_deadline(uint64_t timeout_ns) {
+  return globaltimer() + (timeout_ns > 1000000000ull ? timeout_ns : 1000000000ull);
+}
+
 // 2D tiled TMA load global -> shared (box of the tensor map), completion
 // signalled on `bar`. c0 is the innermost (contiguous) coordinate; callers keep
 // c0 * element size a multiple of 16 bytes.
