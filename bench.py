@@ -287,6 +287,67 @@ def run_sweep(args, dev, world, peaks_hbm):
     return res
 
 
+def run_illumination(args, dev, world, Wd, gd, zb, zp, hbm, bf16_tf):
+    """Many illuminations of one solved sample: the single-wavelength workload
+    (21x21 orders, 32 layers, 256 x 256 x 256 voxels) lit by I incident fields
+    that share W and gamma, each with its own alpha. One plan contracts all I
+    against a single read of W, so the contraction has 8 I columns per layer and
+    turns tensor-bound; every precision is timed on the same inputs."""
+    import torch
+    import paper_2404_07293_gb300 as scw
+    import workloads as wl
+    I = args.illuminations
+    M = U_ORD * U_ORD
+    alpha = wl.random_illuminations(4242, I, U_ORD, U_ORD, L_LAYERS)[0]
+    ad = torch.from_numpy(alpha).to(dev)
+    Fz = len(zp)
+    voxels = I * F_XY * F_XY * Fz
+    out = torch.empty((I, 3, Fz, F_XY, F_XY), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flops = 8.0 * (3 * M) * (4 * M) * Fz * I       # complex multiply-adds of S = W (alpha o g), 8 flops each
+    products = {"fp32": 1, "split_bf16": 3, "fp16": 2}
+    res = {"workload": f"single_wavelength_256cubed_{I}_illuminations", "illuminations": I,
+           "voxels_per_step": voxels, "contract_flops": flops, "unit": "voxels/s"}
+    for prec in ("split_bf16", "fp16", "fp32"):
+        plan = scw.Plan(U_ORD, U_ORD, L_LAYERS, LAM, X_PERIOD, X_PERIOD, zb, F_XY, F_XY, zp,
+                        precision=prec, illuminations=I)
+        plan.set_layers(Wd, gd, ad)
+        for _ in range(max(3, args.warmup)):
+            plan.synthesize(out)
+        plan.check()
+        steps = max(3, min(args.steps, 10))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            plan.synthesize(out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+        plan.enable_timing(True)
+        for _ in range(3):
+            plan.synthesize(out)
+        kt = plan.timings()
+        plan.enable_timing(False)
+        plan.check()
+        tf = flops / (kt["contract_ms"] * 1e-3) / 1e12
+        r = {"value": replica_throughput(voxels, ms * 1e-3, dev)[0], "ms_per_step": ms,
+             "kernel_ms": {k: kt[k] for k in ("phases_ms", "contract_ms", "xpass_ms", "ypass_ms", "total_ms")},
+             "contract_tflops": tf, "k_split": plan.info()["k_split"]}
+        if prec != "fp32":
+            r["tensor_frac_issued"] = tf * products[prec] / bf16_tf  # MMA flops issued / measured bf16 peak
+        res[prec] = r
+        plan.close()
+    res["contract_speedup_split_bf16_vs_fp32"] = res["fp32"]["kernel_ms"]["contract_ms"] / \
+        res["split_bf16"]["kernel_ms"]["contract_ms"]
+    res["step_speedup_split_bf16_vs_fp32"] = res["fp32"]["ms_per_step"] / res["split_bf16"]["ms_per_step"]
+    res["out_bytes"] = out.numel() * 8
+    res["step_hbm_roofline_ms"] = (L_LAYERS * 3 * M * 4 * M * 8 + res["out_bytes"]) / (hbm * 1e9) * 1e3
+    res["peaks"] = {"bf16_tflops": bf16_tf, "hbm_gbs": hbm, "source": "MEASURED_PEAKS.json (burst)"}
+    del out, ad
+    return res
+
+
 def run_surrogate(args, dev, bf16_peaks):
     """Learned surrogate at its full size: 4 Fourier layers of width 32, 16x16
     kept modes on a 64x64 grid, inputs 8 slices of 32x32 complex n (seeded
@@ -505,6 +566,11 @@ def run_ours(args, world, rank, local):
                "includes": "H2D of W, gamma, alpha; W conversion; synthesis; D2H of the field"}
         hplan.close()
 
+    illum = None
+    if args.illuminations > 1:
+        illum = run_illumination(args, dev, world, Wd, gd, zb, zp, hbm, bf16_tf)
+        torch.cuda.empty_cache()
+
     sweep = None
     if not args.no_sweep:
         plan.close()
@@ -553,6 +619,7 @@ def run_ours(args, world, rank, local):
             "cpu_baseline": cpu,
             "variants": variants or None,
             "sweep": sweep,
+            "illumination": illum,
             "surrogate": surrogate,
         }
         print(json.dumps(line), flush=True)
@@ -578,6 +645,8 @@ def main():
     ap.add_argument("--sweep-items", type=int, default=128)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate block")
     ap.add_argument("--fno-batch", type=int, default=256)
+    ap.add_argument("--illuminations", type=int, default=16,
+                    help="incident fields of the multi-illumination block (1 skips it)")
     ap.add_argument("--only-surrogate", action="store_true",
                     help="run only the learned-surrogate block and print its JSON (a profiling aid, not the bench line)")
     ap.add_argument("--layers", type=int, default=32)

@@ -94,6 +94,13 @@ typedef struct {
   int precision;            /* scw_precision                                             */
   unsigned flags;           /* SCW_FLAG_*                                                */
   int k_split;              /* contraction split along the 4M modes; 0 = choose         */
+  int illuminations;        /* I incident fields sharing this solve (0 counts as 1): the
+                               modes (W, gamma) are read once per layer for all of them, alpha
+                               is [I][L][4M], p_inc/p_ref/p_trn are [I][3][M] and the field is
+                               [I][3][Fz][Fy][Fx]; I Fz <= 65535                            */
+  double pupil_na;          /* > 0: below the sample only the orders with |s_bar| <= pupil_na
+                               pass (the numerical aperture of a collecting objective, in the
+                               units of s_bar = lambda (u/X, v/Y)); 0: no pupil             */
 } scw_desc;
 
 typedef struct {

@@ -43,8 +43,21 @@ def propagators(gamma_l: np.ndarray, z: float, z_top: float, z_bot: float, k: fl
     return np.exp(1j * k * gamma_l * (z - zref))
 
 
-def spectrum_at(ls: LayerSet, z: float) -> np.ndarray:
-    """Per-plane Fourier-domain field S[c][m] at height z (Eq. 9 / Eq. 34)."""
+def pupil_mask(ls: LayerSet, na: float) -> np.ndarray:
+    """1 for the orders a collecting objective of numerical aperture `na` passes
+    (|s_bar| <= na, s_bar = lambda (u/X, v/Y), Eq. 6), 0 for the rest; all ones for
+    na <= 0. An imaging system sees the external field below the sample (Sec. 1:
+    objectives of a given NA; Sec. 4.1: only the external field is needed to model
+    an imaging system); the mask is applied there."""
+    sx, sy = directions(ls.U, ls.V, ls.lam, ls.X, ls.Y)
+    if na <= 0:
+        return np.ones(ls.M)
+    return (sx * sx + sy * sy <= na * na * (1.0 + 1e-12)).astype(np.float64)
+
+
+def spectrum_at(ls: LayerSet, z: float, pupil_na: float = 0.0) -> np.ndarray:
+    """Per-plane Fourier-domain field S[c][m] at height z (Eq. 9 / Eq. 34); below the
+    sample the orders outside the pupil (pupil_mask) are dropped when pupil_na > 0."""
     k = 2 * np.pi / ls.lam
     zb = np.asarray(ls.z_bounds)
     r = region(z, zb)
@@ -55,7 +68,7 @@ def spectrum_at(ls: LayerSet, z: float) -> np.ndarray:
             return (ls.p_inc * np.exp(1j * k * st * (z - ls.zbar))
                     + ls.p_ref * np.exp(-1j * k * st * (z - zb[0])))
         sb = s_z(ls.n_bot, sx, sy)
-        return ls.p_trn * np.exp(1j * k * sb * (z - zb[-1]))
+        return ls.p_trn * np.exp(1j * k * sb * (z - zb[-1])) * pupil_mask(ls, pupil_na)
     g = propagators(ls.gamma[r], z, zb[r], zb[r + 1], k)
     return (ls.W[r] @ (ls.alpha[r] * g)).reshape(3, ls.M)
 
@@ -91,19 +104,19 @@ def field_points(ls: LayerSet, pts: np.ndarray) -> np.ndarray:
 
 
 def synthesize_direct(ls: LayerSet, Fx: int, Fy: int, z_planes, x0: float = 0.0,
-                      y0: float = 0.0) -> np.ndarray:
+                      y0: float = 0.0, pupil_na: float = 0.0) -> np.ndarray:
     """The whole volume E[3][Fz][Fy][Fx] by direct summation."""
     xs, ys = pixel_coords(ls, Fx, Fy, x0, y0)
     zs = np.asarray(z_planes, dtype=np.float64)
     out = np.empty((3, len(zs), Fy, Fx), dtype=np.complex128)
     for iz, z in enumerate(zs):
-        out[:, iz] = field_direct(ls, spectrum_at(ls, float(z)), xs, ys)
+        out[:, iz] = field_direct(ls, spectrum_at(ls, float(z), pupil_na), xs, ys)
     return out
 
 
-def spectra(ls: LayerSet, z_planes) -> np.ndarray:
+def spectra(ls: LayerSet, z_planes, pupil_na: float = 0.0) -> np.ndarray:
     """S[Fz][3][M] for every plane."""
-    return np.stack([spectrum_at(ls, float(z)) for z in np.asarray(z_planes)])
+    return np.stack([spectrum_at(ls, float(z), pupil_na) for z in np.asarray(z_planes)])
 
 
 def field_fft(ls: LayerSet, S: np.ndarray, Fx: int, Fy: int, x0: float = 0.0,

@@ -19,7 +19,8 @@ __all__ = ["Plan", "BatchedPlan", "Surrogate", "ScwError", "load", "PRECISION"]
 
 
 def _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0, n_bot=1.0,
-               z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0, autotune=False):
+               z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0, autotune=False,
+               illuminations=1, pupil_na=0.0):
     """scw_desc for one item plus the host arrays it points to (keep them alive)."""
     zb = np.ascontiguousarray(z_bounds, dtype=np.float64)
     zp = np.ascontiguousarray(z_planes, dtype=np.float64)
@@ -33,8 +34,14 @@ def _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n
                 z_planes=zp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                 x0=float(x0), y0=float(y0), n_top=float(n_top), n_bot_re=nb.real, n_bot_im=nb.imag,
                 z_inc=float(zb[0] if z_inc is None else z_inc),
-                precision=PRECISION[precision], flags=flags, k_split=int(k_split))
+                precision=PRECISION[precision], flags=flags, k_split=int(k_split),
+                illuminations=int(illuminations), pupil_na=float(pupil_na))
     return d, (zb, zp)
+
+
+def _per_illum(I, shape):
+    """Shape of an input given once per illumination (I > 1) or once (I == 1)."""
+    return tuple(shape) if I == 1 else (I,) + tuple(shape)
 
 
 def _stream_handle(stream):
@@ -68,14 +75,19 @@ class Plan:
 
     def __init__(self, U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0,
                  n_bot=1.0, z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0,
-                 autotune=False):
+                 autotune=False, illuminations=1, pupil_na=0.0):
+        """``illuminations`` incident fields share this solve: alpha becomes [I][L][4M], p_* [I][3][M]
+        and the field [I][3][Fz][Fy][Fx]. ``pupil_na`` > 0 keeps only the orders inside that NA below
+        the sample."""
         self._lib = load()
         self.U, self.V, self.L = int(U), int(V), int(L)
         self.M = self.U * self.V
         self.Fx, self.Fy = int(Fx), int(Fy)
+        self.I = max(1, int(illuminations))
         self.exterior = bool(exterior)
         d, (self._zb, self._zp) = _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0, y0, n_top, n_bot,
-                                             z_inc, precision, exterior, host_io, k_split, autotune)
+                                             z_inc, precision, exterior, host_io, k_split, autotune,
+                                             illuminations, pupil_na)
         self.Fz = len(self._zp)
         h = ctypes.c_void_p()
         check(self._lib.scw_plan_create(ctypes.byref(d), ctypes.byref(h)), "scw_plan_create")
@@ -84,20 +96,21 @@ class Plan:
 
     # ------------------------------------------------------------------ inputs
     def set_layers(self, W, gamma, alpha, p_inc=None, p_ref=None, p_trn=None, stream=None):
-        """W complex64 [L][3M][4M]; gamma, alpha complex128 [L][4M]; p_* complex128 [3][M]."""
+        """W complex64 [L][3M][4M]; gamma complex128 [L][4M]; alpha complex128 [L][4M] ([I][L][4M]
+        with I illuminations); p_* complex128 [3][M] ([I][3][M])."""
         import torch
-        L, M = self.L, self.M
+        L, M, I = self.L, self.M, self.I
         args = [_dev_ptr(W, torch.complex64, (L, 3 * M, 4 * M), "W"),
                 _dev_ptr(gamma, torch.complex128, (L, 4 * M), "gamma"),
-                _dev_ptr(alpha, torch.complex128, (L, 4 * M), "alpha")]
+                _dev_ptr(alpha, torch.complex128, _per_illum(I, (L, 4 * M)), "alpha")]
         for p, n in ((p_inc, "p_inc"), (p_ref, "p_ref"), (p_trn, "p_trn")):
-            args.append(ctypes.c_void_p(0) if p is None else _dev_ptr(p, torch.complex128, (3, M), n))
+            args.append(ctypes.c_void_p(0) if p is None else _dev_ptr(p, torch.complex128, _per_illum(I, (3, M)), n))
         check(self._lib.scw_plan_set_layers(self._h, *args, _stream_handle(stream)), "scw_plan_set_layers")
         self._keep = (W, gamma, alpha, p_inc, p_ref, p_trn)  # W until its conversion has run
 
     # ------------------------------------------------------------------ compute
     def out_shape(self):
-        return (3, self.Fz, self.Fy, self.Fx)
+        return _per_illum(self.I, (3, self.Fz, self.Fy, self.Fx))
 
     def synthesize(self, out=None, stream=None):
         import torch
@@ -109,7 +122,7 @@ class Plan:
 
     def spectrum(self, S=None, stream=None):
         import torch
-        shape = (self.Fz, 3, self.M)
+        shape = (self.I * self.Fz, 3, self.M)  # plane slot f I + illumination i
         if S is None:
             S = torch.empty(shape, dtype=torch.complex64, device="cuda")
         check(self._lib.scw_spectrum(self._h, _dev_ptr(S, torch.complex64, shape, "S"), _stream_handle(stream)),
@@ -120,21 +133,21 @@ class Plan:
         import torch
         if out is None:
             out = torch.empty(self.out_shape(), dtype=torch.complex64, device="cuda")
-        check(self._lib.scw_recompose(self._h, _dev_ptr(S, torch.complex64, (self.Fz, 3, self.M), "S"),
+        check(self._lib.scw_recompose(self._h, _dev_ptr(S, torch.complex64, (self.I * self.Fz, 3, self.M), "S"),
                                       _dev_ptr(out, torch.complex64, self.out_shape(), "out"),
                                       _stream_handle(stream)), "scw_recompose")
         return out
 
     def synthesize_host(self, W, gamma, alpha, p_inc=None, p_ref=None, p_trn=None, out=None, stream=None):
         """End to end through host memory (plan created with host_io=True)."""
-        L, M = self.L, self.M
+        L, M, I = self.L, self.M, self.I
         if out is None:
             out = np.empty(self.out_shape(), dtype=np.complex64)
         args = [_host_ptr(W, np.complex64, (L, 3 * M, 4 * M), "W"),
                 _host_ptr(gamma, np.complex128, (L, 4 * M), "gamma"),
-                _host_ptr(alpha, np.complex128, (L, 4 * M), "alpha")]
+                _host_ptr(alpha, np.complex128, _per_illum(I, (L, 4 * M)), "alpha")]
         for p, n in ((p_inc, "p_inc"), (p_ref, "p_ref"), (p_trn, "p_trn")):
-            args.append(ctypes.c_void_p(0) if p is None else _host_ptr(p, np.complex128, (3, M), n))
+            args.append(ctypes.c_void_p(0) if p is None else _host_ptr(p, np.complex128, _per_illum(I, (3, M)), n))
         args.append(_host_ptr(out, np.complex64, self.out_shape(), "out"))
         check(self._lib.scw_synthesize_host(self._h, *args, _stream_handle(stream)), "scw_synthesize_host")
         return out
@@ -201,8 +214,9 @@ class BatchedPlan:
             descs[i] = d
             self._keep_desc.append(keep)
             M = int(kw["U"]) * int(kw["V"])
-            self.sizes.append((int(kw["L"]), M))
-            self.shapes.append((3, len(keep[1]), int(kw["Fy"]), int(kw["Fx"])))
+            I = max(1, int(kw.get("illuminations", 1)))
+            self.sizes.append((int(kw["L"]), M, I))
+            self.shapes.append(_per_illum(I, (3, len(keep[1]), int(kw["Fy"]), int(kw["Fx"]))))
         h = ctypes.c_void_p()
         check(self._lib.scw_plan_batched_create(descs, n, ctypes.byref(h)), "scw_plan_batched_create")
         self._h = h
@@ -213,12 +227,12 @@ class BatchedPlan:
 
     def set_layers(self, i, W, gamma, alpha, p_inc=None, p_ref=None, p_trn=None, stream=None):
         import torch
-        L, M = self.sizes[i]
+        L, M, I = self.sizes[i]
         args = [_dev_ptr(W, torch.complex64, (L, 3 * M, 4 * M), "W"),
                 _dev_ptr(gamma, torch.complex128, (L, 4 * M), "gamma"),
-                _dev_ptr(alpha, torch.complex128, (L, 4 * M), "alpha")]
+                _dev_ptr(alpha, torch.complex128, _per_illum(I, (L, 4 * M)), "alpha")]
         for p, nme in ((p_inc, "p_inc"), (p_ref, "p_ref"), (p_trn, "p_trn")):
-            args.append(ctypes.c_void_p(0) if p is None else _dev_ptr(p, torch.complex128, (3, M), nme))
+            args.append(ctypes.c_void_p(0) if p is None else _dev_ptr(p, torch.complex128, _per_illum(I, (3, M)), nme))
         check(self._lib.scw_plan_batched_set_layers(self._h, int(i), *args, _stream_handle(stream)),
               "scw_plan_batched_set_layers")
         self._keep[i] = (W, gamma, alpha, p_inc, p_ref, p_trn)

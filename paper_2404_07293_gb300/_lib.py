@@ -26,7 +26,8 @@ class ScwDesc(ctypes.Structure):
                 ("x0", c_double), ("y0", c_double),
                 ("n_top", c_double), ("n_bot_re", c_double), ("n_bot_im", c_double),
                 ("z_inc", c_double),
-                ("precision", c_int), ("flags", c_uint), ("k_split", c_int)]
+                ("precision", c_int), ("flags", c_uint), ("k_split", c_int),
+                ("illuminations", c_int), ("pupil_na", c_double)]
 
 
 class ScwPlanInfo(ctypes.Structure):

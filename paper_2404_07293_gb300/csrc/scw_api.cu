@@ -60,7 +60,7 @@ static cudaError_t upload(T** p, const std::vector<T>& v, size_t& total) {
 
 static void free_item(Plan* p) {
   if (!p) return;
-  void* ptrs[] = {p->d_units,   p->d_zplanes, p->d_zbounds, p->d_nsplit,   p->d_nsplit1, p->d_ext_planes,
+  void* ptrs[] = {p->d_units,   p->d_zplanes, p->d_zbounds, p->d_nsplit,   p->d_nsplit1, p->d_ext_planes, p->d_pupil,
                   p->d_sz_top,  p->d_sz_bot,  p->d_twx,     p->d_twy,      p->Whi,       p->Wlo,
                   p->Wh,        p->Wt,        p->Bhi,       p->Blo,        p->Cf,        p->S_part,
                   p->T,         p->hio_W,     p->hio_gamma, p->hio_alpha,  p->hio_p,     p->hio_out};
@@ -116,6 +116,12 @@ static scw_status validate_desc(const scw_desc* d) {
   if (d->Fx < 8 || d->Fy < 8 || d->Fx % 8 || d->Fy % 8 || d->Fx > kMaxFx || d->Fy > kMaxFx)
     return set_error(SCW_ERR_INVALID_ARGUMENT, "Fx and Fy must be multiples of 8 in [8, 4096]");
   if (d->Fz < 1 || d->Fz > 65535) return set_error(SCW_ERR_INVALID_ARGUMENT, "Fz must be in [1, 65535]");
+  if (d->illuminations < 0 || d->illuminations > 256)
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "illuminations must be in [0, 256]");
+  if ((long long)std::max(1, d->illuminations) * d->Fz > 65535)
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "illuminations * Fz must be <= 65535");
+  if (!(d->pupil_na >= 0.0) || !std::isfinite(d->pupil_na))
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "pupil_na must be finite and >= 0");
   if (!d->z_bounds || !d->z_planes) return set_error(SCW_ERR_INVALID_ARGUMENT, "z_bounds and z_planes are required");
   if (d->precision < SCW_PREC_FP32 || d->precision > SCW_PREC_FP16)
     return set_error(SCW_ERR_INVALID_ARGUMENT, "unknown precision");
@@ -189,9 +195,11 @@ static scw_status assign_planes(Plan* p, std::vector<int>& ext, int& max_nf) {
 // Tables and every buffer except S_part (whose size depends on the split).
 static scw_status build_item(Plan* p, const std::vector<int>& ext) {
   std::vector<double2> szt(p->M), szb(p->M);
+  std::vector<float> pupil(p->M, 1.f);
   for (int m = 0; m < p->M; ++m) {
     const int u = m % p->U - p->U / 2, v = m / p->U - p->V / 2;
     const double sx = p->lambda * u / p->X, sy = p->lambda * v / p->Y;
+    if (p->pupil_na > 0 && sx * sx + sy * sy > p->pupil_na * p->pupil_na * (1.0 + 1e-12)) pupil[m] = 0.f;
     const auto a = s_z(std::complex<double>(p->n_top, 0.0), sx, sy);
     const auto b = s_z(std::complex<double>(p->n_bot_re, p->n_bot_im), sx, sy);
     szt[m] = make_double2(a.real(), a.imag());
@@ -225,6 +233,7 @@ static scw_status build_item(Plan* p, const std::vector<int>& ext) {
   SCW_TRY(upload(&p->d_ext_planes, ext, tot));
   SCW_TRY(upload(&p->d_sz_top, szt, tot));
   SCW_TRY(upload(&p->d_sz_bot, szb, tot));
+  if (p->pupil_na > 0) SCW_TRY(upload(&p->d_pupil, pupil, tot));
   SCW_TRY(upload(&p->d_twx, twx, tot));
   SCW_TRY(upload(&p->d_twy, twy, tot));
   SCW_TRY(dalloc(&p->T, (size_t)p->Fz * 3 * p->V * p->Fx, tot));
@@ -253,8 +262,8 @@ static scw_status build_item(Plan* p, const std::vector<int>& ext) {
   if (p->flags & SCW_FLAG_HOST_IO) {
     SCW_TRY(dalloc(&p->hio_W, L * 3 * M * 4 * M, tot));
     SCW_TRY(dalloc(&p->hio_gamma, L * 4 * M, tot));
-    SCW_TRY(dalloc(&p->hio_alpha, L * 4 * M, tot));
-    SCW_TRY(dalloc(&p->hio_p, 9 * M, tot));
+    SCW_TRY(dalloc(&p->hio_alpha, p->I * L * 4 * M, tot));
+    SCW_TRY(dalloc(&p->hio_p, p->I * 9 * M, tot));
     SCW_TRY(dalloc(&p->hio_out, (size_t)3 * p->Fz * p->Fy * p->Fx, tot));
   }
   SCW_TRY(cudaEventCreate(&p->ev0));
@@ -297,6 +306,7 @@ static scw_status finish_item(Plan* p) {
   it.split_stride = (size_t)p->Fz * 3 * M;
   it.inv_lam = 1.0 / p->lambda;
   it.M = p->M; it.U = p->U; it.V = p->V; it.Fx = p->Fx; it.Fy = p->Fy; it.Fz = p->Fz;
+  it.I = p->I; it.Fz_out = p->Fz_out; it.alpha_istride = (size_t)p->L * 4 * p->M;
   it.F_pad = p->F_pad;
   it.k_split = p->k_split;
   it.n_tiles = (3 * p->M + 127) / 128;
@@ -310,12 +320,18 @@ static scw_status create_item(const scw_desc* d, int force_F_pad, Plan** out) {
   Plan* p = new (std::nothrow) Plan();
   if (!p) return set_error(SCW_ERR_OUT_OF_MEMORY, "host allocation failed");
   p->U = d->U; p->V = d->V; p->M = d->U * d->V; p->L = d->L;
-  p->Fx = d->Fx; p->Fy = d->Fy; p->Fz = d->Fz;
+  // I illuminations share every plane: plane slot f I + i is output plane f of illumination i
+  p->I = std::max(1, d->illuminations);
+  p->Fz_out = d->Fz;
+  p->Fx = d->Fx; p->Fy = d->Fy; p->Fz = p->I * d->Fz;
+  p->pupil_na = d->pupil_na;
   p->lambda = d->lambda; p->X = d->X; p->Y = d->Y; p->x0 = d->x0; p->y0 = d->y0;
   p->n_top = d->n_top; p->n_bot_re = d->n_bot_re; p->n_bot_im = d->n_bot_im; p->z_inc = d->z_inc;
   p->precision = d->precision; p->flags = d->flags;
   p->z_bounds.assign(d->z_bounds, d->z_bounds + d->L + 1);
-  p->z_planes.assign(d->z_planes, d->z_planes + d->Fz);
+  p->z_planes.clear();
+  for (int f = 0; f < d->Fz; ++f)
+    for (int i = 0; i < p->I; ++i) p->z_planes.push_back(d->z_planes[f]);
   std::vector<int> ext;
   int max_nf = 0;
   scw_status s = assign_planes(p, ext, max_nf);
@@ -1095,13 +1111,14 @@ scw_status scw_synthesize_host(scw_plan_t P, const void* W, const void* gamma, c
   } while (0)
   SCW_CP(p->hio_W, W, L * 3 * M * 4 * M * sizeof(float2), cudaMemcpyHostToDevice);
   SCW_CP(p->hio_gamma, gamma, L * 4 * M * sizeof(double2), cudaMemcpyHostToDevice);
-  SCW_CP(p->hio_alpha, alpha, L * 4 * M * sizeof(double2), cudaMemcpyHostToDevice);
+  SCW_CP(p->hio_alpha, alpha, p->I * L * 4 * M * sizeof(double2), cudaMemcpyHostToDevice);
   const double2 *pi = nullptr, *pr = nullptr, *pt = nullptr;
   if (p_inc && p_ref && p_trn) {
-    SCW_CP(p->hio_p, p_inc, 3 * M * sizeof(double2), cudaMemcpyHostToDevice);
-    SCW_CP(p->hio_p + 3 * M, p_ref, 3 * M * sizeof(double2), cudaMemcpyHostToDevice);
-    SCW_CP(p->hio_p + 6 * M, p_trn, 3 * M * sizeof(double2), cudaMemcpyHostToDevice);
-    pi = p->hio_p; pr = p->hio_p + 3 * M; pt = p->hio_p + 6 * M;
+    const size_t np = (size_t)p->I * 3 * M;  // each of p_inc, p_ref, p_trn: [I][3][M]
+    SCW_CP(p->hio_p, p_inc, np * sizeof(double2), cudaMemcpyHostToDevice);
+    SCW_CP(p->hio_p + np, p_ref, np * sizeof(double2), cudaMemcpyHostToDevice);
+    SCW_CP(p->hio_p + 2 * np, p_trn, np * sizeof(double2), cudaMemcpyHostToDevice);
+    pi = p->hio_p; pr = p->hio_p + np; pt = p->hio_p + 2 * np;
   }
   // same device buffers every call: the layers are re-attached without dropping the graph
   if (!p->layers_set || p->gamma != p->hio_gamma) {

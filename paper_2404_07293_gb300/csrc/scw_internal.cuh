@@ -60,11 +60,16 @@ struct ItemDev {
   int M, U, V, Fx, Fy, Fz;
   int F_pad, k_split, n_tiles, nk, n_units;
   int Up, Vp;              // padded fold lengths roundup(U, 8), roundup(V, 8)
+  int I, Fz_out;           // illuminations; output planes per illumination (Fz = I Fz_out,
+                           // plane index f = (output plane) I + illumination)
+  size_t alpha_istride;    // L 4M: alpha elements per illumination
 };
 
 struct Plan {
   // description
-  int U = 0, V = 0, M = 0, L = 0, Fx = 0, Fy = 0, Fz = 0;
+  int U = 0, V = 0, M = 0, L = 0, Fx = 0, Fy = 0, Fz = 0;  // Fz = I Fz_out plane slots
+  int I = 1, Fz_out = 0;                                  // illuminations, output planes each
+  double pupil_na = 0;
   double lambda = 0, X = 0, Y = 0, x0 = 0, y0 = 0, n_top = 1, z_inc = 0;
   double n_bot_re = 1, n_bot_im = 0;
   int precision = 0;
@@ -90,6 +95,7 @@ struct Plan {
   double2* d_sz_bot = nullptr;     // [M]
   float2* d_twx = nullptr;         // [Up][Fx/8]
   float2* d_twy = nullptr;         // [Fy/8][Vp]
+  float* d_pupil = nullptr;        // [M] 1 / 0 transmission of the pupil (pupil_na > 0)
 
   // attached inputs (not owned)
   const double2* gamma = nullptr;

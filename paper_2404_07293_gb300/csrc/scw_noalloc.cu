@@ -108,6 +108,8 @@ extern "C" scw_status scw_recompose_noalloc(int U, int V, double X, double Y, in
   it.M = U * V; it.U = U; it.V = V; it.Fx = Fx; it.Fy = Fy; it.Fz = Fz;
   it.Up = Up;
   it.Vp = Vp;
+  it.I = 1;
+  it.Fz_out = Fz;
   it.split_stride = (size_t)Fz * 3 * U * V;
   float2* twx = reinterpret_cast<float2*>(base);
   float2* twy = reinterpret_cast<float2*>(base + b_twx);

@@ -121,9 +121,10 @@ __global__ void __launch_bounds__(128) phases_tc_kernel(const __grid_constant__ 
   const int M4 = 4 * M;
   // the mode's constants are requested before the block waits for the plane offsets
   double2 g = make_double2(0.0, 0.0), al = make_double2(0.0, 0.0);
+  const double2* alpha_lj = it.alpha + (size_t)u.layer * M4 + j;  // illumination 0
   if (j < M4) {
     g = it.gamma[(size_t)u.layer * M4 + j];
-    al = it.alpha[(size_t)u.layer * M4 + j];
+    al = alpha_lj[0];
   }
   load_offsets(off, u, it.zplanes, it.zbounds);
   __syncthreads();
@@ -139,7 +140,12 @@ __global__ void __launch_bounds__(128) phases_tc_kernel(const __grid_constant__ 
     if (f < u.nf) {
       const float dh = fwd ? off.f_hi[f] : off.b_hi[f];
       const float dl = fwd ? off.f_lo[f] : off.b_lo[f];
-      cv = cmulf(mc.alpha, mode_factor_df(mc.a_hi, mc.a_lo, mc.c, dh, dl));
+      float2 a = mc.alpha;
+      if (it.I > 1) {  // plane slot f I + i carries illumination i
+        const double2 ai = alpha_lj[(size_t)((u.f0 + f) % it.I) * it.alpha_istride];
+        a = make_float2((float)ai.x, (float)ai.y);
+      }
+      cv = cmulf(a, mode_factor_df(mc.a_hi, mc.a_lo, mc.c, dh, dl));
     }
     const float v0[2] = {cv.x, -cv.y};
     const float v1[2] = {cv.y, cv.x};
@@ -162,7 +168,8 @@ __global__ void __launch_bounds__(128) phases_fp32_kernel(const LayerUnit* __res
                                                           const double* __restrict__ zb,
                                                           const double2* __restrict__ gamma,
                                                           const double2* __restrict__ alpha, int M, int F_pad,
-                                                          double inv_lam, float2* __restrict__ C) {
+                                                          double inv_lam, float2* __restrict__ C, int I,
+                                                          size_t alpha_istride) {
   __shared__ PlaneOffsets off;
   const LayerUnit u = units[blockIdx.y];
   load_offsets(off, u, zplanes, zb);
@@ -173,30 +180,42 @@ __global__ void __launch_bounds__(128) phases_fp32_kernel(const LayerUnit* __res
   const ModeConst mc = mode_const(gamma[(size_t)u.layer * M4 + j], alpha[(size_t)u.layer * M4 + j], inv_lam);
   const bool fwd = j < 2 * M;
   float2* dst = C + ((size_t)blockIdx.y * M4 + j) * F_pad;  // C is per work unit
+  // plane slot f I + i carries illumination i
+  auto alpha_of = [&](int f) {
+    if (I == 1) return mc.alpha;
+    const double2 a = alpha[(size_t)((u.f0 + f) % I) * alpha_istride + (size_t)u.layer * M4 + j];
+    return make_float2((float)a.x, (float)a.y);
+  };
   for (int f = 0; f < F_pad; f += 2) {
     float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
     if (f < u.nf)
-      c0 = cmulf(mc.alpha, mode_factor_df(mc.a_hi, mc.a_lo, mc.c, fwd ? off.f_hi[f] : off.b_hi[f],
-                                          fwd ? off.f_lo[f] : off.b_lo[f]));
+      c0 = cmulf(alpha_of(f), mode_factor_df(mc.a_hi, mc.a_lo, mc.c, fwd ? off.f_hi[f] : off.b_hi[f],
+                                             fwd ? off.f_lo[f] : off.b_lo[f]));
     if (f + 1 < u.nf)
-      c1 = cmulf(mc.alpha, mode_factor_df(mc.a_hi, mc.a_lo, mc.c, fwd ? off.f_hi[f + 1] : off.b_hi[f + 1],
-                                          fwd ? off.f_lo[f + 1] : off.b_lo[f + 1]));
+      c1 = cmulf(alpha_of(f + 1), mode_factor_df(mc.a_hi, mc.a_lo, mc.c, fwd ? off.f_hi[f + 1] : off.b_hi[f + 1],
+                                                 fwd ? off.f_lo[f + 1] : off.b_lo[f + 1]));
     *reinterpret_cast<float4*>(dst + f) = make_float4(c0.x, c0.y, c1.x, c1.y);
   }
 }
 
 // Exterior planes (Eq. 9 with the reflected wave travelling towards -z):
-// S_part[0][f][c M + m].
+// S_part[0][f][c M + m]. Plane slot f carries illumination f mod I (p_* are [I][3][M]);
+// below the sample an optional pupil mask drops the orders outside the objective's NA.
 __global__ void exterior_kernel(const int* __restrict__ ext_planes, const double* __restrict__ zplanes,
                                 double z0, double zL, double z_inc, const double2* __restrict__ sz_top,
                                 const double2* __restrict__ sz_bot, const double2* __restrict__ p_inc,
                                 const double2* __restrict__ p_ref, const double2* __restrict__ p_trn,
-                                int M, double inv_lam, float2* __restrict__ S) {
+                                int M, double inv_lam, float2* __restrict__ S, int I,
+                                const float* __restrict__ pupil) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
   const int f = ext_planes[blockIdx.y];
   const double z = zplanes[f];
   float2* out = S + (size_t)f * 3 * M;
+  const size_t po = (size_t)(f % I) * 3 * M;
+  p_inc += po;
+  p_ref += po;
+  p_trn += po;
   if (z < z0) {
     const double2 st = sz_top[m];
     const float2 gi = mode_factor(st, z - z_inc, inv_lam);
@@ -209,7 +228,8 @@ __global__ void exterior_kernel(const int* __restrict__ ext_planes, const double
     }
   } else {
     const double2 sb = sz_bot[m];
-    const float2 gt = mode_factor(sb, z - zL, inv_lam);
+    float2 gt = mode_factor(sb, z - zL, inv_lam);
+    if (pupil) gt = make_float2(gt.x * pupil[m], gt.y * pupil[m]);
     for (int c = 0; c < 3; ++c) {
       const double2 a = p_trn[c * M + m];
       out[c * M + m] = cmulf(make_float2((float)a.x, (float)a.y), gt);
@@ -325,7 +345,7 @@ cudaError_t launch_phases_fp32(const Plan& p, cudaStream_t st) {
   if (n_units == 0) return cudaSuccess;
   dim3 grid((4 * p.M + 127) / 128, n_units);
   phases_fp32_kernel<<<grid, 128, 0, st>>>(p.d_units, p.d_zplanes, p.d_zbounds, p.gamma, p.alpha, p.M,
-                                           p.F_pad, 1.0 / p.lambda, p.Cf);
+                                           p.F_pad, 1.0 / p.lambda, p.Cf, p.I, (size_t)p.L * 4 * p.M);
   return cudaGetLastError();
 }
 
@@ -334,7 +354,7 @@ cudaError_t launch_exterior(const Plan& p, cudaStream_t st) {
   dim3 grid((p.M + 127) / 128, p.n_exterior);
   const double z0 = p.z_bounds.front(), zL = p.z_bounds.back();
   exterior_kernel<<<grid, 128, 0, st>>>(p.d_ext_planes, p.d_zplanes, z0, zL, p.z_inc, p.d_sz_top, p.d_sz_bot,
-                                        p.p_inc, p.p_ref, p.p_trn, p.M, 1.0 / p.lambda, p.S_part);
+                                        p.p_inc, p.p_ref, p.p_trn, p.M, 1.0 / p.lambda, p.S_part, p.I, p.d_pupil);
   return cudaGetLastError();
 }
 

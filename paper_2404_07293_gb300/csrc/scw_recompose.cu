@@ -138,7 +138,9 @@ __global__ void __launch_bounds__(256, 4) recompose_kernel(const __grid_constant
   const int Fx = it.Fx, Fy = it.Fy;
   const int Qy = Fy >> 3;
   float2* out = BATCH ? outs[e.x] : out_one;
-  float2* dst = out + (((size_t)c * it.Fz + f) * Fy) * Fx + x;
+  // plane slot f = (output plane) I + illumination; the field is [I][3][Fz_out][Fy][Fx]
+  const int fo = f / it.I, il = f - fo * it.I;
+  float2* dst = out + ((size_t)il * 3 * it.Fz_out + (size_t)c * it.Fz_out + fo) * Fy * Fx + x;
   if (bl >= nb) return;  // no __syncthreads below
   for (int b = w; b < Qy; b += 8) {
     float2 G0[8], G1[8];
@@ -289,7 +291,9 @@ __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_c
   if (x >= Fx) return;  // Fx is a multiple of 8, so x + 1 < Fx as well
   const int Q = Fy >> 3;
   float2* out = BATCH ? outs[e.x] : out_one;
-  float2* dst = out + (((size_t)c * it.Fz + f) * Fy) * Fx + x;
+  // plane slot f = (output plane) I + illumination; the field is [I][3][Fz_out][Fy][Fx]
+  const int fo = f / it.I, il = f - fo * it.I;
+  float2* dst = out + ((size_t)il * 3 * it.Fz_out + (size_t)c * it.Fz_out + fo) * Fy * Fx + x;
   const float4* col = ys_col4 + lane;
   if constexpr (!PAIR) {
     for (int b = w; b < Q; b += 8) {

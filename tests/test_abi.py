@@ -62,7 +62,9 @@ def _desc(**kw):
 
 @pytest.mark.parametrize("bad", [
     dict(U=0), dict(L=0), dict(lam=0.0), dict(X=-1.0), dict(Fx=12), dict(Fy=4), dict(Fx=8192), dict(Fz=0),
-    dict(precision=7), dict(k_split=-1), dict(n_top=0.0),
+    dict(precision=7), dict(k_split=-1), dict(n_top=0.0), dict(illuminations=-1), dict(illuminations=257),
+    dict(illuminations=200, Fz=400, zp=np.linspace(0.0, 0.5, 400)), dict(pupil_na=-0.1),
+    dict(pupil_na=float("inf")),
     dict(zb=np.array([0.0, 0.5, 0.5])), dict(zp=np.array([0.3, 0.1])), dict(zp=np.array([0.1, np.nan])),
 ])
 def test_bad_descriptors_are_rejected(lib, bad):

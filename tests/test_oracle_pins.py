@@ -280,3 +280,30 @@ def test_region_half_open():
     assert synth.region(1.0, zb) == 1
     assert synth.region(2.0, zb) == 1
     assert synth.region(2.0 + 1e-12, zb) == 2
+
+
+# objective pupil below the sample -------------------------------------------
+@pytest.mark.parametrize("na,passed", [(0.3, 5), (0.55, 13), (5.0, 49)])
+def test_pupil_is_an_ideal_low_pass_of_the_transmitted_field(na, passed):
+    """Below the sample the pupil keeps exactly the plane waves a lens of the
+    given NA collects: filtering the unfiltered field's own FFT with the disk
+    |lambda f| <= NA (f the FFT's spatial frequencies) gives the pupil field, and
+    the number of passed orders is the lattice-point count of that disk."""
+    sol = cw.solve_problem(wl.config_tiny())
+    Fx = Fy = 32
+    zs = [sol.z_bounds[-1] + 0.3, sol.z_bounds[-1] + 1.7]
+    full = synth.synthesize_direct(sol, Fx, Fy, zs)
+    cut = synth.synthesize_direct(sol, Fx, Fy, zs, pupil_na=na)
+    fx = np.fft.fftfreq(Fx, d=sol.X / Fx)
+    fy = np.fft.fftfreq(Fy, d=sol.Y / Fy)
+    disk = (sol.lam * fx[None, :]) ** 2 + (sol.lam * fy[:, None]) ** 2 <= na * na * (1 + 1e-9)
+    spec = np.fft.fft2(full, axes=(-2, -1))
+    lowpass = np.fft.ifft2(spec * disk, axes=(-2, -1))
+    assert np.abs(cut - lowpass).max() < 1e-12 * np.abs(full).max()
+    assert int(synth.pupil_mask(sol, na).sum()) == passed
+    if passed < sol.U * sol.V:
+        assert np.abs(cut - full).max() > 1e-3 * np.abs(full).max()  # the pupil removes something
+    # above the sample and inside it the pupil changes nothing
+    zin = [sol.z_bounds[0] - 0.4, 0.5 * (sol.z_bounds[0] + sol.z_bounds[-1])]
+    assert np.array_equal(synth.synthesize_direct(sol, 8, 8, zin, pupil_na=na),
+                          synth.synthesize_direct(sol, 8, 8, zin))

@@ -145,6 +145,22 @@ def random_layer_set(seed: int, U: int, V: int, L: int, evanescent_frac: float =
     return W, gamma, alpha, ext[0], ext[1], ext[2]
 
 
+def random_illuminations(seed: int, I: int, U: int, V: int, L: int, backward_scale: float = 0.1):
+    """Amplitudes of I incident fields on one solved sample (same draws as the
+    alpha and p of random_layer_set, one set per illumination).
+
+    Returns ``(alpha, p_inc, p_ref, p_trn)``: alpha [I][L][4M], p_* [I][3][M], complex128.
+    """
+    M = U * V
+    rng = np.random.default_rng(seed)
+    sa = 1.0 / math.sqrt(2 * 2 * M)
+    af = (rng.standard_normal((I, L, 2 * M)) + 1j * rng.standard_normal((I, L, 2 * M))) * sa
+    ab = (rng.standard_normal((I, L, 2 * M)) + 1j * rng.standard_normal((I, L, 2 * M))) * sa * backward_scale
+    sp = 1.0 / math.sqrt(2 * M)
+    ext = [(rng.standard_normal((I, 3, M)) + 1j * rng.standard_normal((I, 3, M))) * sp for _ in range(3)]
+    return np.concatenate([af, ab], axis=2), ext[0], ext[1], ext[2]
+
+
 @dataclass
 class Problem:
     """Everything that defines one forward simulation plus its output grid."""
