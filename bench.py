@@ -348,6 +348,68 @@ def run_illumination(args, dev, world, Wd, gd, zb, zp, hbm, bf16_tf):
     return res
 
 
+def run_points(args, dev, world, Wd, gd, ad, zb, zp, hbm, bf16_tf):
+    """Field off the FFT grid on the single-wavelength workload (21x21 orders, 32
+    layers, 256 planes): a zoomed 256 x 256 window of 4 x 4 um (points between the
+    grid's pixels) and one x-z plane of 256 points, on every plane. The point
+    product is a dense GEMM over the 441 orders; each precision is timed on the
+    same inputs."""
+    import torch
+    import paper_2404_07293_gb300 as scw
+    M = U_ORD * U_ORD
+    Fz = len(zp)
+    n = 256
+    g = (np.arange(n) + 0.5) * (4.0 / n) + 6.0
+    gx, gy = np.meshgrid(g, g)
+    cases = {"window_256x256_of_4um": np.column_stack([gx.ravel(), gy.ravel()]),
+             "xz_plane_256": np.column_stack([np.arange(n) * X_PERIOD / n, np.full(n, 0.5 * X_PERIOD)])}
+    stream = torch.cuda.current_stream(dev)
+    res = {"planes": Fz, "unit": "voxels/s", "peaks": {"bf16_tflops": bf16_tf, "source": "MEASURED_PEAKS.json (burst)"}}
+    products = {"fp32": 1, "split_bf16": 3}
+    for name, xy in cases.items():
+        P = len(xy)
+        flops = 8.0 * M * 3 * Fz * P  # complex multiply-adds of the point product, 8 flops each
+        r = {"points": P, "voxels_per_step": P * Fz, "product_flops": flops}
+        out = torch.empty((3, Fz, P), dtype=torch.complex64, device=dev)
+        for prec in ("split_bf16", "fp32"):
+            plan = scw.Plan(U_ORD, U_ORD, L_LAYERS, LAM, X_PERIOD, X_PERIOD, zb, F_XY, F_XY, zp, precision=prec)
+            plan.set_layers(Wd, gd, ad)
+            plan.set_points(xy)
+            for _ in range(max(3, args.warmup)):
+                plan.synthesize_points(out)
+            plan.check()
+            steps = max(3, min(args.steps, 10))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            for _ in range(steps):
+                plan.synthesize_points(out)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            plan.enable_timing(True)
+            for _ in range(3):
+                plan.synthesize_points(out)
+            kt = plan.timings()
+            plan.enable_timing(False)
+            plan.check()
+            tf = flops / (kt["ypass_ms"] * 1e-3) / 1e12
+            q = {"value": replica_throughput(P * Fz, ms * 1e-3, dev)[0], "ms_per_step": ms,
+                 "kernel_ms": {"phases_ms": kt["phases_ms"], "contract_ms": kt["contract_ms"],
+                               "spectrum_operand_ms": kt["xpass_ms"], "point_product_ms": kt["ypass_ms"],
+                               "total_ms": kt["total_ms"]},
+                 "point_product_tflops": tf}
+            if prec != "fp32":
+                q["tensor_frac_issued"] = tf * products[prec] / bf16_tf
+            r[prec] = q
+            plan.close()
+        r["point_product_speedup_split_bf16_vs_fp32"] = r["fp32"]["kernel_ms"]["point_product_ms"] / \
+            r["split_bf16"]["kernel_ms"]["point_product_ms"]
+        res[name] = r
+        del out
+    return res
+
+
 def run_surrogate(args, dev, bf16_peaks):
     """Learned surrogate at its full size: 4 Fourier layers of width 32, 16x16
     kept modes on a 64x64 grid, inputs 8 slices of 32x32 complex n (seeded
@@ -571,6 +633,11 @@ def run_ours(args, world, rank, local):
         illum = run_illumination(args, dev, world, Wd, gd, zb, zp, hbm, bf16_tf)
         torch.cuda.empty_cache()
 
+    points = None
+    if not args.no_points:
+        points = run_points(args, dev, world, Wd, gd, ad, zb, zp, hbm, bf16_tf)
+        torch.cuda.empty_cache()
+
     sweep = None
     if not args.no_sweep:
         plan.close()
@@ -620,6 +687,7 @@ def run_ours(args, world, rank, local):
             "variants": variants or None,
             "sweep": sweep,
             "illumination": illum,
+            "points": points,
             "surrogate": surrogate,
         }
         print(json.dumps(line), flush=True)
@@ -645,6 +713,7 @@ def main():
     ap.add_argument("--sweep-items", type=int, default=128)
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate block")
     ap.add_argument("--fno-batch", type=int, default=256)
+    ap.add_argument("--no-points", action="store_true", help="skip the off-grid point-set block")
     ap.add_argument("--illuminations", type=int, default=16,
                     help="incident fields of the multi-illumination block (1 skips it)")
     ap.add_argument("--only-surrogate", action="store_true",

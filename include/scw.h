@@ -197,6 +197,34 @@ scw_status scw_synthesize_host(scw_plan_t plan, const void* W, const void* gamma
                                const void* alpha, const void* p_inc, const void* p_ref,
                                const void* p_trn, void* out, void* stream);
 
+/* ---- fields at arbitrary lateral points (x-z / y-z planes, point sets) -------
+ * Eq. 10 evaluated at P given lateral points instead of the Fx x Fy grid:
+ *   E_c(x_p, y_p, z_f) = sum_m S_c[m](z_f) exp(2 pi i (u_m x_p / X + v_m y_p / Y))
+ * on every z plane f of the plan (z_planes, all illuminations). An x-z plane
+ * is the points (x_i, y) for fixed y, a y-z plane (x, y_j) for fixed x; the
+ * paper shows fields in all three plane orientations. The sum runs as a dense
+ * matrix product over the M orders (no FFT), so points need not lie on a grid,
+ * need not be evenly spaced and may lie outside one period (E is periodic).
+ *
+ * scw_plan_set_points: xy is a HOST double [P][2] array of (x, y), the same
+ * length unit as X and Y, finite; 1 <= P <= 2^22 (P = 0 releases the point tables).
+ * Builds the plan's table of exp(2 pi i (u x / X + v y / Y)) per (point,
+ * order), with the phase reduced in cycles in FP64 (plan-owned: 6 (2M rounded
+ * up to 64) bytes per point on tensor-core plans, 8 M bytes on FP32 plans).
+ * Synchronises (the device, when it replaces an earlier point set). Single
+ * (non-batched) plans only; any number of calls.
+ *
+ * scw_synthesize_points: out is a DEVICE complex64 [I][3][Fz][P] array
+ * (caller-owned, I = illuminations). Runs steps (a) and (b) as scw_synthesize
+ * does, then the point product: on tensor-core plans (split-BF16 or FP16 W) a
+ * tcgen05 GEMM with split-BF16 operands (hi + lo, three products, FP32
+ * accumulation); on FP32 plans a SIMT FP32 GEMM. With timing on, the x-pass
+ * slot of scw_kernel_times holds the spectrum operand preparation and the
+ * y-pass slot the point product. SCW_ERR_STATE before scw_plan_set_layers or
+ * without points; SCW_ERR_UNSUPPORTED on batched plans. */
+scw_status scw_plan_set_points(scw_plan_t plan, const double* xy, int n_points);
+scw_status scw_synthesize_points(scw_plan_t plan, void* out, void* stream);
+
 /* Synchronise `stream` and read (then clear) the plan's device error word:
  * SCW_OK, SCW_ERR_TIMEOUT (a bounded device wait ran out) or SCW_ERR_CUDA. */
 scw_status scw_plan_check(scw_plan_t plan, void* stream);

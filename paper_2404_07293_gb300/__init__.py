@@ -83,6 +83,8 @@ class Plan:
         self.U, self.V, self.L = int(U), int(V), int(L)
         self.M = self.U * self.V
         self.Fx, self.Fy = int(Fx), int(Fy)
+        self.X, self.Y, self.x0, self.y0 = float(X), float(Y), float(x0), float(y0)
+        self.n_points = 0
         self.I = max(1, int(illuminations))
         self.exterior = bool(exterior)
         d, (self._zb, self._zp) = _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0, y0, n_top, n_bot,
@@ -136,6 +138,36 @@ class Plan:
         check(self._lib.scw_recompose(self._h, _dev_ptr(S, torch.complex64, (self.I * self.Fz, 3, self.M), "S"),
                                       _dev_ptr(out, torch.complex64, self.out_shape(), "out"),
                                       _stream_handle(stream)), "scw_recompose")
+        return out
+
+    # ------------------------------------------------------------- point sets
+    def set_points(self, xy):
+        """Lateral points (x, y) [P][2] at which synthesize_points evaluates the field on every z plane."""
+        xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
+        check(self._lib.scw_plan_set_points(self._h, xy.ctypes.data_as(ctypes.c_void_p), int(xy.shape[0])),
+              "scw_plan_set_points")
+        self.n_points = int(xy.shape[0])
+
+    def set_xz_plane(self, y, n=None):
+        """Points of the x-z plane at height y: x_i = x0 + i X / n (n = Fx by default)."""
+        n = self.Fx if n is None else int(n)
+        self.set_points(np.stack([self.x0 + np.arange(n) * self.X / n, np.full(n, float(y))], axis=1))
+
+    def set_yz_plane(self, x, n=None):
+        """Points of the y-z plane at x: y_j = y0 + j Y / n (n = Fy by default)."""
+        n = self.Fy if n is None else int(n)
+        self.set_points(np.stack([np.full(n, float(x)), self.y0 + np.arange(n) * self.Y / n], axis=1))
+
+    def points_shape(self):
+        return _per_illum(self.I, (3, self.Fz, self.n_points))
+
+    def synthesize_points(self, out=None, stream=None):
+        """Field at the points of set_points on every z plane: [3][Fz][P] ([I][3][Fz][P])."""
+        import torch
+        if out is None:
+            out = torch.empty(self.points_shape(), dtype=torch.complex64, device="cuda")
+        check(self._lib.scw_synthesize_points(self._h, _dev_ptr(out, torch.complex64, self.points_shape(), "out"),
+                                              _stream_handle(stream)), "scw_synthesize_points")
         return out
 
     def synthesize_host(self, W, gamma, alpha, p_inc=None, p_ref=None, p_trn=None, out=None, stream=None):

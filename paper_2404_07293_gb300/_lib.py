@@ -65,6 +65,8 @@ SIGNATURES = {
     "scw_synthesize": (c_int, [c_void_p, c_void_p, c_void_p]),
     "scw_spectrum": (c_int, [c_void_p, c_void_p, c_void_p]),
     "scw_recompose": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "scw_plan_set_points": (c_int, [c_void_p, c_void_p, c_int]),
+    "scw_synthesize_points": (c_int, [c_void_p, c_void_p, c_void_p]),
     "scw_synthesize_host": (c_int, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
     "scw_plan_batched_create": (c_int, [POINTER(ScwDesc), c_int, POINTER(c_void_p)]),
     "scw_plan_batched_set_layers": (c_int, [c_void_p, c_int] + [c_void_p] * 6 + [c_void_p]),

@@ -73,8 +73,10 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * 128;
-  const int n0 = (EPI == EPI_DW) ? m0 : blockIdx.y * BN;
+  // EPI_FIELD walks the column tiles fastest, so the CTAs that share a row tile of A run together
+  constexpr bool NFAST = (EPI == EPI_FIELD);
+  const int m0 = (NFAST ? blockIdx.y : blockIdx.x) * 128;
+  const int n0 = (EPI == EPI_DW) ? m0 : (NFAST ? blockIdx.x : blockIdx.y) * BN;
   const int kb0 = blockIdx.z * kper;
   const int nkb = max(0, min(K / 64 - kb0, kper));
   // samples of this tile whose 1x1 convolution runs as a second K segment
@@ -532,7 +534,9 @@ static cudaError_t launch_tc_t(const CUtensorMap& mA, const CUtensorMap& mB, con
   if (e != cudaSuccess) return e;
   const int nkb = K / 64;
   const int kper = (nkb + splits - 1) / splits;
-  const dim3 grid((M + 127) / 128, EPI == EPI_DW ? 1 : (N + BN - 1) / BN, splits);
+  const dim3 grid = EPI == EPI_FIELD ? dim3((N + BN - 1) / BN, (M + 127) / 128, splits)
+                                     : dim3((M + 127) / 128, EPI == EPI_DW ? 1 : (N + BN - 1) / BN, splits);
+  if (grid.y > 65535u) return cudaErrorInvalidValue;
   gemm_tc_kernel<BN, EPI><<<grid, kGemmThreads, Cfg::SMEM, st>>>(mA, mB, mA2, mW, ea, K, kper, err, timeout_ns);
   return cudaGetLastError();
 }
@@ -582,6 +586,9 @@ cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtenso
     case EPI_DW:
       return BN == 128 ? launch_tc_t<128, EPI_DW>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st)
                        : cudaErrorInvalidValue;
+    case EPI_FIELD:
+      return splits == 1 ? launch_tc_bn<EPI_FIELD>(BN, mA, mB, mA2, mW, ea, M, N, K, 1, err, timeout_ns, st)
+                         : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }
@@ -616,6 +623,8 @@ cudaError_t launch_gemm_simt(int epi, const float* A, long long lda, const float
     case EPI_LAYER_FWD: return launch_simt_t<EPI_LAYER_FWD>(A, lda, B, ldb, ea, M, N, K, splits, st);
     case EPI_LAYER_BWD: return launch_simt_t<EPI_LAYER_BWD>(A, lda, B, ldb, ea, M, N, K, splits, st);
     case EPI_DW: return launch_simt_t<EPI_DW>(A, lda, B, ldb, ea, M, N, K, splits, st);
+    case EPI_FIELD: return splits == 1 ? launch_simt_t<EPI_FIELD>(A, lda, B, ldb, ea, M, N, K, 1, st)
+                                       : cudaErrorInvalidValue;
     default: return cudaErrorInvalidValue;
   }
 }

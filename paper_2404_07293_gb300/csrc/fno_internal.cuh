@@ -24,7 +24,9 @@ enum Epi : int {
                       // out[split][mode][row] (truncated DFTs)
   EPI_LAYER_FWD = 1,  // rows = pixels, columns = (sample, channel): Z = alpha D + c + W V; V' = GELU(Z)
   EPI_LAYER_BWD = 2,  // rows = pixels, columns = (sample, channel): dV = D + W^T dZ; dZ' = dV GELU'(Z)
-  EPI_DW = 3          // rows = (sample, o), columns = (sample, i) of 4 samples: keep the diagonal blocks
+  EPI_DW = 3,         // rows = (sample, o), columns = (sample, i) of 4 samples: keep the diagonal blocks
+  EPI_FIELD = 4       // field synthesis at points: rows = points, columns = (plane slot f, component c,
+                      // re/im); complex E[(f, c)][p] -> out[il][c][fo][p], f = fo I + il (streaming stores)
 };
 
 struct EpiArgs {
@@ -45,6 +47,8 @@ struct EpiArgs {
   void* out_cf;        // FWD: V_{l+1} [B][C][P]; BWD: dZ_{l-1} [B][C][P], null for l = 0
   void* out_cl;        // FWD: V_{l+1} [B][P][C]; BWD: dZ_{l-1} (or dV_0 for l = 0) [B][P][C]
   int gelu;            // FWD: apply GELU
+  int fz_out;          // FIELD: output planes per illumination
+  int illum;           // FIELD: illuminations I
 };
 
 // ---- element access (T = float or __nv_bfloat16) ----------------------------------------
@@ -131,6 +135,18 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
     for (int j = 0; j < 16; ++j) {
       const int k = col0 / 2 + j;
       if (2 * k < a.cols) o[(size_t)k * a.ld] = make_float2(a.alpha * acc[2 * j], a.alpha * acc[2 * j + 1]);
+    }
+  } else if constexpr (EPI == EPI_FIELD) {
+    if (row >= a.rows) return;
+    float2* o = reinterpret_cast<float2*>(a.out) + row;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = col0 / 2 + j;  // k = f 3 + c
+      if (2 * k < a.cols) {
+        const int f = k / 3, c = k - 3 * f;
+        const int fo = f / a.illum, il = f - fo * a.illum;
+        __stcs(o + ((size_t)(il * 3 + c) * a.fz_out + fo) * (size_t)a.ld, make_float2(acc[2 * j], acc[2 * j + 1]));
+      }
     }
   } else if constexpr (EPI == EPI_LAYER_FWD) {
     const int p = row, b = col0 / C;

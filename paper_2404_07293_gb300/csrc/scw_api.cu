@@ -13,6 +13,7 @@
 #include <queue>
 
 #include "scw_internal.cuh"
+#include "scw_points.cuh"
 
 namespace scw {
 
@@ -60,6 +61,7 @@ static cudaError_t upload(T** p, const std::vector<T>& v, size_t& total) {
 
 static void free_item(Plan* p) {
   if (!p) return;
+  points_free(p->pts);
   void* ptrs[] = {p->d_units,   p->d_zplanes, p->d_zbounds, p->d_nsplit,   p->d_nsplit1, p->d_ext_planes, p->d_pupil,
                   p->d_sz_top,  p->d_sz_bot,  p->d_twx,     p->d_twy,      p->Whi,       p->Wlo,
                   p->Wh,        p->Wt,        p->Bhi,       p->Blo,        p->Cf,        p->S_part,
@@ -1092,6 +1094,47 @@ scw_status scw_recompose(scw_plan_t P, const void* S, void* out, void* stream) {
   cudaError_t e = launch_recompose(p->item, nullptr, P->d_plane_entries, P->n_plane_entries, P->max_Qx, P->rec_smem,
                                    static_cast<const float2*>(S), p->d_nsplit1, static_cast<float2*>(out), nullptr, st);
   if (e != cudaSuccess) return cuda_error(e, "recompose launch");
+  return SCW_OK;
+}
+
+scw_status scw_plan_set_points(scw_plan_t P, const double* xy, int n_points) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+  if (P->batched) return set_error(SCW_ERR_UNSUPPORTED, "point sets are for single plans");
+  if (n_points < 0 || n_points > (1 << 22)) return set_error(SCW_ERR_INVALID_ARGUMENT, "n_points must be in [0, 2^22]");
+  if (n_points > 0 && !xy) return set_error(SCW_ERR_INVALID_ARGUMENT, "xy is required");
+  for (int i = 0; i < 2 * n_points; ++i)
+    if (!std::isfinite(xy[i])) return set_error(SCW_ERR_INVALID_ARGUMENT, "non-finite point coordinate");
+  Plan* p = P->items[0];
+  if (p->pts) {  // earlier calls may still read the old tables
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");
+  }
+  points_free(p->pts);
+  p->pts = nullptr;
+  if (n_points == 0) return SCW_OK;
+  return points_build(&p->pts, *p, P->tc, xy, n_points, P->cap_stream);
+}
+
+scw_status scw_synthesize_points(scw_plan_t P, void* out, void* stream) {
+  if (!P || !out) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and out are required");
+  if (P->batched) return set_error(SCW_ERR_UNSUPPORTED, "point sets are for single plans");
+  Plan* p = P->items[0];
+  if (!p->layers_set) return set_error(SCW_ERR_STATE, "scw_plan_set_layers has not been called");
+  if (!p->pts) return set_error(SCW_ERR_STATE, "scw_plan_set_points has not been called");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const bool marks = P->timing;
+  int n = 0;
+  scw_status s = enqueue_spectrum(P, st, marks, n);
+  if (s != SCW_OK) return s;
+  mark(P, 2, st, marks);
+  cudaError_t e = points_prepare(*p->pts, *p, st);
+  if (e != cudaSuccess) return cuda_error(e, "point spectrum launch");
+  mark(P, 3, st, marks);
+  e = points_product(*p->pts, *p, static_cast<float2*>(out), P->d_err, P->timeout_ns, st);
+  if (e != cudaSuccess) return cuda_error(e, "point product launch");
+  mark(P, 4, st, marks);
+  if (marks && P->tev_used + kMarks <= P->tev.size()) P->tev_used += kMarks;
+  P->kernels_per_synthesis = n + 2;
   return SCW_OK;
 }
 

@@ -65,6 +65,8 @@ struct ItemDev {
   size_t alpha_istride;    // L 4M: alpha elements per illumination
 };
 
+struct PointTables;  // scw_points.cuh
+
 struct Plan {
   // description
   int U = 0, V = 0, M = 0, L = 0, Fx = 0, Fy = 0, Fz = 0;  // Fz = I Fz_out plane slots
@@ -96,6 +98,7 @@ struct Plan {
   float2* d_twx = nullptr;         // [Up][Fx/8]
   float2* d_twy = nullptr;         // [Fy/8][Vp]
   float* d_pupil = nullptr;        // [M] 1 / 0 transmission of the pupil (pupil_na > 0)
+  PointTables* pts = nullptr;      // lateral point set (scw_plan_set_points), owned
 
   // attached inputs (not owned)
   const double2* gamma = nullptr;

@@ -307,3 +307,20 @@ def test_pupil_is_an_ideal_low_pass_of_the_transmitted_field(na, passed):
     zin = [sol.z_bounds[0] - 0.4, 0.5 * (sol.z_bounds[0] + sol.z_bounds[-1])]
     assert np.array_equal(synth.synthesize_direct(sol, 8, 8, zin, pupil_na=na),
                           synth.synthesize_direct(sol, 8, 8, zin))
+
+
+# field at arbitrary points ----------------------------------------------------
+def test_point_sums_match_the_fft_on_the_grid_and_are_periodic():
+    """The per-point sum (x-z / y-z planes and point sets) agrees with numpy's
+    inverse FFT at grid points and repeats with the lateral period."""
+    sol = cw.solve_problem(wl.config_tiny())
+    z = 0.41
+    Fx, Fy, x0, y0 = 16, 8, 0.3, -0.2
+    grid = synth.field_fft(sol, synth.spectrum_at(sol, z), Fx, Fy, x0, y0)
+    xs, ys = synth.pixel_coords(sol, Fx, Fy, x0, y0)
+    gx, gy = np.meshgrid(xs, ys)
+    pts = np.stack([gx.ravel(), gy.ravel(), np.full(gx.size, z)], axis=1)
+    E = synth.field_points(sol, pts).reshape(3, Fy, Fx)
+    assert np.abs(E - grid).max() < 1e-12 * np.abs(grid).max()
+    far = pts + np.array([3 * sol.X, -2 * sol.Y, 0.0])
+    assert np.abs(synth.field_points(sol, far).reshape(3, Fy, Fx) - E).max() < 1e-10 * np.abs(E).max()
