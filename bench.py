@@ -410,6 +410,73 @@ def run_points(args, dev, world, Wd, gd, ad, zb, zp, hbm, bf16_tf):
     return res
 
 
+def run_tiling(args, dev, world, Wd, gd, ad, zb, zp, hbm):
+    """Large lateral fields from the single-wavelength workload (21x21 orders,
+    32 layers, 256 planes of 256 x 256 per period):
+      - periodic tiling: one unit cell stored to 4 x 4 periods (1024 x 1024 x 256);
+      - patch mosaic: 4 x 4 different samples (one batched plan, one graph), each
+        written as a 256 x 256 patch of one 1024 x 1024 x 256 field (strided views).
+    Both write 6.4 GB per step."""
+    import torch
+    import paper_2404_07293_gb300 as scw
+    import workloads as wl
+    Fz, n = len(zp), 4
+    H = W = n * F_XY
+    stream = torch.cuda.current_stream(dev)
+    mosaic = torch.empty((3, Fz, H, W), dtype=torch.complex64, device=dev)
+    out_bytes = mosaic.numel() * 8
+    M = U_ORD * U_ORD
+    w_bytes = L_LAYERS * 3 * M * 4 * M * 8
+
+    def timed(fn, steps):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    steps = max(3, min(args.steps, 10))
+    res = {"unit": "voxels/s", "voxels_per_step": H * W * Fz, "out_bytes": out_bytes}
+    plan = scw.Plan(U_ORD, U_ORD, L_LAYERS, LAM, X_PERIOD, X_PERIOD, zb, F_XY, F_XY, zp, precision=args.precision,
+                    tiles=(n, n))
+    plan.set_layers(Wd, gd, ad)
+    ms = timed(lambda: plan.synthesize(mosaic), steps)
+    plan.check()
+    plan.enable_timing(True)
+    for _ in range(3):
+        plan.synthesize(mosaic)
+    kt = plan.timings()
+    plan.enable_timing(False)
+    plan.close()
+    roof = (w_bytes + out_bytes) / (hbm * 1e9) * 1e3
+    res["periodic_4x4"] = {"value": replica_throughput(H * W * Fz, ms * 1e-3, dev)[0], "ms_per_step": ms,
+                           "ypass_ms": kt["ypass_ms"], "ypass_write_gbs": out_bytes / (kt["ypass_ms"] * 1e-3) / 1e9,
+                           "hbm_roofline_ms": roof, "roofline_frac": roof / ms}
+    items = [dict(U=U_ORD, V=U_ORD, L=L_LAYERS, lam=LAM, X=X_PERIOD, Y=X_PERIOD, z_bounds=zb, Fx=F_XY, Fy=F_XY,
+                  z_planes=zp, out_ld=W, out_plane_stride=H * W) for _ in range(n * n)]
+    bp = scw.BatchedPlan(items, precision=args.precision)
+    for i in range(n * n):
+        Wi, gi, ai, *_ = wl.random_layer_set_torch(20_000 + i, U_ORD, U_ORD, L_LAYERS, device=dev)
+        bp.set_layers(i, Wi, gi, ai)
+        torch.cuda.synchronize(dev)
+        del Wi
+    views = [mosaic[:, :, (i // n) * F_XY:(i // n + 1) * F_XY, (i % n) * F_XY:(i % n + 1) * F_XY]
+             for i in range(n * n)]
+    ms = timed(lambda: bp.synthesize(views), steps)
+    bp.check()
+    bp.close()
+    roof = (n * n * w_bytes + out_bytes) / (hbm * 1e9) * 1e3
+    res["mosaic_4x4_patches"] = {"value": replica_throughput(H * W * Fz, ms * 1e-3, dev)[0], "ms_per_step": ms,
+                                 "hbm_roofline_ms": roof, "roofline_frac": roof / ms}
+    del mosaic
+    return res
+
+
 def run_surrogate(args, dev, bf16_peaks):
     """Learned surrogate at its full size: 4 Fourier layers of width 32, 16x16
     kept modes on a 64x64 grid, inputs 8 slices of 32x32 complex n (seeded
@@ -638,6 +705,11 @@ def run_ours(args, world, rank, local):
         points = run_points(args, dev, world, Wd, gd, ad, zb, zp, hbm, bf16_tf)
         torch.cuda.empty_cache()
 
+    tiling = None
+    if not args.no_tiling:
+        tiling = run_tiling(args, dev, world, Wd, gd, ad, zb, zp, hbm)
+        torch.cuda.empty_cache()
+
     sweep = None
     if not args.no_sweep:
         plan.close()
@@ -688,6 +760,7 @@ def run_ours(args, world, rank, local):
             "sweep": sweep,
             "illumination": illum,
             "points": points,
+            "tiling": tiling,
             "surrogate": surrogate,
         }
         print(json.dumps(line), flush=True)
@@ -714,6 +787,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true", help="skip the learned-surrogate block")
     ap.add_argument("--fno-batch", type=int, default=256)
     ap.add_argument("--no-points", action="store_true", help="skip the off-grid point-set block")
+    ap.add_argument("--no-tiling", action="store_true", help="skip the periodic-tiling / patch-mosaic block")
     ap.add_argument("--illuminations", type=int, default=16,
                     help="incident fields of the multi-illumination block (1 skips it)")
     ap.add_argument("--only-surrogate", action="store_true",

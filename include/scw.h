@@ -101,6 +101,18 @@ typedef struct {
   double pupil_na;          /* > 0: below the sample only the orders with |s_bar| <= pupil_na
                                pass (the numerical aperture of a collecting objective, in the
                                units of s_bar = lambda (u/X, v/Y)); 0: no pupil             */
+  int tiles_x, tiles_y;     /* periodic tiling (0 counts as 1, at most 64 each): the field covers
+                               tiles_x x tiles_y lateral periods, (tiles_y Fy) x (tiles_x Fx)
+                               pixels; the unit cell is computed once and stored to every
+                               tile, since E(x + a X, y + b Y) = E(x, y) (Eq. 10)          */
+  long long out_ld;         /* row pitch of the field in complex elements, even; 0 means
+                               tiles_x Fx. With out_plane_stride it lets the field of a plan (or
+                               of each batched item) be written as a patch of a larger
+                               mosaic: pixel (x, y) of plane slice s goes to
+                               out[s out_plane_stride + y out_ld + x]                     */
+  long long out_plane_stride; /* complex elements between consecutive plane slices
+                               s = (i 3 + c) Fz + f, even; 0 means tiles_y Fy out_ld. The
+                               field pointer must be 16-byte aligned (16-byte stores)       */
 } scw_desc;
 
 typedef struct {

@@ -20,7 +20,7 @@ __all__ = ["Plan", "BatchedPlan", "Surrogate", "ScwError", "load", "PRECISION"]
 
 def _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0, n_bot=1.0,
                z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0, autotune=False,
-               illuminations=1, pupil_na=0.0):
+               illuminations=1, pupil_na=0.0, tiles=(1, 1), out_ld=0, out_plane_stride=0):
     """scw_desc for one item plus the host arrays it points to (keep them alive)."""
     zb = np.ascontiguousarray(z_bounds, dtype=np.float64)
     zp = np.ascontiguousarray(z_planes, dtype=np.float64)
@@ -35,8 +35,39 @@ def _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n
                 x0=float(x0), y0=float(y0), n_top=float(n_top), n_bot_re=nb.real, n_bot_im=nb.imag,
                 z_inc=float(zb[0] if z_inc is None else z_inc),
                 precision=PRECISION[precision], flags=flags, k_split=int(k_split),
-                illuminations=int(illuminations), pupil_na=float(pupil_na))
+                illuminations=int(illuminations), pupil_na=float(pupil_na),
+                tiles_x=int(tiles[0]), tiles_y=int(tiles[1]), out_ld=int(out_ld),
+                out_plane_stride=int(out_plane_stride))
     return d, (zb, zp)
+
+
+def _field_layout(I, Fz, Fy, Fx, tiles=(1, 1), out_ld=0, out_plane_stride=0):
+    """Shape and element strides of a field [I][3][Fz][ty Fy][tx Fx] (I == 1: no leading axis)."""
+    H, W = int(tiles[1]) * int(Fy), int(tiles[0]) * int(Fx)
+    ld = int(out_ld) or W
+    ps = int(out_plane_stride) or H * ld
+    shape, strides = (3, Fz, H, W), (Fz * ps, ps, ld, 1)
+    if I > 1:
+        shape, strides = (I,) + shape, (3 * Fz * ps,) + strides
+    return shape, strides
+
+
+def _field_ptr(t, shape, strides, name):
+    """Pointer of a complex64 CUDA field tensor, possibly a strided view (a patch of a mosaic)."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.complex64:
+        raise TypeError(f"{name} must be a complex64 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if any(n > 1 and a != b for n, a, b in zip(shape, t.stride(), strides)):
+        raise ValueError(f"{name} must have element strides {tuple(strides)}, got {tuple(t.stride())}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _empty_field(shape, strides):
+    import torch
+    n = 1 + sum((s - 1) * st for s, st in zip(shape, strides))
+    return torch.empty(n, dtype=torch.complex64, device="cuda").as_strided(shape, strides)
 
 
 def _per_illum(I, shape):
@@ -75,7 +106,7 @@ class Plan:
 
     def __init__(self, U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0,
                  n_bot=1.0, z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0,
-                 autotune=False, illuminations=1, pupil_na=0.0):
+                 autotune=False, illuminations=1, pupil_na=0.0, tiles=(1, 1), out_ld=0, out_plane_stride=0):
         """``illuminations`` incident fields share this solve: alpha becomes [I][L][4M], p_* [I][3][M]
         and the field [I][3][Fz][Fy][Fx]. ``pupil_na`` > 0 keeps only the orders inside that NA below
         the sample."""
@@ -89,8 +120,9 @@ class Plan:
         self.exterior = bool(exterior)
         d, (self._zb, self._zp) = _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0, y0, n_top, n_bot,
                                              z_inc, precision, exterior, host_io, k_split, autotune,
-                                             illuminations, pupil_na)
+                                             illuminations, pupil_na, tiles, out_ld, out_plane_stride)
         self.Fz = len(self._zp)
+        self._layout = _field_layout(self.I, self.Fz, self.Fy, self.Fx, tiles, out_ld, out_plane_stride)
         h = ctypes.c_void_p()
         check(self._lib.scw_plan_create(ctypes.byref(d), ctypes.byref(h)), "scw_plan_create")
         self._h = h
@@ -112,14 +144,18 @@ class Plan:
 
     # ------------------------------------------------------------------ compute
     def out_shape(self):
-        return _per_illum(self.I, (3, self.Fz, self.Fy, self.Fx))
+        """[3][Fz][tiles_y Fy][tiles_x Fx] ([I][3]... with I illuminations)."""
+        return self._layout[0]
+
+    def out_strides(self):
+        """Element strides the field must have (a custom out_ld / out_plane_stride makes it a strided view)."""
+        return self._layout[1]
 
     def synthesize(self, out=None, stream=None):
-        import torch
         if out is None:
-            out = torch.empty(self.out_shape(), dtype=torch.complex64, device="cuda")
-        check(self._lib.scw_synthesize(self._h, _dev_ptr(out, torch.complex64, self.out_shape(), "out"),
-                                       _stream_handle(stream)), "scw_synthesize")
+            out = _empty_field(*self._layout)
+        check(self._lib.scw_synthesize(self._h, _field_ptr(out, *self._layout, "out"), _stream_handle(stream)),
+              "scw_synthesize")
         return out
 
     def spectrum(self, S=None, stream=None):
@@ -134,10 +170,10 @@ class Plan:
     def recompose(self, S, out=None, stream=None):
         import torch
         if out is None:
-            out = torch.empty(self.out_shape(), dtype=torch.complex64, device="cuda")
+            out = _empty_field(*self._layout)
         check(self._lib.scw_recompose(self._h, _dev_ptr(S, torch.complex64, (self.I * self.Fz, 3, self.M), "S"),
-                                      _dev_ptr(out, torch.complex64, self.out_shape(), "out"),
-                                      _stream_handle(stream)), "scw_recompose")
+                                      _field_ptr(out, *self._layout, "out"), _stream_handle(stream)),
+              "scw_recompose")
         return out
 
     # ------------------------------------------------------------- point sets
@@ -239,6 +275,7 @@ class BatchedPlan:
         descs = (ScwDesc * n)()
         self._keep_desc = []
         self.shapes = []
+        self.layouts = []
         self.sizes = []
         for i, kw in enumerate(items):
             kw = dict(kw)
@@ -248,7 +285,10 @@ class BatchedPlan:
             M = int(kw["U"]) * int(kw["V"])
             I = max(1, int(kw.get("illuminations", 1)))
             self.sizes.append((int(kw["L"]), M, I))
-            self.shapes.append(_per_illum(I, (3, len(keep[1]), int(kw["Fy"]), int(kw["Fx"]))))
+            lay = _field_layout(I, len(keep[1]), kw["Fy"], kw["Fx"], kw.get("tiles", (1, 1)), kw.get("out_ld", 0),
+                                kw.get("out_plane_stride", 0))
+            self.shapes.append(lay[0])
+            self.layouts.append(lay)
         h = ctypes.c_void_p()
         check(self._lib.scw_plan_batched_create(descs, n, ctypes.byref(h)), "scw_plan_batched_create")
         self._h = h
@@ -272,9 +312,11 @@ class BatchedPlan:
     def synthesize(self, outs=None, stream=None):
         import torch
         if outs is None:
-            outs = [torch.empty(s, dtype=torch.complex64, device="cuda") for s in self.shapes]
-        ptrs = (ctypes.c_void_p * len(outs))(*[_dev_ptr(o, torch.complex64, s, "out").value
-                                              for o, s in zip(outs, self.shapes)])
+            outs = [_empty_field(*lay) for lay in self.layouts]
+        if len(outs) != len(self.layouts):
+            raise ValueError("one output per item")
+        ptrs = (ctypes.c_void_p * len(outs))(*[_field_ptr(o, *lay, "out").value
+                                              for o, lay in zip(outs, self.layouts)])
         check(self._lib.scw_synthesize_batched(self._h, ptrs, _stream_handle(stream)), "scw_synthesize_batched")
         return outs
 

@@ -27,7 +27,9 @@ class ScwDesc(ctypes.Structure):
                 ("n_top", c_double), ("n_bot_re", c_double), ("n_bot_im", c_double),
                 ("z_inc", c_double),
                 ("precision", c_int), ("flags", c_uint), ("k_split", c_int),
-                ("illuminations", c_int), ("pupil_na", c_double)]
+                ("illuminations", c_int), ("pupil_na", c_double),
+                ("tiles_x", c_int), ("tiles_y", c_int),
+                ("out_ld", ctypes.c_longlong), ("out_plane_stride", ctypes.c_longlong)]
 
 
 class ScwPlanInfo(ctypes.Structure):

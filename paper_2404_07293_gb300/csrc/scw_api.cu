@@ -124,6 +124,18 @@ static scw_status validate_desc(const scw_desc* d) {
     return set_error(SCW_ERR_INVALID_ARGUMENT, "illuminations * Fz must be <= 65535");
   if (!(d->pupil_na >= 0.0) || !std::isfinite(d->pupil_na))
     return set_error(SCW_ERR_INVALID_ARGUMENT, "pupil_na must be finite and >= 0");
+  if (d->tiles_x < 0 || d->tiles_y < 0 || d->tiles_x > 64 || d->tiles_y > 64)
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "tiles_x and tiles_y must be in [0, 64]");
+  {
+    const long long W = (long long)std::max(1, d->tiles_x) * d->Fx, H = (long long)std::max(1, d->tiles_y) * d->Fy;
+    const long long ld = d->out_ld ? d->out_ld : W;
+    if (d->out_ld < 0 || d->out_plane_stride < 0 || ld < W || (ld & 1))
+      return set_error(SCW_ERR_INVALID_ARGUMENT, "out_ld must be even and >= tiles_x Fx");
+    if (d->out_plane_stride && (d->out_plane_stride < (H - 1) * ld + W || (d->out_plane_stride & 1)))
+      return set_error(SCW_ERR_INVALID_ARGUMENT, "out_plane_stride must be even and hold one plane");
+    if ((d->flags & SCW_FLAG_HOST_IO) && (d->out_ld || d->out_plane_stride))
+      return set_error(SCW_ERR_UNSUPPORTED, "host IO writes the packed field (no custom pitches)");
+  }
   if (!d->z_bounds || !d->z_planes) return set_error(SCW_ERR_INVALID_ARGUMENT, "z_bounds and z_planes are required");
   if (d->precision < SCW_PREC_FP32 || d->precision > SCW_PREC_FP16)
     return set_error(SCW_ERR_INVALID_ARGUMENT, "unknown precision");
@@ -266,7 +278,7 @@ static scw_status build_item(Plan* p, const std::vector<int>& ext) {
     SCW_TRY(dalloc(&p->hio_gamma, L * 4 * M, tot));
     SCW_TRY(dalloc(&p->hio_alpha, p->I * L * 4 * M, tot));
     SCW_TRY(dalloc(&p->hio_p, p->I * 9 * M, tot));
-    SCW_TRY(dalloc(&p->hio_out, (size_t)3 * p->Fz * p->Fy * p->Fx, tot));
+    SCW_TRY(dalloc(&p->hio_out, (size_t)3 * p->Fz * p->out_pstride, tot));
   }
   SCW_TRY(cudaEventCreate(&p->ev0));
   SCW_TRY(cudaEventCreate(&p->ev1));
@@ -309,6 +321,7 @@ static scw_status finish_item(Plan* p) {
   it.inv_lam = 1.0 / p->lambda;
   it.M = p->M; it.U = p->U; it.V = p->V; it.Fx = p->Fx; it.Fy = p->Fy; it.Fz = p->Fz;
   it.I = p->I; it.Fz_out = p->Fz_out; it.alpha_istride = (size_t)p->L * 4 * p->M;
+  it.tx = p->tiles_x; it.ty = p->tiles_y; it.ld = p->out_ld; it.pstride = p->out_pstride;
   it.F_pad = p->F_pad;
   it.k_split = p->k_split;
   it.n_tiles = (3 * p->M + 127) / 128;
@@ -327,6 +340,10 @@ static scw_status create_item(const scw_desc* d, int force_F_pad, Plan** out) {
   p->Fz_out = d->Fz;
   p->Fx = d->Fx; p->Fy = d->Fy; p->Fz = p->I * d->Fz;
   p->pupil_na = d->pupil_na;
+  p->tiles_x = std::max(1, d->tiles_x);
+  p->tiles_y = std::max(1, d->tiles_y);
+  p->out_ld = d->out_ld ? d->out_ld : (long long)p->tiles_x * d->Fx;
+  p->out_pstride = d->out_plane_stride ? d->out_plane_stride : (long long)p->tiles_y * d->Fy * p->out_ld;
   p->lambda = d->lambda; p->X = d->X; p->Y = d->Y; p->x0 = d->x0; p->y0 = d->y0;
   p->n_top = d->n_top; p->n_bot_re = d->n_bot_re; p->n_bot_im = d->n_bot_im; p->z_inc = d->z_inc;
   p->precision = d->precision; p->flags = d->flags;
@@ -492,6 +509,7 @@ struct scw_plan_s {
   int2* d_plane_entries = nullptr;  // y-pass-pair class first (ypass_pairs), then the rest
   int n_plane_entries = 0;
   int n_pair_entries = 0;
+  bool tiled = false;  // some item stores periodic tiles
   int inject_stall = 0;            // scw_plan_inject_stall (tests of the timeout path)
   TcSchedule sched;
   float2** d_outs = nullptr;
@@ -656,7 +674,7 @@ static scw_status enqueue_pipelined(scw_plan_t P, float2* out_one, cudaStream_t 
     e = launch_xpass(one, nullptr, ent, nb, P->xpass_smem, P->st2);
     if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
     int ny = 0;
-    e = launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, out_one, nullptr,
+    e = launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, P->tiled, out_one, nullptr,
                      P->st2, &ny);
     if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
     n += 1 + ny;
@@ -680,7 +698,7 @@ static scw_status enqueue_synthesis(scw_plan_t P, float2* out_one, cudaStream_t 
   if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
   mark(P, 3, st, marks);
   int ny = 0;
-  e = launch_ypass(one, items, P->d_plane_entries, P->n_plane_entries, P->n_pair_entries, P->max_Qx, P->max_Vp,
+  e = launch_ypass(one, items, P->d_plane_entries, P->n_plane_entries, P->n_pair_entries, P->max_Qx, P->max_Vp, P->tiled,
                    out_one, P->d_outs, st, &ny);
   if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
   mark(P, 4, st, marks);
@@ -851,6 +869,7 @@ static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, boo
     P->xpass_smem = std::max(P->xpass_smem, xpass_smem_bytes(p->V, p->item.Up, p->Fx));
     P->max_Vp = std::max(P->max_Vp, p->item.Vp);
     P->rec_smem = std::max(P->rec_smem, recompose_smem_bytes(p->V, p->item.Up, p->item.Vp));
+    P->tiled = P->tiled || p->tiles_x > 1 || p->tiles_y > 1;
   }
   // plane entries of items with long y folds first: they run the two-residue y-pass
   std::stable_partition(pe.begin(), pe.end(),
@@ -1173,7 +1192,7 @@ scw_status scw_synthesize_host(scw_plan_t P, const void* W, const void* gamma, c
   }
   scw_status s = run_synthesis(P, p->hio_out, st);
   if (s != SCW_OK) return s;
-  SCW_CP(out, p->hio_out, (size_t)3 * p->Fz * p->Fy * p->Fx * sizeof(float2), cudaMemcpyDeviceToHost);
+  SCW_CP(out, p->hio_out, (size_t)3 * p->Fz * p->out_pstride * sizeof(float2), cudaMemcpyDeviceToHost);
 #undef SCW_CP
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");

@@ -63,6 +63,8 @@ struct ItemDev {
   int I, Fz_out;           // illuminations; output planes per illumination (Fz = I Fz_out,
                            // plane index f = (output plane) I + illumination)
   size_t alpha_istride;    // L 4M: alpha elements per illumination
+  int tx, ty;              // periodic tiles of the field along x and y
+  long long ld, pstride;   // field row pitch and plane-slice stride (complex elements)
 };
 
 struct PointTables;  // scw_points.cuh
@@ -71,6 +73,8 @@ struct Plan {
   // description
   int U = 0, V = 0, M = 0, L = 0, Fx = 0, Fy = 0, Fz = 0;  // Fz = I Fz_out plane slots
   int I = 1, Fz_out = 0;                                  // illuminations, output planes each
+  int tiles_x = 1, tiles_y = 1;                           // periodic tiling of the field
+  long long out_ld = 0, out_pstride = 0;                  // field pitches (complex elements)
   double pupil_na = 0;
   double lambda = 0, X = 0, Y = 0, x0 = 0, y0 = 0, n_top = 1, z_inc = 0;
   double n_bot_re = 1, n_bot_im = 0;
@@ -201,8 +205,9 @@ cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d
 // entries [0, n_pair) run the two-residue y-pass (long folds, ypass_pairs(Vp)), the rest the
 // one-residue y-pass; *launches receives the number of kernels launched (0, 1 or 2)
 bool ypass_pairs(int Vp);
+// tiled: some item has periodic tiles (selects the y-pass that stores every tile)
 cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int n_pair,
-                         int max_Qx, int max_Vp, float2* out_one, float2* const* d_outs, cudaStream_t st,
+                         int max_Qx, int max_Vp, bool tiled, float2* out_one, float2* const* d_outs, cudaStream_t st,
                          int* launches);
 cudaError_t launch_recompose(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_Qx,
                              size_t smem, const float2* S_override, const int* nsplit_override, float2* out_one,

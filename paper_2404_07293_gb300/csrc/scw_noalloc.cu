@@ -110,6 +110,9 @@ extern "C" scw_status scw_recompose_noalloc(int U, int V, double X, double Y, in
   it.Vp = Vp;
   it.I = 1;
   it.Fz_out = Fz;
+  it.tx = it.ty = 1;
+  it.ld = Fx;
+  it.pstride = (long long)Fy * Fx;
   it.split_stride = (size_t)Fz * 3 * U * V;
   float2* twx = reinterpret_cast<float2*>(base);
   float2* twy = reinterpret_cast<float2*>(base + b_twx);

@@ -61,6 +61,32 @@ __device__ __forceinline__ void idft8(float2 (&x)[8]) {
   }
 }
 
+// Field stores. Row y of plane slice s (its base `dst`, column x included) goes to
+// dst + y ld, streaming; TILED: also to every other periodic tile (E repeats with
+// the period X, Y). Untiled plans use the plain form, so their y-pass keeps a
+// straight sequence of stores.
+template <bool TILED>
+__device__ __forceinline__ void store_row4(const ItemDev& it, float2* dst, int y, float4 v) {
+  float2* r = dst + (long long)y * it.ld;
+  if constexpr (!TILED) {
+    __stcs(reinterpret_cast<float4*>(r), v);
+  } else {
+    for (int b = 0; b < it.ty; ++b)
+      for (int a = 0; a < it.tx; ++a)
+        __stcs(reinterpret_cast<float4*>(r + (long long)b * it.Fy * it.ld + (long long)a * it.Fx), v);
+  }
+}
+template <bool TILED>
+__device__ __forceinline__ void store_row2(const ItemDev& it, float2* dst, int y, float2 v) {
+  float2* r = dst + (long long)y * it.ld;
+  if constexpr (!TILED) {
+    __stcs(r, v);
+  } else {
+    for (int b = 0; b < it.ty; ++b)
+      for (int a = 0; a < it.tx; ++a) __stcs(r + (long long)b * it.Fy * it.ld + (long long)a * it.Fx, v);
+  }
+}
+
 // One CTA per (block of 8 column residues, item-plane, component). The CTA owns
 // the 64 output columns x = b + Qx a (b in its 8 residues, a < 8), which are
 // exactly the outputs of its residues' x-direction folds, so the x-pass rows
@@ -138,9 +164,9 @@ __global__ void __launch_bounds__(256, 4) recompose_kernel(const __grid_constant
   const int Fx = it.Fx, Fy = it.Fy;
   const int Qy = Fy >> 3;
   float2* out = BATCH ? outs[e.x] : out_one;
-  // plane slot f = (output plane) I + illumination; the field is [I][3][Fz_out][Fy][Fx]
+  // plane slot f = (output plane) I + illumination: slice (il 3 + c) Fz_out + fo of the field
   const int fo = f / it.I, il = f - fo * it.I;
-  float2* dst = out + ((size_t)il * 3 * it.Fz_out + (size_t)c * it.Fz_out + fo) * Fy * Fx + x;
+  float2* dst = out + ((long long)il * 3 * it.Fz_out + (long long)c * it.Fz_out + fo) * it.pstride + x;
   if (bl >= nb) return;  // no __syncthreads below
   for (int b = w; b < Qy; b += 8) {
     float2 G0[8], G1[8];
@@ -160,12 +186,11 @@ __global__ void __launch_bounds__(256, 4) recompose_kernel(const __grid_constant
     idft8(G1);
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-      float2* o = dst + (size_t)(b + a * Qy) * Fx;
       if (v16) {
-        __stcs(reinterpret_cast<float4*>(o), make_float4(G0[a].x, G0[a].y, G1[a].x, G1[a].y));
+        store_row4<true>(it, dst, b + a * Qy, make_float4(G0[a].x, G0[a].y, G1[a].x, G1[a].y));
       } else {
-        __stcs(o, G0[a]);
-        if (pair) __stcs(o + 1, G1[a]);
+        store_row2<true>(it, dst, b + a * Qy, G0[a]);
+        if (pair) store_row2<true>(it, dst + 1, b + a * Qy, G1[a]);
       }
     }
   }
@@ -255,7 +280,7 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
 // (b, b + 8), b = w, w + 16, ..., so each shared-memory load feeds four complex FMAs
 // (long folds); otherwise one residue b = w, w + 8, ... at a time and twice the
 // resident warps (short folds, where latency dominates).
-template <bool BATCH, bool PAIR>
+template <bool BATCH, bool PAIR, bool TILED>
 __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_constant__ ItemDev one,
                                                        const ItemDev* __restrict__ items,
                                                        const int2* __restrict__ entries, float2* out_one,
@@ -291,9 +316,9 @@ __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_c
   if (x >= Fx) return;  // Fx is a multiple of 8, so x + 1 < Fx as well
   const int Q = Fy >> 3;
   float2* out = BATCH ? outs[e.x] : out_one;
-  // plane slot f = (output plane) I + illumination; the field is [I][3][Fz_out][Fy][Fx]
+  // plane slot f = (output plane) I + illumination: slice (il 3 + c) Fz_out + fo of the field
   const int fo = f / it.I, il = f - fo * it.I;
-  float2* dst = out + ((size_t)il * 3 * it.Fz_out + (size_t)c * it.Fz_out + fo) * Fy * Fx + x;
+  float2* dst = out + ((long long)il * 3 * it.Fz_out + (long long)c * it.Fz_out + fo) * it.pstride + x;
   const float4* col = ys_col4 + lane;
   if constexpr (!PAIR) {
     for (int b = w; b < Q; b += 8) {
@@ -314,8 +339,7 @@ __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_c
       idft8(G1);
 #pragma unroll
       for (int a = 0; a < 8; ++a)
-        __stcs(reinterpret_cast<float4*>(dst + (size_t)(b + a * Q) * Fx),
-               make_float4(G0[a].x, G0[a].y, G1[a].x, G1[a].y));
+        store_row4<TILED>(it, dst, b + a * Q, make_float4(G0[a].x, G0[a].y, G1[a].x, G1[a].y));
     }
     return;
   }
@@ -342,14 +366,13 @@ __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_c
     idft8(A1);
 #pragma unroll
     for (int a = 0; a < 8; ++a)
-      __stcs(reinterpret_cast<float4*>(dst + (size_t)(b + a * Q) * Fx), make_float4(A0[a].x, A0[a].y, A1[a].x, A1[a].y));
+      store_row4<TILED>(it, dst, b + a * Q, make_float4(A0[a].x, A0[a].y, A1[a].x, A1[a].y));
     if (two) {
       idft8(B0);
       idft8(B1);
 #pragma unroll
       for (int a = 0; a < 8; ++a)
-        __stcs(reinterpret_cast<float4*>(dst + (size_t)(b + 8 + a * Q) * Fx),
-               make_float4(B0[a].x, B0[a].y, B1[a].x, B1[a].y));
+        store_row4<TILED>(it, dst, b + 8 + a * Q, make_float4(B0[a].x, B0[a].y, B1[a].x, B1[a].y));
     }
   }
 }
@@ -386,37 +409,46 @@ cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d
   return cudaGetLastError();
 }
 
-template <bool PAIR>
+template <bool PAIR, bool TILED>
 static cudaError_t launch_ypass_t(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
                                   int max_Qx, size_t ys, float2* out_one, float2* const* d_outs, cudaStream_t st) {
   const dim3 grid((max_Qx * 8 + 63) / 64, n_entries, 3);
   cudaError_t e;
   if (items) {
-    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<true, PAIR>));
+    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<true, PAIR, TILED>));
     if (e != cudaSuccess) return e;
-    ypass_kernel<true, PAIR><<<grid, 256, ys, st>>>(one, items, d_entries, nullptr, d_outs);
+    ypass_kernel<true, PAIR, TILED><<<grid, 256, ys, st>>>(one, items, d_entries, nullptr, d_outs);
   } else {
-    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<false, PAIR>));
+    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<false, PAIR, TILED>));
     if (e != cudaSuccess) return e;
-    ypass_kernel<false, PAIR><<<grid, 256, ys, st>>>(one, nullptr, d_entries, out_one, nullptr);
+    ypass_kernel<false, PAIR, TILED><<<grid, 256, ys, st>>>(one, nullptr, d_entries, out_one, nullptr);
   }
   return cudaGetLastError();
+}
+
+template <bool PAIR>
+static cudaError_t launch_ypass_p(bool tiled, const ItemDev& one, const ItemDev* items, const int2* d_entries,
+                                  int n_entries, int max_Qx, size_t ys, float2* out_one, float2* const* d_outs,
+                                  cudaStream_t st) {
+  return tiled ? launch_ypass_t<PAIR, true>(one, items, d_entries, n_entries, max_Qx, ys, out_one, d_outs, st)
+               : launch_ypass_t<PAIR, false>(one, items, d_entries, n_entries, max_Qx, ys, out_one, d_outs, st);
 }
 
 bool ypass_pairs(int Vp) { return Vp >= 24; }
 
 cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int n_pair,
-                         int max_Qx, int max_Vp, float2* out_one, float2* const* d_outs, cudaStream_t st,
+                         int max_Qx, int max_Vp, bool tiled, float2* out_one, float2* const* d_outs, cudaStream_t st,
                          int* launches) {
   const size_t ys = (size_t)max_Vp * 64 * sizeof(float2);
   int n = 0;
   cudaError_t e = cudaSuccess;
   if (n_pair > 0) {
-    e = launch_ypass_t<true>(one, items, d_entries, n_pair, max_Qx, ys, out_one, d_outs, st);
+    e = launch_ypass_p<true>(tiled, one, items, d_entries, n_pair, max_Qx, ys, out_one, d_outs, st);
     ++n;
   }
   if (e == cudaSuccess && n_entries > n_pair) {
-    e = launch_ypass_t<false>(one, items, d_entries + n_pair, n_entries - n_pair, max_Qx, ys, out_one, d_outs, st);
+    e = launch_ypass_p<false>(tiled, one, items, d_entries + n_pair, n_entries - n_pair, max_Qx, ys, out_one, d_outs,
+                              st);
     ++n;
   }
   if (launches) *launches = n;

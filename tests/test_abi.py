@@ -64,7 +64,8 @@ def _desc(**kw):
     dict(U=0), dict(L=0), dict(lam=0.0), dict(X=-1.0), dict(Fx=12), dict(Fy=4), dict(Fx=8192), dict(Fz=0),
     dict(precision=7), dict(k_split=-1), dict(n_top=0.0), dict(illuminations=-1), dict(illuminations=257),
     dict(illuminations=200, Fz=400, zp=np.linspace(0.0, 0.5, 400)), dict(pupil_na=-0.1),
-    dict(pupil_na=float("inf")),
+    dict(pupil_na=float("inf")), dict(tiles_x=65), dict(tiles_y=-1), dict(out_ld=17), dict(out_ld=14),
+    dict(out_ld=32, out_plane_stride=32 * 15), dict(out_plane_stride=257),
     dict(zb=np.array([0.0, 0.5, 0.5])), dict(zp=np.array([0.3, 0.1])), dict(zp=np.array([0.1, np.nan])),
 ])
 def test_bad_descriptors_are_rejected(lib, bad):
@@ -74,6 +75,13 @@ def test_bad_descriptors_are_rejected(lib, bad):
     assert st == 1, (st, lib.scw_last_error())
     assert not h.value
     assert lib.scw_last_error()
+
+
+def test_host_io_with_custom_pitch_is_unsupported(lib):
+    d, keep = _desc(out_ld=32, flags=2)
+    h = ctypes.c_void_p()
+    assert lib.scw_plan_create(ctypes.byref(d), ctypes.byref(h)) == 2
+    assert not h.value
 
 
 def test_null_arguments(lib):
