@@ -19,7 +19,10 @@
 // Plans run the two directions as two kernels (x-pass rows T through L2, then
 // the y-pass with contiguous 512-byte warp stores); the allocation-free entry
 // point, which has no room for T, runs them fused in one kernel.
+#include <algorithm>
+
 #include "scw_internal.cuh"
+#include "scw_ptx.cuh"
 
 namespace scw {
 
@@ -274,46 +277,15 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
   }
 }
 
-// One CTA per (64-column block, item-plane, component); 8 warps. The x-pass rows of
-// the block sit at their fold positions in shared memory ([Vp][64], padding rows zero).
-// Lane l owns the column pair (2l, 2l+1). PAIR: warp w takes the residue pairs
-// (b, b + 8), b = w, w + 16, ..., so each shared-memory load feeds four complex FMAs
-// (long folds); otherwise one residue b = w, w + 8, ... at a time and twice the
-// resident warps (short folds, where latency dominates).
+// Fold + radix-8 inverse DFT along y of one tile from its rows in shared memory, and the field stores.
 template <bool BATCH, bool PAIR, bool TILED>
-__global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_constant__ ItemDev one,
-                                                       const ItemDev* __restrict__ items,
-                                                       const int2* __restrict__ entries, float2* out_one,
-                                                       float2* const* __restrict__ outs) {
-  extern __shared__ float4 ys_col4[];  // [Vp][32] float4 = [Vp][64] complex
-  float2* tcol = reinterpret_cast<float2*>(ys_col4);
-  const int2 e = entries[blockIdx.y];
-  const ItemDev& it = BATCH ? items[e.x] : one;
-  const int xb = blockIdx.x * 64;
-  if (xb >= it.Fx) return;
-  const int f = e.y, c = blockIdx.z;
-  const int V = it.V, Vp = it.Vp, Fx = it.Fx, Fy = it.Fy;
-  const float2* src = it.T + ((size_t)f * 3 + c) * V * Fx;
-  {
-    // rows of the x-pass result for this column block, 8 requests in flight per thread
-    const int x = threadIdx.x & 63, r0 = threadIdx.x >> 6;
-    for (int p0 = r0; p0 < Vp; p0 += 32) {
-      float2 tv[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int pos = p0 + 4 * k;
-        const int v = pos < Vp ? fold_order(pos, V, Vp) : -1;
-        tv[k] = (v >= 0 && xb + x < Fx) ? src[(size_t)v * Fx + xb + x] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (p0 + 4 * k < Vp) tcol[(p0 + 4 * k) * 64 + x] = tv[k];
-    }
-  }
-  __syncthreads();
+__device__ __forceinline__ void ypass_tile(const ItemDev& it, const float4* ys_col4, int2 e, int c, int xb,
+                                           float2* out_one, float2* const* outs) {
+  const int f = e.y;
+  const int Vp = it.Vp, Fx = it.Fx, Fy = it.Fy;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int x = xb + 2 * lane;
-  if (x >= Fx) return;  // Fx is a multiple of 8, so x + 1 < Fx as well
+  if (x >= Fx) return;  // Fx is a multiple of 8, so x + 1 < Fx as well (no barrier in here)
   const int Q = Fy >> 3;
   float2* out = BATCH ? outs[e.x] : out_one;
   // plane slot f = (output plane) I + illumination: slice (il 3 + c) Fz_out + fo of the field
@@ -377,6 +349,61 @@ __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_c
   }
 }
 
+
+// Persistent: CTA k takes the tiles k, k + grid, ...; a tile is (64-column block,
+// item-plane, component), t = (entry 3 + c) nxb + column block. The x-pass rows of
+// a tile sit at their fold positions in shared memory ([Vp][64], padding rows zero);
+// two buffers: the rows of the CTA's next tile are copied in (cp.async) while the
+// current tile is folded and stored, so no CTA waits on its loads between tiles.
+// Lane l owns the column pair (2l, 2l+1). PAIR: warp w takes the residue pairs
+// (b, b + 8), b = w, w + 16, ..., so each shared-memory load feeds four complex FMAs
+// (long folds); otherwise one residue b = w, w + 8, ... at a time and twice the
+// resident warps (short folds, where latency dominates).
+template <bool BATCH>
+__device__ __forceinline__ void ypass_prefetch(const ItemDev& one, const ItemDev* items, const int2* entries,
+                                               int t, int n_tiles, int nxb, float4* buf) {
+  if (t < n_tiles) {
+    const int r = t / nxb, xb = (t - r * nxb) * 64;
+    const int2 e = entries[r / 3];
+    const int c = r - (r / 3) * 3;
+    const ItemDev& it = BATCH ? items[e.x] : one;
+    if (xb < it.Fx) {
+      const float2* src = it.T + ((size_t)e.y * 3 + c) * it.V * it.Fx;
+      for (int i = threadIdx.x; i < it.Vp * 32; i += blockDim.x) {  // row p = i / 32, column pair i % 32
+        const int p = i >> 5, x = xb + 2 * (i & 31);
+        const int v = fold_order(p, it.V, it.Vp);
+        const bool ok = v >= 0 && x < it.Fx;  // Fx is even: a pair is in or out as a whole
+        ptx::cp_async16(ptx::smem_u32(buf + i), ok ? src + (size_t)v * it.Fx + x : src, ok ? 16u : 0u);
+      }
+    }
+  }
+  ptx::cp_async_commit();
+}
+
+template <bool BATCH, bool PAIR, bool TILED>
+__global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_constant__ ItemDev one,
+                                                       const ItemDev* __restrict__ items,
+                                                       const int2* __restrict__ entries, int n_tiles, int nxb,
+                                                       int buf_f4, float2* out_one, float2* const* __restrict__ outs) {
+  extern __shared__ float4 ys_buf[];  // 2 x [Vp][32] float4 = 2 x [Vp][64] complex
+  int t = blockIdx.x;
+  if (t >= n_tiles) return;
+  ypass_prefetch<BATCH>(one, items, entries, t, n_tiles, nxb, ys_buf);
+  for (int b = 0; t < n_tiles; t += gridDim.x, b ^= 1) {
+    ypass_prefetch<BATCH>(one, items, entries, t + gridDim.x, n_tiles, nxb, ys_buf + (size_t)(b ^ 1) * buf_f4);
+    ptx::cp_async_wait<1>();  // this thread's copies of tile t have landed
+    __syncthreads();          // and everyone's
+    const int r = t / nxb, xb = (t - r * nxb) * 64;
+    const int2 e = entries[r / 3];
+    const int c = r - (r / 3) * 3;
+    const ItemDev& it = BATCH ? items[e.x] : one;
+    if (xb < it.Fx)
+      ypass_tile<BATCH, PAIR, TILED>(it, ys_buf + (size_t)b * buf_f4, e, c, xb, out_one, outs);
+    __syncthreads();          // buffer b is free for the prefetch of the next iteration
+  }
+  ptx::cp_async_wait<0>();
+}
+
 // S[f][3M] = sum of the contraction's partial spectra (scw_spectrum).
 __global__ void gather_kernel(const float2* __restrict__ S_part, size_t split_stride, const int* __restrict__ nsplit,
                               int rows, int Fz, float2* __restrict__ S) {
@@ -411,27 +438,37 @@ cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d
 
 template <bool PAIR, bool TILED>
 static cudaError_t launch_ypass_t(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
-                                  int max_Qx, size_t ys, float2* out_one, float2* const* d_outs, cudaStream_t st) {
-  const dim3 grid((max_Qx * 8 + 63) / 64, n_entries, 3);
-  cudaError_t e;
-  if (items) {
-    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<true, PAIR, TILED>));
-    if (e != cudaSuccess) return e;
-    ypass_kernel<true, PAIR, TILED><<<grid, 256, ys, st>>>(one, items, d_entries, nullptr, d_outs);
-  } else {
-    e = allow_max_smem(reinterpret_cast<const void*>(ypass_kernel<false, PAIR, TILED>));
-    if (e != cudaSuccess) return e;
-    ypass_kernel<false, PAIR, TILED><<<grid, 256, ys, st>>>(one, nullptr, d_entries, out_one, nullptr);
-  }
+                                  int max_Qx, int max_Vp, float2* out_one, float2* const* d_outs, cudaStream_t st) {
+  const int nxb = (max_Qx * 8 + 63) / 64;
+  const long long tiles = (long long)nxb * n_entries * 3;
+  if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+  const int buf_f4 = max_Vp * 32;
+  const size_t smem = 2 * (size_t)buf_f4 * sizeof(float4);
+  const void* fn = items ? reinterpret_cast<const void*>(ypass_kernel<true, PAIR, TILED>)
+                         : reinterpret_cast<const void*>(ypass_kernel<false, PAIR, TILED>);
+  cudaError_t e = allow_max_smem(fn);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = (int)std::min<long long>(tiles, (long long)std::max(1, per_sm) * sms);
+  if (items)
+    ypass_kernel<true, PAIR, TILED><<<grid, 256, smem, st>>>(one, items, d_entries, (int)tiles, nxb, buf_f4, nullptr,
+                                                            d_outs);
+  else
+    ypass_kernel<false, PAIR, TILED><<<grid, 256, smem, st>>>(one, nullptr, d_entries, (int)tiles, nxb, buf_f4,
+                                                             out_one, nullptr);
   return cudaGetLastError();
 }
 
 template <bool PAIR>
 static cudaError_t launch_ypass_p(bool tiled, const ItemDev& one, const ItemDev* items, const int2* d_entries,
-                                  int n_entries, int max_Qx, size_t ys, float2* out_one, float2* const* d_outs,
+                                  int n_entries, int max_Qx, int max_Vp, float2* out_one, float2* const* d_outs,
                                   cudaStream_t st) {
-  return tiled ? launch_ypass_t<PAIR, true>(one, items, d_entries, n_entries, max_Qx, ys, out_one, d_outs, st)
-               : launch_ypass_t<PAIR, false>(one, items, d_entries, n_entries, max_Qx, ys, out_one, d_outs, st);
+  return tiled ? launch_ypass_t<PAIR, true>(one, items, d_entries, n_entries, max_Qx, max_Vp, out_one, d_outs, st)
+               : launch_ypass_t<PAIR, false>(one, items, d_entries, n_entries, max_Qx, max_Vp, out_one, d_outs, st);
 }
 
 bool ypass_pairs(int Vp) { return Vp >= 24; }
@@ -439,16 +476,15 @@ bool ypass_pairs(int Vp) { return Vp >= 24; }
 cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int n_pair,
                          int max_Qx, int max_Vp, bool tiled, float2* out_one, float2* const* d_outs, cudaStream_t st,
                          int* launches) {
-  const size_t ys = (size_t)max_Vp * 64 * sizeof(float2);
   int n = 0;
   cudaError_t e = cudaSuccess;
   if (n_pair > 0) {
-    e = launch_ypass_p<true>(tiled, one, items, d_entries, n_pair, max_Qx, ys, out_one, d_outs, st);
+    e = launch_ypass_p<true>(tiled, one, items, d_entries, n_pair, max_Qx, max_Vp, out_one, d_outs, st);
     ++n;
   }
   if (e == cudaSuccess && n_entries > n_pair) {
-    e = launch_ypass_p<false>(tiled, one, items, d_entries + n_pair, n_entries - n_pair, max_Qx, ys, out_one, d_outs,
-                              st);
+    e = launch_ypass_p<false>(tiled, one, items, d_entries + n_pair, n_entries - n_pair, max_Qx, max_Vp, out_one,
+                              d_outs, st);
     ++n;
   }
   if (launches) *launches = n;
