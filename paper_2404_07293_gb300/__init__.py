@@ -13,9 +13,9 @@ import ctypes
 import numpy as np
 
 from ._lib import (FLAG_AUTOTUNE, FLAG_EXTERIOR, FLAG_HOST_IO, FNO_PRECISION, PRECISION, ScwDesc, ScwError,
-                   ScwFnoDesc, ScwFnoTimes, ScwKernelTimes, ScwPlanInfo, check, load)
+                   ScwFnoDesc, ScwFnoTimes, ScwKernelTimes, ScwPlanInfo, ScwSolveDesc, ScwSolveTimes, check, load)
 
-__all__ = ["Plan", "BatchedPlan", "Surrogate", "ScwError", "load", "PRECISION"]
+__all__ = ["Plan", "BatchedPlan", "Solver", "Surrogate", "ScwError", "load", "PRECISION"]
 
 
 def _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0, n_bot=1.0,
@@ -343,6 +343,69 @@ class BatchedPlan:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.scw_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """The coupled-wave solve stage on the GPU (scw_solver_*): a layered sample n [L][Ny][Nx]
+    (complex128) and an incident field give W, gamma, alpha, p_ref, p_trn, the inputs of
+    ``Plan.set_layers``."""
+
+    def __init__(self, U, V, L, lam, X, Y, z_bounds, Nx, Ny, n_top=1.0, n_bot=1.0, z_inc=None):
+        self._lib = load()
+        self.U, self.V, self.L, self.M = int(U), int(V), int(L), int(U) * int(V)
+        self.Nx, self.Ny = int(Nx), int(Ny)
+        self._zb = np.ascontiguousarray(z_bounds, dtype=np.float64)
+        if len(self._zb) != self.L + 1:
+            raise ValueError("z_bounds must have L+1 entries")
+        nb = complex(n_bot)
+        d = ScwSolveDesc(U=self.U, V=self.V, L=self.L, lam=float(lam), X=float(X), Y=float(Y),
+                         z_bounds=self._zb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), Nx=self.Nx, Ny=self.Ny,
+                         n_top=float(n_top), n_bot_re=nb.real, n_bot_im=nb.imag,
+                         z_inc=float(self._zb[0] if z_inc is None else z_inc))
+        h = ctypes.c_void_p()
+        check(self._lib.scw_solver_create(ctypes.byref(d), ctypes.byref(h)), "scw_solver_create")
+        self._h = h
+
+    def incident(self, image, pol="x", stream=None):
+        """p_inc [3][M] (complex128, device) from a [Ny][Nx] complex128 image of the x or y component."""
+        import torch
+        p = torch.empty((3, self.M), dtype=torch.complex128, device="cuda")
+        check(self._lib.scw_solver_incident(self._h, _dev_ptr(image, torch.complex128, (self.Ny, self.Nx), "image"),
+                                            {"x": 0, "y": 1}[pol], _dev_ptr(p, torch.complex128, (3, self.M), "p_inc"),
+                                            _stream_handle(stream)), "scw_solver_incident")
+        return p
+
+    def solve(self, n, p_inc, stream=None):
+        """Returns (W [L][3M][4M] c64, gamma [L][4M] c128, alpha [L][4M] c128, p_ref, p_trn [3][M] c128)."""
+        import torch
+        L, M = self.L, self.M
+        W = torch.empty((L, 3 * M, 4 * M), dtype=torch.complex64, device="cuda")
+        g = torch.empty((L, 4 * M), dtype=torch.complex128, device="cuda")
+        a = torch.empty((L, 4 * M), dtype=torch.complex128, device="cuda")
+        pr = torch.empty((3, M), dtype=torch.complex128, device="cuda")
+        pt = torch.empty((3, M), dtype=torch.complex128, device="cuda")
+        check(self._lib.scw_solve(self._h, _dev_ptr(n, torch.complex128, (L, self.Ny, self.Nx), "n"),
+                                  _dev_ptr(p_inc, torch.complex128, (3, M), "p_inc"), ctypes.c_void_p(W.data_ptr()),
+                                  ctypes.c_void_p(g.data_ptr()), ctypes.c_void_p(a.data_ptr()),
+                                  ctypes.c_void_p(pr.data_ptr()), ctypes.c_void_p(pt.data_ptr()),
+                                  _stream_handle(stream)), "scw_solve")
+        return W, g, a, pr, pt
+
+    def times(self) -> dict:
+        t = ScwSolveTimes()
+        check(self._lib.scw_solver_get_times(self._h, ctypes.byref(t)), "scw_solver_get_times")
+        return {f: getattr(t, f) for f, _ in ScwSolveTimes._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.scw_solver_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -59,7 +59,18 @@ class ScwKernelTimes(ctypes.Structure):
                 ("xpass_ms", c_double), ("ypass_ms", c_double), ("total_ms", c_double)]
 
 
-# name -> (restype, argtypes); mirrors include/scw.h
+class ScwSolveDesc(ctypes.Structure):
+    _fields_ = [("U", c_int), ("V", c_int), ("L", c_int), ("lam", c_double), ("X", c_double), ("Y", c_double),
+                ("z_bounds", POINTER(c_double)), ("Nx", c_int), ("Ny", c_int), ("n_top", c_double),
+                ("n_bot_re", c_double), ("n_bot_im", c_double), ("z_inc", c_double)]
+
+
+class ScwSolveTimes(ctypes.Structure):
+    _fields_ = [("calls", c_int), ("fourier_ms", c_double), ("modes_ms", c_double), ("connect_ms", c_double),
+                ("system_ms", c_double), ("alpha_ms", c_double), ("erows_ms", c_double), ("total_ms", c_double)]
+
+
+# name -> (restype, argtypes); mirrors include/scw.h, include/scw_fno.h and include/scw_solve.h
 SIGNATURES = {
     "scw_plan_create": (c_int, [POINTER(ScwDesc), POINTER(c_void_p)]),
     "scw_plan_destroy": (c_int, [c_void_p]),
@@ -101,6 +112,11 @@ SIGNATURES = {
     "scw_surrogate_save_state": (c_int, [c_void_p, c_void_p, c_size_t]),
     "scw_surrogate_load_state": (c_int, [c_void_p, c_void_p, c_size_t]),
     "scw_surrogate_get_timings": (c_int, [c_void_p, POINTER(ScwFnoTimes)]),
+    "scw_solver_create": (c_int, [POINTER(ScwSolveDesc), POINTER(c_void_p)]),
+    "scw_solver_destroy": (c_int, [c_void_p]),
+    "scw_solver_incident": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "scw_solve": (c_int, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
+    "scw_solver_get_times": (c_int, [c_void_p, POINTER(ScwSolveTimes)]),
     "scw_status_string": (c_char_p, [c_int]),
     "scw_last_error": (c_char_p, []),
     "scw_version": (c_int, []),

@@ -52,7 +52,10 @@ def build(verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "lib64")
+    # cuBLAS / cuSOLVER serve the solve stage's dense FP64 factorisations and products
+    cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-L" + cuda_lib, "-lcusolver", "-lcublas",
+           "-Xlinker", "-rpath", "-Xlinker", cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -114,3 +114,23 @@ def test_noalloc_rejects_sizes_above_its_scratch(lib):
     assert b"scratch" in lib.scw_last_error()
     assert lib.scw_recompose_noalloc(21, 21, 16.0, 16.0, 256, 256, 8, 0.0, 0.0, None, dummy, None) == 1
     assert lib.scw_recompose_noalloc(21, 97, 16.0, 16.0, 256, 256, 8, 0.0, 0.0, dummy, dummy, None) == 1
+
+
+def _solve_desc(**kw):
+    zb = np.array([0.0, 0.25, 0.5])
+    base = dict(U=3, V=3, L=2, lam=1.0, X=2.0, Y=2.0, Nx=8, Ny=8, n_top=1.0, n_bot_re=1.0, n_bot_im=0.0, z_inc=0.0)
+    base.update(kw)
+    zb = base.pop("zb", zb)
+    d = _lib.ScwSolveDesc(**base)
+    d.z_bounds = zb.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return d, zb
+
+
+@pytest.mark.parametrize("bad", [dict(U=0), dict(L=0), dict(lam=-1.0), dict(Nx=4), dict(Ny=4), dict(n_top=0.0),
+                                 dict(U=64, V=64, Nx=128, Ny=128), dict(zb=np.array([0.0, 0.5, 0.4]))])
+def test_bad_solver_descriptors_are_rejected(lib, bad):
+    d, keep = _solve_desc(**bad)
+    h = ctypes.c_void_p()
+    st = lib.scw_solver_create(ctypes.byref(d), ctypes.byref(h))
+    assert st in (1, 2), (st, lib.scw_last_error())
+    assert not h.value
