@@ -477,6 +477,56 @@ def run_tiling(args, dev, world, Wd, gd, ad, zb, zp, hbm):
     return res
 
 
+def run_solve(args, dev, with_oracle):
+    """The solve stage on the GPU for the single-wavelength sample itself: 64 x 64 x 32
+    voxels of 0.25 um with seeded ellipsoids, a focused Gaussian beam (NA 0.5), 21 x 21
+    orders (4M = 1764 modes per layer). Reports the GPU time per step of the solve and,
+    beside it, the FP64 oracle timed on one layer of the same sample (its eigen-
+    decomposition of D and its connection step), scaled to the 32 layers."""
+    import torch
+    import paper_2404_07293_gb300 as scw
+    import workloads as wl
+    p = wl.config_single_wavelength(0)
+    L = len(p.z_bounds) - 1
+    n = torch.from_numpy(p.n_volume.astype(np.complex128)).to(dev)
+    img = torch.from_numpy(p.incident_image.astype(np.complex128)).to(dev)
+    s = scw.Solver(p.U, p.V, L, p.lam, p.X, p.Y, p.z_bounds, p.n_volume.shape[2], p.n_volume.shape[1])
+    p_inc = s.incident(img)
+    s.solve(n, p_inc)  # warm-up (handles, workspaces, library kernels)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    W, g, a, pr, pt = s.solve(n, p_inc)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    t = s.times()
+    s.close()
+    res = {"workload": "single_wavelength_sample_64x64x32_21x21_orders", "layers": L, "modes_per_layer": 4 * p.U * p.V,
+           "gpu_s": wall, "gpu_step_ms": {k: t[k] for k in ("fourier_ms", "modes_ms", "connect_ms", "system_ms",
+                                                             "alpha_ms", "erows_ms", "total_ms")},
+           "eig_ms_per_layer_effective": t["modes_ms"] / L,
+           "arith": "FP64 (complex128); eigendecompositions of the 2M x 2M reduced problem, 8 worker threads"}
+    if with_oracle:
+        from oracle import cw
+        u, v = cw.orders(p.U, p.V)
+        sx, sy = cw.directions(p.U, p.V, p.lam, p.X, p.Y)
+        t0 = time.perf_counter()
+        _, _, D = cw.layer_operators(p.n_volume[0], sx, sy, u, v)
+        gam, Q = cw.layer_modes(D)
+        t_eig = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        T, B = cw.top_bottom(gam, Q, p.z_bounds[1] - p.z_bounds[0], 2 * np.pi / p.lam)
+        K = B @ np.linalg.solve(T, np.eye(T.shape[0], dtype=np.complex128))
+        t_conn = time.perf_counter() - t0
+        del K
+        res["cpu_baseline"] = {"value": L * (t_eig + t_conn), "unit": "s (32 layers, scaled from one)",
+                               "cores": blas_threads(), "kind": "oracle",
+                               "sample": f"layer 0: assembly + full 4M x 4M eig {t_eig:.2f} s, connection "
+                                         f"step {t_conn:.2f} s; times 32 layers"}
+        res["speedup_vs_oracle"] = res["cpu_baseline"]["value"] / wall
+    del W, g, a, pr, pt, n
+    return res
+
+
 def run_surrogate(args, dev, bf16_peaks):
     """Learned surrogate at its full size: 4 Fourier layers of width 32, 16x16
     kept modes on a 64x64 grid, inputs 8 slices of 32x32 complex n (seeded
@@ -717,6 +767,11 @@ def run_ours(args, world, rank, local):
         torch.cuda.empty_cache()
         sweep = run_sweep(args, dev, world, hbm)
 
+    solve = None
+    if not args.no_solve:
+        torch.cuda.empty_cache()
+        solve = run_solve(args, dev, rank == 0 and not args.no_cpu_baseline)
+
     surrogate = None
     if not args.no_surrogate:
         torch.cuda.empty_cache()
@@ -761,6 +816,7 @@ def run_ours(args, world, rank, local):
             "illumination": illum,
             "points": points,
             "tiling": tiling,
+            "solve": solve,
             "surrogate": surrogate,
         }
         print(json.dumps(line), flush=True)
@@ -788,6 +844,7 @@ def main():
     ap.add_argument("--fno-batch", type=int, default=256)
     ap.add_argument("--no-points", action="store_true", help="skip the off-grid point-set block")
     ap.add_argument("--no-tiling", action="store_true", help="skip the periodic-tiling / patch-mosaic block")
+    ap.add_argument("--no-solve", action="store_true", help="skip the GPU solve-stage block")
     ap.add_argument("--illuminations", type=int, default=16,
                     help="incident fields of the multi-illumination block (1 skips it)")
     ap.add_argument("--only-surrogate", action="store_true",
