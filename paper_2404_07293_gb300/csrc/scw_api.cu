@@ -510,6 +510,7 @@ struct scw_plan_s {
   int n_plane_entries = 0;
   int n_pair_entries = 0;
   bool tiled = false;  // some item stores periodic tiles
+  int max_twy = 0;     // largest y fold-twiddle table (complex elements)
   int inject_stall = 0;            // scw_plan_inject_stall (tests of the timeout path)
   TcSchedule sched;
   float2** d_outs = nullptr;
@@ -674,7 +675,7 @@ static scw_status enqueue_pipelined(scw_plan_t P, float2* out_one, cudaStream_t 
     e = launch_xpass(one, nullptr, ent, nb, P->xpass_smem, P->st2);
     if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
     int ny = 0;
-    e = launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, P->tiled, out_one, nullptr,
+    e = launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, P->max_twy, P->tiled, out_one, nullptr,
                      P->st2, &ny);
     if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
     n += 1 + ny;
@@ -698,7 +699,7 @@ static scw_status enqueue_synthesis(scw_plan_t P, float2* out_one, cudaStream_t 
   if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
   mark(P, 3, st, marks);
   int ny = 0;
-  e = launch_ypass(one, items, P->d_plane_entries, P->n_plane_entries, P->n_pair_entries, P->max_Qx, P->max_Vp, P->tiled,
+  e = launch_ypass(one, items, P->d_plane_entries, P->n_plane_entries, P->n_pair_entries, P->max_Qx, P->max_Vp, P->max_twy, P->tiled,
                    out_one, P->d_outs, st, &ny);
   if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
   mark(P, 4, st, marks);
@@ -870,6 +871,7 @@ static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, boo
     P->max_Vp = std::max(P->max_Vp, p->item.Vp);
     P->rec_smem = std::max(P->rec_smem, recompose_smem_bytes(p->V, p->item.Up, p->item.Vp));
     P->tiled = P->tiled || p->tiles_x > 1 || p->tiles_y > 1;
+    P->max_twy = std::max(P->max_twy, (p->Fy / 8) * p->item.Vp);
   }
   // plane entries of items with long y folds first: they run the two-residue y-pass
   std::stable_partition(pe.begin(), pe.end(),

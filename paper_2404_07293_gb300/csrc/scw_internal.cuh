@@ -205,10 +205,12 @@ cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d
 // entries [0, n_pair) run the two-residue y-pass (long folds, ypass_pairs(Vp)), the rest the
 // one-residue y-pass; *launches receives the number of kernels launched (0, 1 or 2)
 bool ypass_pairs(int Vp);
-// tiled: some item has periodic tiles (selects the y-pass that stores every tile)
+// max_twy: the largest fold-twiddle table (Fy/8) Vp of the items, in complex elements (staged in
+// shared memory when it fits); tiled: some item has periodic tiles (selects the y-pass that stores
+// every tile)
 cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int n_pair,
-                         int max_Qx, int max_Vp, bool tiled, float2* out_one, float2* const* d_outs, cudaStream_t st,
-                         int* launches);
+                         int max_Qx, int max_Vp, int max_twy, bool tiled, float2* out_one, float2* const* d_outs,
+                         cudaStream_t st, int* launches);
 cudaError_t launch_recompose(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int max_Qx,
                              size_t smem, const float2* S_override, const int* nsplit_override, float2* out_one,
                              float2* const* d_outs, cudaStream_t st);

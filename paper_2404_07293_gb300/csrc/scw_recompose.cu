@@ -278,9 +278,10 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
 }
 
 // Fold + radix-8 inverse DFT along y of one tile from its rows in shared memory, and the field stores.
+// twy: the item's fold twiddles [Fy/8][Vp] (staged in shared memory, or the global table).
 template <bool BATCH, bool PAIR, bool TILED>
-__device__ __forceinline__ void ypass_tile(const ItemDev& it, const float4* ys_col4, int2 e, int c, int xb,
-                                           float2* out_one, float2* const* outs) {
+__device__ __forceinline__ void ypass_tile(const ItemDev& it, const float4* ys_col4, const float2* twy, int2 e, int c,
+                                           int xb, float2* out_one, float2* const* outs) {
   const int f = e.y;
   const int Vp = it.Vp, Fx = it.Fx, Fy = it.Fy;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -294,17 +295,20 @@ __device__ __forceinline__ void ypass_tile(const ItemDev& it, const float4* ys_c
   const float4* col = ys_col4 + lane;
   if constexpr (!PAIR) {
     for (int b = w; b < Q; b += 8) {
-      const float2* tw = it.twy + (size_t)b * Vp;
+      const float4* tw = reinterpret_cast<const float4*>(twy + (size_t)b * Vp);  // twiddle pairs (Vp % 8 == 0)
       float2 G0[8], G1[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) G0[r] = G1[r] = make_float2(0.f, 0.f);
       for (int p0 = 0; p0 < Vp; p0 += 8) {
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const float4 d = col[(size_t)(p0 + r) * 32];
-          const float2 t = __ldg(tw + p0 + r);
-          c_fma(G0[r], make_float2(d.x, d.y), t);
-          c_fma(G1[r], make_float2(d.z, d.w), t);
+        for (int r = 0; r < 8; r += 2) {
+          const float4 tt = tw[(p0 + r) >> 1];
+          const float2 t0 = make_float2(tt.x, tt.y), t1 = make_float2(tt.z, tt.w);
+          const float4 d0 = col[(size_t)(p0 + r) * 32], d1 = col[(size_t)(p0 + r + 1) * 32];
+          c_fma(G0[r], make_float2(d0.x, d0.y), t0);
+          c_fma(G1[r], make_float2(d0.z, d0.w), t0);
+          c_fma(G0[r + 1], make_float2(d1.x, d1.y), t1);
+          c_fma(G1[r + 1], make_float2(d1.z, d1.w), t1);
         }
       }
       idft8(G0);
@@ -317,21 +321,26 @@ __device__ __forceinline__ void ypass_tile(const ItemDev& it, const float4* ys_c
   }
   for (int b = w; b < Q; b += 16) {
     const bool two = b + 8 < Q;
-    const float2* twA = it.twy + (size_t)b * Vp;
-    const float2* twB = two ? twA + (size_t)8 * Vp : twA;
+    const float4* twA = reinterpret_cast<const float4*>(twy + (size_t)b * Vp);  // twiddle pairs
+    const float4* twB = two ? twA + (size_t)4 * Vp : twA;
     float2 A0[8], A1[8], B0[8], B1[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) A0[r] = A1[r] = B0[r] = B1[r] = make_float2(0.f, 0.f);
     for (int p0 = 0; p0 < Vp; p0 += 8) {
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const float4 d = col[(size_t)(p0 + r) * 32];
-        const float2 ta = __ldg(twA + p0 + r), tb = __ldg(twB + p0 + r);
-        const float2 d0 = make_float2(d.x, d.y), d1 = make_float2(d.z, d.w);
-        c_fma(A0[r], d0, ta);
-        c_fma(A1[r], d1, ta);
-        c_fma(B0[r], d0, tb);
-        c_fma(B1[r], d1, tb);
+      for (int r = 0; r < 8; r += 2) {
+        const float4 ta2 = twA[(p0 + r) >> 1], tb2 = twB[(p0 + r) >> 1];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const float4 d = col[(size_t)(p0 + r + h) * 32];
+          const float2 ta = h ? make_float2(ta2.z, ta2.w) : make_float2(ta2.x, ta2.y);
+          const float2 tb = h ? make_float2(tb2.z, tb2.w) : make_float2(tb2.x, tb2.y);
+          const float2 d0 = make_float2(d.x, d.y), d1 = make_float2(d.z, d.w);
+          c_fma(A0[r + h], d0, ta);
+          c_fma(A1[r + h], d1, ta);
+          c_fma(B0[r + h], d0, tb);
+          c_fma(B1[r + h], d1, tb);
+        }
       }
     }
     idft8(A0);
@@ -359,9 +368,9 @@ __device__ __forceinline__ void ypass_tile(const ItemDev& it, const float4* ys_c
 // (b, b + 8), b = w, w + 16, ..., so each shared-memory load feeds four complex FMAs
 // (long folds); otherwise one residue b = w, w + 8, ... at a time and twice the
 // resident warps (short folds, where latency dominates).
-template <bool BATCH>
+template <bool BATCH, bool STW>
 __device__ __forceinline__ void ypass_prefetch(const ItemDev& one, const ItemDev* items, const int2* entries,
-                                               int t, int n_tiles, int nxb, float4* buf) {
+                                               int t, int n_tiles, int nxb, int rows_f4, float4* buf) {
   if (t < n_tiles) {
     const int r = t / nxb, xb = (t - r * nxb) * 64;
     const int2 e = entries[r / 3];
@@ -375,30 +384,41 @@ __device__ __forceinline__ void ypass_prefetch(const ItemDev& one, const ItemDev
         const bool ok = v >= 0 && x < it.Fx;  // Fx is even: a pair is in or out as a whole
         ptx::cp_async16(ptx::smem_u32(buf + i), ok ? src + (size_t)v * it.Fx + x : src, ok ? 16u : 0u);
       }
+      if constexpr (STW) {  // the fold twiddles [Fy/8][Vp] after the rows
+        const float4* tw = reinterpret_cast<const float4*>(it.twy);
+        for (int i = threadIdx.x; i < (it.Fy >> 3) * it.Vp / 2; i += blockDim.x)
+          ptx::cp_async16(ptx::smem_u32(buf + rows_f4 + i), tw + i, 16u);
+      }
     }
   }
   ptx::cp_async_commit();
 }
 
-template <bool BATCH, bool PAIR, bool TILED>
+// STW: the fold twiddles travel with the rows into shared memory (when the largest table fits).
+template <bool BATCH, bool PAIR, bool TILED, bool STW>
 __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_constant__ ItemDev one,
                                                        const ItemDev* __restrict__ items,
                                                        const int2* __restrict__ entries, int n_tiles, int nxb,
-                                                       int buf_f4, float2* out_one, float2* const* __restrict__ outs) {
-  extern __shared__ float4 ys_buf[];  // 2 x [Vp][32] float4 = 2 x [Vp][64] complex
+                                                       int rows_f4, int buf_f4, float2* out_one,
+                                                       float2* const* __restrict__ outs) {
+  extern __shared__ float4 ys_buf[];  // 2 x ([Vp][32] float4 rows = [Vp][64] complex, then the twiddles)
   int t = blockIdx.x;
   if (t >= n_tiles) return;
-  ypass_prefetch<BATCH>(one, items, entries, t, n_tiles, nxb, ys_buf);
+  ypass_prefetch<BATCH, STW>(one, items, entries, t, n_tiles, nxb, rows_f4, ys_buf);
   for (int b = 0; t < n_tiles; t += gridDim.x, b ^= 1) {
-    ypass_prefetch<BATCH>(one, items, entries, t + gridDim.x, n_tiles, nxb, ys_buf + (size_t)(b ^ 1) * buf_f4);
+    ypass_prefetch<BATCH, STW>(one, items, entries, t + gridDim.x, n_tiles, nxb, rows_f4,
+                               ys_buf + (size_t)(b ^ 1) * buf_f4);
     ptx::cp_async_wait<1>();  // this thread's copies of tile t have landed
     __syncthreads();          // and everyone's
     const int r = t / nxb, xb = (t - r * nxb) * 64;
     const int2 e = entries[r / 3];
     const int c = r - (r / 3) * 3;
     const ItemDev& it = BATCH ? items[e.x] : one;
-    if (xb < it.Fx)
-      ypass_tile<BATCH, PAIR, TILED>(it, ys_buf + (size_t)b * buf_f4, e, c, xb, out_one, outs);
+    if (xb < it.Fx) {
+      const float4* cur = ys_buf + (size_t)b * buf_f4;
+      ypass_tile<BATCH, PAIR, TILED>(it, cur, STW ? reinterpret_cast<const float2*>(cur + rows_f4) : it.twy, e, c,
+                                     xb, out_one, outs);
+    }
     __syncthreads();          // buffer b is free for the prefetch of the next iteration
   }
   ptx::cp_async_wait<0>();
@@ -436,16 +456,20 @@ cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d
   return cudaGetLastError();
 }
 
-template <bool PAIR, bool TILED>
+constexpr int kYpassTwiddleF4 = 1024;  // fold twiddles staged in shared memory up to 16 KB per table
+
+template <bool PAIR, bool TILED, bool STW>
 static cudaError_t launch_ypass_t(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
-                                  int max_Qx, int max_Vp, float2* out_one, float2* const* d_outs, cudaStream_t st) {
+                                  int max_Qx, int max_Vp, int tw_f4, float2* out_one, float2* const* d_outs,
+                                  cudaStream_t st) {
   const int nxb = (max_Qx * 8 + 63) / 64;
   const long long tiles = (long long)nxb * n_entries * 3;
   if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const int buf_f4 = max_Vp * 32;
+  const int rows_f4 = max_Vp * 32;
+  const int buf_f4 = rows_f4 + (STW ? tw_f4 : 0);
   const size_t smem = 2 * (size_t)buf_f4 * sizeof(float4);
-  const void* fn = items ? reinterpret_cast<const void*>(ypass_kernel<true, PAIR, TILED>)
-                         : reinterpret_cast<const void*>(ypass_kernel<false, PAIR, TILED>);
+  const void* fn = items ? reinterpret_cast<const void*>(ypass_kernel<true, PAIR, TILED, STW>)
+                         : reinterpret_cast<const void*>(ypass_kernel<false, PAIR, TILED, STW>);
   cudaError_t e = allow_max_smem(fn);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -455,36 +479,41 @@ static cudaError_t launch_ypass_t(const ItemDev& one, const ItemDev* items, cons
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<long long>(tiles, (long long)std::max(1, per_sm) * sms);
   if (items)
-    ypass_kernel<true, PAIR, TILED><<<grid, 256, smem, st>>>(one, items, d_entries, (int)tiles, nxb, buf_f4, nullptr,
-                                                            d_outs);
+    ypass_kernel<true, PAIR, TILED, STW><<<grid, 256, smem, st>>>(one, items, d_entries, (int)tiles, nxb, rows_f4,
+                                                                 buf_f4, nullptr, d_outs);
   else
-    ypass_kernel<false, PAIR, TILED><<<grid, 256, smem, st>>>(one, nullptr, d_entries, (int)tiles, nxb, buf_f4,
-                                                             out_one, nullptr);
+    ypass_kernel<false, PAIR, TILED, STW><<<grid, 256, smem, st>>>(one, nullptr, d_entries, (int)tiles, nxb, rows_f4,
+                                                                  buf_f4, out_one, nullptr);
   return cudaGetLastError();
 }
 
 template <bool PAIR>
 static cudaError_t launch_ypass_p(bool tiled, const ItemDev& one, const ItemDev* items, const int2* d_entries,
-                                  int n_entries, int max_Qx, int max_Vp, float2* out_one, float2* const* d_outs,
-                                  cudaStream_t st) {
-  return tiled ? launch_ypass_t<PAIR, true>(one, items, d_entries, n_entries, max_Qx, max_Vp, out_one, d_outs, st)
-               : launch_ypass_t<PAIR, false>(one, items, d_entries, n_entries, max_Qx, max_Vp, out_one, d_outs, st);
+                                  int n_entries, int max_Qx, int max_Vp, int tw_f4, float2* out_one,
+                                  float2* const* d_outs, cudaStream_t st) {
+  const bool stw = tw_f4 <= kYpassTwiddleF4;
+#define SCW_YP(T, S) \
+  launch_ypass_t<PAIR, T, S>(one, items, d_entries, n_entries, max_Qx, max_Vp, tw_f4, out_one, d_outs, st)
+  if (tiled) return stw ? SCW_YP(true, true) : SCW_YP(true, false);
+  return stw ? SCW_YP(false, true) : SCW_YP(false, false);
+#undef SCW_YP
 }
 
 bool ypass_pairs(int Vp) { return Vp >= 24; }
 
 cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int n_pair,
-                         int max_Qx, int max_Vp, bool tiled, float2* out_one, float2* const* d_outs, cudaStream_t st,
-                         int* launches) {
+                         int max_Qx, int max_Vp, int max_twy, bool tiled, float2* out_one, float2* const* d_outs,
+                         cudaStream_t st, int* launches) {
+  const int tw_f4 = (max_twy + 1) / 2;
   int n = 0;
   cudaError_t e = cudaSuccess;
   if (n_pair > 0) {
-    e = launch_ypass_p<true>(tiled, one, items, d_entries, n_pair, max_Qx, max_Vp, out_one, d_outs, st);
+    e = launch_ypass_p<true>(tiled, one, items, d_entries, n_pair, max_Qx, max_Vp, tw_f4, out_one, d_outs, st);
     ++n;
   }
   if (e == cudaSuccess && n_entries > n_pair) {
-    e = launch_ypass_p<false>(tiled, one, items, d_entries + n_pair, n_entries - n_pair, max_Qx, max_Vp, out_one,
-                              d_outs, st);
+    e = launch_ypass_p<false>(tiled, one, items, d_entries + n_pair, n_entries - n_pair, max_Qx, max_Vp, tw_f4,
+                              out_one, d_outs, st);
     ++n;
   }
   if (launches) *launches = n;
