@@ -537,6 +537,15 @@ struct scw_plan_s {
   cudaStream_t st2 = nullptr;
   std::vector<cudaEvent_t> gev;     // contraction of group g done
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // host-IO pipeline (scw_synthesize_host on tensor-core plans): per layer group g the copy of
+  // its W on st_in, its conversion and synthesis on the caller's stream, and the copy of its
+  // planes of the field on st_out, so that both copy directions overlap each other and the kernels
+  int hgroups = 0;
+  std::vector<TcSchedule> hsched;
+  std::vector<int> hplane, hunit, hlayer;  // [hgroups + 1] offsets: plane slots, units, layers
+  cudaStream_t st_in = nullptr, st_out = nullptr;
+  std::vector<cudaEvent_t> hev_in, hev_comp;
+  cudaEvent_t hev_start = nullptr, hev_small = nullptr, hev_out = nullptr;
 };
 
 static void free_plan(scw_plan_t P) {
@@ -555,6 +564,16 @@ static void free_plan(scw_plan_t P) {
     if (g.d_cta_off) cudaFree(g.d_cta_off);
   }
   for (cudaEvent_t ev : P->gev) cudaEventDestroy(ev);
+  for (auto& g : P->hsched) {
+    if (g.d_tasks) cudaFree(g.d_tasks);
+    if (g.d_cta_off) cudaFree(g.d_cta_off);
+  }
+  for (cudaEvent_t ev : P->hev_in) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : P->hev_comp) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : {P->hev_start, P->hev_small, P->hev_out})
+    if (ev) cudaEventDestroy(ev);
+  if (P->st_in) cudaStreamDestroy(P->st_in);
+  if (P->st_out) cudaStreamDestroy(P->st_out);
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
   if (P->st2) cudaStreamDestroy(P->st2);
@@ -903,6 +922,146 @@ static cudaError_t convert_w(Plan* p, const float2* w, cudaStream_t st) {
   return launch_convert_tiled(w, p->Wh, nullptr, p->L, p->M, false, st);
 }
 
+// Conversion of layers [lb, le) of W (tensor-core plans; the tiled layout is contiguous per layer).
+static cudaError_t convert_w_layers(Plan* p, const float2* w, int lb, int le, cudaStream_t st) {
+  const size_t M = p->M, R = 3 * M, nk = (8 * M + 63) / 64;
+  const size_t in_off = (size_t)lb * R * 4 * M, out_off = (size_t)lb * R * nk * 64;
+  if (p->precision == SCW_PREC_SPLIT_BF16)
+    return launch_convert_tiled(w + in_off, p->Whi + out_off, p->Wlo + out_off, le - lb, p->M, true, st);
+  return launch_convert_tiled(w + in_off, p->Wh + out_off, nullptr, le - lb, p->M, false, st);
+}
+
+// Groups of the host-IO pipeline: contiguous units, the layers they span and their plane slots.
+static scw_status host_groups(scw_plan_t P) {
+  if (P->hgroups) return SCW_OK;
+  Plan* p = P->items[0];
+  const int nu = (int)p->units.size();
+  const int G = std::max(1, std::min(16, nu));
+  P->hsched.resize(G);
+  P->hplane.assign(G + 1, 0);
+  P->hunit.assign(G + 1, 0);
+  P->hlayer.assign(G + 1, 0);
+  // boundaries between layers only (a layer with more plane slots than one work unit holds spans
+  // several units, which stay in one group: its W is converted once, by that group)
+  int ub = 0;
+  for (int g = 0; g < G; ++g) {
+    int ue = (g + 1 < G) ? std::max(ub, (int)((long long)nu * (g + 1) / G)) : nu;
+    while (ue < nu && ue > 0 && p->units[ue].layer == p->units[ue - 1].layer) ++ue;
+    if (ue > ub) {  // (an empty range would mean "every unit" to upload_schedule)
+      scw_status s = upload_schedule(P->items, P->NB, P->bf16, P->hsched[g], 0, ub, ue);
+      if (s != SCW_OK) return s;
+    }
+    P->hunit[g + 1] = ue;
+    P->hplane[g + 1] = (ue < nu) ? p->units[ue].f0 : p->Fz;
+    P->hlayer[g + 1] = (ue < nu) ? p->units[ue].layer : p->L;
+    ub = ue;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&P->st_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->st_out, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&P->hev_start, &P->hev_small, &P->hev_out})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+  P->hev_in.assign(G, nullptr);
+  P->hev_comp.assign(G, nullptr);
+  for (int g = 0; g < G && e == cudaSuccess; ++g) {
+    e = cudaEventCreateWithFlags(&P->hev_in[g], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->hev_comp[g], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) return cuda_error(e, "host pipeline streams");
+  P->hgroups = G;
+  return SCW_OK;
+}
+
+static scw_status set_layers_item(scw_plan_t P, int idx, const void* W, const void* gamma, const void* alpha,
+                                  const void* p_inc, const void* p_ref, const void* p_trn, cudaStream_t st);
+
+// scw_synthesize_host on tensor-core plans: layer group g's W goes in on st_in while group g-1 is
+// converted and synthesised on `st` and group g-2's planes of the field come back on st_out.
+static scw_status synthesize_host_pipelined(scw_plan_t P, const void* W, const void* gamma, const void* alpha,
+                                            const void* const* pio, void* out, cudaStream_t st) {
+  Plan* p = P->items[0];
+  scw_status s = host_groups(P);
+  if (s != SCW_OK) return s;
+  const int G = P->hgroups;
+  const size_t L = p->L, M = p->M, wl = 3 * M * 4 * M;  // complex elements of W per layer
+  const float2* Wh = static_cast<const float2*>(W);
+  cudaError_t e;
+#define SCW_TRY_E(x, what)                          \
+  do {                                              \
+    e = (x);                                        \
+    if (e != cudaSuccess) return cuda_error(e, what); \
+  } while (0)
+  SCW_TRY_E(cudaEventRecord(P->hev_start, st), "cudaEventRecord");
+  SCW_TRY_E(cudaStreamWaitEvent(P->st_in, P->hev_start, 0), "cudaStreamWaitEvent");
+  SCW_TRY_E(cudaStreamWaitEvent(P->st_out, P->hev_start, 0), "cudaStreamWaitEvent");
+  SCW_TRY_E(cudaMemcpyAsync(p->hio_gamma, gamma, L * 4 * M * sizeof(double2), cudaMemcpyHostToDevice, P->st_in),
+            "cudaMemcpyAsync");
+  SCW_TRY_E(cudaMemcpyAsync(p->hio_alpha, alpha, p->I * L * 4 * M * sizeof(double2), cudaMemcpyHostToDevice, P->st_in),
+            "cudaMemcpyAsync");
+  const double2 *pi = nullptr, *pr = nullptr, *pt = nullptr;
+  if (pio[0] && pio[1] && pio[2]) {
+    const size_t np = (size_t)p->I * 3 * M;
+    for (int k = 0; k < 3; ++k)
+      SCW_TRY_E(cudaMemcpyAsync(p->hio_p + k * np, pio[k], np * sizeof(double2), cudaMemcpyHostToDevice, P->st_in),
+                "cudaMemcpyAsync");
+    pi = p->hio_p; pr = p->hio_p + np; pt = p->hio_p + 2 * np;
+  }
+  SCW_TRY_E(cudaEventRecord(P->hev_small, P->st_in), "cudaEventRecord");
+  for (int g = 0; g < G; ++g) {
+    const size_t lb = P->hlayer[g], le = P->hlayer[g + 1];
+    SCW_TRY_E(cudaMemcpyAsync(p->hio_W + lb * wl, Wh + lb * wl, (le - lb) * wl * sizeof(float2),
+                              cudaMemcpyHostToDevice, P->st_in), "cudaMemcpyAsync");
+    SCW_TRY_E(cudaEventRecord(P->hev_in[g], P->st_in), "cudaEventRecord");
+  }
+  // the layers point at the plan's own device copies (attached once, without converting here)
+  if (!p->layers_set || p->gamma != p->hio_gamma || p->p_inc != pi) {
+    p->gamma = p->hio_gamma; p->alpha = p->hio_alpha;
+    p->p_inc = pi; p->p_ref = pr; p->p_trn = pt;
+    p->item.gamma = p->gamma; p->item.alpha = p->alpha;
+    p->layers_set = true;
+    invalidate_graph(P);
+  }
+  const ItemDev& one = p->item;
+  SCW_TRY_E(cudaStreamWaitEvent(st, P->hev_small, 0), "cudaStreamWaitEvent");
+  if (p->n_exterior) SCW_TRY_E(launch_exterior(*p, st), "exterior kernel launch");
+  const size_t slice = (size_t)p->out_pstride;  // complex elements per output plane
+  for (int g = 0; g < G; ++g) {
+    SCW_TRY_E(cudaStreamWaitEvent(st, P->hev_in[g], 0), "cudaStreamWaitEvent");
+    if (P->hlayer[g + 1] > P->hlayer[g])
+      SCW_TRY_E(convert_w_layers(p, p->hio_W, P->hlayer[g], P->hlayer[g + 1], st), "W conversion launch");
+    const int ub = P->hunit[g], nu = P->hunit[g + 1] - ub;
+    if (nu > 0) {
+      SCW_TRY_E(launch_phases_tc(one, nullptr, P->d_unit_entries + ub, nu, P->max_M, P->F_pad, P->bf16, st),
+                "phase kernel launch");
+      SCW_TRY_E(launch_contract_tc(one, nullptr, P->hsched[g], P->NB, P->bf16, P->d_err, P->timeout_ns,
+                                   P->inject_stall, st), "contraction kernel launch");
+    }
+    const int fb = P->hplane[g], nb = P->hplane[g + 1] - fb;
+    if (nb > 0) {
+      const int2* ent = P->d_plane_entries + fb;
+      SCW_TRY_E(launch_xpass(one, nullptr, ent, nb, P->xpass_smem, st), "x-pass launch");
+      int ny = 0;
+      SCW_TRY_E(launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, P->max_twy,
+                             P->tiled, p->hio_out, nullptr, st, &ny), "y-pass launch");
+    }
+    SCW_TRY_E(cudaEventRecord(P->hev_comp[g], st), "cudaEventRecord");
+    SCW_TRY_E(cudaStreamWaitEvent(P->st_out, P->hev_comp[g], 0), "cudaStreamWaitEvent");
+    // plane slots [fb, fb + nb) are output planes [fb / I, (fb + nb) / I) of every illumination
+    const int I = p->I, fo_b = fb / I, fo_n = nb / I;
+    if (fo_n > 0)
+      for (int il = 0; il < I; ++il)
+        for (int c = 0; c < 3; ++c) {
+          const size_t off = ((size_t)(il * 3 + c) * p->Fz_out + fo_b) * slice;
+          SCW_TRY_E(cudaMemcpyAsync(static_cast<float2*>(out) + off, p->hio_out + off, fo_n * slice * sizeof(float2),
+                                    cudaMemcpyDeviceToHost, P->st_out), "cudaMemcpyAsync");
+        }
+  }
+  SCW_TRY_E(cudaEventRecord(P->hev_out, P->st_out), "cudaEventRecord");
+  SCW_TRY_E(cudaStreamWaitEvent(st, P->hev_out, 0), "cudaStreamWaitEvent");
+  SCW_TRY_E(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+#undef SCW_TRY_E
+  return SCW_OK;
+}
+
 static scw_status set_layers_item(scw_plan_t P, int idx, const void* W, const void* gamma, const void* alpha,
                                   const void* p_inc, const void* p_ref, const void* p_trn, cudaStream_t st) {
   Plan* p = P->items[idx];
@@ -1166,6 +1325,12 @@ scw_status scw_synthesize_host(scw_plan_t P, const void* W, const void* gamma, c
   Plan* p = P->items[0];
   if (!(p->flags & SCW_FLAG_HOST_IO)) return set_error(SCW_ERR_STATE, "plan was created without SCW_FLAG_HOST_IO");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((p->flags & SCW_FLAG_EXTERIOR) && (!p_inc || !p_ref || !p_trn))
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "SCW_FLAG_EXTERIOR needs p_inc, p_ref and p_trn");
+  if (P->tc && !p->units.empty() && P->groups == 1) {
+    const void* pio[3] = {p_inc, p_ref, p_trn};
+    return synthesize_host_pipelined(P, W, gamma, alpha, pio, out, st);
+  }
   const size_t L = p->L, M = p->M;
   cudaError_t e;
 #define SCW_CP(dst, src, bytes, kind)                              \

@@ -140,3 +140,28 @@ def test_pupil_below_the_sample(two_beams, precision, na, cuda_device):
     assert np.all(S[np.ix_(below, np.arange(3), outside)] == 0)  # blocked orders are exactly zero
     assert np.linalg.norm(S - Sref) / np.linalg.norm(Sref) <= TOL[precision]
     plan.close()
+
+
+def test_host_io_pipeline_with_split_layers(cuda_device):
+    """Host-IO synthesis runs in layer groups (copies overlapping the kernels); a layer
+    with more plane slots than one work unit (3 illuminations x 50 planes) must stay in
+    one group. The result equals the device path bit for bit."""
+    U, V, L, I = 5, 5, 4, 3
+    W, g, _, *_ = wl.random_layer_set(8, U, V, L)
+    amps = [wl.random_layer_set(60 + i, U, V, L)[2:] for i in range(I)]
+    zb = np.array([0.0, 0.2, 1.2, 1.3, 1.5])
+    zp = np.concatenate([[-0.3], np.linspace(0.01, 0.19, 5), np.linspace(0.2, 1.19, 50), [1.25, 1.4], [1.9]])
+    ls = layerset_from_arrays(1.0, 2.0, 2.0, U, V, zb, W, g, *amps[0])
+    args = [np.ascontiguousarray(W, dtype=np.complex64), np.ascontiguousarray(g)] + \
+        [np.ascontiguousarray(np.stack([a[j] for a in amps])) for j in range(4)]
+    host = _plan(ls, 16, 16, zp, "split_bf16", exterior=True, illuminations=I, host_io=True)
+    E = host.synthesize_host(*args)
+    E2 = host.synthesize_host(*args)
+    host.check()
+    dev = _plan(ls, 16, 16, zp, "split_bf16", exterior=True, illuminations=I)
+    dev.set_layers(*[_c(x, np.complex64 if j == 0 else np.complex128) for j, x in enumerate(args)])
+    Ed = dev.synthesize().cpu().numpy()
+    assert np.array_equal(E, Ed)
+    assert np.array_equal(E, E2)
+    host.close()
+    dev.close()
