@@ -936,7 +936,7 @@ static scw_status host_groups(scw_plan_t P) {
   if (P->hgroups) return SCW_OK;
   Plan* p = P->items[0];
   const int nu = (int)p->units.size();
-  const int G = std::max(1, std::min(16, nu));
+  const int G = std::max(1, std::min(8, nu));
   P->hsched.resize(G);
   P->hplane.assign(G + 1, 0);
   P->hunit.assign(G + 1, 0);
