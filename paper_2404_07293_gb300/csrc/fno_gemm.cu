@@ -289,7 +289,13 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
   const int n_tasks = m_tiles * n_tiles;
   const int nkb = K / 64;
   const uint64_t deadline = ptx::globaltimer() + timeout_ns;
-  auto tile_nseg = [&](int n0) { return max(0, min(BN / C, ea.B - n0 / C)); };
+  constexpr bool SEG2 = (EPI == EPI_LAYER_FWD || EPI == EPI_LAYER_BWD);
+  // the layer products walk the row tiles fastest (CTAs in flight share a Wh / GVh tile); the
+  // field product walks the column tiles fastest (they share a row tile of the points table)
+  constexpr bool NFAST = (EPI == EPI_FIELD);
+  auto tile_m0 = [&](int t) { return (NFAST ? t / n_tiles : t % m_tiles) * 128; };
+  auto tile_n0 = [&](int t) { return (NFAST ? t % n_tiles : t / m_tiles) * BN; };
+  auto tile_nseg = [&](int n0) { return SEG2 ? max(0, min(BN / C, ea.B - n0 / C)) : 0; };
 
   if (threadIdx.x < C) {
     const __nv_bfloat16* bias = static_cast<const __nv_bfloat16*>(ea.bias);
@@ -326,7 +332,7 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
     int st = 0, issued = 0;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < n_tasks && !abort_s; t += gridDim.x) {
-      const int m0 = (t % m_tiles) * 128, n0 = (t / m_tiles) * BN;
+      const int m0 = tile_m0(t), n0 = tile_n0(t);
       const int total = nkb + tile_nseg(n0);
       for (int i = 0; i < total && !abort_s; ++i) {
         if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[st]), ph ^ 1u, deadline)) {
@@ -370,7 +376,7 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
     int st = 0, lt = 0;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < n_tasks && !abort_s; t += gridDim.x, ++lt) {
-      const int n0 = (t / m_tiles) * BN;
+      const int n0 = tile_n0(t);
       const int total = nkb + tile_nseg(n0);
       const int acc = lt & 1;
       if (!ptx::mbar_wait(ptx::smem_u32(&acce_bar[acc]), ((uint32_t)(lt >> 1) & 1u) ^ 1u, deadline)) {
@@ -424,7 +430,7 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
     const int third = (warp - 2) >> 2;  // column chunks third, third + 3, ...
     int lt = 0;
     for (int t = blockIdx.x; t < n_tasks; t += gridDim.x, ++lt) {
-      const int m0 = (t % m_tiles) * 128, n0 = (t / m_tiles) * BN;
+      const int m0 = tile_m0(t), n0 = tile_n0(t);
       const int acc = lt & 1;
       bool ok = true;
       for (;;) {
@@ -587,8 +593,10 @@ cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtenso
       return BN == 128 ? launch_tc_t<128, EPI_DW>(mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st)
                        : cudaErrorInvalidValue;
     case EPI_FIELD:
-      return splits == 1 ? launch_tc_bn<EPI_FIELD>(BN, mA, mB, mA2, mW, ea, M, N, K, 1, err, timeout_ns, st)
-                         : cudaErrorInvalidValue;
+      if (splits != 1) return cudaErrorInvalidValue;
+      // BN 256: the persistent form (epilogue of one tile overlapping the next tile's MMAs)
+      return BN == 256 ? launch_layer_persistent<EPI_FIELD>(mA, mB, mA2, mW, ea, M, N, K, err, timeout_ns, st)
+                       : launch_tc_bn<EPI_FIELD>(BN, mA, mB, mA2, mW, ea, M, N, K, 1, err, timeout_ns, st);
     default: return cudaErrorInvalidValue;
   }
 }
