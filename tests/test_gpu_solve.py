@@ -144,3 +144,20 @@ def test_grazing_incidence_is_reported(cuda_device):
         s.incident(_c(img), "x")  # x-polarised: p_x nonzero at s_z = 0
     assert e.value.status == 6
     s.close()
+
+
+def test_medium_sample_eleven_orders(cuda_device):
+    """A larger case (11 x 11 orders, 4M = 484 modes per layer, 5 layers of
+    ellipsoids on a 32 x 32 grid, focused beam): several eigen-workers and
+    longer connection products."""
+    U, L = 11, 5
+    vol = wl.ellipsoid_volume(21, 32, 32, L)
+    zb = np.arange(L + 1) * 0.25
+    img = wl.gaussian_beam_image(32, 8.0, 1.0, 0.5)
+    sol = cw.solve(vol, zb, 1.0, 8.0, 8.0, U, U, img)
+    p_inc, out, t = _gpu_solve(vol, zb, 1.0, 8.0, 8.0, U, U, img)
+    zp = np.array([-0.3, 0.1, 0.6, 1.1, 1.5])
+    err, serr = _compare(sol, p_inc, out, 64, 64, zp, tol_p=1e-7)
+    print("medium", err, serr, t)
+    assert max(err) <= 1e-5
+    assert serr <= 1e-6
