@@ -500,10 +500,19 @@ def run_solve(args, dev, with_oracle):
     wall = time.perf_counter() - t0
     t = s.times()
     s.close()
+    N4 = 4 * p.U * p.V
+    # connection step per layer: LU of T (2/3 N^3), the solve with N right-hand sides (2 N^3) and the
+    # product with B (N^3) complex multiply-adds, 8 real flops each
+    conn_flops = L * (2.0 / 3.0 + 2.0 + 1.0) * N4 ** 3 * 8
+    fp64_peak = 1.25  # TFLOP/s, the nominal FP64 rate of the part (no measured FP64 peak is recorded)
     res = {"workload": "single_wavelength_sample_64x64x32_21x21_orders", "layers": L, "modes_per_layer": 4 * p.U * p.V,
            "gpu_s": wall, "gpu_step_ms": {k: t[k] for k in ("fourier_ms", "modes_ms", "connect_ms", "system_ms",
                                                              "alpha_ms", "erows_ms", "total_ms")},
            "eig_ms_per_layer_effective": t["modes_ms"] / L,
+           "roofline": {"kernel": "connection step (getrf, getrs, zgemm)", "bound": "fp64",
+                        "achieved": conn_flops / (t["connect_ms"] * 1e-3) / 1e12, "peak": fp64_peak,
+                        "unit": "TFLOP/s", "frac": conn_flops / (t["connect_ms"] * 1e-3) / 1e12 / fp64_peak,
+                        "traffic": None, "peak_source": "nominal FP64 rate"},
            "arith": "FP64 (complex128); eigendecompositions of the 2M x 2M reduced problem, 8 worker threads"}
     if with_oracle:
         from oracle import cw
