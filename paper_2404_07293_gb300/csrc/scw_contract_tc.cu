@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int t_begin = cta_off[blockIdx.x], t_end = cta_off[blockIdx.x + 1];
   const uint64_t deadline = ptx::globaltimer() + timeout_ns;
+  ptx::griddep_launch_dependents();  // the x-pass may be scheduled as CTAs of this grid finish
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
@@ -114,6 +115,22 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
     int st = 0;
     uint32_t ph = 0;
     int issued = 0, skipped = -1;
+    // W does not depend on the phase kernel that precedes this grid (programmatic launch): the first
+    // ring of stages gets its A copies at once, their B copies follow once that kernel has finished
+    bool dep_done = false;
+    int npend = 0;
+    uint32_t pend_sb[STAGES], pend_fb[STAGES];
+    const uint16_t* pend_bh[STAGES];
+    const uint16_t* pend_bl[STAGES];
+    auto flush_pending = [&]() {
+      ptx::griddep_wait();
+      for (int q = 0; q < npend; ++q) {
+        ptx::bulk_load(pend_sb[q], pend_bh[q], Cfg::B_BYTES, pend_fb[q], pol_b);
+        ptx::bulk_load(pend_sb[q] + Cfg::B_BYTES, pend_bl[q], Cfg::B_BYTES, pend_fb[q], pol_b);
+      }
+      npend = 0;
+      dep_done = true;
+    };
     for (int t = t_begin; t < t_end && !abort_s; ++t) {
       const int4 tk = tasks[t];
       const ItemDev& it = BATCH ? items[tk.x] : one;
@@ -146,8 +163,16 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
           if (SPLIT) ptx::bulk_load(sa + Cfg::A_BYTES, Al + ao, a_bytes, fb, pol_a);
           const uint32_t sb = sa + Cfg::NA * Cfg::A_BYTES;
           const size_t bo = b0 + (size_t)kc * NB * 64;
-          ptx::bulk_load(sb, Bh + bo, Cfg::B_BYTES, fb, pol_b);
-          ptx::bulk_load(sb + Cfg::B_BYTES, Bl + bo, Cfg::B_BYTES, fb, pol_b);
+          if (dep_done) {
+            ptx::bulk_load(sb, Bh + bo, Cfg::B_BYTES, fb, pol_b);
+            ptx::bulk_load(sb + Cfg::B_BYTES, Bl + bo, Cfg::B_BYTES, fb, pol_b);
+          } else {
+            pend_sb[npend] = sb;
+            pend_fb[npend] = fb;
+            pend_bh[npend] = Bh + bo;
+            pend_bl[npend] = Bl + bo;
+            if (++npend == STAGES) flush_pending();
+          }
         }
         ++issued;
         if (++st == STAGES) {
@@ -156,6 +181,7 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
         }
       }
     }
+    if (!dep_done) flush_pending();  // fewer stages than the ring, or an early stop
     if (abort_s) {
       // let the last issued copies land before the CTA's shared memory goes away
       const uint64_t d2 = ptx::drain_deadline(timeout_ns);
@@ -287,15 +313,15 @@ static cudaError_t launch_tc_t(const ItemDev& one, const ItemDev* items, const T
   if (items) {
     e = allow_max_smem(reinterpret_cast<const void*>(contract_tc_kernel<NB, SPLIT, true>));
     if (e != cudaSuccess) return e;
-    contract_tc_kernel<NB, SPLIT, true><<<s.grid, 192, Cfg::SMEM, st>>>(one, items, s.d_tasks, s.d_cta_off, err,
-                                                                       timeout_ns, inject);
+    e = launch_pdl(contract_tc_kernel<NB, SPLIT, true>, dim3(s.grid), dim3(192), Cfg::SMEM, st, one, items,
+                   (const int4*)s.d_tasks, (const int*)s.d_cta_off, err, timeout_ns, inject);
   } else {
     e = allow_max_smem(reinterpret_cast<const void*>(contract_tc_kernel<NB, SPLIT, false>));
     if (e != cudaSuccess) return e;
-    contract_tc_kernel<NB, SPLIT, false><<<s.grid, 192, Cfg::SMEM, st>>>(one, nullptr, s.d_tasks, s.d_cta_off, err,
-                                                                        timeout_ns, inject);
+    e = launch_pdl(contract_tc_kernel<NB, SPLIT, false>, dim3(s.grid), dim3(192), Cfg::SMEM, st, one,
+                   (const ItemDev*)nullptr, (const int4*)s.d_tasks, (const int*)s.d_cta_off, err, timeout_ns, inject);
   }
-  return cudaGetLastError();
+  return e;
 }
 
 template <bool SPLIT>

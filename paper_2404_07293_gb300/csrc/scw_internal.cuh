@@ -8,6 +8,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/scw.h"
@@ -166,6 +167,24 @@ __host__ __device__ __forceinline__ int fold_order(int pos, int n, int np) {
   if (pos <= n - 1 - h) return pos + h;
   if (pos >= np - h) return pos - np + h;
   return -1;
+}
+
+// Launch with programmatic stream serialisation (the kernel may start before its predecessor on
+// the stream ends and waits for it with griddepcontrol.wait before reading its results).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 // Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum,

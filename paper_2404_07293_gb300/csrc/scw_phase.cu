@@ -113,6 +113,7 @@ __global__ void __launch_bounds__(128) phases_tc_kernel(const __grid_constant__ 
                                                         const ItemDev* __restrict__ items,
                                                         const int2* __restrict__ entries, int F_pad) {
   __shared__ PlaneOffsets off;
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the contraction may start streaming W
   const int2 e = entries[blockIdx.y];
   const ItemDev& it = BATCH ? items[e.x] : one;
   const LayerUnit u = it.units[e.y];

@@ -226,8 +226,10 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
   const int Q = Fx >> 3;
   const bool staged = xpass_twiddles_staged(Up, Fx);
   float2* tw_s = xs_row + V * Up;
+  ptx::griddep_launch_dependents();
   if (staged)
     for (int i = threadIdx.x; i < Up * Q; i += blockDim.x) tw_s[i] = __ldg(it.twx + i);
+  ptx::griddep_wait();  // the partial spectra come from the preceding contraction
   const float2* src = it.S_part + (size_t)f * 3 * M + (size_t)c * M;
   const int ns = it.nsplit[f];
   const size_t stride = it.split_stride;
@@ -404,6 +406,7 @@ __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_c
   extern __shared__ float4 ys_buf[];  // 2 x ([Vp][32] float4 rows = [Vp][64] complex, then the twiddles)
   int t = blockIdx.x;
   if (t >= n_tiles) return;
+  ptx::griddep_wait();  // the x-pass rows come from the preceding kernel
   ypass_prefetch<BATCH, STW>(one, items, entries, t, n_tiles, nxb, rows_f4, ys_buf);
   for (int b = 0; t < n_tiles; t += gridDim.x, b ^= 1) {
     ypass_prefetch<BATCH, STW>(one, items, entries, t + gridDim.x, n_tiles, nxb, rows_f4,
@@ -447,11 +450,14 @@ cudaError_t launch_xpass(const ItemDev& one, const ItemDev* items, const int2* d
   if (items) {
     e = allow_max_smem(reinterpret_cast<const void*>(xpass_kernel<true>));
     if (e != cudaSuccess) return e;
-    xpass_kernel<true><<<dim3(n_entries, 3), 256, xs, st>>>(one, items, d_entries);
+    e = launch_pdl(xpass_kernel<true>, dim3(n_entries, 3), dim3(256), xs, st, one, items, d_entries);
+    if (e != cudaSuccess) return e;
   } else {
     e = allow_max_smem(reinterpret_cast<const void*>(xpass_kernel<false>));
     if (e != cudaSuccess) return e;
-    xpass_kernel<false><<<dim3(n_entries, 3), 256, xs, st>>>(one, nullptr, d_entries);
+    e = launch_pdl(xpass_kernel<false>, dim3(n_entries, 3), dim3(256), xs, st, one, (const ItemDev*)nullptr,
+                   d_entries);
+    if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
 }
@@ -479,12 +485,11 @@ static cudaError_t launch_ypass_t(const ItemDev& one, const ItemDev* items, cons
   if (e != cudaSuccess) return e;
   const int grid = (int)std::min<long long>(tiles, (long long)std::max(1, per_sm) * sms);
   if (items)
-    ypass_kernel<true, PAIR, TILED, STW><<<grid, 256, smem, st>>>(one, items, d_entries, (int)tiles, nxb, rows_f4,
-                                                                 buf_f4, nullptr, d_outs);
-  else
-    ypass_kernel<false, PAIR, TILED, STW><<<grid, 256, smem, st>>>(one, nullptr, d_entries, (int)tiles, nxb, rows_f4,
-                                                                  buf_f4, out_one, nullptr);
-  return cudaGetLastError();
+    return launch_pdl(ypass_kernel<true, PAIR, TILED, STW>, dim3(grid), dim3(256), smem, st, one, items, d_entries,
+                      (int)tiles, nxb, rows_f4, buf_f4, (float2*)nullptr, d_outs);
+  return launch_pdl(ypass_kernel<false, PAIR, TILED, STW>, dim3(grid), dim3(256), smem, st, one,
+                    (const ItemDev*)nullptr, d_entries, (int)tiles, nxb, rows_f4, buf_f4, out_one,
+                    (float2* const*)nullptr);
 }
 
 template <bool PAIR>
