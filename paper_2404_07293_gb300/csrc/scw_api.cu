@@ -297,8 +297,19 @@ static scw_status finish_item(Plan* p) {
     p->d_nsplit = nullptr;
   }
   const size_t M = p->M;
-  std::vector<int> nsplit(p->Fz);
-  for (int f = 0; f < p->Fz; ++f) nsplit[f] = (p->plane_region[f] >= 0 && p->plane_region[f] < p->L) ? p->k_split : 1;
+  // per-unit K splits (the contraction's tasks and the partials the x-pass sums per plane)
+  if ((int)p->unit_ks.size() != (int)p->units.size()) p->unit_ks.clear();
+  std::vector<int> nsplit(p->Fz, 1);
+  int ks_max = 1;
+  for (size_t u = 0; u < p->units.size(); ++u) {
+    const int ks = p->unit_ks.empty() ? p->k_split : p->unit_ks[u];
+    p->units[u].ks = ks;
+    ks_max = std::max(ks_max, ks);
+    for (int f = p->units[u].f0; f < p->units[u].f0 + p->units[u].nf; ++f) nsplit[f] = ks;
+  }
+  p->k_split = std::max(p->k_split, ks_max);
+  if (!p->units.empty())
+    SCW_TRY(cudaMemcpy(p->d_units, p->units.data(), p->units.size() * sizeof(LayerUnit), cudaMemcpyHostToDevice));
   SCW_TRY(upload(&p->d_nsplit, nsplit, tot));
   SCW_TRY(dalloc(&p->S_part, (size_t)p->k_split * p->Fz * 3 * M, tot));
   SCW_TRY(cudaMemset(p->S_part, 0, (size_t)p->k_split * p->Fz * 3 * M * sizeof(float2)));
@@ -376,16 +387,20 @@ struct TaskCost {
   int4 t;
 };
 
-static void item_tasks(const Plan* p, int item, int ks, std::vector<TaskCost>& out) {
+// Tasks of one item; uks (optional) gives each unit its own K split instead of ks.
+static void item_tasks(const Plan* p, int item, int ks, std::vector<TaskCost>& out,
+                       const std::vector<int>* uks = nullptr) {
   const int nk = (8 * p->M + 63) / 64;
-  const int per = (nk + ks - 1) / ks;
   const int tiles = (3 * p->M + 127) / 128;
-  for (int u = 0; u < (int)p->units.size(); ++u)
+  for (int u = 0; u < (int)p->units.size(); ++u) {
+    const int k = uks ? (*uks)[u] : ks;
+    const int per = (nk + k - 1) / k;
     for (int t = 0; t < tiles; ++t)
-      for (int s = 0; s < ks; ++s) {
+      for (int s = 0; s < k; ++s) {
         const int kc = std::max(0, std::min(nk, s * per + per) - s * per);
         out.push_back({kc + 2.0, make_int4(item, u, t, s)});  // +2 stages: epilogue and hand-off
       }
+  }
 }
 
 // Longest-processing-time-first assignment of tasks to G persistent CTAs.
@@ -441,7 +456,8 @@ static double model_makespan(const std::vector<Plan*>& items, const std::vector<
 static scw_status upload_schedule(const std::vector<Plan*>& items, int NB, bool bf16, TcSchedule& s,
                                   int ctas_per_sm = 0, int unit_begin = 0, int unit_end = 0) {
   std::vector<TaskCost> t;
-  for (size_t i = 0; i < items.size(); ++i) item_tasks(items[i], (int)i, items[i]->k_split, t);
+  for (size_t i = 0; i < items.size(); ++i)
+    item_tasks(items[i], (int)i, items[i]->k_split, t, items[i]->unit_ks.empty() ? nullptr : &items[i]->unit_ks);
   if (unit_begin < unit_end) {
     std::vector<TaskCost> keep;
     for (const auto& tc : t)
@@ -783,6 +799,7 @@ static scw_status choose_splits(scw_plan_t P, bool timed, const std::vector<int>
     }
     return SCW_OK;
   }
+  for (auto* p : P->items) p->unit_ks.clear();
   bool all_user = true;
   for (int k : user_ks) all_user = all_user && k > 0;
   std::vector<int> best_ks;
@@ -863,6 +880,39 @@ static scw_status choose_splits(scw_plan_t P, bool timed, const std::vector<int>
     for (size_t i = 0; i < P->items.size(); ++i)
       if (user_ks[i] > 0) best_ks[i] = user_ks[i];
     P->tune_report += "; chosen T=" + std::to_string(chosen) + (cached ? " (cached)" : "");
+  }
+  // A single plan's tasks rarely divide evenly over the persistent CTAs. Mixing two neighbouring
+  // splits over the units (x units with b = a + 1, the rest with a) gives LPT tasks of two sizes
+  // to pack; keep the mix whose modelled makespan is lowest (ties: the uniform split).
+  if (!P->batched && user_ks[0] <= 0 && !P->items[0]->units.empty()) {
+    Plan* p = P->items[0];
+    const int k = best_ks[0], nu = (int)p->units.size();
+    auto makespan = [&](const std::vector<int>& uks) {
+      std::vector<TaskCost> t;
+      item_tasks(p, 0, k, t, &uks);
+      std::vector<int> off;
+      std::vector<int4> order;
+      double mx = 0, mean = 0;
+      lpt(t, schedule_grid((int)t.size(), P->NB, P->bf16), off, order, mx, mean);
+      return mx;
+    };
+    std::vector<int> best(nu, k);
+    double best_ms = makespan(best);
+    const int step = std::max(1, nu / 64);
+    for (int a = std::max(1, k - 1); a <= k; ++a)
+      for (int x = 0; x <= nu; x += step) {
+        std::vector<int> uks(nu);
+        for (int u = 0; u < nu; ++u) uks[u] = u < x ? a + 1 : a;
+        const double ms = makespan(uks);
+        if (ms < best_ms - 1e-9) {
+          best_ms = ms;
+          best = uks;
+        }
+      }
+    if (best != std::vector<int>(nu, k)) {
+      p->unit_ks = best;
+      P->tune_report += "; unit splits mixed (modelled makespan " + std::to_string(best_ms) + ")";
+    }
   }
   for (size_t i = 0; i < P->items.size(); ++i) {
     P->items[i]->k_split = best_ks[i];

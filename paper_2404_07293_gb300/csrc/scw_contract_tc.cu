@@ -50,7 +50,8 @@ struct TaskGeom {
 __device__ __forceinline__ TaskGeom task_geom(const int4 tk, const ItemDev& it) {
   TaskGeom g;
   const LayerUnit u = it.units[tk.y];
-  const int per = (it.nk + it.k_split - 1) / it.k_split;
+  const int ks = u.ks > 0 ? u.ks : it.k_split;
+  const int per = (it.nk + ks - 1) / ks;
   g.kb = tk.w * per;
   g.kcount = max(0, min(it.nk, g.kb + per) - g.kb);
   g.layer = u.layer;

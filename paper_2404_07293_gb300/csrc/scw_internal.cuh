@@ -34,7 +34,7 @@ struct LayerUnit {
   int layer;
   int f0;
   int nf;
-  int pad;
+  int ks;  // K splits of this unit's contraction tasks (tensor-core plans; 0 = the item's k_split)
 };
 
 // Everything a kernel needs to know about one synthesis item. Kernels take it
@@ -88,7 +88,8 @@ struct Plan {
   std::vector<LayerUnit> units;
   int F_pad = 8;      // plane slots per layer (multiple of 8)
   int NB = 16;        // 2 * F_pad: real columns of the tensor-core B operand
-  int k_split = 1;
+  int k_split = 1;                // the largest K split over the units (S_part holds that many partials)
+  std::vector<int> unit_ks;        // per-unit K split (tensor-core plans; empty = k_split everywhere)
   int n_exterior = 0;
 
   // device tables
