@@ -160,17 +160,22 @@ __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__
                          : make_float2(0.f, 0.f);
   }
   __syncthreads();
+  // thread (samples w + 8 j, o = lane): each R element loaded once feeds the four samples
+  float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+  for (int i = 0; i < C; ++i) {
+    const float2 r = Rs[i][lane];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const float2 v = Vs[w + 8 * j][i];
+      re[j] = fmaf(r.x, v.x, fmaf(-r.y, v.y, re[j]));
+      im[j] = fmaf(r.x, v.y, fmaf(r.y, v.x, im[j]));
+    }
+  }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
-    const int s = w + 8 * j, b = b0 + s;
-    float re = 0.f, im = 0.f;
-#pragma unroll 8
-    for (int i = 0; i < C; ++i) {
-      const float2 r = Rs[i][lane], v = Vs[s][i];
-      re = fmaf(r.x, v.x, fmaf(-r.y, v.y, re));
-      im = fmaf(r.x, v.y, fmaf(r.y, v.x, im));
-    }
-    if (b < B) st_pair(Wh, (((size_t)b * C + lane) * Kp) / 2 + k, make_float2(scale * re, scale * im));
+    const int b = b0 + w + 8 * j;
+    if (b < B) st_pair(Wh, (((size_t)b * C + lane) * Kp) / 2 + k, make_float2(scale * re[j], scale * im[j]));
   }
 }
 
@@ -201,31 +206,42 @@ __global__ void __launch_bounds__(256) mix_bwd_kernel(const float2* __restrict__
     Vs[row][col] = b < B ? ld_spec(Vh, off, splits, split_stride) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  // GVh: thread (s = w + 8 j, i = lane)
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int s = w + 8 * j, b = b0 + s;
-    float re = 0.f, im = 0.f;
+  // GVh: thread (samples w + 8 j, i = lane); each R element loaded once feeds the four samples
+  {
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
     for (int o = 0; o < C; ++o) {
-      const float2 r = Rs[o][lane], g = Gs[s][o];  // conj(r) g
-      re = fmaf(r.x, g.x, fmaf(r.y, g.y, re));
-      im = fmaf(r.x, g.y, fmaf(-r.y, g.x, im));
-    }
-    if (b < B) st_pair(GVh, (((size_t)b * C + lane) * Kp) / 2 + k, make_float2(re, im));
-  }
-  // dR: thread (o = w + 8 j, i = lane), summed over the block's samples
+      const float2 r = Rs[o][lane];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int o = w + 8 * j;
-    float re = 0.f, im = 0.f;
+      for (int j = 0; j < 4; ++j) {
+        const float2 g = Gs[w + 8 * j][o];  // conj(r) g
+        re[j] = fmaf(r.x, g.x, fmaf(r.y, g.y, re[j]));
+        im[j] = fmaf(r.x, g.y, fmaf(-r.y, g.x, im[j]));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int b = b0 + w + 8 * j;
+      if (b < B) st_pair(GVh, (((size_t)b * C + lane) * Kp) / 2 + k, make_float2(re[j], im[j]));
+    }
+  }
+  // dR: thread (outputs o = w + 8 j, i = lane), summed over the block's samples; each V element
+  // loaded once feeds the four outputs
+  {
+    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
     for (int s = 0; s < MIX_SAMPLES; ++s) {
-      const float2 g = Gs[s][o], v = Vs[s][lane];  // g conj(v)
-      re = fmaf(g.x, v.x, fmaf(g.y, v.y, re));
-      im = fmaf(g.y, v.x, fmaf(-g.x, v.y, im));
+      const float2 v = Vs[s][lane];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float2 g = Gs[s][w + 8 * j];  // g conj(v)
+        re[j] = fmaf(g.x, v.x, fmaf(g.y, v.y, re[j]));
+        im[j] = fmaf(g.y, v.x, fmaf(-g.x, v.y, im[j]));
+      }
     }
-    reinterpret_cast<float2*>(part + row0)[((size_t)k * C + o) * C + lane] = make_float2(re, im);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      reinterpret_cast<float2*>(part + row0)[((size_t)k * C + w + 8 * j) * C + lane] = make_float2(re[j], im[j]);
   }
   if (k == kdc && t < C) {
     float d = 0.f;
