@@ -237,6 +237,15 @@ scw_status scw_synthesize_host(scw_plan_t plan, const void* W, const void* gamma
 scw_status scw_plan_set_points(scw_plan_t plan, const double* xy, int n_points);
 scw_status scw_synthesize_points(scw_plan_t plan, void* out, void* stream);
 
+/* Scattered points in 3-D: plane is a HOST int [P] array (after scw_plan_set_points) giving each
+ * point the index of its z plane in the plan's z_planes, so that point p is evaluated at
+ * (x_p, y_p, z_planes[plane[p]]) only. scw_synthesize_points then writes out as DEVICE complex64
+ * [I][3][P]: per (point, illumination) one M-term sum of the plane's spectrum (partials of the
+ * contraction summed) against the point's row of the point table, on the CUDA cores. NULL returns
+ * to every point on every plane. SCW_ERR_STATE without points; INVALID_ARGUMENT for an index
+ * outside [0, Fz). Synchronises. */
+scw_status scw_plan_set_point_planes(scw_plan_t plan, const int* plane);
+
 /* Synchronise `stream` and read (then clear) the plan's device error word:
  * SCW_OK, SCW_ERR_TIMEOUT (a bounded device wait ran out) or SCW_ERR_CUDA. */
 scw_status scw_plan_check(scw_plan_t plan, void* stream);

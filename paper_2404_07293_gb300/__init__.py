@@ -177,12 +177,22 @@ class Plan:
         return out
 
     # ------------------------------------------------------------- point sets
-    def set_points(self, xy):
-        """Lateral points (x, y) [P][2] at which synthesize_points evaluates the field on every z plane."""
+    def set_points(self, xy, plane=None):
+        """Lateral points (x, y) [P][2] at which synthesize_points evaluates the field on every z plane,
+        or, with ``plane`` (int [P], indices into z_planes), scattered 3-D points: point p only at
+        z_planes[plane[p]]."""
         xy = np.ascontiguousarray(np.asarray(xy, dtype=np.float64).reshape(-1, 2))
         check(self._lib.scw_plan_set_points(self._h, xy.ctypes.data_as(ctypes.c_void_p), int(xy.shape[0])),
               "scw_plan_set_points")
         self.n_points = int(xy.shape[0])
+        self.point_planes = None
+        if plane is not None:
+            pl = np.ascontiguousarray(np.asarray(plane, dtype=np.int32).reshape(-1))
+            if pl.shape[0] != self.n_points:
+                raise ValueError("plane must have one entry per point")
+            check(self._lib.scw_plan_set_point_planes(self._h, pl.ctypes.data_as(ctypes.c_void_p)),
+                  "scw_plan_set_point_planes")
+            self.point_planes = pl
 
     def set_xz_plane(self, y, n=None):
         """Points of the x-z plane at height y: x_i = x0 + i X / n (n = Fx by default)."""
@@ -195,6 +205,8 @@ class Plan:
         self.set_points(np.stack([np.full(n, float(x)), self.y0 + np.arange(n) * self.Y / n], axis=1))
 
     def points_shape(self):
+        if getattr(self, "point_planes", None) is not None:
+            return _per_illum(self.I, (3, self.n_points))
         return _per_illum(self.I, (3, self.Fz, self.n_points))
 
     def synthesize_points(self, out=None, stream=None):

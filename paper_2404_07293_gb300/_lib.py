@@ -80,6 +80,7 @@ SIGNATURES = {
     "scw_recompose": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "scw_plan_set_points": (c_int, [c_void_p, c_void_p, c_int]),
     "scw_synthesize_points": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "scw_plan_set_point_planes": (c_int, [c_void_p, c_void_p]),
     "scw_synthesize_host": (c_int, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
     "scw_plan_batched_create": (c_int, [POINTER(ScwDesc), c_int, POINTER(c_void_p)]),
     "scw_plan_batched_set_layers": (c_int, [c_void_p, c_int] + [c_void_p] * 6 + [c_void_p]),

@@ -1345,6 +1345,16 @@ scw_status scw_plan_set_points(scw_plan_t P, const double* xy, int n_points) {
   return points_build(&p->pts, *p, P->tc, xy, n_points, P->cap_stream);
 }
 
+scw_status scw_plan_set_point_planes(scw_plan_t P, const int* plane) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+  if (P->batched) return set_error(SCW_ERR_UNSUPPORTED, "point sets are for single plans");
+  Plan* p = P->items[0];
+  if (!p->pts) return set_error(SCW_ERR_STATE, "scw_plan_set_points has not been called");
+  cudaError_t e = cudaDeviceSynchronize();  // earlier calls may still read the old table
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");
+  return points_set_planes(*p->pts, plane, p->Fz_out, P->cap_stream);
+}
+
 scw_status scw_synthesize_points(scw_plan_t P, void* out, void* stream) {
   if (!P || !out) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and out are required");
   if (P->batched) return set_error(SCW_ERR_UNSUPPORTED, "point sets are for single plans");

@@ -119,10 +119,59 @@ __global__ void points_spectrum_fp32_kernel(const float2* __restrict__ S_part, s
 
 unsigned blocks_for(size_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
+// Scattered 3-D points: one warp per (point, illumination). E_c = sum_m S_c[m](z_f) phi_m(p) with
+// S of plane slot f = plane[p] I + il (the contraction's partials summed) and phi from the point
+// table (split-BF16 tables: hi + lo). out [I][3][P].
+template <bool TC>
+__global__ void points_scattered_kernel(const float2* __restrict__ S_part, size_t split_stride,
+                                        const int* __restrict__ nsplit, const int* __restrict__ plane,
+                                        const void* __restrict__ table, int P, int M, int Kp, int I,
+                                        float2* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  if (wid >= (long long)P * I) return;
+  const int p = (int)(wid % P), il = (int)(wid / P);
+  const int f = plane[p] * I + il;
+  const int ns = nsplit[f];
+  const float2* S = S_part + (size_t)f * 3 * M;
+  float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  for (int m = lane; m < M; m += 32) {
+    float2 ph;
+    if constexpr (TC) {
+      const __nv_bfloat162* row = static_cast<const __nv_bfloat162*>(table) + (size_t)p * 3 * (Kp / 2);
+      const __nv_bfloat162 hi = row[m], lo = row[Kp + m];  // segments hi | hi | lo of Kp / 2 pairs each
+      ph = make_float2(__bfloat162float(hi.x) + __bfloat162float(lo.x), __bfloat162float(hi.y) + __bfloat162float(lo.y));
+    } else {
+      ph = static_cast<const float2*>(table)[(size_t)p * M + m];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float2 s = make_float2(0.f, 0.f);
+      for (int k = 0; k < ns; ++k) {
+        const float2 t = S[(size_t)k * split_stride + (size_t)c * M + m];
+        s.x += t.x;
+        s.y += t.y;
+      }
+      acc[c].x = fmaf(s.x, ph.x, fmaf(-s.y, ph.y, acc[c].x));
+      acc[c].y = fmaf(s.x, ph.y, fmaf(s.y, ph.x, acc[c].y));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, o);
+      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, o);
+    }
+    if (lane == 0) out[((size_t)il * 3 + c) * P + p] = acc[c];
+  }
+}
+
 }  // namespace
 
 void points_free(PointTables* t) {
   if (!t) return;
+  if (t->d_plane) cudaFree(t->d_plane);
   if (t->d_xy) cudaFree(t->d_xy);
   if (t->A) cudaFree(t->A);
   if (t->B) cudaFree(t->B);
@@ -187,7 +236,22 @@ scw_status points_build(PointTables** out, const Plan& p, bool tc, const double*
   return SCW_OK;
 }
 
+scw_status points_set_planes(PointTables& t, const int* plane, int Fz_out, cudaStream_t st) {
+  if (!plane) {
+    if (t.d_plane) cudaFree(t.d_plane);
+    t.d_plane = nullptr;
+    return SCW_OK;
+  }
+  for (int i = 0; i < t.P; ++i)
+    if (plane[i] < 0 || plane[i] >= Fz_out) return set_error(SCW_ERR_INVALID_ARGUMENT, "point plane index out of range");
+  cudaError_t e = t.d_plane ? cudaSuccess : cudaMalloc(&t.d_plane, (size_t)t.P * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t.d_plane, plane, (size_t)t.P * sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? SCW_OK : cuda_error(e, "point planes");
+}
+
 cudaError_t points_prepare(const PointTables& t, const Plan& p, cudaStream_t st) {
+  if (t.d_plane) return cudaSuccess;  // scattered points read the partials directly
   const size_t n = (size_t)t.rows3 * p.M;
   const size_t stride = (size_t)p.Fz * 3 * p.M;
   if (t.tc)
@@ -201,6 +265,17 @@ cudaError_t points_prepare(const PointTables& t, const Plan& p, cudaStream_t st)
 
 cudaError_t points_product(const PointTables& t, const Plan& p, float2* out, int* err, uint64_t timeout_ns,
                            cudaStream_t st) {
+  if (t.d_plane) {
+    const size_t warps = (size_t)t.P * p.I;
+    const size_t stride = (size_t)p.Fz * 3 * p.M;
+    if (t.tc)
+      points_scattered_kernel<true><<<blocks_for(warps * 32, 256), 256, 0, st>>>(
+          p.S_part, stride, p.d_nsplit, t.d_plane, t.A, t.P, p.M, t.Kp, p.I, out);
+    else
+      points_scattered_kernel<false><<<blocks_for(warps * 32, 256), 256, 0, st>>>(
+          p.S_part, stride, p.d_nsplit, t.d_plane, t.A, t.P, p.M, t.Kp, p.I, out);
+    return cudaGetLastError();
+  }
   fno::EpiArgs ea{};
   ea.alpha = 1.f;
   ea.rows = t.P;

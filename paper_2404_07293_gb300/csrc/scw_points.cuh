@@ -15,6 +15,7 @@ struct PointTables {
   double2* d_xy = nullptr;
   void* A = nullptr;
   void* B = nullptr;
+  int* d_plane = nullptr;  // per-point output plane (scattered 3-D points), or null
   CUtensorMap mA, mB;
 };
 
@@ -23,7 +24,9 @@ scw_status points_build(PointTables** out, const Plan& p, bool tc, const double*
 void points_free(PointTables* t);
 // spectrum operand from the plan's partial spectra (after steps (a) and (b))
 cudaError_t points_prepare(const PointTables& t, const Plan& p, cudaStream_t st);
-// the point product into out [I][3][Fz][P] complex64
+// scattered 3-D points: plane [P] (host) -> d_plane; null clears
+scw_status points_set_planes(PointTables& t, const int* plane, int Fz_out, cudaStream_t st);
+// the point product into out [I][3][Fz][P] complex64 (or [I][3][P] with per-point planes)
 cudaError_t points_product(const PointTables& t, const Plan& p, float2* out, int* err, uint64_t timeout_ns,
                            cudaStream_t st);
 

@@ -2,7 +2,8 @@
 
 Eq. 10 evaluated at given lateral points on every z plane of a plan, as a
 dense product over the orders (split-BF16 tcgen05 GEMM on tensor-core plans,
-FP32 SIMT GEMM on FP32 plans), against the FP64 oracle's per-point sum.
+FP32 SIMT GEMM on FP32 plans), against the FP64 oracle's per-point sum; and
+scattered 3-D points, each evaluated on its own plane only.
 """
 import numpy as np
 import pytest
@@ -140,4 +141,33 @@ def test_point_errors(sphere, cuda_device):
     plan.set_points(np.zeros((0, 2)))  # released
     with pytest.raises(scw.ScwError):
         plan.synthesize_points()
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "split_bf16"])
+def test_scattered_3d_points(sphere, precision, cuda_device):
+    """Each point on its own plane: (x_p, y_p, z_planes[plane_p]) against the oracle, and against
+    the same points evaluated on every plane by the GEMM path."""
+    p, sol, zp = sphere
+    rng = np.random.default_rng(11)
+    P = 777
+    xy = rng.uniform(-sol.X, 2 * sol.X, size=(P, 2))
+    plane = rng.integers(0, len(zp), size=P)
+    plan = _plan(sol, p.Fx, p.Fy, zp, precision, exterior=True)
+    plan.set_layers(_c(sol.W, np.complex64), _c(sol.gamma), _c(sol.alpha), _c(sol.p_inc), _c(sol.p_ref),
+                    _c(sol.p_trn))
+    plan.set_points(xy)
+    full = plan.synthesize_points().cpu().numpy()          # [3][Fz][P]
+    plan.set_points(xy, plane=plane)
+    E = plan.synthesize_points().cpu().numpy()             # [3][P]
+    plan.check()
+    assert E.shape == (3, P)
+    ref = synth.field_points(sol, np.column_stack([xy, zp[plane]]))
+    err = _err(E, ref, precision)
+    print(precision, "scattered", err)
+    assert max(err) <= TOL[precision]
+    picked = full[:, plane, np.arange(P)]
+    assert np.linalg.norm(E - picked) / np.linalg.norm(picked) <= (1e-6 if precision == "fp32" else 1e-4)
+    with pytest.raises(Exception):
+        plan.set_points(xy, plane=np.full(P, len(zp)))      # index out of range
     plan.close()
