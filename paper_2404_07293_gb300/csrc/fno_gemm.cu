@@ -1,4 +1,5 @@
-// The surrogate's dense contractions: D = A B^T over K with a fused epilogue.
+// Dense contractions D = A B^T over K with a fused epilogue: the surrogate's
+// products and the point-set field product.
 //
 // Tensor-core form (BF16 mode). A and B are K-major BF16 matrices read by TMA
 // (2D tensor maps, 64-element = 128-byte inner box, 128-byte swizzle, zero fill
@@ -24,6 +25,9 @@
 //                        then + c and GELU in the epilogue                       (EPI_LAYER_FWD)
 //   backward of both     dV^T [N^2][B C]  = E . GVh^T + dZ_cl W, * GELU'(Z)      (EPI_LAYER_BWD)
 //   weight gradient      dW = sum_b dZ_b V_b^T over pixels, 4 samples per tile  (EPI_DW)
+// The field synthesis at arbitrary lateral points uses the same engine for its
+// product over the orders, E[point][(plane, component)] (EPI_FIELD, split-BF16
+// operands along a tripled K; see scw_points.cu).
 // SIMT form (FP32 test mode): the same products and the same epilogue code on
 // FP32 operands, 128 rows x 32 columns per CTA.
 #include <cudaTypedefs.h>
