@@ -43,7 +43,13 @@ struct scw_fno_s {
   void* dZcf[2] = {};
   void* dZcl[2] = {};
   float* part_tn = nullptr, *part_err = nullptr, *part_pool = nullptr, *part_proj = nullptr;
-  float* part_mix = nullptr, *part_dw = nullptr, *part_lift = nullptr, *part_head = nullptr, *scratch = nullptr;
+  float* part_lift = nullptr, *part_head = nullptr, *scratch = nullptr;
+  float* part_mix[8] = {};  // per layer: the gradient partials are reduced together after the backward pass
+  float* part_dw[8] = {};
+  size_t scratch_floats = 0;
+  // the backward pass's partial-sum reductions, all run by two launches at its end (per batch size)
+  RedSeg* d_segs = nullptr;
+  int segs_B = -1, nseg = 0, seg_items1 = 0, seg_items2 = 0;
   float* loss_d = nullptr, *h_d = nullptr, *rel2_d = nullptr;
   int* d_err = nullptr;
   uint64_t timeout_ns = 2000000000ull;
@@ -84,6 +90,9 @@ static cudaError_t falloc(scw_fno_s* f, void** p, size_t bytes) {
 static void free_all(scw_fno_s* f) {
   for (void* p : f->allocs) cudaFree(p);
   f->allocs.clear();
+  if (f->d_segs) cudaFree(f->d_segs);
+  f->d_segs = nullptr;
+  f->segs_B = -1;
   for (cudaEvent_t ev : f->events) cudaEventDestroy(ev);
   f->events.clear();
 }
@@ -236,12 +245,36 @@ static scw_status forward(scw_fno_s* f, const float2* n, int B, bool keep_z, cud
   return SCW_OK;
 }
 
-static scw_status reduce_into(scw_fno_s* f, const float* part, int rows, int width, long long pitch, float* out,
-                              cudaStream_t st) {
-  const int passes = rows > 256 ? 2 : 1;
-  cudaError_t e = launch_reduce_rows_ex(part, rows, width, pitch, 1.0f, out, f->scratch, st);
-  f->counter += passes - 1;
-  return launch_ok(f, e, "partial-sum reduction");
+// A reduction of the backward pass, queued for reduce_all.
+static void reduce_into(std::vector<RedSeg>& segs, const float* part, int rows, int width, long long pitch,
+                        float* out) {
+  RedSeg sg{};
+  sg.part = part;
+  sg.out = out;
+  sg.pitch = pitch;
+  sg.rows = rows;
+  sg.width = width;
+  segs.push_back(sg);
+}
+
+// Every queued reduction in two launches; the table is uploaded when the batch size changes.
+static scw_status reduce_all(scw_fno_s* f, std::vector<RedSeg>& segs, int B, cudaStream_t st) {
+  if (f->segs_B != B) {
+    if (!plan_reduce_segments(segs, f->scratch, f->scratch_floats, f->seg_items1, f->seg_items2))
+      return set_error(SCW_ERR_UNSUPPORTED, "reduction scratch too small");
+    if (f->d_segs) cudaFree(f->d_segs);
+    f->d_segs = nullptr;
+    cudaError_t e = cudaMalloc(&f->d_segs, segs.size() * sizeof(RedSeg));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(f->d_segs, segs.data(), segs.size() * sizeof(RedSeg), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // segs is a local table
+    if (e != cudaSuccess) return cuda_error(e, "reduction table");
+    f->nseg = (int)segs.size();
+    f->segs_B = B;
+  }
+  cudaError_t e = launch_reduce_segments(f->d_segs, f->nseg, f->seg_items1, f->seg_items2, st);
+  if (f->seg_items2) ++f->counter;
+  return launch_ok(f, e, "partial-sum reductions");
 }
 
 // ---------------------------------------------------------------- backward ---
@@ -251,20 +284,21 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
   FNO_TRY(forward<T>(f, n, B, true, st));
   const int BC = B * C, P = f->P, nblk = f->nblk;
+  std::vector<RedSeg> segs;
   FNO_TRY(launch_ok(f, launch_target_norm(target, f->part_tn, B, P, st), "target norm"));
   FNO_TRY(launch_ok(f, launch_project_train<T>(static_cast<const T*>(f->Vcl[f->L]), target, at<T>(f->wcopy, f->off_Q),
                                                f->part_tn, static_cast<T*>(f->dZcf[0]),
                                                static_cast<T*>(f->dZcl[0]), f->part_err, f->part_pool, f->part_proj, B,
                                                P, st),
                     "projection"));
-  FNO_TRY(reduce_into(f, f->part_proj, B * nblk, OUT * C + OUT, OUT * C + OUT, f->grad + f->off_Q, st));
+  reduce_into(segs, f->part_proj, B * nblk, OUT * C + OUT, OUT * C + OUT, f->grad + f->off_Q);
   FNO_TRY(launch_ok(f, launch_head<T>(f->part_tn, f->part_err, f->part_pool, at<T>(f->wcopy, f->off_e), f->part_head,
                                       f->h_d, f->rel2_d, B, P, st),
                     "error head"));
   e = cudaMemsetAsync(f->loss_d, 0, 4 * sizeof(float), st);
   if (e != cudaSuccess) return cuda_error(e, "cudaMemsetAsync");
-  FNO_TRY(reduce_into(f, f->part_head, B, C + 1, C + 3, f->grad + f->off_e, st));
-  FNO_TRY(reduce_into(f, f->part_head + C + 1, B, 2, C + 3, f->loss_d + 1, st));
+  reduce_into(segs, f->part_head, B, C + 1, C + 3, f->grad + f->off_e);
+  reduce_into(segs, f->part_head + C + 1, B, 2, C + 3, f->loss_d + 1);
   const long long ld = (long long)f->Bmax * C;
   const long long vstride = ld * (f->Kc / 2);
   const long long mix_w = (long long)f->m * f->m * C * C * 2;
@@ -290,23 +324,23 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     EpiArgs ew{};
     ew.rows = BC;
     ew.B = B;
-    ew.out = f->part_dw;
+    ew.out = f->part_dw[l];
     ew.splits = kw;
     e = f->bf16 ? launch_gemm_tc(EPI_DW, 128, f->map_dZcf[cur], f->map_Vcf[l], f->map_D, f->map_D, ew, groups * 128,
                                  groups * 128, P, kw, f->d_err, f->timeout_ns, st)
                 : launch_gemm_simt(EPI_DW, static_cast<const float*>(f->dZcf[cur]), P,
                                    static_cast<const float*>(f->Vcf[l]), P, ew, groups * 128, groups * 128, P, kw, st);
     FNO_TRY(launch_ok(f, e, "weight gradient", CAT_DW, 2.0 * BC * C * P));
-    FNO_TRY(reduce_into(f, f->part_dw, groups * kw * 4, C * C, C * C, f->grad + f->off_W[l], st));
+    reduce_into(segs, f->part_dw[l], groups * kw * 4, C * C, C * C, f->grad + f->off_W[l]);
     // mixing backward
     const int sb = mix_sample_blocks(B);
     FNO_TRY(launch_ok(f, launch_mix_bwd<T>(reinterpret_cast<const float2*>(f->GWh),
                                            reinterpret_cast<const float2*>(f->Vh[l]), ks, vstride, ld,
-                                           at<T>(f->wcopy, f->off_R[l]), static_cast<T*>(f->GVh), f->part_mix, B,
+                                           at<T>(f->wcopy, f->off_R[l]), static_cast<T*>(f->GVh), f->part_mix[l], B,
                                            f->m, f->Kp, f->N, st),
                       "mode mixing backward", CAT_MIX, 16.0 * f->m * f->m * C * C * B));
-    FNO_TRY(reduce_into(f, f->part_mix, sb, (int)mix_w, mix_w + C, f->grad + f->off_R[l], st));
-    FNO_TRY(reduce_into(f, f->part_mix + mix_w, sb, C, mix_w + C, f->grad + f->off_c[l], st));
+    reduce_into(segs, f->part_mix[l], sb, (int)mix_w, mix_w + C, f->grad + f->off_R[l]);
+    reduce_into(segs, f->part_mix[l] + mix_w, sb, C, mix_w + C, f->grad + f->off_c[l]);
     // dV_l = Re IDFT(GVh) + W^T dZ, times GELU'(Z_{l-1})
     EpiArgs eb{};
     eb.alpha = 1.f;
@@ -330,8 +364,8 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
                                           f->N, st),
                     "lift backward"));
   const int lift_rows = (B * f->in_grid * f->in_grid + 127) / 128;
-  FNO_TRY(reduce_into(f, f->part_lift, lift_rows, C * 2 * f->S + C, C * 2 * f->S + C, f->grad + f->off_P, st));
-  return SCW_OK;
+  reduce_into(segs, f->part_lift, lift_rows, C * 2 * f->S + C, C * 2 * f->S + C, f->grad + f->off_P);
+  return reduce_all(f, segs, B, st);
 }
 
 template <typename T>
@@ -451,11 +485,15 @@ scw_status scw_surrogate_create(const scw_fno_desc* d, scw_fno_t* out) {
   A((void**)&f->part_err, Bm * f->nblk * 4);
   A((void**)&f->part_pool, Bm * f->nblk * C * 4);
   A((void**)&f->part_proj, Bm * f->nblk * (OUT * C + OUT) * 4);
-  A((void**)&f->part_mix, (size_t)mix_sample_blocks(f->Bmax) * ((size_t)f->m * f->m * C * C * 2 + C) * 4);
+  for (int l = 0; l < f->L; ++l)
+    A((void**)&f->part_mix[l], (size_t)mix_sample_blocks(f->Bmax) * ((size_t)f->m * f->m * C * C * 2 + C) * 4);
   A(&f->WT, (size_t)f->L * C * C * esz);
-  A((void**)&f->part_dw, ((Bm + 3) / 4) * kMaxSplit * 4 * C * C * 4);
+  for (int l = 0; l < f->L; ++l) A((void**)&f->part_dw[l], ((Bm + 3) / 4) * kMaxSplit * 4 * C * C * 4);
   A((void**)&f->part_lift, ((Bm * f->in_grid * f->in_grid + 127) / 128) * (C * 2 * f->S + C) * 4);
-  A((void**)&f->scratch, (size_t)64 * 4096 * 4);
+  // reduction chunks: at most 64 rows of every reduced width, for the projection, the weight
+  // gradients of every layer and the lift
+  f->scratch_floats = (size_t)64 * ((OUT * C + OUT) + (size_t)f->L * C * C + (C * 2 * f->S + C) + 4096);
+  A((void**)&f->scratch, f->scratch_floats * 4);
   A((void**)&f->loss_d, 4 * 4);
   A((void**)&f->h_d, Bm * 4);
   A((void**)&f->rel2_d, Bm * 4);

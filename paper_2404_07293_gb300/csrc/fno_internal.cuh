@@ -269,6 +269,23 @@ cudaError_t launch_lift_bwd(const T* dV0cl, const float2* n, float* part, int B,
                             cudaStream_t st);
 cudaError_t launch_reduce_rows_ex(const float* part, int rows, int width, long long pitch, float scale, float* out,
                                   float* scratch, cudaStream_t st);
+
+// One deterministic partial-sum reduction out[j] += sum_r part[r pitch + j] of a set, all run by
+// two launches (reduce_segments). Rows above 256 are summed in ry chunks of `chunk` rows into
+// `scratch` ([ry][width]) and the chunks then in a second pass, with the same order of additions
+// as launch_reduce_rows_ex.
+struct RedSeg {
+  const float* part;
+  float* out;
+  float* scratch;
+  long long pitch;
+  int rows, width, ry, chunk;
+  int item1, item2;  // first item of this segment in pass 1 (gx ry blocks) and pass 2 (gx blocks, ry > 1)
+};
+// Fills ry, chunk, item1, item2 and the scratch slices (from `scratch`, of `scratch_floats`);
+// returns false if the scratch is too small.
+bool plan_reduce_segments(std::vector<RedSeg>& segs, float* scratch, size_t scratch_floats, int& items1, int& items2);
+cudaError_t launch_reduce_segments(const RedSeg* d_segs, int nseg, int items1, int items2, cudaStream_t st);
 template <typename T>
 cudaError_t launch_adam(float* master, const float* grad, float* m, float* v, T* copy, long long n, float lr,
                         float bc1, float bc2, cudaStream_t st);

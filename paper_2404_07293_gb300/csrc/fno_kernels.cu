@@ -642,6 +642,88 @@ cudaError_t launch_lift_bwd(const T* dV0cl, const float2* n, float* part, int B,
   return cudaGetLastError();
 }
 
+// Segmented form of reduce_rows_kernel: block b belongs to the last segment whose first item is <= b.
+__device__ __forceinline__ int find_segment(const RedSeg* segs, int nseg, int b, bool second) {
+  int s = 0;
+  for (int i = 1; i < nseg; ++i)
+    if ((second ? segs[i].item2 : segs[i].item1) <= b && (!second || segs[i].ry > 1)) s = i;
+  return s;
+}
+
+__global__ void __launch_bounds__(256) reduce_segments_kernel(const RedSeg* __restrict__ segs, int nseg, int second) {
+  __shared__ float red[8][33];
+  const int b = blockIdx.x;
+  const int si = find_segment(segs, nseg, b, second != 0);
+  const RedSeg sg = segs[si];
+  const int gx = (sg.width + 31) / 32;
+  const float* src;
+  long long pitch;
+  int r0, r1, cb, k;
+  if (!second) {
+    const int local = b - sg.item1;
+    k = local / gx;
+    cb = local - k * gx;
+    src = sg.part;
+    pitch = sg.pitch;
+    r0 = k * sg.chunk;
+    r1 = min(sg.rows, r0 + sg.chunk);
+  } else {
+    k = 0;
+    cb = b - sg.item2;
+    src = sg.scratch;
+    pitch = sg.width;
+    r0 = 0;
+    r1 = sg.ry;
+  }
+  const int col = cb * 32 + threadIdx.x;
+  float s = 0.f;
+  if (col < sg.width)
+    for (int r = r0 + threadIdx.y; r < r1; r += 8) s += src[(size_t)r * pitch + col];
+  red[threadIdx.y][threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.y == 0 && col < sg.width) {
+    float t = 0.f;
+    for (int y = 0; y < 8; ++y) t += red[y][threadIdx.x];
+    if (!second && sg.ry > 1)
+      sg.scratch[(size_t)k * sg.width + col] = t;
+    else
+      sg.out[col] += t;
+  }
+}
+
+bool plan_reduce_segments(std::vector<RedSeg>& segs, float* scratch, size_t scratch_floats, int& items1,
+                          int& items2) {
+  items1 = items2 = 0;
+  size_t used = 0;
+  for (auto& sg : segs) {
+    const int gx = (sg.width + 31) / 32;
+    if (sg.rows <= 256) {
+      sg.ry = 1;
+      sg.chunk = sg.rows;
+      sg.scratch = nullptr;
+    } else {
+      sg.ry = std::min(64, (sg.rows + 255) / 256);
+      sg.chunk = (sg.rows + sg.ry - 1) / sg.ry;
+      sg.scratch = scratch + used;
+      used += (size_t)sg.ry * sg.width;
+    }
+    sg.item1 = items1;
+    items1 += gx * sg.ry;
+    sg.item2 = items2;
+    if (sg.ry > 1) items2 += gx;
+  }
+  return used <= scratch_floats;
+}
+
+cudaError_t launch_reduce_segments(const RedSeg* d_segs, int nseg, int items1, int items2, cudaStream_t st) {
+  if (nseg == 0 || items1 == 0) return cudaSuccess;
+  reduce_segments_kernel<<<items1, dim3(32, 8), 0, st>>>(d_segs, nseg, 0);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || items2 == 0) return e;
+  reduce_segments_kernel<<<items2, dim3(32, 8), 0, st>>>(d_segs, nseg, 1);
+  return cudaGetLastError();
+}
+
 // out[j] += scale * sum_r part[r pitch + j]; rows above 256 go through `scratch`
 // (64 rows of `width`) in a second pass so that no thread sums more than ~32 rows.
 cudaError_t launch_reduce_rows_ex(const float* part, int rows, int width, long long pitch, float scale, float* out,
