@@ -107,6 +107,7 @@ static double uniform_pm1(unsigned long long seed, unsigned long long i) {
 }
 
 static int dft_splits(const scw_fno_s* f, int B, int BN) {
+  if (f->bf16 && BN == 256) return 1;  // the persistent GEMM form: deep pipeline, no K splits
   const int tiles = ((B * C + 127) / 128) * ((f->Kc + BN - 1) / BN);
   int ks = std::max(1, (2 * 152) / std::max(1, tiles));
   ks = std::min(ks, kMaxSplit);

@@ -295,8 +295,9 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
   const uint64_t deadline = ptx::globaltimer() + timeout_ns;
   constexpr bool SEG2 = (EPI == EPI_LAYER_FWD || EPI == EPI_LAYER_BWD);
   // the layer products walk the row tiles fastest (CTAs in flight share a Wh / GVh tile); the
-  // field product walks the column tiles fastest (they share a row tile of the points table)
-  constexpr bool NFAST = (EPI == EPI_FIELD);
+  // field product and the truncated DFT walk the column tiles fastest (they share a row tile of
+  // the points table / the activations)
+  constexpr bool NFAST = (EPI == EPI_FIELD || EPI == EPI_MODES);
   auto tile_m0 = [&](int t) { return (NFAST ? t / n_tiles : t % m_tiles) * 128; };
   auto tile_n0 = [&](int t) { return (NFAST ? t % n_tiles : t / m_tiles) * BN; };
   auto tile_nseg = [&](int n0) { return SEG2 ? max(0, min(BN / C, ea.B - n0 / C)) : 0; };
@@ -588,7 +589,11 @@ cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtenso
   // the 1x1 segment shares the accumulator: the DFT part must come pre-scaled (alpha 1)
   if (layer && (splits != 1 || BN != 256 || ea.alpha != 1.0f)) return cudaErrorInvalidValue;
   switch (epi) {
-    case EPI_MODES: return launch_tc_bn<EPI_MODES>(BN, mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
+    case EPI_MODES:
+      // BN 256 without K splits: the persistent form (four stages, overlapped epilogue)
+      if (BN == 256 && splits == 1)
+        return launch_layer_persistent<EPI_MODES>(mA, mB, mA2, mW, ea, M, N, K, err, timeout_ns, st);
+      return launch_tc_bn<EPI_MODES>(BN, mA, mB, mA2, mW, ea, M, N, K, splits, err, timeout_ns, st);
     case EPI_LAYER_FWD:
       return launch_layer_persistent<EPI_LAYER_FWD>(mA, mB, mA2, mW, ea, M, N, K, err, timeout_ns, st);
     case EPI_LAYER_BWD:
