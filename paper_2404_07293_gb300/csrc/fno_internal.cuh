@@ -115,10 +115,28 @@ __device__ __forceinline__ void st32(T* p, const float (&v)[32]) {
   }
 }
 
-// GELU(z) = z Phi(z) and its derivative Phi(z) + z phi(z), Phi the standard normal CDF
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU(z) = z Phi(z) and its derivative Phi(z) + z phi(z), Phi the standard normal CDF and phi its
+// density. Phi(z) = (1 + sign(z) erf(|z| / sqrt 2)) / 2 with erf from Abramowitz & Stegun, Handbook of
+// Mathematical Functions, formula 7.1.26: erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2},
+// t = 1 / (1 + p x), x >= 0, |error| <= 1.5e-7. Its factor e^{-x^2} = e^{-z^2/2} is also phi(z) sqrt(2 pi),
+// so GELU' costs one exponential and one reciprocal.
+__device__ __forceinline__ void normal_cdf_and_gauss(float z, float& Phi, float& E) {
+  const float x = fabsf(z) * 0.70710678118654752f;
+  const float t = __fdividef(1.f, fmaf(0.3275911f, x, 1.f));
+  const float poly =
+      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+  E = __expf(-0.5f * z * z);
+  Phi = 0.5f + copysignf(0.5f * (1.f - poly * E), z);
+}
+__device__ __forceinline__ float gelu_f(float z) {
+  float Phi, E;
+  normal_cdf_and_gauss(z, Phi, E);
+  return z * Phi;
+}
 __device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+  float Phi, E;
+  normal_cdf_and_gauss(z, Phi, E);
+  return fmaf(z * 0.39894228040143268f, E, Phi);
 }
 
 // ---- epilogues, shared by the tensor-core and the SIMT GEMM ------------------------------

@@ -138,3 +138,24 @@ def test_conformal_offset_quantile():
     q = fno.conformal_offset(h, true_rel, miss=0.1)
     assert q == pytest.approx(8.9)                  # ceil(0.9 * 100) = 90th smallest
     assert np.mean(np.log(true_rel) <= q) >= 0.9
+
+
+def test_kernel_gelu_erf_approximation_error_bound():
+    """The surrogate kernels evaluate the normal CDF through Abramowitz & Stegun's formula 7.1.26
+    for erf (stated |error| <= 1.5e-7). Check that bound, and the GELU / GELU' it gives, against
+    the exact erf on a dense grid (the kernels' other rounding is FP32)."""
+    import math
+    z = np.linspace(-12.0, 12.0, 200001)
+    x = np.abs(z) / math.sqrt(2.0)
+    t = 1.0 / (1.0 + 0.3275911 * x)
+    poly = t * (0.254829592 + t * (-0.284496736 + t * (1.421413741 + t * (-1.453152027 + t * 1.061405429))))
+    E = np.exp(-0.5 * z * z)
+    erf_abs = 1.0 - poly * E
+    exact = np.array([math.erf(v) for v in x])
+    assert np.abs(erf_abs - exact).max() <= 1.5e-7
+    Phi = 0.5 + np.sign(z) * 0.5 * erf_abs
+    Phi_exact = 0.5 * (1.0 + np.array([math.erf(v / math.sqrt(2.0)) for v in z]))
+    assert np.abs(z * Phi - z * Phi_exact).max() <= 1.5e-7 * 12
+    grad = Phi + z * E / math.sqrt(2.0 * math.pi)
+    grad_exact = Phi_exact + z * E / math.sqrt(2.0 * math.pi)
+    assert np.abs(grad - grad_exact).max() <= 1e-7
