@@ -365,21 +365,30 @@ __global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restri
     for (int w = 0; w < 8; ++w) s += red[w];
     part_err[blk] = s;
   }
+  // block sums over the 256 pixels, four independent accumulators each (pixels q = 4 i + a),
+  // combined in a fixed order
   if (t < OUT * C) {
     const int j = t / C, o = t % C;
-    float s = 0.f;
-    for (int q = 0; q < PIX_BLOCK; ++q) s = fmaf(Fs[j][q], Vs[q][o], s);
-    part_proj[blk * (OUT * C + OUT) + t] = s;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+    for (int q = 0; q < PIX_BLOCK; q += 4)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) s[a] = fmaf(Fs[j][q + a], Vs[q + a][o], s[a]);
+    part_proj[blk * (OUT * C + OUT) + t] = (s[0] + s[1]) + (s[2] + s[3]);
   } else if (t < OUT * C + OUT) {
     const int j = t - OUT * C;
-    float s = 0.f;
-    for (int q = 0; q < PIX_BLOCK; ++q) s += Fs[j][q];
-    part_proj[blk * (OUT * C + OUT) + t] = s;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q < PIX_BLOCK; q += 4)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) s[a] += Fs[j][q + a];
+    part_proj[blk * (OUT * C + OUT) + t] = (s[0] + s[1]) + (s[2] + s[3]);
   } else if (t >= 224) {
     const int o = t - 224;
-    float s = 0.f;
-    for (int q = 0; q < PIX_BLOCK; ++q) s += Vs[q][o];
-    part_pool[blk * C + o] = s;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int q = 0; q < PIX_BLOCK; q += 4)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) s[a] += Vs[q + a][o];
+    part_pool[blk * C + o] = (s[0] + s[1]) + (s[2] + s[3]);
   }
 }
 
@@ -460,15 +469,19 @@ __global__ void __launch_bounds__(128) lift_bwd_kernel(const T* __restrict__ dV0
   const int width = C * cin + C;
   float* dst = part + (size_t)blockIdx.x * width;
   for (int q = threadIdx.x; q < width; q += 128) {
-    float s = 0.f;
+    float s[4] = {0.f, 0.f, 0.f, 0.f};  // four independent accumulators (pixels j = 4 i + k), fixed order
     if (q < C * cin) {
       const int o = q / cin, c = q % cin;
-      for (int j = 0; j < 128; ++j) s = fmaf(dv_s[j][o], a_s[j][c], s);
+      for (int j = 0; j < 128; j += 4)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s[k] = fmaf(dv_s[j + k][o], a_s[j + k][c], s[k]);
     } else {
       const int o = q - C * cin;
-      for (int j = 0; j < 128; ++j) s += dv_s[j][o];
+      for (int j = 0; j < 128; j += 4)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) s[k] += dv_s[j + k][o];
     }
-    dst[q] = s;
+    dst[q] = (s[0] + s[1]) + (s[2] + s[3]);
   }
 }
 
