@@ -299,6 +299,7 @@ struct RedSeg {
   long long pitch;
   int rows, width, ry, chunk;
   int item1, item2;  // first item of this segment in pass 1 (gx ry blocks) and pass 2 (gx blocks, ry > 1)
+  int wide;          // rows <= 8: each block takes 256 columns and each thread sums its column's rows
 };
 // Fills ry, chunk, item1, item2 and the scratch slices (from `scratch`, of `scratch_floats`);
 // returns false if the scratch is too small.

@@ -668,6 +668,16 @@ __global__ void __launch_bounds__(256) reduce_segments_kernel(const RedSeg* __re
   const int b = blockIdx.x;
   const int si = find_segment(segs, nseg, b, second != 0);
   const RedSeg sg = segs[si];
+  if (!second && sg.wide) {
+    // few rows: one thread per column, rows added in order (the same additions as the 8-way block form)
+    const int col = (b - sg.item1) * 256 + threadIdx.y * 32 + threadIdx.x;
+    if (col < sg.width) {
+      float t = 0.f;
+      for (int r = 0; r < sg.rows; ++r) t += sg.part[(size_t)r * sg.pitch + col];
+      sg.out[col] += t;
+    }
+    return;
+  }
   const int gx = (sg.width + 31) / 32;
   const float* src;
   long long pitch;
@@ -709,7 +719,8 @@ bool plan_reduce_segments(std::vector<RedSeg>& segs, float* scratch, size_t scra
   items1 = items2 = 0;
   size_t used = 0;
   for (auto& sg : segs) {
-    const int gx = (sg.width + 31) / 32;
+    sg.wide = sg.rows <= 8 ? 1 : 0;
+    const int gx = sg.wide ? (sg.width + 255) / 256 : (sg.width + 31) / 32;
     if (sg.rows <= 256) {
       sg.ry = 1;
       sg.chunk = sg.rows;
