@@ -548,15 +548,14 @@ scw_status scw_surrogate_create(const scw_fno_desc* d, scw_fno_t* out) {
     if (s == SCW_OK) s = make_map_bf16(&f->map_GVh, f->GVh, f->Kp, BCm, f->Kp, 256);
     for (int l = 0; l <= f->L && s == SCW_OK; ++l) s = make_map_bf16(&f->map_Vcf[l], f->Vcf[l], f->P, BCm, f->P, 128);
     for (int i = 0; i < 2 && s == SCW_OK; ++i) s = make_map_bf16(&f->map_dZcf[i], f->dZcf[i], f->P, BCm, f->P, 128);
-    const long long BPm = (long long)f->Bmax * f->P;
     for (int l = 0; l < f->L && s == SCW_OK; ++l) {
-      s = make_map_bf16(&f->map_Vcl[l], f->Vcl[l], C, BPm, C, 128, 32);
+      s = make_map_act3d(&f->map_Vcl[l], f->Vcl[l], f->P, f->Bmax);
       if (s == SCW_OK)
         s = make_map_bf16(&f->map_W[l], static_cast<__nv_bfloat16*>(f->wcopy) + f->off_W[l], C, C, C, C, 32);
       if (s == SCW_OK)
         s = make_map_bf16(&f->map_WT[l], static_cast<__nv_bfloat16*>(f->WT) + (size_t)l * C * C, C, C, C, C, 32);
     }
-    for (int i = 0; i < 2 && s == SCW_OK; ++i) s = make_map_bf16(&f->map_dZcl[i], f->dZcl[i], C, BPm, C, 128, 32);
+    for (int i = 0; i < 2 && s == SCW_OK; ++i) s = make_map_act3d(&f->map_dZcl[i], f->dZcl[i], f->P, f->Bmax);
     if (s != SCW_OK) {
       free_all(f);
       delete f;

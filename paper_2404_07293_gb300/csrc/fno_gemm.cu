@@ -14,7 +14,8 @@
 // The layer products add the 1x1 convolution as a second K segment: for each
 // sample s of the tile, D[:, 32 s .. 32 s + 32) += X_s W^T (X_s = that sample's
 // channel-last activations of the tile's 128 pixels, K = 32, 64-byte swizzle,
-// N = 32 MMAs into the sample's own accumulator columns).
+// N = 32 MMAs into the sample's own accumulator columns); one 3D TMA box brings
+// the X_s of four samples into one operand stage, beside W.
 // Every wait is bounded by a %globaltimer deadline; on timeout the CTA sets the
 // error word, lets issued copies and MMAs land, frees its tensor memory and exits.
 //
@@ -53,7 +54,9 @@ struct GemmCfg {
 };
 
 constexpr int kGemmThreads = 320;
-constexpr uint32_t kSeg2Bytes = 128u * 64u + 32u * 64u;  // X_s tile + W tile (64-byte rows)
+// one operand stage of the 1x1 convolution: kSeg2Samples X_s tiles [128][32] and the W tile [32][32]
+constexpr uint32_t kSeg2XBytes = 128u * 64u;
+constexpr uint32_t kSeg2Bytes = kSeg2Samples * kSeg2XBytes + 32u * 64u;
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_constant__ CUtensorMap mA,
@@ -64,7 +67,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
                                                                   int* err, uint64_t timeout_ns) {
   using Cfg = GemmCfg<BN>;
   constexpr int STAGES = Cfg::STAGES;
-  constexpr bool SEG2 = (EPI == EPI_LAYER_FWD || EPI == EPI_LAYER_BWD);
+  static_assert(EPI == EPI_MODES || EPI == EPI_DW || EPI == EPI_FIELD, "layer products run persistent");
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
@@ -72,8 +75,6 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
-  __shared__ __align__(16) float w_s[C * C];
-  __shared__ __align__(16) float b_s[C];
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -83,17 +84,9 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
   const int n0 = (EPI == EPI_DW) ? m0 : (NFAST ? blockIdx.x : blockIdx.y) * BN;
   const int kb0 = blockIdx.z * kper;
   const int nkb = max(0, min(K / 64 - kb0, kper));
-  // samples of this tile whose 1x1 convolution runs as a second K segment
-  const int nseg = SEG2 ? max(0, min(BN / C, ea.B - n0 / C)) : 0;
-  const int total = nkb + nseg;
+  const int total = nkb;
   const uint64_t deadline = ptx::globaltimer() + timeout_ns;
 
-  if constexpr (SEG2) {
-    const __nv_bfloat16* w = static_cast<const __nv_bfloat16*>(ea.w);
-    const __nv_bfloat16* bias = static_cast<const __nv_bfloat16*>(ea.bias);
-    (void)w;
-    if (threadIdx.x < C) b_s[threadIdx.x] = bias ? __bfloat162float(bias[threadIdx.x]) : 0.f;
-  }
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) {
       ptx::mbar_init(ptx::smem_u32(&full_bar[i]), 1);
@@ -105,10 +98,6 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
     ptx::fence_mbar_init();
     ptx::prefetch_tensormap(&mA);
     ptx::prefetch_tensormap(&mB);
-    if (SEG2 && nseg > 0) {
-      ptx::prefetch_tensormap(&mA2);
-      ptx::prefetch_tensormap(&mW);
-    }
   }
   if (warp == 0) {
     ptx::tmem_alloc(ptx::smem_u32(&tmem_base_s), Cfg::TMEM_COLS);
@@ -131,18 +120,10 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
       }
       const uint32_t fb = ptx::smem_u32(&full_bar[st]);
       const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE);
-      if (i < nkb) {
-        ptx::mbar_arrive_expect_tx(fb, Cfg::STAGE);
-        const int kc = (kb0 + i) * 64;
-        ptx::tma_load_2d(sa, &mA, kc, m0, fb);
-        ptx::tma_load_2d(sa + Cfg::A_BYTES, &mB, kc, n0, fb);
-      } else {
-        // X_s: rows (sample n0/C + s, pixels m0 .. m0 + 127) of the channel-last activations
-        const int smp = n0 / C + (i - nkb);
-        ptx::mbar_arrive_expect_tx(fb, kSeg2Bytes);
-        ptx::tma_load_2d(sa, &mA2, 0, smp * ea.P + m0, fb);
-        ptx::tma_load_2d(sa + Cfg::A_BYTES, &mW, 0, 0, fb);
-      }
+      ptx::mbar_arrive_expect_tx(fb, Cfg::STAGE);
+      const int kc = (kb0 + i) * 64;
+      ptx::tma_load_2d(sa, &mA, kc, m0, fb);
+      ptx::tma_load_2d(sa + Cfg::A_BYTES, &mB, kc, n0, fb);
       ++issued;
       if (++st == STAGES) {
         st = 0;
@@ -162,7 +143,6 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
   } else if (warp == 1 && lane == 0) {
     // ---------------- tcgen05.mma issuer ----------------
     constexpr uint32_t idesc = ptx::idesc_f16(true, 128, BN);
-    constexpr uint32_t idesc32 = ptx::idesc_f16(true, 128, 32);
     int st = 0;
     uint32_t ph = 0;
     for (int i = 0; i < total && !abort_s; ++i) {
@@ -173,21 +153,11 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
       }
       ptx::tc_fence_after();
       const uint32_t sa = ptx::smem_u32(smem + (size_t)st * Cfg::STAGE);
-      if (i < nkb) {
-        const uint64_t da = ptx::sw128_desc(sa), db = ptx::sw128_desc(sa + Cfg::A_BYTES);
+      const uint64_t da = ptx::sw128_desc(sa), db = ptx::sw128_desc(sa + Cfg::A_BYTES);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t o = (uint64_t)(2 * kk);  // 16 elements = 32 bytes, in 16-byte units
-          ptx::mma_f16(tmem, da + o, db + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
-        }
-      } else {
-        const uint64_t da = ptx::sw64_desc(sa), db = ptx::sw64_desc(sa + Cfg::A_BYTES);
-        const uint32_t d = tmem + (uint32_t)(C * (i - nkb));
-#pragma unroll
-        for (int kk = 0; kk < 2; ++kk) {
-          const uint64_t o = (uint64_t)(2 * kk);
-          ptx::mma_f16(d, da + o, db + o, idesc32, (nkb > 0 || kk > 0) ? 1u : 0u);
-        }
+      for (int kk = 0; kk < 4; ++kk) {
+        const uint64_t o = (uint64_t)(2 * kk);  // 16 elements = 32 bytes, in 16-byte units
+        ptx::mma_f16(tmem, da + o, db + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
       }
       ptx::mma_commit(ptx::smem_u32(&empty_bar[st]));
       if (++st == STAGES) {
@@ -239,7 +209,7 @@ __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_c
           acc[16 + j] = total > 0 ? __uint_as_float(r2[j]) : 0.f;
           acc[24 + j] = total > 0 ? __uint_as_float(r3[j]) : 0.f;
         }
-        epilogue<EPI, __nv_bfloat16, SEG2>(ea, w_s, b_s, row, n0 + 32 * c, blockIdx.z, acc);
+        epilogue<EPI, __nv_bfloat16, true>(ea, nullptr, nullptr, row, n0 + 32 * c, blockIdx.z, acc);
       }
     }
   }
@@ -300,7 +270,11 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
   constexpr bool NFAST = (EPI == EPI_FIELD || EPI == EPI_MODES);
   auto tile_m0 = [&](int t) { return (NFAST ? t / n_tiles : t % m_tiles) * 128; };
   auto tile_n0 = [&](int t) { return (NFAST ? t % n_tiles : t / m_tiles) * BN; };
+  // samples of a tile whose 1x1 convolution runs as an extra K segment, and the operand stages
+  // they take (kSeg2Samples samples each)
   auto tile_nseg = [&](int n0) { return SEG2 ? max(0, min(BN / C, ea.B - n0 / C)) : 0; };
+  auto tile_ngrp = [&](int n0) { return (tile_nseg(n0) + kSeg2Samples - 1) / kSeg2Samples; };
+  static_assert(kSeg2Bytes <= kLayerStage, "a 1x1-convolution stage must fit an operand stage");
 
   if (threadIdx.x < C) {
     const __nv_bfloat16* bias = static_cast<const __nv_bfloat16*>(ea.bias);
@@ -338,7 +312,7 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < n_tasks && !abort_s; t += gridDim.x) {
       const int m0 = tile_m0(t), n0 = tile_n0(t);
-      const int total = nkb + tile_nseg(n0);
+      const int total = nkb + tile_ngrp(n0);
       for (int i = 0; i < total && !abort_s; ++i) {
         if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[st]), ph ^ 1u, deadline)) {
           atomicOr(err, DEV_ERR_TIMEOUT_EMPTY);
@@ -352,10 +326,11 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
           ptx::tma_load_2d(sa, &mA, i * 64, m0, fb);
           ptx::tma_load_2d(sa + A_BYTES, &mB, i * 64, n0, fb);
         } else {
-          const int smp = n0 / C + (i - nkb);
+          // X_s for samples smp0 .. smp0 + kSeg2Samples - 1 (pixels m0 .. m0 + 127), then W
+          const int smp0 = n0 / C + kSeg2Samples * (i - nkb);
           ptx::mbar_arrive_expect_tx(fb, kSeg2Bytes);
-          ptx::tma_load_2d(sa, &mA2, 0, smp * ea.P + m0, fb);
-          ptx::tma_load_2d(sa + A_BYTES, &mW, 0, 0, fb);
+          ptx::tma_load_3d(sa, &mA2, 0, m0, smp0, fb);
+          ptx::tma_load_2d(sa + kSeg2Samples * kSeg2XBytes, &mW, 0, 0, fb);
         }
         ++issued;
         if (++st == STAGES) {
@@ -382,7 +357,8 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < n_tasks && !abort_s; t += gridDim.x, ++lt) {
       const int n0 = tile_n0(t);
-      const int total = nkb + tile_nseg(n0);
+      const int nseg = tile_nseg(n0);
+      const int total = nkb + tile_ngrp(n0);
       const int acc = lt & 1;
       if (!ptx::mbar_wait(ptx::smem_u32(&acce_bar[acc]), ((uint32_t)(lt >> 1) & 1u) ^ 1u, deadline)) {
         atomicOr(err, DEV_ERR_TIMEOUT_ACCUM);
@@ -407,12 +383,16 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
             ptx::mma_f16(d_tmem, da + o, db + o, idesc, (i > 0 || kk > 0) ? 1u : 0u);
           }
         } else {
-          const uint64_t da = ptx::sw64_desc(sa), db = ptx::sw64_desc(sa + A_BYTES);
-          const uint32_t d = d_tmem + (uint32_t)(C * (i - nkb));
+          const int s0 = kSeg2Samples * (i - nkb);
+          const uint64_t db = ptx::sw64_desc(sa + kSeg2Samples * kSeg2XBytes);
+          for (int j = 0; j < kSeg2Samples && s0 + j < nseg; ++j) {
+            const uint64_t da = ptx::sw64_desc(sa + (uint32_t)j * kSeg2XBytes);
+            const uint32_t d = d_tmem + (uint32_t)(C * (s0 + j));
 #pragma unroll
-          for (int kk = 0; kk < 2; ++kk) {
-            const uint64_t o = (uint64_t)(2 * kk);
-            ptx::mma_f16(d, da + o, db + o, idesc32, 1u);
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint64_t o = (uint64_t)(2 * kk);
+              ptx::mma_f16(d, da + o, db + o, idesc32, 1u);
+            }
           }
         }
         ptx::mma_commit(ptx::smem_u32(&empty_bar[st]));
@@ -676,6 +656,22 @@ scw_status make_map_bf16(CUtensorMap* m, const void* base, long long cols, long 
                   CU_TENSOR_MAP_INTERLEAVE_NONE,
                   box_cols == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(SCW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+  return SCW_OK;
+}
+
+scw_status make_map_act3d(CUtensorMap* m, const void* base, long long P, long long samples) {
+  auto fn = encode_fn();
+  if (!fn) return set_error(SCW_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) || P < 1 || samples < 1)
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "tensor map: base or extent out of range");
+  cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)P, (cuuint64_t)samples};
+  cuuint64_t strides[2] = {(cuuint64_t)(C * 2), (cuuint64_t)(P * C * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)C, 128u, (cuuint32_t)kSeg2Samples};
+  cuuint32_t estr[3] = {1u, 1u, 1u};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(SCW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return SCW_OK;
 }

@@ -240,9 +240,10 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
 // a 64-element inner box): A rows in boxes of 128, B rows in boxes of BN (32..256).
 // grid = (ceil(M/128), ceil(N/BN), splits); EPI_DW uses grid.x = groups and the same row
 // offset for A and B. Each split covers kper 64-wide K blocks.
-// EPI_LAYER_*: mA2 / mW are the 1x1-convolution operands (channel-last activations [B P][C]
-// and W or W^T [C][C], 64-byte swizzle, boxes {32, 128} and {32, 32}); they run on the tensor
-// cores as one extra K = 32 segment per sample of the tile, into that sample's 32 columns.
+// EPI_LAYER_*: mA2 / mW are the 1x1-convolution operands (channel-last activations [B][P][C]
+// as a 3D map with box {32, 128, kSeg2Samples}, and W or W^T [C][C] with box {32, 32}; 64-byte
+// swizzle); they run on the tensor cores as one extra K = 32 segment per sample of the tile,
+// into that sample's 32 columns, kSeg2Samples samples per operand stage.
 cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
                            const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int splits, int* err,
                            uint64_t timeout_ns, cudaStream_t st);
@@ -257,6 +258,11 @@ int gemm_tc_ctas_per_sm(int BN);
 // out-of-bounds elements read as zero
 scw_status make_map_bf16(CUtensorMap* m, const void* base, long long cols, long long rows, long long pitch,
                          int box_rows, int box_cols = 64);
+// 1x1-convolution samples per operand stage of the layer products
+constexpr int kSeg2Samples = 4;
+// encode the 3D bf16 tensor map of channel-last activations [samples][P][C]: box
+// {C, 128 pixels, kSeg2Samples samples}, 64-byte swizzle, out-of-bounds elements read as zero
+scw_status make_map_act3d(CUtensorMap* m, const void* base, long long P, long long samples);
 
 template <typename T>
 cudaError_t launch_tables(T* D, T* E, int N, int m, int Kp, cudaStream_t st);
