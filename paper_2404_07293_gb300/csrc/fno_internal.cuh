@@ -94,6 +94,12 @@ __device__ __forceinline__ void ld32(const T* p, float (&v)[32]) {
   }
 }
 
+// two floats as one bf16x2 word (a in the low half), round to nearest even
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 template <typename T>
 __device__ __forceinline__ void st32(T* p, const float (&v)[32]) {
   if constexpr (sizeof(T) == 4) {

@@ -102,10 +102,16 @@ __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n,
 }
 
 // ---- mixing (per kept mode k, complex C x C), spectra mode-major Vh[split][k][b C + i] ------
-// One CTA per (mode, block of 32 samples), 256 threads: thread (warp w, lane) handles
-// samples w + 8 j (j < 4) and channel `lane`. Many small CTAs keep enough warps in flight
-// to hide the global-load latency of the per-mode operands.
+// One CTA per (NM = 4 consecutive kept modes, block of 32 samples), 256 threads: thread (warp w,
+// lane) handles samples w + 8 j (j < 4), channel `lane` and the NM modes, so each (sample,
+// channel) row of the K-major outputs Wh / GVh receives its NM consecutive modes in one
+// 16-byte store (m is a multiple of 4, so m^2 is a multiple of NM). Operands are staged in
+// shared memory as [mode][32][34] complex tiles.
 constexpr int MIX_SAMPLES = 32;
+constexpr int MIX_MODES_FWD = 4;
+constexpr int MIX_MODES_BWD = 1;
+constexpr int MIX_LD = C + 2;          // row stride of a staged tile (float2): rows stay 16-byte aligned
+constexpr int MIX_TILE = C * MIX_LD;   // float2 elements of one staged [32][34] tile
 
 template <typename T>
 __device__ __forceinline__ float2 ld_pair(const T* base, size_t pair);
@@ -130,6 +136,31 @@ __device__ __forceinline__ void st_pair<__nv_bfloat16>(__nv_bfloat16* base, size
   reinterpret_cast<__nv_bfloat162*>(base)[pair] = __floats2bfloat162_rn(v.x, v.y);
 }
 
+// NM consecutive complex values (pairs pair .. pair + NM - 1); 16-byte aligned when NM = 4
+template <typename T, int NM>
+__device__ __forceinline__ void st_pairs(T* base, size_t pair, const float (&re)[NM], const float (&im)[NM]) {
+  if constexpr (NM == 4 && sizeof(T) == 2) {
+    uint4 u;
+    u.x = pack_bf16x2(re[0], im[0]);
+    u.y = pack_bf16x2(re[1], im[1]);
+    u.z = pack_bf16x2(re[2], im[2]);
+    u.w = pack_bf16x2(re[3], im[3]);
+    *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat162*>(base) + pair) = u;
+  } else if constexpr (NM == 4) {
+    float4* q = reinterpret_cast<float4*>(reinterpret_cast<float2*>(base) + pair);
+    q[0] = make_float4(re[0], im[0], re[1], im[1]);
+    q[1] = make_float4(re[2], im[2], re[3], im[3]);
+  } else if constexpr (NM == 2 && sizeof(T) == 2) {
+    *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat162*>(base) + pair) =
+        make_uint2(pack_bf16x2(re[0], im[0]), pack_bf16x2(re[1], im[1]));
+  } else if constexpr (NM == 2) {
+    *reinterpret_cast<float4*>(reinterpret_cast<float2*>(base) + pair) = make_float4(re[0], im[0], re[1], im[1]);
+  } else {
+#pragma unroll
+    for (int kk = 0; kk < NM; ++kk) st_pair(base, pair + kk, make_float2(re[kk], im[kk]));
+  }
+}
+
 // split-summed complex value of a mode-major spectrum
 __device__ __forceinline__ float2 ld_spec(const float2* __restrict__ X, size_t off, int splits,
                                           long long split_stride) {
@@ -143,39 +174,53 @@ __device__ __forceinline__ float2 ld_spec(const float2* __restrict__ X, size_t o
 }
 
 // forward: Wh[b][o][k] = scale sum_i R[k][o][i] Vh[b][i][k]
-template <typename T>
+template <typename T, int NM>
 __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__ Vh, int splits,
                                                       long long split_stride, long long ld, const T* __restrict__ R,
                                                       T* __restrict__ Wh, float scale, int B, int Kp) {
-  __shared__ float2 Rs[C][C + 1];            // [i][o]
-  __shared__ float2 Vs[MIX_SAMPLES][C + 1];  // [s][i]
-  const int k = blockIdx.x, b0 = blockIdx.y * MIX_SAMPLES;
+  extern __shared__ __align__(16) float2 mix_smem[];
+  float2* Rs = mix_smem;                 // [mode][i][o]
+  float2* Vs = mix_smem + NM * MIX_TILE;  // [mode][s][i]
+  const int k0 = blockIdx.x * NM, b0 = blockIdx.y * MIX_SAMPLES;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int idx = t + 256 * q, row = idx / C, col = idx % C;
-    Rs[col][row] = ld_pair(R, ((size_t)k * C + row) * C + col);
+  for (int q = 0; q < 4 * NM; ++q) {
+    const int idx = t + 256 * q, kk = idx / (C * C), row = (idx / C) % C, col = idx % C;
+    Rs[kk * MIX_TILE + col * MIX_LD + row] = ld_pair(R, ((size_t)(k0 + kk) * C + row) * C + col);
     const int b = b0 + row;
-    Vs[row][col] = b < B ? ld_spec(Vh, (size_t)k * ld + (size_t)b * C + col, splits, split_stride)
-                         : make_float2(0.f, 0.f);
+    Vs[kk * MIX_TILE + row * MIX_LD + col] =
+        b < B ? ld_spec(Vh, (size_t)(k0 + kk) * ld + (size_t)b * C + col, splits, split_stride)
+              : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  // thread (samples w + 8 j, o = lane): each R element loaded once feeds the four samples
-  float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-  for (int i = 0; i < C; ++i) {
-    const float2 r = Rs[i][lane];
+  // each R element loaded once feeds the four samples; V is read two channels per 16-byte load
+  float re[4][NM], im[4][NM];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const float2 v = Vs[w + 8 * j][i];
-      re[j] = fmaf(r.x, v.x, fmaf(-r.y, v.y, re[j]));
-      im[j] = fmaf(r.x, v.y, fmaf(r.y, v.x, im[j]));
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int kk = 0; kk < NM; ++kk) re[j][kk] = im[j][kk] = 0.f;
+#pragma unroll 2
+  for (int i = 0; i < C; i += 2) {
+#pragma unroll
+    for (int kk = 0; kk < NM; ++kk) {
+      const float2 r0 = Rs[kk * MIX_TILE + i * MIX_LD + lane], r1 = Rs[kk * MIX_TILE + (i + 1) * MIX_LD + lane];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float4 v = *reinterpret_cast<const float4*>(Vs + kk * MIX_TILE + (w + 8 * j) * MIX_LD + i);
+        re[j][kk] = fmaf(r1.x, v.z, fmaf(-r1.y, v.w, fmaf(r0.x, v.x, fmaf(-r0.y, v.y, re[j][kk]))));
+        im[j][kk] = fmaf(r1.x, v.w, fmaf(r1.y, v.z, fmaf(r0.x, v.y, fmaf(r0.y, v.x, im[j][kk]))));
+      }
     }
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int b = b0 + w + 8 * j;
-    if (b < B) st_pair(Wh, (((size_t)b * C + lane) * Kp) / 2 + k, make_float2(scale * re[j], scale * im[j]));
+#pragma unroll
+    for (int kk = 0; kk < NM; ++kk) {
+      re[j][kk] *= scale;
+      im[j][kk] *= scale;
+    }
+    if (b < B) st_pairs<T, NM>(Wh, (((size_t)b * C + lane) * Kp) / 2 + k0, re[j], im[j]);
   }
 }
 
@@ -184,68 +229,84 @@ __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__
 //   part dR[k][o][i] = sum_b G[b][o][k] conj(Vh[b][i][k])   (this CTA's samples)
 //   part dc[o] = N^2 sum_b Re G[b][o][k_dc]                   (the DC mode carries sum_x dZ / N^2)
 // part row (one per sample block): [m^2][C][C][2] then [C]
-template <typename T>
+template <typename T, int NM>
 __global__ void __launch_bounds__(256) mix_bwd_kernel(const float2* __restrict__ G, const float2* __restrict__ Vh,
                                                       int splits, long long split_stride, long long ld,
                                                       const T* __restrict__ R, T* __restrict__ GVh,
                                                       float* __restrict__ part, int B, int m, int Kp, int N) {
-  __shared__ float2 Rs[C][C + 1];            // [o][i]
-  __shared__ float2 Gs[MIX_SAMPLES][C + 1];  // [s][o]
-  __shared__ float2 Vs[MIX_SAMPLES][C + 1];  // [s][i]
-  const int k = blockIdx.x, b0 = blockIdx.y * MIX_SAMPLES;
+  extern __shared__ __align__(16) float2 mix_smem[];
+  float2* Rs = mix_smem;                     // [mode][o][i]
+  float2* Gs = mix_smem + NM * MIX_TILE;      // [mode][s][o]
+  float2* Vs = mix_smem + 2 * NM * MIX_TILE;  // [mode][s][i]
+  const int k0 = blockIdx.x * NM, b0 = blockIdx.y * MIX_SAMPLES;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int kdc = (m / 2) * m + m / 2;
   const size_t row0 = (size_t)blockIdx.y * ((size_t)m * m * C * C * 2 + C);
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int idx = t + 256 * q, row = idx / C, col = idx % C;
-    Rs[row][col] = ld_pair(R, ((size_t)k * C + row) * C + col);
+  for (int q = 0; q < 4 * NM; ++q) {
+    const int idx = t + 256 * q, kk = idx / (C * C), row = (idx / C) % C, col = idx % C;
+    const int e = kk * MIX_TILE + row * MIX_LD + col;
+    Rs[e] = ld_pair(R, ((size_t)(k0 + kk) * C + row) * C + col);
     const int b = b0 + row;
-    const size_t off = (size_t)k * ld + (size_t)b * C + col;
-    Gs[row][col] = b < B ? ld_spec(G, off, splits, split_stride) : make_float2(0.f, 0.f);
-    Vs[row][col] = b < B ? ld_spec(Vh, off, splits, split_stride) : make_float2(0.f, 0.f);
+    const size_t off = (size_t)(k0 + kk) * ld + (size_t)b * C + col;
+    Gs[e] = b < B ? ld_spec(G, off, splits, split_stride) : make_float2(0.f, 0.f);
+    Vs[e] = b < B ? ld_spec(Vh, off, splits, split_stride) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  // GVh: thread (samples w + 8 j, i = lane); each R element loaded once feeds the four samples
+  // GVh: thread (samples w + 8 j, i = lane); each R element loaded once feeds the four samples,
+  // G is read two outputs per 16-byte load
   {
-    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-    for (int o = 0; o < C; ++o) {
-      const float2 r = Rs[o][lane];
+    float re[4][NM], im[4][NM];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 g = Gs[w + 8 * j][o];  // conj(r) g
-        re[j] = fmaf(r.x, g.x, fmaf(r.y, g.y, re[j]));
-        im[j] = fmaf(r.x, g.y, fmaf(-r.y, g.x, im[j]));
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int kk = 0; kk < NM; ++kk) re[j][kk] = im[j][kk] = 0.f;
+#pragma unroll 2
+    for (int o = 0; o < C; o += 2) {
+#pragma unroll
+      for (int kk = 0; kk < NM; ++kk) {
+        const float2 r0 = Rs[kk * MIX_TILE + o * MIX_LD + lane], r1 = Rs[kk * MIX_TILE + (o + 1) * MIX_LD + lane];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const float4 g = *reinterpret_cast<const float4*>(Gs + kk * MIX_TILE + (w + 8 * j) * MIX_LD + o);
+          // conj(r) g
+          re[j][kk] = fmaf(r1.x, g.z, fmaf(r1.y, g.w, fmaf(r0.x, g.x, fmaf(r0.y, g.y, re[j][kk]))));
+          im[j][kk] = fmaf(r1.x, g.w, fmaf(-r1.y, g.z, fmaf(r0.x, g.y, fmaf(-r0.y, g.x, im[j][kk]))));
+        }
       }
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int b = b0 + w + 8 * j;
-      if (b < B) st_pair(GVh, (((size_t)b * C + lane) * Kp) / 2 + k, make_float2(re[j], im[j]));
+      if (b < B) st_pairs<T, NM>(GVh, (((size_t)b * C + lane) * Kp) / 2 + k0, re[j], im[j]);
     }
   }
-  // dR: thread (outputs o = w + 8 j, i = lane), summed over the block's samples; each V element
-  // loaded once feeds the four outputs
-  {
+  // dR: thread (outputs o = 4 w + jj, i = lane), summed over the block's samples; each V element
+  // loaded once feeds the four outputs, whose G values come in two 16-byte loads
+#pragma unroll 1
+  for (int kk = 0; kk < NM; ++kk) {
     float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
     for (int s = 0; s < MIX_SAMPLES; ++s) {
-      const float2 v = Vs[s][lane];
+      const float2 v = Vs[kk * MIX_TILE + s * MIX_LD + lane];
+      const float4* g4 = reinterpret_cast<const float4*>(Gs + kk * MIX_TILE + s * MIX_LD + 4 * w);
+      const float4 ga = g4[0], gb = g4[1];
+      const float2 g[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
+                           make_float2(gb.z, gb.w)};
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float2 g = Gs[s][w + 8 * j];  // g conj(v)
-        re[j] = fmaf(g.x, v.x, fmaf(g.y, v.y, re[j]));
-        im[j] = fmaf(g.y, v.x, fmaf(-g.x, v.y, im[j]));
+      for (int jj = 0; jj < 4; ++jj) {  // g conj(v)
+        re[jj] = fmaf(g[jj].x, v.x, fmaf(g[jj].y, v.y, re[jj]));
+        im[jj] = fmaf(g[jj].y, v.x, fmaf(-g[jj].x, v.y, im[jj]));
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      reinterpret_cast<float2*>(part + row0)[((size_t)k * C + w + 8 * j) * C + lane] = make_float2(re[j], im[j]);
+    for (int jj = 0; jj < 4; ++jj)
+      reinterpret_cast<float2*>(part + row0)[((size_t)(k0 + kk) * C + 4 * w + jj) * C + lane] =
+          make_float2(re[jj], im[jj]);
   }
-  if (k == kdc && t < C) {
+  if (kdc >= k0 && kdc < k0 + NM && t < C) {
     float d = 0.f;
-    for (int s = 0; s < MIX_SAMPLES; ++s) d += Gs[s][t].x;
+    for (int s = 0; s < MIX_SAMPLES; ++s) d += Gs[(kdc - k0) * MIX_TILE + s * MIX_LD + t].x;
     part[row0 + (size_t)m * m * C * C * 2 + t] = d * (float)N * (float)N;
   }
 }
@@ -600,22 +661,45 @@ cudaError_t launch_lift(const float2* n, const T* params, T* Vcf, T* Vcl, int B,
   return cudaGetLastError();
 }
 
+template <typename T, int NM>
+static cudaError_t launch_mix_fwd_t(const float2* Vh, int splits, long long split_stride, long long ld, const T* R,
+                                    T* Wh, float scale, int B, int m, int Kp, cudaStream_t st) {
+  const size_t smem = (size_t)2 * NM * MIX_TILE * sizeof(float2);
+  const void* fn = reinterpret_cast<const void*>(mix_fwd_kernel<T, NM>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(m * m / NM, (B + MIX_SAMPLES - 1) / MIX_SAMPLES);
+  mix_fwd_kernel<T, NM><<<grid, 256, smem, st>>>(Vh, splits, split_stride, ld, R, Wh, scale, B, Kp);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_mix_fwd(const float2* Vh, int splits, long long split_stride, long long ld, const T* R, T* Wh,
                            float scale, int B, int m, int Kp, cudaStream_t st) {
-  const dim3 grid(m * m, (B + MIX_SAMPLES - 1) / MIX_SAMPLES);
-  mix_fwd_kernel<T><<<grid, 256, 0, st>>>(Vh, splits, split_stride, ld, R, Wh, scale, B, Kp);
-  return cudaGetLastError();
+  if ((m * m) % MIX_MODES_FWD) return cudaErrorInvalidValue;
+  return launch_mix_fwd_t<T, MIX_MODES_FWD>(Vh, splits, split_stride, ld, R, Wh, scale, B, m, Kp, st);
 }
 
 int mix_sample_blocks(int B) { return (B + MIX_SAMPLES - 1) / MIX_SAMPLES; }
 
+template <typename T, int NM>
+static cudaError_t launch_mix_bwd_t(const float2* G, const float2* Vh, int splits, long long split_stride,
+                                    long long ld, const T* R, T* GVh, float* part, int B, int m, int Kp, int N,
+                                    cudaStream_t st) {
+  const size_t smem = (size_t)3 * NM * MIX_TILE * sizeof(float2);
+  const void* fn = reinterpret_cast<const void*>(mix_bwd_kernel<T, NM>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(m * m / NM, mix_sample_blocks(B));
+  mix_bwd_kernel<T, NM><<<grid, 256, smem, st>>>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_mix_bwd(const float2* G, const float2* Vh, int splits, long long split_stride, long long ld,
                            const T* R, T* GVh, float* part, int B, int m, int Kp, int N, cudaStream_t st) {
-  const dim3 grid(m * m, mix_sample_blocks(B));
-  mix_bwd_kernel<T><<<grid, 256, 0, st>>>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N);
-  return cudaGetLastError();
+  if ((m * m) % MIX_MODES_BWD) return cudaErrorInvalidValue;
+  return launch_mix_bwd_t<T, MIX_MODES_BWD>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N, st);
 }
 
 template <typename T>
