@@ -358,8 +358,10 @@ __global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restri
                                                                float* __restrict__ part_pool,
                                                                float* __restrict__ part_proj, int B, int P) {
   __shared__ __align__(16) float Qs[OUT * C + OUT];
-  __shared__ float Vs[PIX_BLOCK][C + 1];
-  __shared__ float Fs[OUT][PIX_BLOCK];
+  // the block sums below are one product F' V' over the block's pixels: F' = (dF rows, a row of
+  // ones, a zero row), V' = (V columns, a column of ones, zero columns)
+  __shared__ __align__(16) float Vs[PIX_BLOCK][C + 4];
+  __shared__ __align__(16) float Fs[OUT + 2][PIX_BLOCK];
   __shared__ float red[8];
   __shared__ float tn_s;
   const int nblk = gridDim.x, b = blockIdx.y, t = threadIdx.x, p = blockIdx.x * PIX_BLOCK + t;
@@ -373,7 +375,10 @@ __global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restri
   float v[32];
   ld32(Vcl + ((size_t)b * P + p) * C, v);
 #pragma unroll
-  for (int o = 0; o < C; ++o) Vs[t][o] = v[o];
+  for (int o = 0; o < C; o += 4) *reinterpret_cast<float4*>(&Vs[t][o]) = make_float4(v[o], v[o + 1], v[o + 2], v[o + 3]);
+  *reinterpret_cast<float4*>(&Vs[t][C]) = make_float4(1.f, 0.f, 0.f, 0.f);
+  Fs[OUT][t] = 1.f;
+  Fs[OUT + 1][t] = 0.f;
   const float4* Q4 = reinterpret_cast<const float4*>(Qs);  // row j: Q4[8 j .. 8 j + 8)
   float d[OUT];
 #pragma unroll
@@ -426,30 +431,53 @@ __global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restri
     for (int w = 0; w < 8; ++w) s += red[w];
     part_err[blk] = s;
   }
-  // block sums over the 256 pixels, four independent accumulators each (pixels q = 4 i + a),
-  // combined in a fixed order
-  if (t < OUT * C) {
-    const int j = t / C, o = t % C;
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 4
-    for (int q = 0; q < PIX_BLOCK; q += 4)
+  // block sums over the 256 pixels: the product F' V' as 2 x 4 register tiles (rows 2 jp, 2 jp + 1;
+  // columns 4 og .. 4 og + 3), the pixels split over NSPLIT threads per tile (q = split + NSPLIT i),
+  // then the splits summed in a fixed order:
+  //   part_proj row: dQ[j][o] = (F' V')[j][o], dq[j] = (F' V')[j][C]; part_pool[o] = (F' V')[OUT][o]
+  constexpr int NJP = (OUT + 2) / 2, NOG = (C + 4) / 4, NT = NJP * NOG, NSPLIT = 256 / NT;
+  float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  if (t < NT * NSPLIT) {
+    const int tile = t % NT, split = t / NT, jp = tile / NOG, og = tile % NOG;
+    for (int q = split; q < PIX_BLOCK; q += NSPLIT) {
+      const float f0 = Fs[2 * jp][q], f1 = Fs[2 * jp + 1][q];
+      const float4 w4 = *reinterpret_cast<const float4*>(&Vs[q][4 * og]);
+      acc[0][0] = fmaf(f0, w4.x, acc[0][0]);
+      acc[0][1] = fmaf(f0, w4.y, acc[0][1]);
+      acc[0][2] = fmaf(f0, w4.z, acc[0][2]);
+      acc[0][3] = fmaf(f0, w4.w, acc[0][3]);
+      acc[1][0] = fmaf(f1, w4.x, acc[1][0]);
+      acc[1][1] = fmaf(f1, w4.y, acc[1][1]);
+      acc[1][2] = fmaf(f1, w4.z, acc[1][2]);
+      acc[1][3] = fmaf(f1, w4.w, acc[1][3]);
+    }
+  }
+  __syncthreads();
+  float* red_s = &Vs[0][0];  // the tiles' partial sums [NT NSPLIT][8], over V' (no longer read)
+  if (t < NT * NSPLIT) {
 #pragma unroll
-      for (int a = 0; a < 4; ++a) s[a] = fmaf(Fs[j][q + a], Vs[q + a][o], s[a]);
-    part_proj[blk * (OUT * C + OUT) + t] = (s[0] + s[1]) + (s[2] + s[3]);
-  } else if (t < OUT * C + OUT) {
-    const int j = t - OUT * C;
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int q = 0; q < PIX_BLOCK; q += 4)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) s[a] += Fs[j][q + a];
-    part_proj[blk * (OUT * C + OUT) + t] = (s[0] + s[1]) + (s[2] + s[3]);
-  } else if (t >= 224) {
-    const int o = t - 224;
-    float s[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int q = 0; q < PIX_BLOCK; q += 4)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) s[a] += Vs[q + a][o];
-    part_pool[blk * C + o] = (s[0] + s[1]) + (s[2] + s[3]);
+    for (int e = 0; e < 8; ++e) red_s[t * 8 + e] = acc[e / 4][e % 4];
+  }
+  __syncthreads();
+  for (int q = t; q < OUT * C + OUT + C; q += blockDim.x) {
+    int j, o;
+    if (q < OUT * C) {
+      j = q / C;
+      o = q % C;
+    } else if (q < OUT * C + OUT) {
+      j = q - OUT * C;
+      o = C;
+    } else {
+      j = OUT;
+      o = q - OUT * C - OUT;
+    }
+    const int tile = (j / 2) * NOG + o / 4, e = 4 * (j % 2) + o % 4;
+    float sum = 0.f;
+    for (int sp = 0; sp < NSPLIT; ++sp) sum += red_s[(sp * NT + tile) * 8 + e];
+    if (q < OUT * C + OUT)
+      part_proj[blk * (OUT * C + OUT) + q] = sum;
+    else
+      part_pool[blk * C + o] = sum;
   }
 }
 
@@ -498,14 +526,18 @@ __global__ void __launch_bounds__(256) head_kernel(const float* __restrict__ par
 template <typename T>
 __global__ void __launch_bounds__(128) lift_bwd_kernel(const T* __restrict__ dV0cl, const float2* __restrict__ n,
                                                        float* __restrict__ part, int B, int S, int in_grid, int N) {
-  __shared__ float dv_s[128][C + 1];
-  __shared__ float a_s[128][33];
+  __shared__ __align__(16) float dv_s[128][C + 4];  // rows 16-byte aligned
+  __shared__ __align__(16) float a_s[128][C + 4];   // features, zero past 2S
+  __shared__ __align__(16) float red_s[128][16];
   const int cin = 2 * S, P = N * N, Pi = in_grid * in_grid, r = N / in_grid;
-  const long long idx = blockIdx.x * 128LL + threadIdx.x;
+  const int t = threadIdx.x;
+  const long long idx = blockIdx.x * 128LL + t;
   const bool valid = idx < (long long)B * Pi;
   float dv[32];
 #pragma unroll
   for (int o = 0; o < C; ++o) dv[o] = 0.f;
+#pragma unroll
+  for (int c = 0; c < C; ++c) a_s[t][c] = 0.f;
   if (valid) {
     const int b = (int)(idx / Pi), pi = (int)(idx % Pi);
     const int yi = pi / in_grid, xi = pi % in_grid;
@@ -518,31 +550,56 @@ __global__ void __launch_bounds__(128) lift_bwd_kernel(const T* __restrict__ dV0
       }
     for (int s = 0; s < S; ++s) {
       const float2 v = n[(((size_t)b * S + s) * in_grid + yi) * in_grid + xi];
-      a_s[threadIdx.x][2 * s] = v.x - 1.0f;
-      a_s[threadIdx.x][2 * s + 1] = v.y;
+      a_s[t][2 * s] = v.x - 1.0f;
+      a_s[t][2 * s + 1] = v.y;
     }
-  } else {
-    for (int c = 0; c < cin; ++c) a_s[threadIdx.x][c] = 0.f;
   }
 #pragma unroll
-  for (int o = 0; o < C; ++o) dv_s[threadIdx.x][o] = dv[o];
+  for (int o = 0; o < C; o += 4)
+    *reinterpret_cast<float4*>(&dv_s[t][o]) = make_float4(dv[o], dv[o + 1], dv[o + 2], dv[o + 3]);
+  __syncthreads();
+  // dP over the block's 128 pixels as 4 x 4 register tiles (outputs 4 og .. 4 og + 3, features
+  // 4 cg .. 4 cg + 3), the pixels split over nsplit threads per tile (pixels j = split + nsplit i),
+  // the splits then summed in a fixed order
+  const int ncg = (cin + 3) / 4, ntile = (C / 4) * ncg, nsplit = 128 / ntile;
+  if (t < ntile * nsplit) {
+    const int tile = t % ntile, split = t / ntile, og = tile / ncg, cg = tile % ncg;
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+    for (int j = split; j < 128; j += nsplit) {
+      const float4 d = *reinterpret_cast<const float4*>(&dv_s[j][4 * og]);
+      const float4 a = *reinterpret_cast<const float4*>(&a_s[j][4 * cg]);
+      const float dd[4] = {d.x, d.y, d.z, d.w}, aa[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(dd[u], aa[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) red_s[t][4 * u + v] = acc[u][v];
+  }
   __syncthreads();
   const int width = C * cin + C;
   float* dst = part + (size_t)blockIdx.x * width;
-  for (int q = threadIdx.x; q < width; q += 128) {
-    float s[4] = {0.f, 0.f, 0.f, 0.f};  // four independent accumulators (pixels j = 4 i + k), fixed order
+  for (int q = t; q < width; q += 128) {
+    float s = 0.f;
     if (q < C * cin) {
-      const int o = q / cin, c = q % cin;
-      for (int j = 0; j < 128; j += 4)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) s[k] = fmaf(dv_s[j + k][o], a_s[j + k][c], s[k]);
+      const int o = q / cin, c = q % cin, tile = (o / 4) * ncg + c / 4, e = 4 * (o % 4) + c % 4;
+      for (int sp = 0; sp < nsplit; ++sp) s += red_s[sp * ntile + tile][e];
     } else {
       const int o = q - C * cin;
+      float s4[4] = {0.f, 0.f, 0.f, 0.f};  // four independent accumulators (pixels j = 4 i + k), fixed order
       for (int j = 0; j < 128; j += 4)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) s[k] += dv_s[j + k][o];
+        for (int k = 0; k < 4; ++k) s4[k] += dv_s[j + k][o];
+      s = (s4[0] + s4[1]) + (s4[2] + s4[3]);
     }
-    dst[q] = (s[0] + s[1]) + (s[2] + s[3]);
+    dst[q] = s;
   }
 }
 
