@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restri
   // the block sums below are one product F' V' over the block's pixels: F' = (dF rows, a row of
   // ones, a zero row), V' = (V columns, a column of ones, zero columns)
   __shared__ __align__(16) float Vs[PIX_BLOCK][C + 4];
-  __shared__ __align__(16) float Fs[OUT + 2][PIX_BLOCK];
+  __shared__ __align__(16) float Fs[PIX_BLOCK][OUT + 2];  // pixel-major: a tile's two rows in one load
   __shared__ float red[8];
   __shared__ float tn_s;
   const int nblk = gridDim.x, b = blockIdx.y, t = threadIdx.x, p = blockIdx.x * PIX_BLOCK + t;
@@ -377,8 +377,6 @@ __global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restri
 #pragma unroll
   for (int o = 0; o < C; o += 4) *reinterpret_cast<float4*>(&Vs[t][o]) = make_float4(v[o], v[o + 1], v[o + 2], v[o + 3]);
   *reinterpret_cast<float4*>(&Vs[t][C]) = make_float4(1.f, 0.f, 0.f, 0.f);
-  Fs[OUT][t] = 1.f;
-  Fs[OUT + 1][t] = 0.f;
   const float4* Q4 = reinterpret_cast<const float4*>(Qs);  // row j: Q4[8 j .. 8 j + 8)
   float d[OUT];
 #pragma unroll
@@ -398,8 +396,10 @@ __global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restri
   for (int j = 0; j < OUT; ++j) {
     e2 = fmaf(d[j], d[j], e2);
     d[j] *= sc;
-    Fs[j][t] = d[j];
   }
+  static_assert(OUT == 6, "F' rows: six outputs, a row of ones, a zero row");
+  *reinterpret_cast<float4*>(&Fs[t][0]) = make_float4(d[0], d[1], d[2], d[3]);
+  *reinterpret_cast<float4*>(&Fs[t][4]) = make_float4(d[4], d[5], 1.f, 0.f);
   __syncwarp();  // Q is re-read from shared memory below rather than held in registers across both products
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
@@ -440,7 +440,8 @@ __global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restri
   if (t < NT * NSPLIT) {
     const int tile = t % NT, split = t / NT, jp = tile / NOG, og = tile % NOG;
     for (int q = split; q < PIX_BLOCK; q += NSPLIT) {
-      const float f0 = Fs[2 * jp][q], f1 = Fs[2 * jp + 1][q];
+      const float2 f01 = *reinterpret_cast<const float2*>(&Fs[q][2 * jp]);
+      const float f0 = f01.x, f1 = f01.y;
       const float4 w4 = *reinterpret_cast<const float4*>(&Vs[q][4 * og]);
       acc[0][0] = fmaf(f0, w4.x, acc[0][0]);
       acc[0][1] = fmaf(f0, w4.y, acc[0][1]);
