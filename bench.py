@@ -593,7 +593,7 @@ def run_surrogate(args, dev, bf16_peaks):
         "infer_samples_per_s": B / (infer_ms * 1e-3), "infer_ms_per_batch": infer_ms,
         "loss_after": [float(x) for x in loss],
         "kernel_ms_per_train_step": fam, "tflops": tf,
-        "roofline": {"kernel": {"dft": "gemm_tc_kernel<256, EPI_MODES> (truncated DFT)",
+        "roofline": {"kernel": {"dft": "gemm_layer_persistent<EPI_MODES> (truncated DFT)",
                                 "layer": "gemm_layer_persistent (inverse DFT + 1x1 conv + GELU)"}[dom],
                      "bound": "tensor", "achieved": tf[dom], "peak": peak, "unit": "TFLOP/s",
                      "frac": tf[dom] / peak, "traffic": None,
