@@ -2,7 +2,7 @@
 
 The surrogate is not part of the coupled-wave paper: it is the learned
 shortcut that maps refractive-index slices to the exit-plane field, with the
-coupled-wave solve as its fallback and judge. Its network is the Fourier
+coupled-wave solve as its fallback and its reference. Its network is the Fourier
 neural operator of Li et al. (ICLR 2021), written out here from that
 definition with numpy FFTs (the GPU side uses truncated DFT matrices; the two
 share nothing).
