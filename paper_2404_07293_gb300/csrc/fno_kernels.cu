@@ -30,10 +30,12 @@ __global__ void tables_kernel(T* __restrict__ D, T* __restrict__ E, int N, int m
 }
 
 // ---- lift: V_0 = P a + p, a = (Re n - 1, Im n) per slice, nearest upsampling.
-// One thread per input pixel: the r x r output pixels it covers share one value,
-// written channel-last (32 contiguous values each) and channel-first (pairs of
-// horizontally adjacent pixels in one store when r is even). Features beyond the
-// 2S inputs are zero, so the channel loop has a fixed trip count.
+// One thread per input pixel: the r x r output pixels it covers share one value.
+// The 32 channels are produced eight at a time and stored at once, channel-last
+// (one 16-byte chunk per output pixel in BF16) and channel-first (pairs of
+// horizontally adjacent pixels in one store when r is even), so that few outputs
+// are live at a time. Only the float4 groups of features that can be non-zero
+// (the first 2S) enter the products.
 template <typename T>
 __device__ __forceinline__ void st_same_pair(T* p, float v);
 template <>
@@ -45,8 +47,21 @@ __device__ __forceinline__ void st_same_pair<__nv_bfloat16>(__nv_bfloat16* p, fl
   *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v, v);
 }
 
+// 8 contiguous values (p 16-byte aligned)
 template <typename T>
-__global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n, const T* __restrict__ prm,
+__device__ __forceinline__ void st8(T* p, const float (&v)[8]) {
+  if constexpr (sizeof(T) == 4) {
+    float4* q = reinterpret_cast<float4*>(p);
+    q[0] = make_float4(v[0], v[1], v[2], v[3]);
+    q[1] = make_float4(v[4], v[5], v[6], v[7]);
+  } else {
+    *reinterpret_cast<uint4*>(p) = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                              pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256, 3) lift_kernel(const float2* __restrict__ n, const T* __restrict__ prm,
                                                    T* __restrict__ Vcf, T* __restrict__ Vcl, int B, int S,
                                                    int in_grid, int N) {
   __shared__ __align__(16) float Ps[C * 32];  // [c][32], zero-padded past 2S
@@ -72,30 +87,37 @@ __global__ void __launch_bounds__(256) lift_kernel(const float2* __restrict__ n,
     a[2 * s + 1] = v.y;
   }
   const float4* P4 = reinterpret_cast<const float4*>(Ps);
-  float o[32];
+  const int nf4 = (cin + 3) / 4;  // float4 groups of features that can be non-zero
+#pragma unroll 1
+  for (int q = 0; q < C / 8; ++q) {
+    float o[8];
 #pragma unroll
-  for (int c = 0; c < C; ++c) {
-    float t = ps[c];
+    for (int cc = 0; cc < 8; ++cc) {
+      const int c = 8 * q + cc;
+      float t = ps[c];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const float4 w = P4[c * 8 + i];
-      t = fmaf(w.x, a[4 * i], fmaf(w.y, a[4 * i + 1], fmaf(w.z, a[4 * i + 2], fmaf(w.w, a[4 * i + 3], t))));
-    }
-    o[c] = t;
-  }
-  for (int dy = 0; dy < r; ++dy) {
-    const int row = (yi * r + dy) * N + xi * r;
-    for (int dx = 0; dx < r; ++dx) st32(Vcl + ((size_t)b * P + row + dx) * C, o);
-    T* cf = Vcf + (size_t)b * C * P + row;
-    if ((r & 1) == 0) {
-      for (int dx = 0; dx < r; dx += 2) {
-#pragma unroll
-        for (int c = 0; c < C; ++c) st_same_pair(cf + (size_t)c * P + dx, o[c]);
+      for (int i = 0; i < 8; ++i) {
+        if (i < nf4) {
+          const float4 w = P4[c * 8 + i];
+          t = fmaf(w.x, a[4 * i], fmaf(w.y, a[4 * i + 1], fmaf(w.z, a[4 * i + 2], fmaf(w.w, a[4 * i + 3], t))));
+        }
       }
-    } else {
-      for (int dx = 0; dx < r; ++dx) {
+      o[cc] = t;
+    }
+    for (int dy = 0; dy < r; ++dy) {
+      const int row = (yi * r + dy) * N + xi * r;
+      for (int dx = 0; dx < r; ++dx) st8(Vcl + ((size_t)b * P + row + dx) * C + 8 * q, o);
+      T* cf = Vcf + ((size_t)b * C + 8 * q) * P + row;
+      if ((r & 1) == 0) {
+        for (int dx = 0; dx < r; dx += 2) {
 #pragma unroll
-        for (int c = 0; c < C; ++c) cf[(size_t)c * P + dx] = from_f<T>(o[c]);
+          for (int cc = 0; cc < 8; ++cc) st_same_pair(cf + (size_t)cc * P + dx, o[cc]);
+        }
+      } else {
+        for (int dx = 0; dx < r; ++dx) {
+#pragma unroll
+          for (int cc = 0; cc < 8; ++cc) cf[(size_t)cc * P + dx] = from_f<T>(o[cc]);
+        }
       }
     }
   }
