@@ -124,11 +124,12 @@ __global__ void __launch_bounds__(256, 3) lift_kernel(const float2* __restrict__
 }
 
 // ---- mixing (per kept mode k, complex C x C), spectra mode-major Vh[split][k][b C + i] ------
-// One CTA per (NM = 4 consecutive kept modes, block of 32 samples), 256 threads: thread (warp w,
+// One CTA per (NM consecutive kept modes, block of 32 samples), 256 threads: thread (warp w,
 // lane) handles samples w + 8 j (j < 4), channel `lane` and the NM modes, so each (sample,
 // channel) row of the K-major outputs Wh / GVh receives its NM consecutive modes in one
-// 16-byte store (m is a multiple of 4, so m^2 is a multiple of NM). Operands are staged in
-// shared memory as [mode][32][34] complex tiles.
+// store (16 bytes for NM = 4; m is a multiple of 4, so m^2 is a multiple of NM). Operands are
+// staged in shared memory as [mode][32][34] complex tiles. The forward takes NM = 4; the
+// backward stages three operands per mode and keeps NM = 1, where more blocks fit an SM.
 constexpr int MIX_SAMPLES = 32;
 constexpr int MIX_MODES_FWD = 4;
 constexpr int MIX_MODES_BWD = 1;
