@@ -124,15 +124,13 @@ __global__ void __launch_bounds__(256, 3) lift_kernel(const float2* __restrict__
 }
 
 // ---- mixing (per kept mode k, complex C x C), spectra mode-major Vh[split][k][b C + i] ------
-// One CTA per (NM consecutive kept modes, block of 32 samples), 256 threads: thread (warp w,
-// lane) handles samples w + 8 j (j < 4), channel `lane` and the NM modes, so each (sample,
-// channel) row of the K-major outputs Wh / GVh receives its NM consecutive modes in one
-// store (16 bytes for NM = 4; m is a multiple of 4, so m^2 is a multiple of NM). Operands are
-// staged in shared memory as [mode][32][34] complex tiles. The forward takes NM = 4; the
-// backward stages three operands per mode and keeps NM = 1, where more blocks fit an SM.
+// Per kept mode and block of 32 samples the mixing is a 32 x 32 complex product over 32 terms. The
+// operands are staged in shared memory as [32][34] complex tiles (16-byte aligned rows) and each
+// thread computes a 4 x 4 register tile. The forward takes NM = 4 consecutive modes per CTA (m is
+// a multiple of 4, so m^2 is a multiple of NM), so that each (sample, channel) row of the K-major
+// output Wh receives its four modes in one 16-byte store; the backward takes one mode per CTA.
 constexpr int MIX_SAMPLES = 32;
 constexpr int MIX_MODES_FWD = 4;
-constexpr int MIX_MODES_BWD = 1;
 constexpr int MIX_LD = C + 2;          // row stride of a staged tile (float2): rows stay 16-byte aligned
 constexpr int MIX_TILE = C * MIX_LD;   // float2 elements of one staged [32][34] tile
 
@@ -196,54 +194,83 @@ __device__ __forceinline__ float2 ld_spec(const float2* __restrict__ X, size_t o
   return v;
 }
 
+// Per-mode products as 4 x 4 register tiles: each k-step reads its four values of each operand from one
+// staged row in two 16-byte loads (no operand is read as a warp-wide broadcast per product), and a
+// thread then does 16 complex multiply-adds.
+__device__ __forceinline__ void ld4c(const float2* p, float2 (&v)[4]) {  // p 16-byte aligned
+  const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  v[0] = make_float2(a.x, a.y);
+  v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y);
+  v[3] = make_float2(b.z, b.w);
+}
+
 // forward: Wh[b][o][k] = scale sum_i R[k][o][i] Vh[b][i][k]
+// Thread t owns the tile (mode kk = t / 64, samples 4 sg .. 4 sg + 3, outputs 4 og .. 4 og + 3) with
+// sg = (t % 64) / 8 and og = t % 8; R is staged [mode][i][o] and V [mode][i][s]. The results pass
+// through shared memory ([mode][s][o]) so that each (sample, output) row of Wh receives its NM modes
+// in one store.
 template <typename T, int NM>
 __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__ Vh, int splits,
                                                       long long split_stride, long long ld, const T* __restrict__ R,
                                                       T* __restrict__ Wh, float scale, int B, int Kp) {
+  static_assert(NM * 64 == 256, "one 64-thread group per mode");
   extern __shared__ __align__(16) float2 mix_smem[];
   float2* Rs = mix_smem;                 // [mode][i][o]
-  float2* Vs = mix_smem + NM * MIX_TILE;  // [mode][s][i]
+  float2* Vs = mix_smem + NM * MIX_TILE;  // [mode][i][s], then the results [mode][s][o]
   const int k0 = blockIdx.x * NM, b0 = blockIdx.y * MIX_SAMPLES;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int t = threadIdx.x;
 #pragma unroll
   for (int q = 0; q < 4 * NM; ++q) {
     const int idx = t + 256 * q, kk = idx / (C * C), row = (idx / C) % C, col = idx % C;
     Rs[kk * MIX_TILE + col * MIX_LD + row] = ld_pair(R, ((size_t)(k0 + kk) * C + row) * C + col);
     const int b = b0 + row;
-    Vs[kk * MIX_TILE + row * MIX_LD + col] =
+    Vs[kk * MIX_TILE + col * MIX_LD + row] =
         b < B ? ld_spec(Vh, (size_t)(k0 + kk) * ld + (size_t)b * C + col, splits, split_stride)
               : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  // each R element loaded once feeds the four samples; V is read two channels per 16-byte load
-  float re[4][NM], im[4][NM];
+  const int kk = t >> 6, sg = (t & 63) >> 3, og = t & 7;
+  float re[4][4], im[4][4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int kk = 0; kk < NM; ++kk) re[j][kk] = im[j][kk] = 0.f;
-#pragma unroll 2
-  for (int i = 0; i < C; i += 2) {
+    for (int c = 0; c < 4; ++c) re[a][c] = im[a][c] = 0.f;
+  const float2* vb = Vs + kk * MIX_TILE + 4 * sg;
+  const float2* rb = Rs + kk * MIX_TILE + 4 * og;
+#pragma unroll 4
+  for (int i = 0; i < C; ++i) {
+    float2 v[4], r[4];
+    ld4c(vb + i * MIX_LD, v);
+    ld4c(rb + i * MIX_LD, r);
 #pragma unroll
-    for (int kk = 0; kk < NM; ++kk) {
-      const float2 r0 = Rs[kk * MIX_TILE + i * MIX_LD + lane], r1 = Rs[kk * MIX_TILE + (i + 1) * MIX_LD + lane];
+    for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const float4 v = *reinterpret_cast<const float4*>(Vs + kk * MIX_TILE + (w + 8 * j) * MIX_LD + i);
-        re[j][kk] = fmaf(r1.x, v.z, fmaf(-r1.y, v.w, fmaf(r0.x, v.x, fmaf(-r0.y, v.y, re[j][kk]))));
-        im[j][kk] = fmaf(r1.x, v.w, fmaf(r1.y, v.z, fmaf(r0.x, v.y, fmaf(r0.y, v.x, im[j][kk]))));
+      for (int c = 0; c < 4; ++c) {
+        re[a][c] = fmaf(r[c].x, v[a].x, fmaf(-r[c].y, v[a].y, re[a][c]));
+        im[a][c] = fmaf(r[c].x, v[a].y, fmaf(r[c].y, v[a].x, im[a][c]));
       }
-    }
   }
+  __syncthreads();  // every tile is done with Vs
+  float2* Os = Vs;  // [mode][s][o], row stride MIX_LD
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int b = b0 + w + 8 * j;
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int kk = 0; kk < NM; ++kk) {
-      re[j][kk] *= scale;
-      im[j][kk] *= scale;
+    for (int c = 0; c < 4; ++c)
+      Os[kk * MIX_TILE + (4 * sg + a) * MIX_LD + 4 * og + c] = make_float2(scale * re[a][c], scale * im[a][c]);
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < C * MIX_SAMPLES / 256; ++q) {
+    const int p = t + 256 * q, sm = p / C, o = p % C, b = b0 + sm;
+    if (b >= B) continue;
+    float xr[NM], xi[NM];
+#pragma unroll
+    for (int m2 = 0; m2 < NM; ++m2) {
+      const float2 x = Os[m2 * MIX_TILE + sm * MIX_LD + o];
+      xr[m2] = x.x;
+      xi[m2] = x.y;
     }
-    if (b < B) st_pairs<T, NM>(Wh, (((size_t)b * C + lane) * Kp) / 2 + k0, re[j], im[j]);
+    st_pairs<T, NM>(Wh, (((size_t)b * C + o) * Kp) / 2 + k0, xr, xi);
   }
 }
 
@@ -252,84 +279,91 @@ __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__
 //   part dR[k][o][i] = sum_b G[b][o][k] conj(Vh[b][i][k])   (this CTA's samples)
 //   part dc[o] = N^2 sum_b Re G[b][o][k_dc]                   (the DC mode carries sum_x dZ / N^2)
 // part row (one per sample block): [m^2][C][C][2] then [C]
-template <typename T, int NM>
-__global__ void __launch_bounds__(256) mix_bwd_kernel(const float2* __restrict__ G, const float2* __restrict__ Vh,
+// One CTA per (kept mode, block of 32 samples), 128 threads: threads 0-63 own GVh tiles (samples
+// 4 sg .., channels 4 ig ..), threads 64-127 dR tiles (outputs 4 og .., channels 4 ig ..). G is
+// staged both as [s][o] and as [o][s], so each product reads its rows contiguously.
+template <typename T>
+__global__ void __launch_bounds__(128) mix_bwd_kernel(const float2* __restrict__ G, const float2* __restrict__ Vh,
                                                       int splits, long long split_stride, long long ld,
                                                       const T* __restrict__ R, T* __restrict__ GVh,
                                                       float* __restrict__ part, int B, int m, int Kp, int N) {
   extern __shared__ __align__(16) float2 mix_smem[];
-  float2* Rs = mix_smem;                     // [mode][o][i]
-  float2* Gs = mix_smem + NM * MIX_TILE;      // [mode][s][o]
-  float2* Vs = mix_smem + 2 * NM * MIX_TILE;  // [mode][s][i]
-  const int k0 = blockIdx.x * NM, b0 = blockIdx.y * MIX_SAMPLES;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  float2* Rs = mix_smem;                 // [o][i]
+  float2* Gs = mix_smem + MIX_TILE;      // [s][o]
+  float2* Gt = mix_smem + 2 * MIX_TILE;  // [o][s]
+  float2* Vs = mix_smem + 3 * MIX_TILE;  // [s][i]
+  const int k = blockIdx.x, b0 = blockIdx.y * MIX_SAMPLES;
+  const int t = threadIdx.x;
   const int kdc = (m / 2) * m + m / 2;
   const size_t row0 = (size_t)blockIdx.y * ((size_t)m * m * C * C * 2 + C);
 #pragma unroll
-  for (int q = 0; q < 4 * NM; ++q) {
-    const int idx = t + 256 * q, kk = idx / (C * C), row = (idx / C) % C, col = idx % C;
-    const int e = kk * MIX_TILE + row * MIX_LD + col;
-    Rs[e] = ld_pair(R, ((size_t)(k0 + kk) * C + row) * C + col);
+  for (int q = 0; q < (C * C) / 128; ++q) {
+    const int idx = t + 128 * q, row = idx / C, col = idx % C;
+    Rs[row * MIX_LD + col] = ld_pair(R, ((size_t)k * C + row) * C + col);
     const int b = b0 + row;
-    const size_t off = (size_t)(k0 + kk) * ld + (size_t)b * C + col;
-    Gs[e] = b < B ? ld_spec(G, off, splits, split_stride) : make_float2(0.f, 0.f);
-    Vs[e] = b < B ? ld_spec(Vh, off, splits, split_stride) : make_float2(0.f, 0.f);
+    const size_t off = (size_t)k * ld + (size_t)b * C + col;
+    const float2 g = b < B ? ld_spec(G, off, splits, split_stride) : make_float2(0.f, 0.f);
+    Gs[row * MIX_LD + col] = g;
+    Gt[col * MIX_LD + row] = g;
+    Vs[row * MIX_LD + col] = b < B ? ld_spec(Vh, off, splits, split_stride) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  // GVh: thread (samples w + 8 j, i = lane); each R element loaded once feeds the four samples,
-  // G is read two outputs per 16-byte load
-  {
-    float re[4][NM], im[4][NM];
+  float re[4][4], im[4][4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+  for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int kk = 0; kk < NM; ++kk) re[j][kk] = im[j][kk] = 0.f;
-#pragma unroll 2
-    for (int o = 0; o < C; o += 2) {
+    for (int c = 0; c < 4; ++c) re[a][c] = im[a][c] = 0.f;
+  if (t < 64) {
+    // GVh tile: samples 4 sg + a, channels 4 ig + c; conj(r) g over the outputs o
+    const int sg = t >> 3, ig = t & 7;
+#pragma unroll 4
+    for (int o = 0; o < C; ++o) {
+      float2 g[4], r[4];
+      ld4c(Gt + o * MIX_LD + 4 * sg, g);
+      ld4c(Rs + o * MIX_LD + 4 * ig, r);
 #pragma unroll
-      for (int kk = 0; kk < NM; ++kk) {
-        const float2 r0 = Rs[kk * MIX_TILE + o * MIX_LD + lane], r1 = Rs[kk * MIX_TILE + (o + 1) * MIX_LD + lane];
+      for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const float4 g = *reinterpret_cast<const float4*>(Gs + kk * MIX_TILE + (w + 8 * j) * MIX_LD + o);
-          // conj(r) g
-          re[j][kk] = fmaf(r1.x, g.z, fmaf(r1.y, g.w, fmaf(r0.x, g.x, fmaf(r0.y, g.y, re[j][kk]))));
-          im[j][kk] = fmaf(r1.x, g.w, fmaf(-r1.y, g.z, fmaf(r0.x, g.y, fmaf(-r0.y, g.x, im[j][kk]))));
+        for (int c = 0; c < 4; ++c) {
+          re[a][c] = fmaf(r[c].x, g[a].x, fmaf(r[c].y, g[a].y, re[a][c]));
+          im[a][c] = fmaf(r[c].x, g[a].y, fmaf(-r[c].y, g[a].x, im[a][c]));
         }
-      }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int b = b0 + w + 8 * j;
-      if (b < B) st_pairs<T, NM>(GVh, (((size_t)b * C + lane) * Kp) / 2 + k0, re[j], im[j]);
+    for (int a = 0; a < 4; ++a) {
+      const int b = b0 + 4 * sg + a;
+      if (b >= B) continue;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        st_pair(GVh, (((size_t)b * C + 4 * ig + c) * Kp) / 2 + k, make_float2(re[a][c], im[a][c]));
+    }
+  } else {
+    // dR tile: outputs 4 og + a, channels 4 ig + c; g conj(v) over the block's samples
+    const int og = (t - 64) >> 3, ig = t & 7;
+#pragma unroll 4
+    for (int sm = 0; sm < MIX_SAMPLES; ++sm) {
+      float2 g[4], v[4];
+      ld4c(Gs + sm * MIX_LD + 4 * og, g);
+      ld4c(Vs + sm * MIX_LD + 4 * ig, v);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          re[a][c] = fmaf(g[a].x, v[c].x, fmaf(g[a].y, v[c].y, re[a][c]));
+          im[a][c] = fmaf(g[a].y, v[c].x, fmaf(-g[a].x, v[c].y, im[a][c]));
+        }
+    }
+    float4* dst = reinterpret_cast<float4*>(part + row0);  // complex pairs (c, c + 1)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const size_t e = ((size_t)k * C + 4 * og + a) * C + 4 * ig;  // complex index, a multiple of 4
+      dst[e / 2] = make_float4(re[a][0], im[a][0], re[a][1], im[a][1]);
+      dst[e / 2 + 1] = make_float4(re[a][2], im[a][2], re[a][3], im[a][3]);
     }
   }
-  // dR: thread (outputs o = 4 w + jj, i = lane), summed over the block's samples; each V element
-  // loaded once feeds the four outputs, whose G values come in two 16-byte loads
-#pragma unroll 1
-  for (int kk = 0; kk < NM; ++kk) {
-    float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-    for (int s = 0; s < MIX_SAMPLES; ++s) {
-      const float2 v = Vs[kk * MIX_TILE + s * MIX_LD + lane];
-      const float4* g4 = reinterpret_cast<const float4*>(Gs + kk * MIX_TILE + s * MIX_LD + 4 * w);
-      const float4 ga = g4[0], gb = g4[1];
-      const float2 g[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w), make_float2(gb.x, gb.y),
-                           make_float2(gb.z, gb.w)};
-#pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {  // g conj(v)
-        re[jj] = fmaf(g[jj].x, v.x, fmaf(g[jj].y, v.y, re[jj]));
-        im[jj] = fmaf(g[jj].y, v.x, fmaf(-g[jj].x, v.y, im[jj]));
-      }
-    }
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj)
-      reinterpret_cast<float2*>(part + row0)[((size_t)(k0 + kk) * C + 4 * w + jj) * C + lane] =
-          make_float2(re[jj], im[jj]);
-  }
-  if (kdc >= k0 && kdc < k0 + NM && t < C) {
+  if (k == kdc && t < C) {
     float d = 0.f;
-    for (int s = 0; s < MIX_SAMPLES; ++s) d += Gs[(kdc - k0) * MIX_TILE + s * MIX_LD + t].x;
+    for (int sm = 0; sm < MIX_SAMPLES; ++sm) d += Gs[sm * MIX_LD + t].x;
     part[row0 + (size_t)m * m * C * C * 2 + t] = d * (float)N * (float)N;
   }
 }
@@ -763,24 +797,16 @@ cudaError_t launch_mix_fwd(const float2* Vh, int splits, long long split_stride,
 
 int mix_sample_blocks(int B) { return (B + MIX_SAMPLES - 1) / MIX_SAMPLES; }
 
-template <typename T, int NM>
-static cudaError_t launch_mix_bwd_t(const float2* G, const float2* Vh, int splits, long long split_stride,
-                                    long long ld, const T* R, T* GVh, float* part, int B, int m, int Kp, int N,
-                                    cudaStream_t st) {
-  const size_t smem = (size_t)3 * NM * MIX_TILE * sizeof(float2);
-  const void* fn = reinterpret_cast<const void*>(mix_bwd_kernel<T, NM>);
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const dim3 grid(m * m / NM, mix_sample_blocks(B));
-  mix_bwd_kernel<T, NM><<<grid, 256, smem, st>>>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N);
-  return cudaGetLastError();
-}
-
 template <typename T>
 cudaError_t launch_mix_bwd(const float2* G, const float2* Vh, int splits, long long split_stride, long long ld,
                            const T* R, T* GVh, float* part, int B, int m, int Kp, int N, cudaStream_t st) {
-  if ((m * m) % MIX_MODES_BWD) return cudaErrorInvalidValue;
-  return launch_mix_bwd_t<T, MIX_MODES_BWD>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N, st);
+  const size_t smem = (size_t)4 * MIX_TILE * sizeof(float2);
+  const void* fn = reinterpret_cast<const void*>(mix_bwd_kernel<T>);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid(m * m, mix_sample_blocks(B));
+  mix_bwd_kernel<T><<<grid, 128, smem, st>>>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N);
+  return cudaGetLastError();
 }
 
 template <typename T>
