@@ -205,6 +205,34 @@ __device__ __forceinline__ void ld4c(const float2* p, float2 (&v)[4]) {  // p 16
   v[3] = make_float2(b.z, b.w);
 }
 
+// R staged as the parameters' own complex pairs: BF16 pairs (one 32-bit word, rows of 36 words) or
+// FP32 pairs (float2, rows of MIX_LD); four consecutive outputs are one 16-byte aligned group.
+template <typename T>
+struct MixRStage;
+template <>
+struct MixRStage<__nv_bfloat16> {
+  using E = uint32_t;
+  static constexpr int LD = C + 4;
+  __device__ static E load(const __nv_bfloat16* R, size_t pair) { return reinterpret_cast<const uint32_t*>(R)[pair]; }
+  __device__ static void ld4(const E* p, float2 (&v)[4]) {
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int c = 0; c < 4; ++c) v[c] = make_float2(__uint_as_float(w[c] << 16), __uint_as_float(w[c] & 0xffff0000u));
+  }
+};
+template <>
+struct MixRStage<float> {
+  using E = float2;
+  static constexpr int LD = MIX_LD;
+  __device__ static E load(const float* R, size_t pair) { return reinterpret_cast<const float2*>(R)[pair]; }
+  __device__ static void ld4(const E* p, float2 (&v)[4]) { ld4c(p, v); }
+};
+template <typename T>
+constexpr size_t mix_fwd_rs_bytes(int NM) {
+  return (size_t)NM * C * MixRStage<T>::LD * sizeof(typename MixRStage<T>::E);
+}
+
 // forward: Wh[b][o][k] = scale sum_i R[k][o][i] Vh[b][i][k]
 // Thread t owns the tile (mode kk = t / 64, samples 4 sg .. 4 sg + 3, outputs 4 og .. 4 og + 3) with
 // sg = (t % 64) / 8 and og = t % 8; R is staged [mode][i][o] and V [mode][i][s]. The results pass
@@ -215,15 +243,18 @@ __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__
                                                       long long split_stride, long long ld, const T* __restrict__ R,
                                                       T* __restrict__ Wh, float scale, int B, int Kp) {
   static_assert(NM * 64 == 256, "one 64-thread group per mode");
+  using RS = MixRStage<T>;
+  constexpr int RT = C * RS::LD;  // staged R elements per mode
   extern __shared__ __align__(16) float2 mix_smem[];
-  float2* Rs = mix_smem;                 // [mode][i][o]
-  float2* Vs = mix_smem + NM * MIX_TILE;  // [mode][i][s], then the results [mode][s][o]
+  typename RS::E* Rs = reinterpret_cast<typename RS::E*>(mix_smem);  // [mode][i][o]
+  float2* Vs = reinterpret_cast<float2*>(reinterpret_cast<uint8_t*>(mix_smem) + mix_fwd_rs_bytes<T>(NM));
+  // Vs: [mode][i][s], then the results [mode][s][o]
   const int k0 = blockIdx.x * NM, b0 = blockIdx.y * MIX_SAMPLES;
   const int t = threadIdx.x;
 #pragma unroll
   for (int q = 0; q < 4 * NM; ++q) {
     const int idx = t + 256 * q, kk = idx / (C * C), row = (idx / C) % C, col = idx % C;
-    Rs[kk * MIX_TILE + col * MIX_LD + row] = ld_pair(R, ((size_t)(k0 + kk) * C + row) * C + col);
+    Rs[kk * RT + col * RS::LD + row] = RS::load(R, ((size_t)(k0 + kk) * C + row) * C + col);
     const int b = b0 + row;
     Vs[kk * MIX_TILE + col * MIX_LD + row] =
         b < B ? ld_spec(Vh, (size_t)(k0 + kk) * ld + (size_t)b * C + col, splits, split_stride)
@@ -237,12 +268,12 @@ __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__
 #pragma unroll
     for (int c = 0; c < 4; ++c) re[a][c] = im[a][c] = 0.f;
   const float2* vb = Vs + kk * MIX_TILE + 4 * sg;
-  const float2* rb = Rs + kk * MIX_TILE + 4 * og;
+  const typename RS::E* rb = Rs + kk * RT + 4 * og;
 #pragma unroll 4
   for (int i = 0; i < C; ++i) {
     float2 v[4], r[4];
     ld4c(vb + i * MIX_LD, v);
-    ld4c(rb + i * MIX_LD, r);
+    RS::ld4(rb + i * RS::LD, r);
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -779,7 +810,7 @@ cudaError_t launch_lift(const float2* n, const T* params, T* Vcf, T* Vcl, int B,
 template <typename T, int NM>
 static cudaError_t launch_mix_fwd_t(const float2* Vh, int splits, long long split_stride, long long ld, const T* R,
                                     T* Wh, float scale, int B, int m, int Kp, cudaStream_t st) {
-  const size_t smem = (size_t)2 * NM * MIX_TILE * sizeof(float2);
+  const size_t smem = mix_fwd_rs_bytes<T>(NM) + (size_t)NM * MIX_TILE * sizeof(float2);
   const void* fn = reinterpret_cast<const void*>(mix_fwd_kernel<T, NM>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
