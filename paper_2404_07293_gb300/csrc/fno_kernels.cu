@@ -305,6 +305,19 @@ __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__
   }
 }
 
+// Split row layout of a staged 32-complex row: element j at split_pos(j), so that the two halves
+// (j, j + 1) and (j + 2, j + 3) of every aligned group of four sit in two separate 128-byte runs. Eight
+// lanes reading eight different groups then touch 128 contiguous bytes per 16-byte load.
+__device__ __forceinline__ int split_pos(int j) { return ((j & 2) << 3) + ((j >> 2) << 1) + (j & 1); }
+__device__ __forceinline__ void ld4s(const float2* row, int g, float2 (&v)[4]) {  // group g of a split row
+  const float4 a = *reinterpret_cast<const float4*>(row + 2 * g);
+  const float4 b = *reinterpret_cast<const float4*>(row + 16 + 2 * g);
+  v[0] = make_float2(a.x, a.y);
+  v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y);
+  v[3] = make_float2(b.z, b.w);
+}
+
 // backward (G = dL/dRe + i dL/dIm convention):
 //   GVh[b][i][k] = sum_o conj(R[k][o][i]) G[b][o][k]
 //   part dR[k][o][i] = sum_b G[b][o][k] conj(Vh[b][i][k])   (this CTA's samples)
@@ -312,31 +325,32 @@ __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__
 // part row (one per sample block): [m^2][C][C][2] then [C]
 // One CTA per (kept mode, block of 32 samples), 128 threads: threads 0-63 own GVh tiles (samples
 // 4 sg .., channels 4 ig ..), threads 64-127 dR tiles (outputs 4 og .., channels 4 ig ..). G is
-// staged both as [s][o] and as [o][s], so each product reads its rows contiguously.
+// staged both as [s][o] and as [o][s], so each product reads its rows contiguously; the rows read
+// by eight different groups per warp use the split layout.
 template <typename T>
 __global__ void __launch_bounds__(128) mix_bwd_kernel(const float2* __restrict__ G, const float2* __restrict__ Vh,
                                                       int splits, long long split_stride, long long ld,
                                                       const T* __restrict__ R, T* __restrict__ GVh,
                                                       float* __restrict__ part, int B, int m, int Kp, int N) {
   extern __shared__ __align__(16) float2 mix_smem[];
-  float2* Rs = mix_smem;                 // [o][i]
-  float2* Gs = mix_smem + MIX_TILE;      // [s][o]
+  float2* Rs = mix_smem;                 // [o][i], split rows
+  float2* Gs = mix_smem + MIX_TILE;      // [s][o], split rows
   float2* Gt = mix_smem + 2 * MIX_TILE;  // [o][s]
-  float2* Vs = mix_smem + 3 * MIX_TILE;  // [s][i]
+  float2* Vs = mix_smem + 3 * MIX_TILE;  // [s][i], split rows
   const int k = blockIdx.x, b0 = blockIdx.y * MIX_SAMPLES;
   const int t = threadIdx.x;
   const int kdc = (m / 2) * m + m / 2;
   const size_t row0 = (size_t)blockIdx.y * ((size_t)m * m * C * C * 2 + C);
 #pragma unroll
   for (int q = 0; q < (C * C) / 128; ++q) {
-    const int idx = t + 128 * q, row = idx / C, col = idx % C;
-    Rs[row * MIX_LD + col] = ld_pair(R, ((size_t)k * C + row) * C + col);
+    const int idx = t + 128 * q, row = idx / C, col = idx % C, sc = split_pos(col);
+    Rs[row * MIX_LD + sc] = ld_pair(R, ((size_t)k * C + row) * C + col);
     const int b = b0 + row;
     const size_t off = (size_t)k * ld + (size_t)b * C + col;
     const float2 g = b < B ? ld_spec(G, off, splits, split_stride) : make_float2(0.f, 0.f);
-    Gs[row * MIX_LD + col] = g;
+    Gs[row * MIX_LD + sc] = g;
     Gt[col * MIX_LD + row] = g;
-    Vs[row * MIX_LD + col] = b < B ? ld_spec(Vh, off, splits, split_stride) : make_float2(0.f, 0.f);
+    Vs[row * MIX_LD + sc] = b < B ? ld_spec(Vh, off, splits, split_stride) : make_float2(0.f, 0.f);
   }
   __syncthreads();
   float re[4][4], im[4][4];
@@ -351,7 +365,7 @@ __global__ void __launch_bounds__(128) mix_bwd_kernel(const float2* __restrict__
     for (int o = 0; o < C; ++o) {
       float2 g[4], r[4];
       ld4c(Gt + o * MIX_LD + 4 * sg, g);
-      ld4c(Rs + o * MIX_LD + 4 * ig, r);
+      ld4s(Rs + o * MIX_LD, ig, r);
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -374,8 +388,8 @@ __global__ void __launch_bounds__(128) mix_bwd_kernel(const float2* __restrict__
 #pragma unroll 4
     for (int sm = 0; sm < MIX_SAMPLES; ++sm) {
       float2 g[4], v[4];
-      ld4c(Gs + sm * MIX_LD + 4 * og, g);
-      ld4c(Vs + sm * MIX_LD + 4 * ig, v);
+      ld4s(Gs + sm * MIX_LD, og, g);
+      ld4s(Vs + sm * MIX_LD, ig, v);
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
@@ -394,7 +408,7 @@ __global__ void __launch_bounds__(128) mix_bwd_kernel(const float2* __restrict__
   }
   if (k == kdc && t < C) {
     float d = 0.f;
-    for (int sm = 0; sm < MIX_SAMPLES; ++sm) d += Gs[sm * MIX_LD + t].x;
+    for (int sm = 0; sm < MIX_SAMPLES; ++sm) d += Gs[sm * MIX_LD + split_pos(t)].x;
     part[row0 + (size_t)m * m * C * C * 2 + t] = d * (float)N * (float)N;
   }
 }
