@@ -288,7 +288,7 @@ scw_status scw_plan_get_timings(scw_plan_t plan, scw_kernel_times* t);
  * device synchronisation, or processes that forbid allocation after start-up.
  * Such callers cannot create a plan (plan creation allocates its workspace), so
  * this call takes the sizes directly and does the recompose step of
- * scw_recompose (Eq. 10: x-pass and y-pass) with the same kernels.
+ * scw_recompose (x-pass and y-pass) with the same kernels.
  *
  *   S    DEVICE complex64 [Fz][3][U V] spectra (caller-owned input)
  *   out  DEVICE complex64 [3][Fz][Fy][Fx] field (caller-owned output, 16-byte aligned)

@@ -308,6 +308,9 @@ __global__ void __launch_bounds__(256) mix_fwd_kernel(const float2* __restrict__
 // Split row layout of a staged 32-complex row: element j at split_pos(j), so that the two halves
 // (j, j + 1) and (j + 2, j + 3) of every aligned group of four sit in two separate 128-byte runs. Eight
 // lanes reading eight different groups then touch 128 contiguous bytes per 16-byte load.
+// The split layout puts the second half-group at offset 16 and loads 16-byte pairs: it assumes
+// 32-element rows and an even row stride.
+static_assert(C == 32 && MIX_LD % 2 == 0, "split_pos/ld4s assume C == 32 and an even MIX_LD");
 __device__ __forceinline__ int split_pos(int j) { return ((j & 2) << 3) + ((j >> 2) << 1) + (j & 1); }
 __device__ __forceinline__ void ld4s(const float2* row, int g, float2 (&v)[4]) {  // group g of a split row
   const float4 a = *reinterpret_cast<const float4*>(row + 2 * g);

@@ -222,6 +222,61 @@ def test_convolution_matrix_is_the_product_rule():
     assert np.abs(Phi @ fhat - ghat).max() < 1e-12
 
 
+def _ez_from_curl(Q, n_grid, U, V, X, Y, lam):
+    """E_z spectrum of each column of Q (rows [Px, Py, Bx, By]) from Maxwell on
+    the sample grid: B_x, B_y as band-limited fields, (curl B)_z by exact spectral
+    derivatives of those trigonometric polynomials, then E_z = (curl B)_z /
+    (-i k n^2) pointwise (curl B = -i k n^2 E in the oracle's units), and its
+    spectrum at the orders."""
+    M = U * V
+    k = 2 * np.pi / lam
+    ny, nx = n_grid.shape
+    u, v = cw.orders(U, V)
+    out = np.empty((M, Q.shape[1]), dtype=complex)
+    fx = np.fft.fftfreq(nx, d=X / nx)  # cycles per unit length of each FFT bin
+    fy = np.fft.fftfreq(ny, d=Y / ny)
+    for j in range(Q.shape[1]):
+        grids = []
+        for blk in (2, 3):  # B_x, B_y
+            spec = np.zeros((ny, nx), dtype=complex)
+            spec[v % ny, u % nx] = Q[blk * M:(blk + 1) * M, j] * nx * ny
+            grids.append(spec)
+        dBy_dx = np.fft.ifft2(grids[1] * (2j * np.pi * fx[None, :]))
+        dBx_dy = np.fft.ifft2(grids[0] * (2j * np.pi * fy[:, None]))
+        ez = (dBy_dx - dBx_dy) / (-1j * k * n_grid.astype(complex) ** 2)
+        out[:, j] = (np.fft.fft2(ez) / (nx * ny))[v % ny, u % nx]
+    return out
+
+
+@pytest.mark.parametrize("kind", ["random", "ellipsoids"])
+def test_ez_rows_follow_maxwell_in_a_heterogeneous_layer(kind):
+    """The E_z rows of W (Eq. 33, reading R5) inside a heterogeneous complex-n
+    layer equal the truncated spectrum of (curl B)_z / (-i k n^2) on the sample
+    grid. Exact (no aliasing) because the grid holds every order difference
+    (N >= 2U-1). The sample has no inversion symmetry, so Psi^T differs from Psi
+    and an index reversal inside e_rows would fail here."""
+    U, V, nx, ny, X, Y, lam = 5, 4, 12, 10, 2.3, 1.9, 1.0
+    rng = np.random.default_rng(17)
+    if kind == "random":
+        n = 1.2 + 0.4 * rng.random((ny, nx)) + 0.08j * rng.random((ny, nx))
+    else:
+        n = wl.ellipsoid_volume(4, nx, ny, 3, semi_axes=(2, 5), kappa=(0.01, 0.05))[1]
+        assert np.ptp(n.real) > 0.2  # the slice cuts an ellipsoid
+    sx, sy = cw.directions(U, V, lam, X, Y)
+    u, v = cw.orders(U, V)
+    _, Psi, _ = cw.layer_operators(n, sx, sy, u, v)
+    M = U * V
+    Q = rng.standard_normal((4 * M, 6)) + 1j * rng.standard_normal((4 * M, 6))
+    W = cw.e_rows(Q, Psi, sx, sy)
+    ez = _ez_from_curl(Q, n, U, V, X, Y, lam)
+    scale = np.abs(ez).max()
+    assert np.abs(W[2 * M:] - ez).max() < 1e-12 * scale
+    assert np.array_equal(W[:2 * M], Q[:2 * M])  # E_x, E_y rows are the P rows themselves
+    # the test tells the two convolution orientations apart on this sample
+    h = sy[:, None] * Q[2 * M:3 * M] - sx[:, None] * Q[3 * M:]
+    assert np.abs(Psi.T @ h - ez).max() > 1e-3 * scale
+
+
 # P10 ------------------------------------------------------------------------
 def test_translation_covariance():
     p = wl.config_tiny()

@@ -3,15 +3,18 @@
 The allocation-free entry point serves callers that cannot allocate device
 memory (a host framework's own pool, loops that must not pay cudaMalloc's
 implicit synchronisation, processes that forbid allocation after start-up).
-It must give the same field as the plan path; two calls in a row with
-different sizes also check that the shared fixed scratch, which keeps the
-previous call's contents, never leaks into a result. This file is collected
+It must give the same field as the plan path and as the FP64 oracle's direct
+sum of Eq. 10; two calls in a row with different sizes also check that the
+shared fixed scratch, which keeps the previous call's contents, never leaks
+into a result. This file is collected
 last so that a stop-at-first-failure run has already run every other test.
 """
 import ctypes
 
 import numpy as np
 import pytest
+
+from oracle import cw, synth
 
 pytestmark = pytest.mark.gpu
 
@@ -48,5 +51,12 @@ def test_noalloc_matches_plan_recompose_two_calls(cuda_device):
         err = _rel(out.cpu().numpy(), ref)
         print("no-alloc call", call, "rel-L2 vs plan recompose", err)
         assert max(err) <= TOL
+        ls = cw.LayerSet(lam=1.0, X=X, Y=Y, U=U, V=V, z_bounds=np.array([0.0, 1.0]), W=None, gamma=None,
+                         alpha=None, p_inc=None, p_ref=None, p_trn=None)
+        xs, ys = synth.pixel_coords(ls, Fx, Fy, x0, y0)
+        got = out.cpu().numpy()
+        for f in range(Fz):
+            ora = synth.field_direct(ls, S[f].astype(np.complex128), xs, ys)
+            assert max(_rel(got[:, f], ora)) <= TOL, (call, f)
         plan.close()
 
