@@ -132,11 +132,18 @@ typedef struct {
 } scw_plan_info;
 
 /* Validate `desc`, assign planes to layers (Sec. 2.6.2: half-open layers, the
- * last one closed), build the order/twiddle tables and allocate the
- * workspace. Synchronous. On success *out owns the workspace.
+ * last one closed), build the order/twiddle tables of the orders (Sec. 2.2)
+ * and the output grid (Eq. 10) and allocate the workspace. The table uploads,
+ * workspace clears and (with SCW_FLAG_AUTOTUNE) the timed contraction
+ * candidates are queued on `stream` (a cudaStream_t; NULL = the legacy default
+ * stream), so they are ordered after the caller's earlier work there; the
+ * call synchronises `stream` before it returns. On success *out owns the
+ * workspace.
  * Errors: INVALID_ARGUMENT (sizes, non-ascending z, planes outside [z0,z_L]
  * without SCW_FLAG_EXTERIOR), UNSUPPORTED (sizes above the build's limits),
  * OUT_OF_MEMORY, CUDA (no sm_103a device). */
+scw_status scw_plan(const scw_desc* desc, void* stream, scw_plan_t* out);
+/* scw_plan on the legacy default stream. */
 scw_status scw_plan_create(const scw_desc* desc, scw_plan_t* out);
 
 /* Free everything the plan owns. NULL is accepted. */
@@ -170,16 +177,30 @@ scw_status scw_synthesize(scw_plan_t plan, void* out, void* stream);
  * phase / recompose launches -- replayed as one CUDA graph. All items share the
  * precision; on the tensor-core path they also share the plane-slot count
  * (the largest item's). SCW_FLAG_HOST_IO is not available here.
- *   descs  HOST [n] descriptors (copied); k_split 0 lets the autotuner choose. */
+ *   descs  HOST [n] descriptors (copied); k_split 0 lets the autotuner choose.
+ * Set-up work is queued on `stream` and synchronised as in scw_plan. */
+scw_status scw_plan_batched(const scw_desc* descs, int n, void* stream, scw_plan_t* out);
+/* scw_plan_batched on the legacy default stream. */
 scw_status scw_plan_batched_create(const scw_desc* descs, int n, scw_plan_t* out);
 /* As scw_plan_set_layers, for item `item` of a batched plan. */
 scw_status scw_plan_batched_set_layers(scw_plan_t plan, int item, const void* W, const void* gamma,
                                        const void* alpha, const void* p_inc, const void* p_ref,
                                        const void* p_trn, void* stream);
-/* Synthesise every item: outs is a HOST array of n DEVICE pointers, item i's
- * field complex64 [3][Fz_i][Fy_i][Fx_i]. Waits for the previous call's work on
- * `stream` to have consumed the pointer table, then queues one graph launch. */
-scw_status scw_synthesize_batched(scw_plan_t plan, void* const* outs, void* stream);
+/* Synthesise every item (Eq. 34 and Eq. 10 per item). The per-item inputs (W,
+ * gamma, alpha, p) were bound by scw_plan_batched_set_layers, which converts W
+ * into the plan's own layout, so the per-call item table holds the outputs:
+ * item i's field is complex64 [3][Fz_i][Fy_i][Fx_i] (or the strided patch its
+ * out_ld / out_plane_stride describe). Pass exactly one of
+ *   item_table  DEVICE [n] array of DEVICE pointers (8-byte aligned; each
+ *               pointer non-NULL and 16-byte aligned -- not checked on the
+ *               host, which cannot see them). It is copied on `stream` into the
+ *               plan's table, so the call does not synchronise and the table
+ *               may be rewritten once that copy has run;
+ *   outs        HOST [n] array of DEVICE pointers (checked). The call waits for
+ *               the previous call's work on `stream` to have consumed the
+ *               plan's pinned staging table before rewriting it.
+ * Then one graph launch is queued on `stream`. */
+scw_status scw_synthesize_batched(scw_plan_t plan, const void* item_table, void* const* outs, void* stream);
 /* Human-readable record of the split choice (model and timed candidates). */
 const char* scw_plan_tune_report(scw_plan_t plan);
 

@@ -77,6 +77,8 @@ def _per_illum(I, shape):
 
 def _stream_handle(stream):
     import torch
+    if stream is None and not torch.cuda.is_available():
+        return ctypes.c_void_p(0)  # no device: the library call itself reports it (no CPU fallback)
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
 
@@ -102,11 +104,12 @@ def _host_ptr(a, dtype, shape, name):
 
 
 class Plan:
-    """One synthesis configuration (scw_plan_create) and its workspace."""
+    """One synthesis configuration (scw_plan) and its workspace."""
 
     def __init__(self, U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0,
                  n_bot=1.0, z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0,
-                 autotune=False, illuminations=1, pupil_na=0.0, tiles=(1, 1), out_ld=0, out_plane_stride=0):
+                 autotune=False, illuminations=1, pupil_na=0.0, tiles=(1, 1), out_ld=0, out_plane_stride=0,
+                 stream=None):
         """``illuminations`` incident fields share this solve: alpha becomes [I][L][4M], p_* [I][3][M]
         and the field [I][3][Fz][Fy][Fx]. ``pupil_na`` > 0 keeps only the orders inside that NA below
         the sample."""
@@ -124,7 +127,7 @@ class Plan:
         self.Fz = len(self._zp)
         self._layout = _field_layout(self.I, self.Fz, self.Fy, self.Fx, tiles, out_ld, out_plane_stride)
         h = ctypes.c_void_p()
-        check(self._lib.scw_plan_create(ctypes.byref(d), ctypes.byref(h)), "scw_plan_create")
+        check(self._lib.scw_plan(ctypes.byref(d), _stream_handle(stream), ctypes.byref(h)), "scw_plan")
         self._h = h
         self._keep = ()
 
@@ -276,12 +279,12 @@ class Plan:
 
 class BatchedPlan:
     """Many independent items (e.g. the wavenumbers of a sweep) synthesised by
-    one set of kernels and replayed as one CUDA graph (scw_plan_batched_create).
+    one set of kernels and replayed as one CUDA graph (scw_plan_batched).
 
     ``items`` is a list of keyword dicts with the arguments of ``Plan`` (without
     ``precision``/``host_io``)."""
 
-    def __init__(self, items, precision="split_bf16", autotune=False):
+    def __init__(self, items, precision="split_bf16", autotune=False, stream=None):
         self._lib = load()
         n = len(items)
         descs = (ScwDesc * n)()
@@ -302,7 +305,7 @@ class BatchedPlan:
             self.shapes.append(lay[0])
             self.layouts.append(lay)
         h = ctypes.c_void_p()
-        check(self._lib.scw_plan_batched_create(descs, n, ctypes.byref(h)), "scw_plan_batched_create")
+        check(self._lib.scw_plan_batched(descs, n, _stream_handle(stream), ctypes.byref(h)), "scw_plan_batched")
         self._h = h
         self._keep = [()] * n
 
@@ -329,8 +332,25 @@ class BatchedPlan:
             raise ValueError("one output per item")
         ptrs = (ctypes.c_void_p * len(outs))(*[_field_ptr(o, *lay, "out").value
                                               for o, lay in zip(outs, self.layouts)])
-        check(self._lib.scw_synthesize_batched(self._h, ptrs, _stream_handle(stream)), "scw_synthesize_batched")
+        check(self._lib.scw_synthesize_batched(self._h, None, ptrs, _stream_handle(stream)), "scw_synthesize_batched")
         return outs
+
+    def item_table(self, outs):
+        """DEVICE int64 [n] table of the outputs' addresses (validated here), for synthesize_table."""
+        import torch
+        if len(outs) != len(self.layouts):
+            raise ValueError("one output per item")
+        ptrs = [_field_ptr(o, *lay, "out").value for o, lay in zip(outs, self.layouts)]
+        return torch.tensor(ptrs, dtype=torch.int64).to(outs[0].device)
+
+    def synthesize_table(self, table, stream=None):
+        """scw_synthesize_batched with a DEVICE item table (int64 [n] of field addresses)."""
+        import torch
+        if not (table.is_cuda and table.dtype == torch.int64 and table.is_contiguous() and
+                table.numel() == len(self.layouts)):
+            raise ValueError("table must be a contiguous CUDA int64 tensor with one address per item")
+        check(self._lib.scw_synthesize_batched(self._h, ctypes.c_void_p(table.data_ptr()), None,
+                                               _stream_handle(stream)), "scw_synthesize_batched")
 
     def check(self, stream=None):
         check(self._lib.scw_plan_check(self._h, _stream_handle(stream)), "scw_plan_check")

@@ -73,6 +73,7 @@ class ScwSolveTimes(ctypes.Structure):
 # name -> (restype, argtypes); mirrors include/scw.h, include/scw_fno.h and include/scw_solve.h
 SIGNATURES = {
     "scw_plan_create": (c_int, [POINTER(ScwDesc), POINTER(c_void_p)]),
+    "scw_plan": (c_int, [POINTER(ScwDesc), c_void_p, POINTER(c_void_p)]),
     "scw_plan_destroy": (c_int, [c_void_p]),
     "scw_plan_set_layers": (c_int, [c_void_p] + [c_void_p] * 6 + [c_void_p]),
     "scw_synthesize": (c_int, [c_void_p, c_void_p, c_void_p]),
@@ -83,8 +84,9 @@ SIGNATURES = {
     "scw_plan_set_point_planes": (c_int, [c_void_p, c_void_p]),
     "scw_synthesize_host": (c_int, [c_void_p] + [c_void_p] * 7 + [c_void_p]),
     "scw_plan_batched_create": (c_int, [POINTER(ScwDesc), c_int, POINTER(c_void_p)]),
+    "scw_plan_batched": (c_int, [POINTER(ScwDesc), c_int, c_void_p, POINTER(c_void_p)]),
     "scw_plan_batched_set_layers": (c_int, [c_void_p, c_int] + [c_void_p] * 6 + [c_void_p]),
-    "scw_synthesize_batched": (c_int, [c_void_p, POINTER(c_void_p), c_void_p]),
+    "scw_synthesize_batched": (c_int, [c_void_p, c_void_p, POINTER(c_void_p), c_void_p]),
     "scw_plan_tune_report": (c_char_p, [c_void_p]),
     "scw_plan_set_pipeline": (c_int, [c_void_p, c_int]),
     "scw_plan_check": (c_int, [c_void_p, c_void_p]),

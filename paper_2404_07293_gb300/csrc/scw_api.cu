@@ -43,6 +43,17 @@ static float2 cis_cycles(double t) {
   return make_float2((float)std::cos(2.0 * M_PI * r), (float)std::sin(2.0 * M_PI * r));
 }
 
+// Stream on which plan creation queues its table uploads, clears and autotune launches: the
+// caller's stream for scw_plan / scw_plan_batched, nullptr (the legacy default stream) for the
+// *_create forms. Creation synchronises it before returning.
+static thread_local cudaStream_t t_setup = nullptr;
+
+struct SetupStream {
+  cudaStream_t prev;
+  explicit SetupStream(cudaStream_t s) : prev(t_setup) { t_setup = s; }
+  ~SetupStream() { t_setup = prev; }
+};
+
 template <typename T>
 static cudaError_t dalloc(T** p, size_t count, size_t& total) {
   *p = nullptr;
@@ -56,7 +67,8 @@ template <typename T>
 static cudaError_t upload(T** p, const std::vector<T>& v, size_t& total) {
   cudaError_t e = dalloc(p, v.size(), total);
   if (e != cudaSuccess || v.empty()) return e;
-  return cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  e = cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, t_setup);
+  return e == cudaSuccess ? cudaStreamSynchronize(t_setup) : e;  // v is the caller's temporary
 }
 
 static void free_item(Plan* p) {
@@ -269,8 +281,8 @@ static scw_status build_item(Plan* p, const std::vector<int>& ext) {
       p->Bhi = bh;
       SCW_TRY(dalloc(&bl, nB, tot));
       p->Blo = bl;
-      SCW_TRY(cudaMemset(p->Bhi, 0, nB * 2));
-      SCW_TRY(cudaMemset(p->Blo, 0, nB * 2));
+      SCW_TRY(cudaMemsetAsync(p->Bhi, 0, nB * 2, t_setup));
+      SCW_TRY(cudaMemsetAsync(p->Blo, 0, nB * 2, t_setup));
     }
   }
   if (p->flags & SCW_FLAG_HOST_IO) {
@@ -308,11 +320,14 @@ static scw_status finish_item(Plan* p) {
     for (int f = p->units[u].f0; f < p->units[u].f0 + p->units[u].nf; ++f) nsplit[f] = ks;
   }
   p->k_split = std::max(p->k_split, ks_max);
-  if (!p->units.empty())
-    SCW_TRY(cudaMemcpy(p->d_units, p->units.data(), p->units.size() * sizeof(LayerUnit), cudaMemcpyHostToDevice));
+  if (!p->units.empty()) {
+    SCW_TRY(cudaMemcpyAsync(p->d_units, p->units.data(), p->units.size() * sizeof(LayerUnit), cudaMemcpyHostToDevice,
+                            t_setup));
+    SCW_TRY(cudaStreamSynchronize(t_setup));
+  }
   SCW_TRY(upload(&p->d_nsplit, nsplit, tot));
   SCW_TRY(dalloc(&p->S_part, (size_t)p->k_split * p->Fz * 3 * M, tot));
-  SCW_TRY(cudaMemset(p->S_part, 0, (size_t)p->k_split * p->Fz * 3 * M * sizeof(float2)));
+  SCW_TRY(cudaMemsetAsync(p->S_part, 0, (size_t)p->k_split * p->Fz * 3 * M * sizeof(float2), t_setup));
   ItemDev& it = p->item;
   it.units = p->d_units;
   it.zplanes = p->d_zplanes;
@@ -838,7 +853,7 @@ static scw_status choose_splits(scw_plan_t P, bool timed, const std::vector<int>
       // time the three best model candidates with the real kernel on the plan's buffers
       const int n_try = std::min<int>(3, (int)cand.size());
       float best_ms = 1e30f;
-      cudaStream_t ts = P->cap_stream;
+      cudaStream_t ts = t_setup ? t_setup : P->cap_stream;
       cudaEvent_t a, b;
       cudaEventCreate(&a);
       cudaEventCreate(&b);
@@ -872,7 +887,8 @@ static scw_status choose_splits(scw_plan_t P, bool timed, const std::vector<int>
       }
       cudaEventDestroy(a);
       cudaEventDestroy(b);
-      cudaMemset(P->d_err, 0, sizeof(int));
+      cudaMemsetAsync(P->d_err, 0, sizeof(int), ts);
+      cudaStreamSynchronize(ts);
       std::lock_guard<std::mutex> lock(g_tune_mu);
       g_tune_cache[key] = chosen;
     }
@@ -926,7 +942,7 @@ static scw_status choose_splits(scw_plan_t P, bool timed, const std::vector<int>
 static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, bool timed) {
   size_t tot = 0;
   SCW_TRY(dalloc(&P->d_err, 1, tot));
-  SCW_TRY(cudaMemset(P->d_err, 0, sizeof(int)));
+  SCW_TRY(cudaMemsetAsync(P->d_err, 0, sizeof(int), t_setup));
   SCW_TRY(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
   std::vector<int2> ue, pe;
   for (size_t i = 0; i < P->items.size(); ++i) {
@@ -956,7 +972,10 @@ static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, boo
   if (P->batched) SCW_TRY(dalloc(&P->d_items, P->items.size(), tot));
   scw_status s = choose_splits(P, timed, user_ks);
   if (s != SCW_OK) return s;
-  return upload_items(P, P->cap_stream);
+  s = upload_items(P, t_setup ? t_setup : P->cap_stream);
+  if (s != SCW_OK) return s;
+  cudaError_t e = cudaStreamSynchronize(t_setup);
+  return e == cudaSuccess ? SCW_OK : cuda_error(e, "plan set-up stream");
 }
 
 static scw_status check_item_index(scw_plan_t P, int item) {
@@ -1166,7 +1185,8 @@ const char* scw_status_string(scw_status s) {
   return "unknown status";
 }
 
-scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
+scw_status scw_plan(const scw_desc* d, void* stream, scw_plan_t* out) {
+  SetupStream guard(static_cast<cudaStream_t>(stream));
   if (!out) return set_error(SCW_ERR_INVALID_ARGUMENT, "out is NULL");
   *out = nullptr;
   scw_status s = validate_desc(d);
@@ -1196,7 +1216,10 @@ scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) {
   return SCW_OK;
 }
 
-scw_status scw_plan_batched_create(const scw_desc* descs, int n, scw_plan_t* out) {
+scw_status scw_plan_create(const scw_desc* d, scw_plan_t* out) { return scw_plan(d, nullptr, out); }
+
+scw_status scw_plan_batched(const scw_desc* descs, int n, void* stream, scw_plan_t* out) {
+  SetupStream guard(static_cast<cudaStream_t>(stream));
   if (!out) return set_error(SCW_ERR_INVALID_ARGUMENT, "out is NULL");
   *out = nullptr;
   if (!descs || n < 1) return set_error(SCW_ERR_INVALID_ARGUMENT, "need at least one item");
@@ -1254,6 +1277,10 @@ scw_status scw_plan_batched_create(const scw_desc* descs, int n, scw_plan_t* out
   return SCW_OK;
 }
 
+scw_status scw_plan_batched_create(const scw_desc* descs, int n, scw_plan_t* out) {
+  return scw_plan_batched(descs, n, nullptr, out);
+}
+
 scw_status scw_plan_destroy(scw_plan_t plan) {
   if (plan) {
     cudaDeviceSynchronize();
@@ -1284,15 +1311,24 @@ scw_status scw_synthesize(scw_plan_t P, void* out, void* stream) {
   return run_synthesis(P, static_cast<float2*>(out), static_cast<cudaStream_t>(stream));
 }
 
-scw_status scw_synthesize_batched(scw_plan_t P, void* const* outs, void* stream) {
-  if (!P || !outs) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and outs are required");
+scw_status scw_synthesize_batched(scw_plan_t P, const void* item_table, void* const* outs, void* stream) {
+  if (!P || (!outs && !item_table) || (outs && item_table))
+    return set_error(SCW_ERR_INVALID_ARGUMENT, "plan and exactly one of item_table and outs are required");
   if (!P->batched) return set_error(SCW_ERR_STATE, "single plan: use scw_synthesize");
   for (size_t i = 0; i < P->items.size(); ++i) {
     if (!P->items[i]->layers_set) return set_error(SCW_ERR_STATE, "item " + std::to_string(i) + " has no layers");
-    if (!outs[i] || (reinterpret_cast<uintptr_t>(outs[i]) & 15u) != 0)
+    if (outs && (!outs[i] || (reinterpret_cast<uintptr_t>(outs[i]) & 15u) != 0))
       return set_error(SCW_ERR_INVALID_ARGUMENT, "every out must be non-NULL and 16-byte aligned");
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (item_table) {
+    // the device table is copied in stream order: the previous replay on `st` has read the old one
+    if ((reinterpret_cast<uintptr_t>(item_table) & 7u) != 0)
+      return set_error(SCW_ERR_INVALID_ARGUMENT, "item_table must be 8-byte aligned");
+    cudaError_t e = cudaMemcpyAsync(P->d_outs, item_table, P->items.size() * sizeof(float2*), cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_error(e, "item table copy");
+    return run_synthesis(P, nullptr, st);
+  }
   // the previous call's copy of the pointer table must have been consumed before it is rewritten
   cudaError_t e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_error(e, "cudaStreamSynchronize");

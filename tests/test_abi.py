@@ -77,6 +77,41 @@ def test_bad_descriptors_are_rejected(lib, bad):
     assert lib.scw_last_error()
 
 
+@pytest.mark.parametrize("entry", ["scw_plan", "scw_plan_batched"])
+def test_stream_forms_reject_bad_descriptors(lib, entry):
+    """The stream-taking plan constructors validate before they touch a device."""
+    for bad in (dict(U=0), dict(Fx=12), dict(zp=np.array([0.3, 0.1]))):
+        d, keep = _desc(**bad)
+        h = ctypes.c_void_p()
+        if entry == "scw_plan":
+            st = lib.scw_plan(ctypes.byref(d), None, ctypes.byref(h))
+        else:
+            st = lib.scw_plan_batched(ctypes.byref(d), 1, None, ctypes.byref(h))
+        assert st == 1, (entry, bad, st)
+        assert not h.value
+
+
+def test_boundary_names_of_the_scope_table(lib):
+    """Every entry point the hot path's boundary names is exported and callable through
+    ctypes; with NULL handles each returns INVALID_ARGUMENT (host checks, no device)."""
+    h = ctypes.c_void_p()
+    assert lib.scw_plan(None, None, ctypes.byref(h)) == 1
+    assert lib.scw_plan_batched(None, 1, None, ctypes.byref(h)) == 1
+    assert lib.scw_plan_set_layers(None, None, None, None, None, None, None, None) == 1
+    assert lib.scw_synthesize(None, None, None) == 1
+    table = ctypes.c_void_p(256)
+    outs = (ctypes.c_void_p * 1)(256)
+    assert lib.scw_synthesize_batched(None, table, None, None) == 1
+    assert lib.scw_synthesize_batched(None, None, outs, None) == 1
+    assert lib.scw_surrogate_create(None, ctypes.byref(h)) == 1
+    assert lib.scw_surrogate_train_step(None, None, None, 1, ctypes.c_float(1e-3), None, None) == 1
+    assert lib.scw_surrogate_infer(None, None, 1, None, None, None, ctypes.c_float(5e-2), None) == 1
+    assert lib.scw_surrogate_destroy(None) == 0
+    assert lib.scw_plan_destroy(None) == 0
+    assert lib.scw_status_string(0) == b"ok"
+    assert lib.scw_last_error() is not None
+
+
 def test_host_io_with_custom_pitch_is_unsupported(lib):
     d, keep = _desc(out_ld=32, flags=2)
     h = ctypes.c_void_p()

@@ -1,4 +1,4 @@
-"""Batched sweep (scw_plan_batched_create / scw_synthesize_batched) on the GPU.
+"""Batched sweep (scw_plan_batched / scw_synthesize_batched) on the GPU.
 
 Item i of a batched run must equal the single-plan scw_synthesize of item i
 (rel-L2 <= 1e-6: only the order of FP32 partial sums may differ) and the FP64
@@ -65,6 +65,20 @@ def test_batched_equals_single_and_oracle(precision, cuda_device):
     for i in range(len(items)):
         assert torch.equal(again[i], other[i])
     bp.check()
+    # the DEVICE item table form, created on a side stream (scw_plan_batched with a stream), twice
+    side = torch.cuda.Stream()
+    bp2 = scw.BatchedPlan([kw for _, kw in items], precision=precision, stream=side)
+    for i in range(len(items)):
+        bp2.set_layers(i, *dev[i], stream=side)
+    for rep in range(2):
+        tab_outs = [torch.full_like(o, float("nan")) for o in outs]
+        table = bp2.item_table(tab_outs)
+        bp2.synthesize_table(table, stream=side)
+        side.synchronize()
+        bp2.check(stream=side)
+        for i in range(len(items)):
+            assert torch.equal(tab_outs[i], other[i]), (rep, i)
+    bp2.close()
 
 
 def test_sweep_items_from_real_solves(cuda_device):
