@@ -1,11 +1,17 @@
 #!/usr/bin/env python3
 """Benchmark of volumetric field synthesis (voxels/s).
 
-Workload: 21x21 orders (M = 441), 32 layers, output 256 x 256 x 256 voxels (8
-planes per layer), synthetic solved layers (workloads.random_layer_set, seed
-= rank). A step is one scw_synthesize: phases (a), mode contraction (b),
-pruned inverse FFT (c). W (597 MB) and the output (403 MB) are both larger
-than the 129 MB L2, so no flush is needed between steps.
+Workload: the single-wavelength sample -- 64 x 64 x 32 voxels of 0.25 um with
+1-8 seeded ellipsoids (seed = rank), lit by a focused Gaussian beam (NA 0.5),
+solved on the GPU at 21x21 orders (M = 441) -- synthesised on a 256 x 256 x 256
+grid (8 planes per layer). A step is one scw_synthesize: phases (a), mode
+contraction (b), pruned inverse FFT (c). W (597 MB) and the output (403 MB) are
+both larger than the 129 MB L2, so no flush is needed between steps.
+
+The line carries the metric's two arms on the same inputs -- split-BF16 tensor
+cores (the headline value) and the FP32 SIMT contraction -- and, from the
+oracle leg on rank 0, every voxel of both compared with the FP64 oracle's
+direct sum (per-component rel-L2 and max-abs).
 
 Prints ONE JSON line on rank 0. With --impl reference the FP64 CPU oracle is
 timed instead (bounded sample of the same workload on the host cores).
@@ -219,6 +225,9 @@ def run_reference(args, world, rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_name(), "orders": "21x21", "layers": L_LAYERS,
                                             "grid": [F_XY, F_XY, L_LAYERS * PLANES_PER_LAYER],
+                                            "inputs": "synthetic layer sets of the sample's shapes (the oracle's "
+                                                      "own solve of the 32 layers takes minutes; the synthesis cost "
+                                                      "does not depend on the values)",
                                             "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": value, "unit": "voxels/s", "cores": cores, "kind": "oracle",
                              "sample": "2 whole 256x256 planes per step (spectrum + direct sum), FP64 NumPy"},
@@ -287,29 +296,31 @@ def run_sweep(args, dev, world, peaks_hbm):
     return res
 
 
-def run_illumination(args, dev, world, Wd, gd, zb, zp, hbm, bf16_tf):
+def run_illumination(args, dev, world, Wd, gd, zb, zp, hbm, bf16_tf, fxy=None, precisions=("split_bf16", "fp16", "fp32")):
     """Many illuminations of one solved sample: the single-wavelength workload
-    (21x21 orders, 32 layers, 256 x 256 x 256 voxels) lit by I incident fields
-    that share W and gamma, each with its own alpha. One plan contracts all I
-    against a single read of W, so the contraction has 8 I columns per layer and
-    turns tensor-bound; every precision is timed on the same inputs."""
+    (21x21 orders, 32 layers, fxy x fxy x 256 voxels, fxy = 256 by default) lit by I
+    incident fields that share W and gamma, each with its own alpha (random draws
+    of a solved alpha's distribution). One plan contracts all I against a single
+    read of W, so the contraction has 8 I columns per layer and turns tensor-bound;
+    every precision is timed on the same inputs."""
     import torch
     import paper_2404_07293_gb300 as scw
     import workloads as wl
     I = args.illuminations
     M = U_ORD * U_ORD
+    fxy = fxy or F_XY
     alpha = wl.random_illuminations(4242, I, U_ORD, U_ORD, L_LAYERS)[0]
     ad = torch.from_numpy(alpha).to(dev)
     Fz = len(zp)
-    voxels = I * F_XY * F_XY * Fz
-    out = torch.empty((I, 3, Fz, F_XY, F_XY), dtype=torch.complex64, device=dev)
+    voxels = I * fxy * fxy * Fz
+    out = torch.empty((I, 3, Fz, fxy, fxy), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
     flops = 8.0 * (3 * M) * (4 * M) * Fz * I       # complex multiply-adds of S = W (alpha o g), 8 flops each
     products = {"fp32": 1, "split_bf16": 3, "fp16": 2}
-    res = {"workload": f"single_wavelength_256cubed_{I}_illuminations", "illuminations": I,
+    res = {"workload": f"single_wavelength_{fxy}x{fxy}x{Fz}_{I}_illuminations", "illuminations": I,
            "voxels_per_step": voxels, "contract_flops": flops, "unit": "voxels/s"}
-    for prec in ("split_bf16", "fp16", "fp32"):
-        plan = scw.Plan(U_ORD, U_ORD, L_LAYERS, LAM, X_PERIOD, X_PERIOD, zb, F_XY, F_XY, zp,
+    for prec in precisions:
+        plan = scw.Plan(U_ORD, U_ORD, L_LAYERS, LAM, X_PERIOD, X_PERIOD, zb, fxy, fxy, zp,
                         precision=prec, illuminations=I)
         plan.set_layers(Wd, gd, ad)
         for _ in range(max(3, args.warmup)):
@@ -341,6 +352,11 @@ def run_illumination(args, dev, world, Wd, gd, zb, zp, hbm, bf16_tf):
     res["contract_speedup_split_bf16_vs_fp32"] = res["fp32"]["kernel_ms"]["contract_ms"] / \
         res["split_bf16"]["kernel_ms"]["contract_ms"]
     res["step_speedup_split_bf16_vs_fp32"] = res["fp32"]["ms_per_step"] / res["split_bf16"]["ms_per_step"]
+    # the steps share everything but the contraction: (phases, recompose) cost the same on both paths
+    rest = res["split_bf16"]["ms_per_step"] - res["split_bf16"]["kernel_ms"]["contract_ms"]
+    res["common_ms"] = rest
+    res["step_speedup_bound"] = (res["fp32"]["kernel_ms"]["contract_ms"] + rest) / \
+        (res["split_bf16"]["kernel_ms"]["contract_ms"] + rest)
     res["out_bytes"] = out.numel() * 8
     res["step_hbm_roofline_ms"] = (L_LAYERS * 3 * M * 4 * M * 8 + res["out_bytes"]) / (hbm * 1e9) * 1e3
     res["peaks"] = {"bf16_tflops": bf16_tf, "hbm_gbs": hbm, "source": "MEASURED_PEAKS.json (burst)"}
@@ -477,35 +493,46 @@ def run_tiling(args, dev, world, Wd, gd, ad, zb, zp, hbm):
     return res
 
 
-def run_solve(args, dev, with_oracle):
-    """The solve stage on the GPU for the single-wavelength sample itself: 64 x 64 x 32
-    voxels of 0.25 um with seeded ellipsoids, a focused Gaussian beam (NA 0.5), 21 x 21
-    orders (4M = 1764 modes per layer). Reports the GPU time per step of the solve and,
-    beside it, the FP64 oracle timed on one layer of the same sample (its eigen-
-    decomposition of D and its connection step), scaled to the 32 layers."""
+def solve_sample(dev, seed, L):
+    """The single-wavelength sample (64 x 64 x L voxels of 0.25 um, seeded ellipsoids,
+    focused Gaussian beam at NA 0.5) solved on the GPU at 21 x 21 orders. The first
+    solve also creates the solver's library handles. Returns (problem, solver, n,
+    p_inc, (W, gamma, alpha), seconds)."""
     import torch
     import paper_2404_07293_gb300 as scw
     import workloads as wl
-    p = wl.config_single_wavelength(0)
-    L = len(p.z_bounds) - 1
+    p = wl.config_single_wavelength(seed, U=U_ORD, L=L)
     n = torch.from_numpy(p.n_volume.astype(np.complex128)).to(dev)
     img = torch.from_numpy(p.incident_image.astype(np.complex128)).to(dev)
+    t0 = time.perf_counter()
     s = scw.Solver(p.U, p.V, L, p.lam, p.X, p.Y, p.z_bounds, p.n_volume.shape[2], p.n_volume.shape[1])
     p_inc = s.incident(img)
-    s.solve(n, p_inc)  # warm-up (handles, workspaces, library kernels)
+    W, g, a, _, _ = s.solve(n, p_inc)
+    torch.cuda.synchronize(dev)
+    return p, s, n, p_inc, (W, g, a), time.perf_counter() - t0
+
+
+def run_solve(args, dev, with_oracle, p, s, n, p_inc):
+    """The solve stage on the GPU for the single-wavelength sample itself: 64 x 64 x 32
+    voxels of 0.25 um with seeded ellipsoids, a focused Gaussian beam (NA 0.5), 21 x 21
+    orders (4M = 1764 modes per layer). Times a second solve on the already warmed-up
+    solver and reports, beside it, the FP64 oracle timed on one layer of the same
+    sample (its eigendecomposition of D and its connection step), scaled to the layers."""
+    import torch
+    L = len(p.z_bounds) - 1
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     W, g, a, pr, pt = s.solve(n, p_inc)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
     t = s.times()
-    s.close()
     N4 = 4 * p.U * p.V
     # connection step per layer: LU of T (2/3 N^3), the solve with N right-hand sides (2 N^3) and the
     # product with B (N^3) complex multiply-adds, 8 real flops each
     conn_flops = L * (2.0 / 3.0 + 2.0 + 1.0) * N4 ** 3 * 8
     fp64_peak = 1.25  # TFLOP/s, the nominal FP64 rate of the part (no measured FP64 peak is recorded)
-    res = {"workload": "single_wavelength_sample_64x64x32_21x21_orders", "layers": L, "modes_per_layer": 4 * p.U * p.V,
+    res = {"workload": f"single_wavelength_sample_64x64x{L}_21x21_orders", "layers": L,
+           "modes_per_layer": 4 * p.U * p.V,
            "gpu_s": wall, "gpu_step_ms": {k: t[k] for k in ("fourier_ms", "modes_ms", "connect_ms", "system_ms",
                                                              "alpha_ms", "erows_ms", "total_ms")},
            "eig_ms_per_layer_effective": t["modes_ms"] / L,
@@ -527,12 +554,126 @@ def run_solve(args, dev, with_oracle):
         K = B @ np.linalg.solve(T, np.eye(T.shape[0], dtype=np.complex128))
         t_conn = time.perf_counter() - t0
         del K
-        res["cpu_baseline"] = {"value": L * (t_eig + t_conn), "unit": "s (32 layers, scaled from one)",
+        res["cpu_baseline"] = {"value": L * (t_eig + t_conn), "unit": f"s ({L} layers, scaled from one)",
                                "cores": blas_threads(), "kind": "oracle",
                                "sample": f"layer 0: assembly + full 4M x 4M eig {t_eig:.2f} s, connection "
-                                         f"step {t_conn:.2f} s; times 32 layers"}
+                                         f"step {t_conn:.2f} s; times {L} layers"}
         res["speedup_vs_oracle"] = res["cpu_baseline"]["value"] / wall
-    del W, g, a, pr, pt, n
+    del W, g, a, pr, pt
+    return res
+
+
+def timed_steps(fn, steps, warmup, stream, barrier):
+    """ms per call of fn() over `steps` calls after `warmup` untimed ones (CUDA events on
+    `stream`, barrier + synchronize on both sides)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    barrier()
+    return e0.elapsed_time(e1) / steps
+
+
+def kernel_times(plan, fn, calls=3):
+    """Per-kernel CUDA-event times of `calls` direct (non-graph) calls."""
+    plan.enable_timing(True)
+    for _ in range(calls):
+        fn()
+    kt = plan.timings()
+    plan.enable_timing(False)
+    return {k: kt[k] for k in ("phases_ms", "contract_ms", "xpass_ms", "ypass_ms", "recompose_ms", "total_ms")}
+
+
+def oracle_volume(W, g, a, zb, zp, U=None, X=None, Fxy=None):
+    """The FP64 oracle's field of every voxel (spectrum per plane, then the direct sum
+    of Eq. 10) and the seconds it took on the host cores."""
+    from oracle import cw, synth
+    U = U or U_ORD
+    X = X or X_PERIOD
+    Fxy = Fxy or F_XY
+    ls = cw.LayerSet(lam=LAM, X=X, Y=X, U=U, V=U, z_bounds=zb, W=W, gamma=g, alpha=a,
+                     p_inc=None, p_ref=None, p_trn=None)
+    t0 = time.perf_counter()
+    E = synth.synthesize_direct(ls, Fxy, Fxy, zp)
+    return E, time.perf_counter() - t0
+
+
+def error_vs_oracle(E, ref):
+    """Per-component rel-L2 and max-abs (absolute, and over the component's largest magnitude)."""
+    out = {"rel_l2": [], "max_abs": [], "max_abs_over_max": []}
+    for c in range(3):
+        d = E[c].astype(np.complex128) - ref[c]
+        out["rel_l2"].append(float(np.linalg.norm(d) / np.linalg.norm(ref[c])))
+        m = float(np.abs(d).max())
+        out["max_abs"].append(m)
+        out["max_abs_over_max"].append(m / float(np.abs(ref[c]).max()))
+    out["components"] = ["Ex", "Ey", "Ez"]
+    return out
+
+
+def run_config3(args, dev, world, barrier, with_oracle):
+    """The precision form of the tiny sample and the compute-bound variant of the
+    single-wavelength sample.
+      tiny: 16x16x4 voxels, one sphere, 7x7 orders, 64x64x32 output, solved by the
+            oracle; FP32, split-BF16 and FP16 fields against the oracle's direct sum
+            (per-component rel-L2 and max-abs).
+      layers_4_planes_64: the single-wavelength geometry with 4 layers of 0.25 um
+            (64 x 64 x 4 voxels, solved on the GPU) and 64 planes per layer, 256^3
+            output: the contraction has 64 columns per layer against each read of W.
+            FP32 and split-BF16 timed on the same inputs (contraction and whole step)."""
+    import torch
+    import paper_2404_07293_gb300 as scw
+    import workloads as wl
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    if with_oracle:
+        from oracle import cw, synth
+        p = wl.config_tiny()
+        sol = cw.solve_problem(p)
+        ref = synth.synthesize_direct(sol, p.Fx, p.Fy, p.z_planes)
+        Wt = torch.from_numpy(sol.W.astype(np.complex64)).to(dev)
+        gt, at = torch.from_numpy(sol.gamma).to(dev), torch.from_numpy(sol.alpha).to(dev)
+        tiny = {"workload": "tiny_16x16x4_sphere_7x7_orders_64x64x32"}
+        for prec in ("fp32", "split_bf16", "fp16"):
+            plan = scw.Plan(p.U, p.V, p.L, p.lam, p.X, p.Y, p.z_bounds, p.Fx, p.Fy, p.z_planes, precision=prec)
+            plan.set_layers(Wt, gt, at)
+            E = plan.synthesize().cpu().numpy()
+            plan.check()
+            plan.close()
+            tiny[prec] = error_vs_oracle(E, ref)
+        res["tiny"] = tiny
+    # compute-bound variant: 4 solved layers, 64 planes each
+    L4 = 4
+    p4, s4, _, _, (W4, g4, a4), solve_s = solve_sample(dev, replica_seed(int(os.environ.get("RANK", "0"))), L4)
+    s4.close()
+    zb4 = p4.z_bounds
+    zp4 = wl.cell_centred_planes(zb4[0], zb4[-1], 256)
+    voxels = F_XY * F_XY * len(zp4)
+    out = torch.empty((3, len(zp4), F_XY, F_XY), dtype=torch.complex64, device=dev)
+    v = {"workload": "single_wavelength_4_layers_64_planes_per_layer_256x256x256", "solve_s": solve_s}
+    steps = max(3, min(args.steps, 20))
+    for prec in ("split_bf16", "fp32"):
+        plan = scw.Plan(U_ORD, U_ORD, L4, LAM, X_PERIOD, X_PERIOD, zb4, F_XY, F_XY, zp4, precision=prec)
+        plan.set_layers(W4, g4, a4)
+        ms = timed_steps(lambda: plan.synthesize(out), steps, max(3, args.warmup), stream, barrier)
+        kt = kernel_times(plan, lambda: plan.synthesize(out))
+        plan.check()
+        plan.close()
+        v[prec] = {"value": replica_throughput(voxels, ms * 1e-3, dev)[0], "ms_per_step": ms, "kernel_ms": kt}
+    v["contract_speedup_split_bf16_vs_fp32"] = v["fp32"]["kernel_ms"]["contract_ms"] / \
+        v["split_bf16"]["kernel_ms"]["contract_ms"]
+    v["step_speedup_split_bf16_vs_fp32"] = v["fp32"]["ms_per_step"] / v["split_bf16"]["ms_per_step"]
+    rest = v["split_bf16"]["ms_per_step"] - v["split_bf16"]["kernel_ms"]["contract_ms"]
+    v["common_ms"] = rest
+    v["step_speedup_bound"] = (v["fp32"]["kernel_ms"]["contract_ms"] + rest) / \
+        (v["split_bf16"]["kernel_ms"]["contract_ms"] + rest)
+    res["layers_4_planes_64"] = v
+    del out, W4, g4, a4
     return res
 
 
@@ -618,30 +759,38 @@ def run_ours(args, world, rank, local):
     zb, zp = geometry()
     Fz = len(zp)
     voxels = F_XY * F_XY * Fz
+    oracle_leg = rank == 0 and not args.no_cpu_baseline
 
-    W, g, a, *_ = wl.random_layer_set(replica_seed(rank), U_ORD, U_ORD, L_LAYERS)
-    Wd = torch.from_numpy(W).to(dev)
-    gd = torch.from_numpy(g).to(dev)
-    ad = torch.from_numpy(a).to(dev)
+    # inputs: the sample solved on the GPU (default), or synthetic layer sets of the same shapes
+    solver = None
+    if args.input == "solved":
+        prob, solver, n_dev, pinc_dev, (Wd, gd, ad), first_solve_s = solve_sample(dev, replica_seed(rank), L_LAYERS)
+        inputs = (f"single-wavelength sample seed {replica_seed(rank)} (64x64x{L_LAYERS} voxels of ellipsoids, "
+                  "Gaussian beam NA 0.5) solved on the GPU by scw_solve")
+    else:
+        W, g, a, *_ = wl.random_layer_set(replica_seed(rank), U_ORD, U_ORD, L_LAYERS)
+        Wd, gd, ad = (torch.from_numpy(x).to(dev) for x in (W, g, a))
+        inputs = "synthetic layer sets (workloads.random_layer_set) of the same shapes"
+        first_solve_s = None
 
     def make_plan(precision, host_io=False):
         return scw.Plan(U_ORD, U_ORD, L_LAYERS, LAM, X_PERIOD, X_PERIOD, zb, F_XY, F_XY, zp,
                         precision=precision, host_io=host_io, k_split=args.k_split)
 
     stream = torch.cuda.current_stream(dev)
-    plan = make_plan(args.precision)
-    if args.pipeline > 1:
-        plan.set_pipeline(args.pipeline)
-    t0 = time.perf_counter()
-    plan.set_layers(Wd, gd, ad)
-    torch.cuda.synchronize(dev)
-    plan_ms = plan.info()["convert_ms"]
-    out = torch.empty(plan.out_shape(), dtype=torch.complex64, device=dev)
 
     def barrier():
         if dist:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
+
+    plan = make_plan(args.precision)
+    if args.pipeline > 1:
+        plan.set_pipeline(args.pipeline)
+    plan.set_layers(Wd, gd, ad)
+    torch.cuda.synchronize(dev)
+    plan_ms = plan.info()["convert_ms"]
+    out = torch.empty(plan.out_shape(), dtype=torch.complex64, device=dev)
 
     for _ in range(args.warmup):
         plan.synthesize(out)
@@ -661,6 +810,7 @@ def run_ours(args, world, rank, local):
         barrier()
     plan.check()
     ms = ev0.elapsed_time(ev1)
+    E_head = out.cpu().numpy() if oracle_leg else None
     # per-kernel breakdown: the same steps as direct launches with events between the kernels
     plan.enable_timing(True)
     barrier()
@@ -704,27 +854,35 @@ def run_ours(args, world, rank, local):
     whole_bytes = w_bytes + out_bytes
     step_roofline_ms = whole_bytes / (hbm * 1e9) * 1e3
 
+    # the metric's other arm: the FP32 SIMT contraction on the same inputs, same timing rules
+    other = "fp32" if args.precision != "fp32" else "split_bf16"
+    fp = make_plan(other)
+    fp.set_layers(Wd, gd, ad)
+    f_ms = timed_steps(lambda: fp.synthesize(out), args.steps, args.warmup, stream, barrier)
+    fp.check()
+    E_other = out.cpu().numpy() if oracle_leg else None
+    f_kt = kernel_times(fp, lambda: fp.synthesize(out))
+    fp.check()
+    fp.close()
+    arm = {"value": replica_throughput(voxels, f_ms * 1e-3, dev)[0], "ms_per_step": f_ms, "kernel_ms": f_kt,
+           "precision": other, "dtype": {"fp32": "fp32", "split_bf16": "bf16x3->fp32"}[other]}
+    head_c, other_c = kt["contract_ms"], f_kt["contract_ms"]
+    if args.precision == "fp32":
+        head_c, other_c = other_c, head_c
+    ratio = {"step": (f_ms / (ms / args.steps)) if other == "fp32" else ((ms / args.steps) / f_ms),
+             "contraction": other_c / head_c,
+             "note": "FP32 time / split-BF16 time on the same inputs; the phases and the recompose are the same "
+                     "kernels on both paths, so the step ratio is bounded by (C32 + R) / (Cs + R)"}
+
     # the other contraction precisions on the same inputs (same step, same timing rules)
     variants = {}
     if args.compare:
-        for prec in ("fp32", "split_bf16", "fp16"):
-            if prec == args.precision:
-                continue
+        for prec in ("fp16",):
             vp = make_plan(prec)
             vp.set_layers(Wd, gd, ad)
-            for _ in range(args.warmup):
-                vp.synthesize(out)
-            vp.enable_timing(True)
-            barrier()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(args.steps):
-                vp.synthesize(out)
-            e1.record(stream)
-            barrier()
-            vk = vp.timings()
+            vms = timed_steps(lambda: vp.synthesize(out), args.steps, args.warmup, stream, barrier)
+            vk = kernel_times(vp, lambda: vp.synthesize(out))
             vp.check()
-            vms = e0.elapsed_time(e1) / args.steps
             variants[prec] = {"value": world * voxels / (vms * 1e-3), "ms_per_step": vms,
                               "contract_ms": vk["contract_ms"], "k_split": vp.info()["k_split"]}
             vp.close()
@@ -732,11 +890,15 @@ def run_ours(args, world, rank, local):
     # end to end through the C ABI with HOST buffers (H2D of W/gamma/alpha, D2H of the field)
     e2e = None
     out = None  # the device output is not needed any more; free it for the next measurements
+    Wh = gh = ah = None
+    if not args.no_e2e or oracle_leg:
+        Wh = torch.empty(tuple(Wd.shape), dtype=torch.complex64).pin_memory()
+        Wh.copy_(Wd)
+        gh = gd.cpu().pin_memory()
+        ah = ad.cpu().pin_memory()
+        Wh, gh, ah = Wh.numpy(), gh.numpy(), ah.numpy()
     if not args.no_e2e:
         hplan = make_plan(args.precision, host_io=True)
-        Wh = torch.from_numpy(W).pin_memory().numpy()
-        gh = torch.from_numpy(g).pin_memory().numpy()
-        ah = torch.from_numpy(a).pin_memory().numpy()
         oh = torch.empty(hplan.out_shape(), dtype=torch.complex64).pin_memory().numpy()
         for _ in range(max(1, args.warmup // 2)):
             hplan.synthesize_host(Wh, gh, ah, out=oh)
@@ -749,14 +911,32 @@ def run_ours(args, world, rank, local):
         e2e_value, t_e2e = replica_throughput(voxels * n_e2e, t_e2e, dev)
         hplan.check()
         e2e = {"value": e2e_value, "unit": "voxels/s",
-               "h2d_bytes_per_step": W.nbytes + g.nbytes + a.nbytes, "d2h_bytes_per_step": oh.nbytes,
+               "h2d_bytes_per_step": Wh.nbytes + gh.nbytes + ah.nbytes, "d2h_bytes_per_step": oh.nbytes,
                "steps": n_e2e, "ms_per_step": 1e3 * t_e2e / n_e2e,
                "includes": "H2D of W, gamma, alpha; W conversion; synthesis; D2H of the field"}
         hplan.close()
+        del oh
 
     illum = None
     if args.illuminations > 1:
         illum = run_illumination(args, dev, world, Wd, gd, zb, zp, hbm, bf16_tf)
+        torch.cuda.empty_cache()
+
+    config3 = None
+    if not args.no_config3:
+        config3 = run_config3(args, dev, world, barrier, oracle_leg)
+        if illum is not None:
+            config3["illuminations_16_256x256"] = {
+                k: illum[k] for k in ("contract_speedup_split_bf16_vs_fp32", "step_speedup_split_bf16_vs_fp32",
+                                      "common_ms", "step_speedup_bound")}
+            small = run_illumination(args, dev, world, Wd, gd, zb, zp, hbm, bf16_tf, fxy=128,
+                                     precisions=("split_bf16", "fp32"))
+            config3["illuminations_16_128x128"] = {
+                "workload": small["workload"],
+                "fp32_ms_per_step": small["fp32"]["ms_per_step"],
+                "split_bf16_ms_per_step": small["split_bf16"]["ms_per_step"],
+                **{k: small[k] for k in ("contract_speedup_split_bf16_vs_fp32", "step_speedup_split_bf16_vs_fp32",
+                                         "common_ms", "step_speedup_bound")}}
         torch.cuda.empty_cache()
 
     points = None
@@ -769,29 +949,39 @@ def run_ours(args, world, rank, local):
         tiling = run_tiling(args, dev, world, Wd, gd, ad, zb, zp, hbm)
         torch.cuda.empty_cache()
 
+    plan.close()
+    del Wd, gd, ad
+    torch.cuda.empty_cache()
+
     sweep = None
     if not args.no_sweep:
-        plan.close()
-        del Wd, gd, ad
-        torch.cuda.empty_cache()
         sweep = run_sweep(args, dev, world, hbm)
 
     solve = None
-    if not args.no_solve:
+    if solver is not None and not args.no_solve:
         torch.cuda.empty_cache()
-        solve = run_solve(args, dev, rank == 0 and not args.no_cpu_baseline)
+        solve = run_solve(args, dev, oracle_leg, prob, solver, n_dev, pinc_dev)
+        solve["first_call_s"] = first_solve_s
+    if solver is not None:
+        solver.close()
 
     surrogate = None
     if not args.no_surrogate:
         torch.cuda.empty_cache()
         surrogate = run_surrogate(args, dev, (bf16_tf, bf16_sustained()))
 
+    # the oracle leg: the FP64 oracle synthesises every voxel of the same inputs on the host
+    # cores (timed: cpu_baseline); both GPU arms are compared with it voxel by voxel
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        rate, n, dt = oracle_sample_rate(W.astype(np.complex128), g, a, zb, zp, seconds=args.cpu_seconds)
-        cpu = {"value": rate, "unit": "voxels/s", "cores": blas_threads(), "kind": "oracle",
-               "sample": f"{n} whole 256x256 planes in z order, cycling the volume (FP64 spectrum + direct sum), "
-                             f"{dt:.1f} s"}
+    error = None
+    if oracle_leg:
+        ref, dt = oracle_volume(Wh.astype(np.complex128), gh, ah, zb, zp)
+        cpu = {"value": voxels / dt, "unit": "voxels/s", "cores": blas_threads(), "kind": "oracle",
+               "sample": f"the whole {F_XY}x{F_XY}x{Fz} volume of the timed inputs (FP64 spectrum per plane + "
+                         f"direct sum of Eq. 10), {dt:.1f} s"}
+        error = {args.precision: error_vs_oracle(E_head, ref), other: error_vs_oracle(E_other, ref),
+                 "voxels": voxels, "oracle": "FP64 direct sum, every voxel"}
+        del ref
 
     if rank == 0:
         line = {
@@ -802,11 +992,15 @@ def run_ours(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": workload_name(), "orders": "21x21", "M": M, "layers": L_LAYERS,
                        "grid": [F_XY, F_XY, Fz], "precision": args.precision, "k_split": info["k_split"],
+                       "inputs": inputs,
                        "l2": "inputs larger than L2 (W 597 MB, field 403 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "step_roofline": {"bytes": whole_bytes, "ms": step_roofline_ms,
                               "frac": step_roofline_ms / (ms / args.steps)},
+            other: arm,
+            "split_bf16_vs_fp32": ratio,
+            "error_vs_fp64": error,
             "kernel_ms": {k: kt[k] for k in ("phases_ms", "contract_ms", "xpass_ms", "ypass_ms", "recompose_ms",
                                              "total_ms")},
             "kernel_roofline": kernels,
@@ -820,6 +1014,7 @@ def run_ours(args, world, rank, local):
             "clocks": clocks.summary(),
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "config3": config3,
             "variants": variants or None,
             "sweep": sweep,
             "illumination": illum,
@@ -829,7 +1024,6 @@ def run_ours(args, world, rank, local):
             "surrogate": surrogate,
         }
         print(json.dumps(line), flush=True)
-    plan.close()
     if dist:
         torch.distributed.destroy_process_group()
     return 0
@@ -854,6 +1048,9 @@ def main():
     ap.add_argument("--no-points", action="store_true", help="skip the off-grid point-set block")
     ap.add_argument("--no-tiling", action="store_true", help="skip the periodic-tiling / patch-mosaic block")
     ap.add_argument("--no-solve", action="store_true", help="skip the GPU solve-stage block")
+    ap.add_argument("--no-config3", action="store_true", help="skip the precision / compute-bound block")
+    ap.add_argument("--input", choices=["solved", "random"], default="solved",
+                    help="headline inputs: the GPU-solved sample or synthetic layer sets of the same shapes")
     ap.add_argument("--illuminations", type=int, default=16,
                     help="incident fields of the multi-illumination block (1 skips it)")
     ap.add_argument("--only-surrogate", action="store_true",

@@ -45,3 +45,11 @@ def fno_init_groups(sh):
             sc = 0.1
         out.append((n, sc))
     return out
+
+
+def max_abs(a, b):
+    """Per-component max |a_c - b_c| over all voxels, and the same over max |b_c|."""
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    ab = [float(np.abs(a[c] - b[c]).max()) for c in range(a.shape[0])]
+    return ab, [x / max(float(np.abs(b[c]).max()), 1e-300) for c, x in enumerate(ab)]
