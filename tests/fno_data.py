@@ -1,6 +1,8 @@
 """Training data for the surrogate tests: exit-plane fields of seeded ellipsoid
-phantoms computed by the FP64 oracle (coupled-wave solve, then the field just
-below the sample, Eq. 9), in a pool of spawned worker processes.
+phantoms, computed either by the FP64 oracle (coupled-wave solve, then the field
+just below the sample, Eq. 9) in a pool of spawned worker processes, or by the
+library's plain method on the GPU (scw_solve, then the recomposition of the
+transmitted spectrum p_trn on the 64x64 exit plane) in a few host threads.
 
 The phantoms are those of the surrogate workload (32x32x8 voxels of 0.25 um,
 1-8 ellipsoids with semi-axes of 2-8 voxels, x-polarised unit plane wave,
@@ -66,3 +68,66 @@ def _limit_threads():
         threadpool_limits(1)
     except Exception:
         pass
+
+
+def exit_fields_gpu(seeds, U=15, workers=4, device="cuda"):
+    """(n [S][8][32][32] complex64, E [S][3][64][64] complex64, seconds per sample [S]) from the
+    library's plain method on the GPU: per sample one scw_solve (FP64) of the phantom, then the
+    field just below the sample, E = sum_m p_trn,m exp(2 pi i (u x / X + v y / Y)) (Eq. 9 at
+    z = z_L, Eq. 10), recomposed by scw_recompose. `workers` host threads each own a solver, a
+    recompose plan and a CUDA stream (the library calls release the GIL), so that the solves of
+    different samples overlap on the device. Seconds per sample are each solve's own wall time."""
+    import threading
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    import paper_2404_07293_gb300 as scw
+    import workloads as wl
+
+    probs = [dataclasses.replace(wl.config_surrogate_sample(int(s)), U=U, V=U) for s in seeds]
+    p0 = probs[0]
+    L = p0.L
+    ny, nx = p0.n_volume.shape[1:]
+    n_out = np.stack([p.n_volume.astype(np.complex64) for p in probs])
+    E_out = np.empty((len(seeds), 3, p0.Fy, p0.Fx), dtype=np.complex64)
+    secs = np.empty(len(seeds))
+    local = threading.local()
+    made = []
+    lock = threading.Lock()
+
+    def ctx():
+        if not hasattr(local, "solver"):
+            dev = torch.device(device)
+            torch.cuda.set_device(dev if dev.index is not None else torch.device("cuda", 0))
+            st = torch.cuda.Stream()
+            solver = scw.Solver(U, U, L, p0.lam, p0.X, p0.Y, p0.z_bounds, nx, ny)
+            with torch.cuda.stream(st):
+                img = torch.from_numpy(p0.incident_image.astype(np.complex128)).to(device)
+                p_inc = solver.incident(img, stream=st)
+            plan = scw.Plan(U, U, 1, p0.lam, p0.X, p0.Y, [0.0, 1.0], p0.Fx, p0.Fy, [0.5], precision="fp32",
+                            stream=st)
+            local.solver, local.stream, local.p_inc, local.plan = solver, st, p_inc, plan
+            with lock:
+                made.append((solver, plan))
+        return local
+
+    def one(i):
+        c = ctx()
+        with torch.cuda.stream(c.stream):
+            nv = torch.from_numpy(probs[i].n_volume.astype(np.complex128)).to(device, non_blocking=False)
+            t0 = time.perf_counter()
+            _, _, _, _, pt = c.solver.solve(nv, c.p_inc, stream=c.stream)
+            S = pt.to(torch.complex64).reshape(1, 3, -1).contiguous()
+            E = c.plan.recompose(S, stream=c.stream)
+            c.stream.synchronize()
+            secs[i] = time.perf_counter() - t0
+            E_out[i] = E[:, 0].cpu().numpy()
+
+    with ThreadPoolExecutor(workers) as ex:
+        list(ex.map(one, range(len(seeds))))
+    torch.cuda.synchronize()
+    for solver, plan in made:
+        solver.close()
+        plan.close()
+    return n_out, E_out, secs
