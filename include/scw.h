@@ -60,7 +60,8 @@ typedef enum {
   SCW_ERR_CUDA = 4,             /* a CUDA runtime/driver call failed             */
   SCW_ERR_TIMEOUT = 5,          /* a device-side bounded wait ran out            */
   SCW_ERR_NUMERIC = 6,          /* non-finite value detected                     */
-  SCW_ERR_STATE = 7             /* call order violated (e.g. no layers set)     */
+  SCW_ERR_STATE = 7,            /* call order violated (e.g. no layers set)     */
+  SCW_ERR_BOUNDS = 8            /* SCW_FLAG_DEBUG_BOUNDS: an index left its buffer */
 } scw_status;
 
 /* Arithmetic of the mode contraction (the other steps are FP64-argument /
@@ -76,9 +77,20 @@ enum {
   SCW_FLAG_EXTERIOR = 1u, /* planes outside [z0, z_L] allowed (needs p_inc/p_ref/p_trn) */
   SCW_FLAG_HOST_IO = 2u,  /* plan also owns device copies of W/gamma/alpha/p for
                              scw_synthesize_host                                        */
-  SCW_FLAG_AUTOTUNE = 4u  /* time the best contraction schedules on the device at plan
+  SCW_FLAG_AUTOTUNE = 4u, /* time the best contraction schedules on the device at plan
                              creation (otherwise a makespan model picks the split);
                              results are cached per device and problem shape           */
+  SCW_FLAG_DEBUG_BOUNDS = 8u /* index checks: every kernel of the plan compares each global
+                             index it forms (spectra, x-pass rows, twiddles, B operand,
+                             gamma/alpha, the FP32 path's operands, the field) with the
+                             extent of its buffer; an index outside is not accessed, the
+                             device error word records it and scw_plan_check returns
+                             SCW_ERR_BOUNDS. The bulk copies of the tensor-core contraction
+                             are driven by a task table built on the host: plan creation
+                             checks every task's W, B and partial-spectrum ranges against
+                             their allocations and fails with SCW_ERR_BOUNDS. Results are
+                             the same as without the flag; the checks cost a compare per
+                             access or per loop                                         */
 };
 
 typedef struct {
@@ -271,6 +283,14 @@ scw_status scw_plan_set_point_planes(scw_plan_t plan, const int* plane);
  * SCW_OK, SCW_ERR_TIMEOUT (a bounded device wait ran out) or SCW_ERR_CUDA. */
 scw_status scw_plan_check(scw_plan_t plan, void* stream);
 
+/* Test hook of SCW_FLAG_DEBUG_BOUNDS plans: lower the extent (in elements) that the checks use
+ * for one buffer -- 0 spectra partials, 1 x-pass rows, 2 x twiddles, 3 y twiddles, 4 B operand,
+ * 5 gamma, 6 alpha, 7 field, 8 FP32 weights C, 9 FP32 transposed W -- to min(real, elements), or
+ * restore the real extent with elements = 0. Accesses the lowered extent rejects are skipped and
+ * reported, although they lie inside the real buffer: the checks can be exercised without any
+ * access outside an allocation. Drops the graph. SCW_ERR_STATE without the flag. */
+scw_status scw_plan_debug_set_extent(scw_plan_t plan, int buffer, unsigned long long elements);
+
 /* Device-side wait limit in nanoseconds for the plan's kernels (default 2 s). */
 scw_status scw_plan_set_timeout_ns(scw_plan_t plan, uint64_t ns);
 
@@ -283,6 +303,19 @@ scw_status scw_plan_set_timeout_ns(scw_plan_t plan, uint64_t ns);
 scw_status scw_plan_inject_stall(scw_plan_t plan, int on);
 
 scw_status scw_plan_get_info(scw_plan_t plan, scw_plan_info* info);
+
+/* Kernel trace of the calls' own launches (graph replay included, where events between kernels
+ * would break their programmatic overlap): with tracing on, thread 0 of every CTA stamps the
+ * %globaltimer when its work begins (after any wait on the preceding kernel) and when it ends;
+ * per slot the earliest begin and the latest end are kept. Slots: 0 phases (a), 1 exterior
+ * planes, 2 contraction (b), 3 x-pass and 4 y-pass (c). scw_plan_enable_trace synchronises the
+ * device, allocates (on != 0) or frees the 128-byte stamp buffer and drops the graph.
+ * scw_plan_get_trace synchronises the device, writes us[2 s] / us[2 s + 1] = begin / end of slot s
+ * in microseconds from the earliest begin (-1 for slots no kernel stamped; n_slots entries
+ * pairs) and clears the stamps, so each read covers the calls since the previous one.
+ * SCW_ERR_STATE when tracing is off. */
+scw_status scw_plan_enable_trace(scw_plan_t plan, int on);
+scw_status scw_plan_get_trace(scw_plan_t plan, double* us, int n_slots);
 
 /* Per-step kernel durations, measured with CUDA events recorded on the
  * launching stream between the kernels of each scw_synthesize call while

@@ -12,7 +12,7 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (FLAG_AUTOTUNE, FLAG_EXTERIOR, FLAG_HOST_IO, FNO_PRECISION, PRECISION, ScwDesc, ScwError,
+from ._lib import (FLAG_AUTOTUNE, FLAG_DEBUG_BOUNDS, FLAG_EXTERIOR, FLAG_HOST_IO, FNO_PRECISION, PRECISION, ScwDesc, ScwError,
                    ScwFnoDesc, ScwFnoTimes, ScwKernelTimes, ScwPlanInfo, ScwSolveDesc, ScwSolveTimes, check, load)
 
 __all__ = ["Plan", "BatchedPlan", "Solver", "Surrogate", "ScwError", "load", "PRECISION"]
@@ -20,14 +20,15 @@ __all__ = ["Plan", "BatchedPlan", "Solver", "Surrogate", "ScwError", "load", "PR
 
 def _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0, n_bot=1.0,
                z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0, autotune=False,
-               illuminations=1, pupil_na=0.0, tiles=(1, 1), out_ld=0, out_plane_stride=0):
+               illuminations=1, pupil_na=0.0, tiles=(1, 1), out_ld=0, out_plane_stride=0, debug_bounds=False):
     """scw_desc for one item plus the host arrays it points to (keep them alive)."""
     zb = np.ascontiguousarray(z_bounds, dtype=np.float64)
     zp = np.ascontiguousarray(z_planes, dtype=np.float64)
     if len(zb) != int(L) + 1:
         raise ValueError("z_bounds must have L+1 entries")
     nb = complex(n_bot)
-    flags = (FLAG_EXTERIOR if exterior else 0) | (FLAG_HOST_IO if host_io else 0) | (FLAG_AUTOTUNE if autotune else 0)
+    flags = (FLAG_EXTERIOR if exterior else 0) | (FLAG_HOST_IO if host_io else 0) | (FLAG_AUTOTUNE if autotune else 0) \
+        | (FLAG_DEBUG_BOUNDS if debug_bounds else 0)
     d = ScwDesc(U=int(U), V=int(V), L=int(L), lam=float(lam), X=float(X), Y=float(Y),
                 z_bounds=zb.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                 Fx=int(Fx), Fy=int(Fy), Fz=len(zp),
@@ -75,6 +76,10 @@ def _per_illum(I, shape):
     return tuple(shape) if I == 1 else (I,) + tuple(shape)
 
 
+TRACE_SLOTS = ("phases", "exterior", "contraction", "xpass", "ypass")
+DEBUG_BUFFERS = ("s_part", "t", "twx", "twy", "b", "gamma", "alpha", "field", "c", "wt")
+
+
 def _stream_handle(stream):
     import torch
     if stream is None and not torch.cuda.is_available():
@@ -109,7 +114,7 @@ class Plan:
     def __init__(self, U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0=0.0, y0=0.0, n_top=1.0,
                  n_bot=1.0, z_inc=None, precision="split_bf16", exterior=False, host_io=False, k_split=0,
                  autotune=False, illuminations=1, pupil_na=0.0, tiles=(1, 1), out_ld=0, out_plane_stride=0,
-                 stream=None):
+                 stream=None, debug_bounds=False):
         """``illuminations`` incident fields share this solve: alpha becomes [I][L][4M], p_* [I][3][M]
         and the field [I][3][Fz][Fy][Fx]. ``pupil_na`` > 0 keeps only the orders inside that NA below
         the sample."""
@@ -123,7 +128,7 @@ class Plan:
         self.exterior = bool(exterior)
         d, (self._zb, self._zp) = _make_desc(U, V, L, lam, X, Y, z_bounds, Fx, Fy, z_planes, x0, y0, n_top, n_bot,
                                              z_inc, precision, exterior, host_io, k_split, autotune,
-                                             illuminations, pupil_na, tiles, out_ld, out_plane_stride)
+                                             illuminations, pupil_na, tiles, out_ld, out_plane_stride, debug_bounds)
         self.Fz = len(self._zp)
         self._layout = _field_layout(self.I, self.Fz, self.Fy, self.Fx, tiles, out_ld, out_plane_stride)
         h = ctypes.c_void_p()
@@ -257,6 +262,21 @@ class Plan:
         i = ScwPlanInfo()
         check(self._lib.scw_plan_get_info(self._h, ctypes.byref(i)), "scw_plan_get_info")
         return {f: getattr(i, f) for f, _ in ScwPlanInfo._fields_}
+
+    def debug_set_extent(self, buffer, elements=0):
+        """SCW_FLAG_DEBUG_BOUNDS plans: lower the extent the index checks use for `buffer` (a name of
+        DEBUG_BUFFERS or its index); 0 restores the real extent."""
+        b = DEBUG_BUFFERS.index(buffer) if isinstance(buffer, str) else int(buffer)
+        check(self._lib.scw_plan_debug_set_extent(self._h, b, int(elements)), "scw_plan_debug_set_extent")
+
+    def enable_trace(self, on=True):
+        check(self._lib.scw_plan_enable_trace(self._h, 1 if on else 0), "scw_plan_enable_trace")
+
+    def trace(self) -> dict:
+        """Kernel begin/end (us from the earliest begin) since the previous read, per step."""
+        buf = (ctypes.c_double * (2 * len(TRACE_SLOTS)))()
+        check(self._lib.scw_plan_get_trace(self._h, buf, len(TRACE_SLOTS)), "scw_plan_get_trace")
+        return {name: (buf[2 * i], buf[2 * i + 1]) for i, name in enumerate(TRACE_SLOTS) if buf[2 * i + 1] >= 0}
 
     def tune_report(self) -> str:
         r = self._lib.scw_plan_tune_report(self._h)

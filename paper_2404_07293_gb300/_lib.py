@@ -10,11 +10,12 @@ LIB_PATH = os.path.join(HERE, "libscw.so")
 
 SCW_OK = 0
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARGUMENT", 2: "UNSUPPORTED", 3: "OUT_OF_MEMORY", 4: "CUDA",
-                5: "TIMEOUT", 6: "NUMERIC", 7: "STATE"}
+                5: "TIMEOUT", 6: "NUMERIC", 7: "STATE", 8: "BOUNDS"}
 PRECISION = {"fp32": 0, "split_bf16": 1, "fp16": 2}
 FLAG_EXTERIOR = 1
 FLAG_HOST_IO = 2
 FLAG_AUTOTUNE = 4
+FLAG_DEBUG_BOUNDS = 8
 
 
 class ScwDesc(ctypes.Structure):
@@ -74,6 +75,9 @@ class ScwSolveTimes(ctypes.Structure):
 SIGNATURES = {
     "scw_plan_create": (c_int, [POINTER(ScwDesc), POINTER(c_void_p)]),
     "scw_plan": (c_int, [POINTER(ScwDesc), c_void_p, POINTER(c_void_p)]),
+    "scw_plan_enable_trace": (c_int, [c_void_p, c_int]),
+    "scw_plan_debug_set_extent": (c_int, [c_void_p, c_int, ctypes.c_ulonglong]),
+    "scw_plan_get_trace": (c_int, [c_void_p, POINTER(ctypes.c_double), c_int]),
     "scw_plan_destroy": (c_int, [c_void_p]),
     "scw_plan_set_layers": (c_int, [c_void_p] + [c_void_p] * 6 + [c_void_p]),
     "scw_synthesize": (c_int, [c_void_p, c_void_p, c_void_p]),

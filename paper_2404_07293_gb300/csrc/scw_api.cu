@@ -77,7 +77,8 @@ static void free_item(Plan* p) {
   void* ptrs[] = {p->d_units,   p->d_zplanes, p->d_zbounds, p->d_nsplit,   p->d_nsplit1, p->d_ext_planes, p->d_pupil,
                   p->d_sz_top,  p->d_sz_bot,  p->d_twx,     p->d_twy,      p->Whi,       p->Wlo,
                   p->Wh,        p->Wt,        p->Bhi,       p->Blo,        p->Cf,        p->S_part,
-                  p->T,         p->hio_W,     p->hio_gamma, p->hio_alpha,  p->hio_p,     p->hio_out};
+                  p->T,         p->hio_W,     p->hio_gamma, p->hio_alpha,  p->hio_p,     p->hio_out,
+                  p->d_xcount};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -326,6 +327,15 @@ static scw_status finish_item(Plan* p) {
     SCW_TRY(cudaStreamSynchronize(t_setup));
   }
   SCW_TRY(upload(&p->d_nsplit, nsplit, tot));
+  const int n_tiles = (3 * p->M + p->rows_tile - 1) / p->rows_tile;
+  if (p->d_xcount) {
+    cudaFree(p->d_xcount);
+    p->d_xcount = nullptr;
+  }
+  if (p->fuse_x && !p->units.empty()) {
+    SCW_TRY(dalloc(&p->d_xcount, p->units.size() * n_tiles, tot));
+    SCW_TRY(cudaMemsetAsync(p->d_xcount, 0, p->units.size() * n_tiles * sizeof(int), t_setup));
+  }
   SCW_TRY(dalloc(&p->S_part, (size_t)p->k_split * p->Fz * 3 * M, tot));
   SCW_TRY(cudaMemsetAsync(p->S_part, 0, (size_t)p->k_split * p->Fz * 3 * M * sizeof(float2), t_setup));
   ItemDev& it = p->item;
@@ -350,7 +360,27 @@ static scw_status finish_item(Plan* p) {
   it.tx = p->tiles_x; it.ty = p->tiles_y; it.ld = p->out_ld; it.pstride = p->out_pstride;
   it.F_pad = p->F_pad;
   it.k_split = p->k_split;
-  it.n_tiles = (3 * p->M + 127) / 128;
+  it.n_tiles = n_tiles;
+  it.rows_tile = p->rows_tile;
+  it.fuse_x = p->fuse_x ? 1 : 0;
+  it.xcount = p->d_xcount;
+  if (p->flags & SCW_FLAG_DEBUG_BOUNDS) {
+    const unsigned long long nk = (8 * M + 63) / 64, Fz = p->Fz, L = p->L, nu = p->units.size();
+    unsigned long long* b = p->bnd_real;
+    b[BND_S_PART] = (unsigned long long)p->k_split * Fz * 3 * M;
+    b[BND_T] = Fz * 3 * p->V * p->Fx;
+    b[BND_TWX] = (unsigned long long)fold_np(p->U) * (p->Fx / 8);
+    b[BND_TWY] = (unsigned long long)(p->Fy / 8) * fold_np(p->V);
+    b[BND_B] = p->precision == SCW_PREC_FP32 ? 0 : nu * nk * p->NB * 64;
+    b[BND_GAMMA] = L * 4 * M;
+    b[BND_ALPHA] = (unsigned long long)p->I * L * 4 * M;
+    b[BND_OUT] = (unsigned long long)((long long)(p->I * 3 * p->Fz_out - 1) * p->out_pstride +
+                                      (long long)(p->tiles_y * p->Fy - 1) * p->out_ld + (long long)p->tiles_x * p->Fx);
+    b[BND_C] = p->precision == SCW_PREC_FP32 ? nu * 4 * M * p->F_pad : 0;
+    b[BND_WT] = p->precision == SCW_PREC_FP32 ? L * 4 * M * 3 * M : 0;
+    it.dbg = 1;
+    for (int k = 0; k < BND_COUNT; ++k) it.bnd[k] = b[k];
+  }
   it.nk = (8 * p->M + 63) / 64;
   it.n_units = (int)p->units.size();
   return SCW_OK;
@@ -406,7 +436,7 @@ struct TaskCost {
 static void item_tasks(const Plan* p, int item, int ks, std::vector<TaskCost>& out,
                        const std::vector<int>* uks = nullptr) {
   const int nk = (8 * p->M + 63) / 64;
-  const int tiles = (3 * p->M + 127) / 128;
+  const int tiles = (3 * p->M + p->rows_tile - 1) / p->rows_tile;
   for (int u = 0; u < (int)p->units.size(); ++u) {
     const int k = uks ? (*uks)[u] : ks;
     const int per = (nk + k - 1) / k;
@@ -468,6 +498,28 @@ static double model_makespan(const std::vector<Plan*>& items, const std::vector<
 
 // Schedule of the tasks of every item, or (unit_begin < unit_end) only of those
 // units of item 0; ctas_per_sm > 0 caps the persistent grid per SM.
+// SCW_FLAG_DEBUG_BOUNDS: the ranges a contraction task's bulk copies and epilogue stores cover, as the
+// kernel derives them (task_geom), against the buffers' allocations.
+static scw_status check_task_ranges(const Plan* p, const int4& tk) {
+  const int R = 3 * p->M, nk = (8 * p->M + 63) / 64;
+  const LayerUnit& u = p->units[tk.y];
+  const int ks = u.ks > 0 ? u.ks : p->k_split;
+  const int per = (nk + ks - 1) / ks;
+  const int kb = tk.w * per, kcount = std::max(0, std::min(nk, kb + per) - kb);
+  const int rt = std::min(p->rows_tile, R - p->rows_tile * tk.z);
+  const size_t a_end = (size_t)u.layer * R * nk * 64 + (size_t)tk.z * p->rows_tile * nk * 64 + (size_t)(kb + kcount) * rt * 64;
+  const size_t b_end = ((size_t)tk.y * nk + kb + kcount) * p->NB * 64;
+  const size_t s_end = ((size_t)tk.w * p->Fz + u.f0 + u.nf - 1) * R + (size_t)p->rows_tile * tk.z + rt;
+  std::string why;
+  if (rt <= 0 || tk.w >= ks || u.layer < 0 || u.layer >= p->L) why = "its row tile, split or layer";
+  else if (a_end > (size_t)p->L * R * nk * 64) why = "W";
+  else if (b_end > p->units.size() * (size_t)nk * p->NB * 64) why = "the B operand";
+  else if (s_end > (size_t)p->k_split * p->Fz * R) why = "the partial spectra";
+  if (why.empty()) return SCW_OK;
+  return set_error(SCW_ERR_BOUNDS, "contraction task (unit " + std::to_string(tk.y) + ", tile " + std::to_string(tk.z) +
+                                       ", split " + std::to_string(tk.w) + ") would reach outside " + why);
+}
+
 static scw_status upload_schedule(const std::vector<Plan*>& items, int NB, bool bf16, TcSchedule& s,
                                   int ctas_per_sm = 0, int unit_begin = 0, int unit_end = 0) {
   std::vector<TaskCost> t;
@@ -488,6 +540,11 @@ static scw_status upload_schedule(const std::vector<Plan*>& items, int NB, bool 
     s.grid = 0;
     return SCW_OK;
   }
+  for (const auto& tc : t)
+    if (items[tc.t.x]->flags & SCW_FLAG_DEBUG_BOUNDS) {
+      scw_status st = check_task_ranges(items[tc.t.x], tc.t);
+      if (st != SCW_OK) return st;
+    }
   s.grid = schedule_grid(s.n_tasks, NB, bf16, ctas_per_sm);
   std::vector<int> off;
   std::vector<int4> order;
@@ -543,10 +600,12 @@ struct scw_plan_s {
   bool tiled = false;  // some item stores periodic tiles
   int max_twy = 0;     // largest y fold-twiddle table (complex elements)
   int inject_stall = 0;            // scw_plan_inject_stall (tests of the timeout path)
+  unsigned long long* d_trace = nullptr;  // kernel trace stamps (scw_plan_enable_trace), or null
   TcSchedule sched;
   float2** d_outs = nullptr;
   float2** h_outs = nullptr;       // pinned
   int max_M = 0, max_Qx = 0, max_V = 0, max_Vp = 0;
+  bool fuse_x = false;  // the contraction writes the x-pass rows itself (ItemDev::fuse_x)
   size_t xpass_smem = 0;
   size_t rec_smem = 0;
   // graph replay
@@ -583,7 +642,7 @@ static void free_plan(scw_plan_t P) {
   if (!P) return;
   for (auto* p : P->items) free_item(p);
   void* ptrs[] = {P->d_err, P->d_items, P->d_unit_entries, P->d_plane_entries, P->sched.d_tasks,
-                  P->sched.d_cta_off, P->d_outs};
+                  P->sched.d_cta_off, P->d_outs, P->d_trace};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (P->h_outs) cudaFreeHost(P->h_outs);
@@ -722,13 +781,15 @@ static scw_status enqueue_pipelined(scw_plan_t P, float2* out_one, cudaStream_t 
     const int nb = P->gplane[g + 1] - P->gplane[g];
     if (nb == 0) continue;
     const int2* ent = P->d_plane_entries + P->gplane[g];
-    e = launch_xpass(one, nullptr, ent, nb, P->xpass_smem, P->st2);
-    if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
+    if (!P->fuse_x) {  // fused: the contraction wrote this group's x-pass rows
+      e = launch_xpass(one, nullptr, ent, nb, P->xpass_smem, P->st2);
+      if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
+    }
     int ny = 0;
     e = launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, P->max_twy, P->tiled, out_one, nullptr,
                      P->st2, &ny);
     if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
-    n += 1 + ny;
+    n += (P->fuse_x ? 0 : 1) + ny;
   }
   e = cudaEventRecord(P->ev_join, P->st2);
   if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
@@ -745,15 +806,19 @@ static scw_status enqueue_synthesis(scw_plan_t P, float2* out_one, cudaStream_t 
   const ItemDev& one = P->items[0]->item;
   const ItemDev* items = P->batched ? P->d_items : nullptr;
   mark(P, 2, st, marks);
-  cudaError_t e = launch_xpass(one, items, P->d_plane_entries, P->n_plane_entries, P->xpass_smem, st);
-  if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
+  cudaError_t e = cudaSuccess;
+  if (!P->fuse_x) {  // fused: the contraction's last K split of each row tile wrote the x-pass rows
+    e = launch_xpass(one, items, P->d_plane_entries, P->n_plane_entries, P->xpass_smem, st);
+    if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
+    ++n;
+  }
   mark(P, 3, st, marks);
   int ny = 0;
   e = launch_ypass(one, items, P->d_plane_entries, P->n_plane_entries, P->n_pair_entries, P->max_Qx, P->max_Vp, P->max_twy, P->tiled,
                    out_one, P->d_outs, st, &ny);
   if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
   mark(P, 4, st, marks);
-  n += 1 + ny;
+  n += ny;
   if (marks && P->timing && P->tev_used + kMarks <= P->tev.size()) P->tev_used += kMarks;
   return SCW_OK;
 }
@@ -944,6 +1009,7 @@ static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, boo
   SCW_TRY(dalloc(&P->d_err, 1, tot));
   SCW_TRY(cudaMemsetAsync(P->d_err, 0, sizeof(int), t_setup));
   SCW_TRY(cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking));
+  for (auto* p : P->items) p->item.err = P->d_err;  // debug-path reports (finish_item keeps it)
   std::vector<int2> ue, pe;
   for (size_t i = 0; i < P->items.size(); ++i) {
     Plan* p = P->items[i];
@@ -957,6 +1023,18 @@ static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, boo
     P->rec_smem = std::max(P->rec_smem, recompose_smem_bytes(p->V, p->item.Up, p->item.Vp));
     P->tiled = P->tiled || p->tiles_x > 1 || p->tiles_y > 1;
     P->max_twy = std::max(P->max_twy, (p->Fy / 8) * p->item.Vp);
+  }
+  // The x-direction recomposition runs inside the tensor-core contraction when every item's order
+  // rows fit whole into a row tile of W (U rows each, U padded to <= 64 positions) and no plane
+  // lies outside the sample (exterior spectra come from their own kernel and take the x-pass).
+  // The fused work of a row tile grows with the unit's plane slots: with more than 16 the separate
+  // x-pass (the whole GPU at once) is faster than the last arrivals' epilogue warps.
+  bool fuse = P->tc && P->F_pad <= 16;
+  for (auto* p : P->items) fuse = fuse && p->n_exterior == 0 && fold_np(p->U) <= 64;
+  P->fuse_x = fuse;
+  for (auto* p : P->items) {
+    p->fuse_x = fuse;
+    p->rows_tile = fuse ? p->U * (128 / p->U) : 128;
   }
   // plane entries of items with long y folds first: they run the two-residue y-pass
   std::stable_partition(pe.begin(), pe.end(),
@@ -987,8 +1065,9 @@ static scw_status check_item_index(scw_plan_t P, int item) {
 // W into the chosen precision's layout (transposed FP32, or tile-major swizzled 16-bit).
 static cudaError_t convert_w(Plan* p, const float2* w, cudaStream_t st) {
   if (p->precision == SCW_PREC_FP32) return launch_transpose_layers(w, p->Wt, p->L, 3 * p->M, 4 * p->M, st);
-  if (p->precision == SCW_PREC_SPLIT_BF16) return launch_convert_tiled(w, p->Whi, p->Wlo, p->L, p->M, true, st);
-  return launch_convert_tiled(w, p->Wh, nullptr, p->L, p->M, false, st);
+  if (p->precision == SCW_PREC_SPLIT_BF16)
+    return launch_convert_tiled(w, p->Whi, p->Wlo, p->L, p->M, p->rows_tile, true, st);
+  return launch_convert_tiled(w, p->Wh, nullptr, p->L, p->M, p->rows_tile, false, st);
 }
 
 // Conversion of layers [lb, le) of W (tensor-core plans; the tiled layout is contiguous per layer).
@@ -996,8 +1075,8 @@ static cudaError_t convert_w_layers(Plan* p, const float2* w, int lb, int le, cu
   const size_t M = p->M, R = 3 * M, nk = (8 * M + 63) / 64;
   const size_t in_off = (size_t)lb * R * 4 * M, out_off = (size_t)lb * R * nk * 64;
   if (p->precision == SCW_PREC_SPLIT_BF16)
-    return launch_convert_tiled(w + in_off, p->Whi + out_off, p->Wlo + out_off, le - lb, p->M, true, st);
-  return launch_convert_tiled(w + in_off, p->Wh + out_off, nullptr, le - lb, p->M, false, st);
+    return launch_convert_tiled(w + in_off, p->Whi + out_off, p->Wlo + out_off, le - lb, p->M, p->rows_tile, true, st);
+  return launch_convert_tiled(w + in_off, p->Wh + out_off, nullptr, le - lb, p->M, p->rows_tile, false, st);
 }
 
 // Groups of the host-IO pipeline: contiguous units, the layers they span and their plane slots.
@@ -1107,7 +1186,7 @@ static scw_status synthesize_host_pipelined(scw_plan_t P, const void* W, const v
     const int fb = P->hplane[g], nb = P->hplane[g + 1] - fb;
     if (nb > 0) {
       const int2* ent = P->d_plane_entries + fb;
-      SCW_TRY_E(launch_xpass(one, nullptr, ent, nb, P->xpass_smem, st), "x-pass launch");
+      if (!P->fuse_x) SCW_TRY_E(launch_xpass(one, nullptr, ent, nb, P->xpass_smem, st), "x-pass launch");
       int ny = 0;
       SCW_TRY_E(launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, P->max_twy,
                              P->tiled, p->hio_out, nullptr, st, &ny), "y-pass launch");
@@ -1181,6 +1260,7 @@ const char* scw_status_string(scw_status s) {
     case SCW_ERR_TIMEOUT: return "device wait timed out";
     case SCW_ERR_NUMERIC: return "non-finite value";
     case SCW_ERR_STATE: return "call order violated";
+    case SCW_ERR_BOUNDS: return "index outside its buffer";
   }
   return "unknown status";
 }
@@ -1471,6 +1551,12 @@ scw_status scw_plan_check(scw_plan_t P, void* stream) {
   if (e != cudaSuccess) return cuda_error(e, "reading the device error word");
   if (word) {
     cudaMemset(P->d_err, 0, sizeof(int));
+    // a stopped contraction can leave K-split arrivals counted: start the next call from zero
+    for (auto* p : P->items)
+      if (p->d_xcount) cudaMemset(p->d_xcount, 0, p->units.size() * (size_t)p->item.n_tiles * sizeof(int));
+    if (word == DEV_ERR_BOUNDS)
+      return set_error(SCW_ERR_BOUNDS, "a kernel formed an index outside its buffer (SCW_FLAG_DEBUG_BOUNDS; the "
+                                       "access was skipped, so this call's results are invalid)");
     return set_error(SCW_ERR_TIMEOUT, "device error word " + std::to_string(word) +
                                           " (1: stage fill, 2: stage free, 4: accumulator, 8: drain, 16: dependency)");
   }
@@ -1531,6 +1617,69 @@ scw_status scw_plan_get_timings(scw_plan_t P, scw_kernel_times* t) {
     t->total_ms /= calls;
   }
   P->tev_used = 0;
+  return SCW_OK;
+}
+
+static void trace_init_values(unsigned long long* h) {
+  for (int s = 0; s < TRACE_SLOTS; ++s) {
+    h[2 * s] = ~0ull;
+    h[2 * s + 1] = 0ull;
+  }
+}
+
+scw_status scw_plan_enable_trace(scw_plan_t P, int on) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+  cudaError_t e = cudaDeviceSynchronize();  // no kernel of this plan may still hold the old pointer
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");
+  if (on && !P->d_trace) {
+    e = cudaMalloc(reinterpret_cast<void**>(&P->d_trace), 2 * TRACE_SLOTS * sizeof(unsigned long long));
+    if (e != cudaSuccess) return cuda_error(e, "trace buffer");
+    unsigned long long h[2 * TRACE_SLOTS];
+    trace_init_values(h);
+    e = cudaMemcpy(P->d_trace, h, sizeof(h), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_error(e, "trace buffer");
+  } else if (!on && P->d_trace) {
+    cudaFree(P->d_trace);
+    P->d_trace = nullptr;
+  }
+  for (auto* p : P->items) p->item.trace = P->d_trace;
+  invalidate_graph(P);  // the kernels take the pointer by value: recapture
+  return upload_items(P, nullptr);
+}
+
+scw_status scw_plan_debug_set_extent(scw_plan_t P, int buffer, unsigned long long elements) {
+  if (!P) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan is NULL");
+  if (buffer < 0 || buffer >= BND_COUNT) return set_error(SCW_ERR_INVALID_ARGUMENT, "unknown buffer");
+  if (!(P->items[0]->flags & SCW_FLAG_DEBUG_BOUNDS)) return set_error(SCW_ERR_STATE, "plan without SCW_FLAG_DEBUG_BOUNDS");
+  cudaError_t e = cudaDeviceSynchronize();  // no kernel of this plan may still read the old extents
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");
+  for (auto* p : P->items) {
+    const unsigned long long real = p->bnd_real[buffer];
+    p->item.bnd[buffer] = elements == 0 ? real : std::min(real, elements);
+  }
+  invalidate_graph(P);
+  return upload_items(P, nullptr);
+}
+
+scw_status scw_plan_get_trace(scw_plan_t P, double* us, int n_slots) {
+  if (!P || !us || n_slots < 1) return set_error(SCW_ERR_INVALID_ARGUMENT, "plan, us and n_slots > 0 are required");
+  if (!P->d_trace) return set_error(SCW_ERR_STATE, "tracing is off (scw_plan_enable_trace)");
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_error(e, "cudaDeviceSynchronize");
+  unsigned long long h[2 * TRACE_SLOTS];
+  e = cudaMemcpy(h, P->d_trace, sizeof(h), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_error(e, "trace read-back");
+  unsigned long long t0 = ~0ull;
+  for (int s = 0; s < TRACE_SLOTS; ++s)
+    if (h[2 * s + 1] != 0ull) t0 = std::min(t0, h[2 * s]);
+  for (int s = 0; s < n_slots; ++s) {
+    const bool used = s < TRACE_SLOTS && h[2 * s + 1] != 0ull && h[2 * s] != ~0ull;
+    us[2 * s] = used ? (double)(h[2 * s] - t0) * 1e-3 : -1.0;
+    us[2 * s + 1] = used ? (double)(h[2 * s + 1] - t0) * 1e-3 : -1.0;
+  }
+  trace_init_values(h);
+  e = cudaMemcpy(P->d_trace, h, sizeof(h), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_error(e, "trace reset");
   return SCW_OK;
 }
 

@@ -14,8 +14,11 @@ namespace scw {
 template <int FCH>
 __global__ void __launch_bounds__(128) contract_fp32_kernel(const float2* __restrict__ Wt, const float2* __restrict__ C,
                                                             const LayerUnit* __restrict__ units, int n_rblk, int ksplit,
-                                                            int M, int F_pad, int Fz, float2* __restrict__ S_part) {
+                                                            int M, int F_pad, int Fz, float2* __restrict__ S_part,
+                                                            unsigned long long* trace,
+                                                            const __grid_constant__ ItemDev chk) {
   extern __shared__ float4 cs4[];
+  trace_begin(trace, TRACE_CONTRACT);
   float2* Cs = reinterpret_cast<float2*>(cs4);
   const int split = blockIdx.x % ksplit;
   const int rest = blockIdx.x / ksplit;
@@ -32,13 +35,16 @@ __global__ void __launch_bounds__(128) contract_fp32_kernel(const float2* __rest
 
   for (int i = threadIdx.x; i < kc * FCH; i += blockDim.x) {
     const int k = i / FCH, f = i - k * FCH;
-    Cs[i] = (fc0 + f < F_pad) ? C[((size_t)ui * K + kb + k) * F_pad + fc0 + f] : make_float2(0.f, 0.f);
+    const size_t ci = ((size_t)ui * K + kb + k) * F_pad + fc0 + f;
+    Cs[i] = (fc0 + f < F_pad && in_bounds(chk, BND_C, ci)) ? C[ci] : make_float2(0.f, 0.f);
   }
   __syncthreads();
 
   const int r0 = rblk * 256 + threadIdx.x;
   const int r1 = r0 + 128;
-  const bool v0 = r0 < rows, v1 = r1 < rows;
+  // W^T rows (layer, mode) and columns r: the loop's largest index, checked once (indices grow with k)
+  const bool wt_ok = kc == 0 || in_bounds(chk, BND_WT, ((size_t)u.layer * K + kb + kc - 1) * rows + min(r1, rows - 1));
+  const bool v0 = r0 < rows && wt_ok, v1 = r1 < rows && wt_ok;
   float2 a0[FCH], a1[FCH];
 #pragma unroll
   for (int f = 0; f < FCH; ++f) a0[f] = a1[f] = make_float2(0.f, 0.f);
@@ -63,14 +69,16 @@ __global__ void __launch_bounds__(128) contract_fp32_kernel(const float2* __rest
     }
   }
 
-  float2* dst = S_part + ((size_t)split * Fz + u.f0 + fc0) * rows;
+  const size_t d0 = ((size_t)split * Fz + u.f0 + fc0) * rows;
+  float2* dst = S_part + d0;
 #pragma unroll
   for (int f = 0; f < FCH; ++f) {
     if (fc0 + f < u.nf) {
-      if (v0) dst[(size_t)f * rows + r0] = a0[f];
-      if (v1) dst[(size_t)f * rows + r1] = a1[f];
+      if (v0 && in_bounds(chk, BND_S_PART, d0 + (size_t)f * rows + r0)) dst[(size_t)f * rows + r0] = a0[f];
+      if (v1 && in_bounds(chk, BND_S_PART, d0 + (size_t)f * rows + r1)) dst[(size_t)f * rows + r1] = a1[f];
     }
   }
+  trace_end(trace, TRACE_CONTRACT);
 }
 
 cudaError_t launch_contract_fp32(const Plan& p, cudaStream_t st) {
@@ -87,12 +95,12 @@ cudaError_t launch_contract_fp32(const Plan& p, cudaStream_t st) {
     e = allow_max_smem(reinterpret_cast<const void*>(contract_fp32_kernel<16>));
     if (e != cudaSuccess) return e;
     contract_fp32_kernel<16><<<grid, 128, smem, st>>>(p.Wt, p.Cf, p.d_units, n_rblk, p.k_split, p.M, p.F_pad, p.Fz,
-                                                      p.S_part);
+                                                      p.S_part, p.item.trace, p.item);
   } else {
     e = allow_max_smem(reinterpret_cast<const void*>(contract_fp32_kernel<8>));
     if (e != cudaSuccess) return e;
     contract_fp32_kernel<8><<<grid, 128, smem, st>>>(p.Wt, p.Cf, p.d_units, n_rblk, p.k_split, p.M, p.F_pad, p.Fz,
-                                                     p.S_part);
+                                                     p.S_part, p.item.trace, p.item);
   }
   return cudaGetLastError();
 }

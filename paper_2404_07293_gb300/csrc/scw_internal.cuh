@@ -21,8 +21,32 @@ enum : int {
   DEV_ERR_TIMEOUT_EMPTY = 2,   // producer wait on a free stage ran out
   DEV_ERR_TIMEOUT_ACCUM = 4,   // wait on an accumulator buffer ran out
   DEV_ERR_TIMEOUT_DRAIN = 8,   // wait for in-flight work after an abort ran out
-  DEV_ERR_TIMEOUT_DEP = 16     // wait on a cross-CTA dependency counter ran out
+  DEV_ERR_TIMEOUT_DEP = 16,    // wait on a cross-CTA dependency counter ran out
+  DEV_ERR_BOUNDS = 32          // SCW_FLAG_DEBUG_BOUNDS: an index left its buffer (the access was skipped)
 };
+
+// Buffers whose indices the SCW_FLAG_DEBUG_BOUNDS path checks (ItemDev::bnd holds their extents).
+enum : int { BND_S_PART = 0, BND_T, BND_TWX, BND_TWY, BND_B, BND_GAMMA, BND_ALPHA, BND_OUT, BND_C, BND_WT,
+             BND_COUNT };
+
+// Kernel trace (scw_plan_enable_trace): per slot, the %globaltimer nanoseconds at which the first CTA
+// of a kernel began its work (after any wait on the kernel before it) and the last CTA finished:
+// trace[2 slot] = min over CTAs, trace[2 slot + 1] = max over CTAs.
+enum : int { TRACE_PHASES = 0, TRACE_EXTERIOR = 1, TRACE_CONTRACT = 2, TRACE_XPASS = 3, TRACE_YPASS = 4,
+             TRACE_SLOTS = 8 };
+
+__device__ __forceinline__ unsigned long long trace_clock() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// thread 0 of each CTA stamps; a null trace pointer (tracing off) costs one predicated branch
+__device__ __forceinline__ void trace_begin(unsigned long long* tr, int slot) {
+  if (tr != nullptr && threadIdx.x == 0) atomicMin(tr + 2 * slot, trace_clock());
+}
+__device__ __forceinline__ void trace_end(unsigned long long* tr, int slot) {
+  if (tr != nullptr && threadIdx.x == 0) atomicMax(tr + 2 * slot + 1, trace_clock());
+}
 
 constexpr int kMaxFx = 4096;
 constexpr int kMaxM = 4096;              // U*V
@@ -66,7 +90,24 @@ struct ItemDev {
   size_t alpha_istride;    // L 4M: alpha elements per illumination
   int tx, ty;              // periodic tiles of the field along x and y
   long long ld, pstride;   // field row pitch and plane-slice stride (complex elements)
+  unsigned long long* trace;  // kernel trace stamps [TRACE_SLOTS][2], or null (tracing off)
+  int rows_tile;           // rows of W per contraction row tile (a whole number of order rows U when
+                           // the x-direction recomposition is fused into the contraction, else 128)
+  int fuse_x;              // the contraction's last K split of each (unit, row tile) writes T itself
+  int* xcount;             // [n_units][n_tiles] arrivals of the K splits (fuse_x; each step leaves 0)
+  int dbg;                 // SCW_FLAG_DEBUG_BOUNDS: kernels check every global index against bnd
+  int* err;                // the plan's device error word (DEV_ERR_BOUNDS)
+  unsigned long long bnd[BND_COUNT];  // extents in elements of the checked buffers (dbg only)
 };
+
+// Index check of the debug path: true when element i of buffer `buf` exists (always true for
+// plans without SCW_FLAG_DEBUG_BOUNDS: one uniform branch); otherwise record DEV_ERR_BOUNDS and
+// return false so that the caller skips the access.
+__device__ __forceinline__ bool in_bounds(const ItemDev& it, int buf, size_t i) {
+  if (!it.dbg || i < it.bnd[buf]) return true;
+  atomicOr(it.err, DEV_ERR_BOUNDS);
+  return false;
+}
 
 struct PointTables;  // scw_points.cuh
 
@@ -89,6 +130,10 @@ struct Plan {
   int F_pad = 8;      // plane slots per layer (multiple of 8)
   int NB = 16;        // 2 * F_pad: real columns of the tensor-core B operand
   int k_split = 1;                // the largest K split over the units (S_part holds that many partials)
+  int rows_tile = 128;            // rows of W per contraction row tile (ItemDev::rows_tile)
+  bool fuse_x = false;            // x-direction recomposition fused into the contraction
+  int* d_xcount = nullptr;        // [units][tiles] K-split arrival counters (fuse_x)
+  unsigned long long bnd_real[BND_COUNT] = {};  // buffer extents (SCW_FLAG_DEBUG_BOUNDS plans)
   std::vector<int> unit_ks;        // per-unit K split (tensor-core plans; empty = k_split everywhere)
   int n_exterior = 0;
 
@@ -198,7 +243,8 @@ scw_status cuda_error(cudaError_t e, const char* what);
 scw_status check_device();  // SCW_OK on an sm_103 device
 
 // launchers (host side), each returns cudaSuccess or the launch error
-cudaError_t launch_convert_tiled(const float2* W, void* hi, void* lo, int L, int M, bool bf16_split, cudaStream_t st);
+cudaError_t launch_convert_tiled(const float2* W, void* hi, void* lo, int L, int M, int rows_tile, bool bf16_split,
+                                 cudaStream_t st);
 cudaError_t launch_transpose_layers(const float2* W, float2* Wt, int L, int rows, int cols, cudaStream_t st);
 
 // step (a): unit entries are (item, unit) pairs; items == nullptr means "the single item `one`"

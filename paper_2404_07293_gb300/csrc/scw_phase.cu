@@ -105,62 +105,76 @@ __device__ __forceinline__ size_t swz_offset(int n, int k, int rows) {
 // (NB = 2 F_pad) in the layout above: row f holds (Re c_j, -Im c_j) at columns
 // (2j, 2j+1), row F_pad + f holds (Im c_j, Re c_j); with A = W viewed as
 // interleaved reals this gives [Re S | Im S] (the complex product as one real
-// GEMM). hi = round(x), lo = round(x - hi). One thread per mode j and all planes
-// of its unit (the mode's constants are loaded and reduced once); blocks are
-// (mode block, (item, unit) entry).
+// GEMM). hi = round(x), lo = round(x - hi). A block is 32 consecutive modes x
+// kPhaseGroups plane groups: lane l of warp w takes mode 32 blockIdx.x + l and the
+// planes f = w, w + kPhaseGroups, ... of its unit, so the planes of a mode run in
+// parallel and every warp store covers whole 128-byte rows. Blocks are (mode
+// block, (item, unit) entry).
+constexpr int kPhaseGroups = 4;
+
 template <typename T, bool BATCH>
-__global__ void __launch_bounds__(128) phases_tc_kernel(const __grid_constant__ ItemDev one,
-                                                        const ItemDev* __restrict__ items,
-                                                        const int2* __restrict__ entries, int F_pad) {
+__global__ void __launch_bounds__(32 * kPhaseGroups) phases_tc_kernel(const __grid_constant__ ItemDev one,
+                                                                      const ItemDev* __restrict__ items,
+                                                                      const int2* __restrict__ entries, int F_pad) {
   __shared__ PlaneOffsets off;
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");  // the contraction may start streaming W
+  trace_begin(one.trace, TRACE_PHASES);
   const int2 e = entries[blockIdx.y];
   const ItemDev& it = BATCH ? items[e.x] : one;
   const LayerUnit u = it.units[e.y];
   const int M = it.M;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int fg = threadIdx.x >> 5;
   const int M4 = 4 * M;
   // the mode's constants are requested before the block waits for the plane offsets
   double2 g = make_double2(0.0, 0.0), al = make_double2(0.0, 0.0);
-  const double2* alpha_lj = it.alpha + (size_t)u.layer * M4 + j;  // illumination 0
+  const size_t lj = (size_t)u.layer * M4 + j;
+  const double2* alpha_lj = it.alpha + lj;  // illumination 0
   if (j < M4) {
-    g = it.gamma[(size_t)u.layer * M4 + j];
-    al = alpha_lj[0];
+    if (in_bounds(it, BND_GAMMA, lj)) g = it.gamma[lj];
+    if (in_bounds(it, BND_ALPHA, lj)) al = alpha_lj[0];
   }
   load_offsets(off, u, it.zplanes, it.zbounds);
   __syncthreads();
-  if (j >= M4) return;
-  const int NB = 2 * F_pad;
-  const ModeConst mc = mode_const(g, al, it.inv_lam);
-  const bool fwd = j < 2 * M;
-  const size_t base = (size_t)e.y * it.nk * NB * 64;  // B is per work unit
-  T* Bhi = static_cast<T*>(it.Bhi) + base;
-  T* Blo = static_cast<T*>(it.Blo) + base;
-  for (int f = 0; f < F_pad; ++f) {
-    float2 cv = make_float2(0.f, 0.f);
-    if (f < u.nf) {
-      const float dh = fwd ? off.f_hi[f] : off.b_hi[f];
-      const float dl = fwd ? off.f_lo[f] : off.b_lo[f];
-      float2 a = mc.alpha;
-      if (it.I > 1) {  // plane slot f I + i carries illumination i
-        const double2 ai = alpha_lj[(size_t)((u.f0 + f) % it.I) * it.alpha_istride];
-        a = make_float2((float)ai.x, (float)ai.y);
+  if (j < M4) {
+    const int NB = 2 * F_pad;
+    const ModeConst mc = mode_const(g, al, it.inv_lam);
+    const bool fwd = j < 2 * M;
+    const size_t base = (size_t)e.y * it.nk * NB * 64;  // B is per work unit
+    T* Bhi = static_cast<T*>(it.Bhi) + base;
+    T* Blo = static_cast<T*>(it.Blo) + base;
+    for (int f = fg; f < F_pad; f += kPhaseGroups) {
+      float2 cv = make_float2(0.f, 0.f);
+      if (f < u.nf) {
+        const float dh = fwd ? off.f_hi[f] : off.b_hi[f];
+        const float dl = fwd ? off.f_lo[f] : off.b_lo[f];
+        float2 a = mc.alpha;
+        if (it.I > 1) {  // plane slot f I + i carries illumination i
+          const size_t ia = (size_t)((u.f0 + f) % it.I) * it.alpha_istride;
+          const double2 ai = in_bounds(it, BND_ALPHA, lj + ia) ? alpha_lj[ia] : make_double2(0.0, 0.0);
+          a = make_float2((float)ai.x, (float)ai.y);
+        }
+        cv = cmulf(a, mode_factor_df(mc.a_hi, mc.a_lo, mc.c, dh, dl));
       }
-      cv = cmulf(a, mode_factor_df(mc.a_hi, mc.a_lo, mc.c, dh, dl));
+      const float v0[2] = {cv.x, -cv.y};
+      const float v1[2] = {cv.y, cv.x};
+      Pair<T> h0, l0, h1, l1;
+      h0.a = to_lp<T>(v0[0]); h0.b = to_lp<T>(v0[1]);
+      l0.a = to_lp<T>(v0[0] - from_lp<T>(h0.a)); l0.b = to_lp<T>(v0[1] - from_lp<T>(h0.b));
+      h1.a = to_lp<T>(v1[0]); h1.b = to_lp<T>(v1[1]);
+      l1.a = to_lp<T>(v1[0] - from_lp<T>(h1.a)); l1.b = to_lp<T>(v1[1] - from_lp<T>(h1.b));
+      const size_t i0 = swz_offset(f, 2 * j, NB), i1 = swz_offset(F_pad + f, 2 * j, NB);
+      if (in_bounds(it, BND_B, base + i0 + 1)) {  // a pair: its second element is the last one written
+        *reinterpret_cast<Pair<T>*>(Bhi + i0) = h0;
+        *reinterpret_cast<Pair<T>*>(Blo + i0) = l0;
+      }
+      if (in_bounds(it, BND_B, base + i1 + 1)) {
+        *reinterpret_cast<Pair<T>*>(Bhi + i1) = h1;
+        *reinterpret_cast<Pair<T>*>(Blo + i1) = l1;
+      }
     }
-    const float v0[2] = {cv.x, -cv.y};
-    const float v1[2] = {cv.y, cv.x};
-    Pair<T> h0, l0, h1, l1;
-    h0.a = to_lp<T>(v0[0]); h0.b = to_lp<T>(v0[1]);
-    l0.a = to_lp<T>(v0[0] - from_lp<T>(h0.a)); l0.b = to_lp<T>(v0[1] - from_lp<T>(h0.b));
-    h1.a = to_lp<T>(v1[0]); h1.b = to_lp<T>(v1[1]);
-    l1.a = to_lp<T>(v1[0] - from_lp<T>(h1.a)); l1.b = to_lp<T>(v1[1] - from_lp<T>(h1.b));
-    const size_t i0 = swz_offset(f, 2 * j, NB), i1 = swz_offset(F_pad + f, 2 * j, NB);
-    *reinterpret_cast<Pair<T>*>(Bhi + i0) = h0;
-    *reinterpret_cast<Pair<T>*>(Blo + i0) = l0;
-    *reinterpret_cast<Pair<T>*>(Bhi + i1) = h1;
-    *reinterpret_cast<Pair<T>*>(Blo + i1) = l1;
   }
+  trace_end(one.trace, TRACE_PHASES);  // thread 0 (mode 32 blockIdx.x < 4M) stamps after its planes
 }
 
 // FP32 path: C[unit][j][f] complex64, plane index fastest; one thread per mode.
@@ -170,21 +184,26 @@ __global__ void __launch_bounds__(128) phases_fp32_kernel(const LayerUnit* __res
                                                           const double2* __restrict__ gamma,
                                                           const double2* __restrict__ alpha, int M, int F_pad,
                                                           double inv_lam, float2* __restrict__ C, int I,
-                                                          size_t alpha_istride) {
+                                                          size_t alpha_istride, unsigned long long* trace,
+                                                          const __grid_constant__ ItemDev chk) {
   __shared__ PlaneOffsets off;
+  trace_begin(trace, TRACE_PHASES);
   const LayerUnit u = units[blockIdx.y];
   load_offsets(off, u, zplanes, zb);
   __syncthreads();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int M4 = 4 * M;
   if (j >= M4) return;
-  const ModeConst mc = mode_const(gamma[(size_t)u.layer * M4 + j], alpha[(size_t)u.layer * M4 + j], inv_lam);
+  const size_t lj = (size_t)u.layer * M4 + j;
+  const ModeConst mc = mode_const(in_bounds(chk, BND_GAMMA, lj) ? gamma[lj] : make_double2(0.0, 0.0),
+                                  in_bounds(chk, BND_ALPHA, lj) ? alpha[lj] : make_double2(0.0, 0.0), inv_lam);
   const bool fwd = j < 2 * M;
   float2* dst = C + ((size_t)blockIdx.y * M4 + j) * F_pad;  // C is per work unit
   // plane slot f I + i carries illumination i
   auto alpha_of = [&](int f) {
     if (I == 1) return mc.alpha;
-    const double2 a = alpha[(size_t)((u.f0 + f) % I) * alpha_istride + (size_t)u.layer * M4 + j];
+    const size_t ia = (size_t)((u.f0 + f) % I) * alpha_istride + lj;
+    const double2 a = in_bounds(chk, BND_ALPHA, ia) ? alpha[ia] : make_double2(0.0, 0.0);
     return make_float2((float)a.x, (float)a.y);
   };
   for (int f = 0; f < F_pad; f += 2) {
@@ -195,8 +214,10 @@ __global__ void __launch_bounds__(128) phases_fp32_kernel(const LayerUnit* __res
     if (f + 1 < u.nf)
       c1 = cmulf(alpha_of(f + 1), mode_factor_df(mc.a_hi, mc.a_lo, mc.c, fwd ? off.f_hi[f + 1] : off.b_hi[f + 1],
                                                  fwd ? off.f_lo[f + 1] : off.b_lo[f + 1]));
-    *reinterpret_cast<float4*>(dst + f) = make_float4(c0.x, c0.y, c1.x, c1.y);
+    if (in_bounds(chk, BND_C, ((size_t)blockIdx.y * M4 + j) * F_pad + f + 1))
+      *reinterpret_cast<float4*>(dst + f) = make_float4(c0.x, c0.y, c1.x, c1.y);
   }
+  trace_end(trace, TRACE_PHASES);
 }
 
 // Exterior planes (Eq. 9 with the reflected wave travelling towards -z):
@@ -207,7 +228,9 @@ __global__ void exterior_kernel(const int* __restrict__ ext_planes, const double
                                 const double2* __restrict__ sz_bot, const double2* __restrict__ p_inc,
                                 const double2* __restrict__ p_ref, const double2* __restrict__ p_trn,
                                 int M, double inv_lam, float2* __restrict__ S, int I,
-                                const float* __restrict__ pupil) {
+                                const float* __restrict__ pupil, unsigned long long* trace,
+                                const __grid_constant__ ItemDev chk) {
+  trace_begin(trace, TRACE_EXTERIOR);
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= M) return;
   const int f = ext_planes[blockIdx.y];
@@ -225,7 +248,7 @@ __global__ void exterior_kernel(const int* __restrict__ ext_planes, const double
       const double2 a = p_inc[c * M + m], b = p_ref[c * M + m];
       const float2 x = cmulf(make_float2((float)a.x, (float)a.y), gi);
       const float2 y = cmulf(make_float2((float)b.x, (float)b.y), gr);
-      out[c * M + m] = make_float2(x.x + y.x, x.y + y.y);
+      if (in_bounds(chk, BND_S_PART, (size_t)f * 3 * M + c * M + m)) out[c * M + m] = make_float2(x.x + y.x, x.y + y.y);
     }
   } else {
     const double2 sb = sz_bot[m];
@@ -233,20 +256,23 @@ __global__ void exterior_kernel(const int* __restrict__ ext_planes, const double
     if (pupil) gt = make_float2(gt.x * pupil[m], gt.y * pupil[m]);
     for (int c = 0; c < 3; ++c) {
       const double2 a = p_trn[c * M + m];
-      out[c * M + m] = cmulf(make_float2((float)a.x, (float)a.y), gt);
+      if (in_bounds(chk, BND_S_PART, (size_t)f * 3 * M + c * M + m))
+        out[c * M + m] = cmulf(make_float2((float)a.x, (float)a.y), gt);
     }
   }
+  trace_end(trace, TRACE_EXTERIOR);  // thread 0 always has an order (m = 128 blockIdx.x < M)
 }
 
 // ---- one-off conversions of W (plan time) -----------------------------------
 // W [L][R = 3M][K8 = 8M] reals (the complex64 layout) -> tile-major, swizzled
 // 16-bit copies for the tensor-core contraction: for layer l, row tile t
-// (rows 128 t .. 128 t + rt - 1, rt = min(128, R - 128 t)) and K chunk kc, one
-// contiguous block of rt x 64 elements (swz_offset layout; K beyond 8M is zero).
+// (rows RT t .. RT t + rt - 1, rt = min(RT, R - RT t), RT <= 128 the plan's rows per
+// tile) and K chunk kc, one contiguous block of rt x 64 elements (swz_offset layout;
+// K beyond 8M is zero).
 // One thread per (l, row, kc, 16-byte group): 8 reals in, 8 (hi) + 8 (lo) out.
 template <typename T, bool SPLIT>
 __global__ void convert_tiled_kernel(const float* __restrict__ W, T* __restrict__ hi, T* __restrict__ lo, int L, int R,
-                                     int K8, int nk) {
+                                     int K8, int nk, int RT) {
   const size_t total = (size_t)L * R * nk * 8;
   for (size_t g = blockIdx.x * (size_t)blockDim.x + threadIdx.x; g < total; g += (size_t)gridDim.x * blockDim.x) {
     const int grp = (int)(g & 7);
@@ -265,9 +291,9 @@ __global__ void convert_tiled_kernel(const float* __restrict__ W, T* __restrict_
 #pragma unroll
       for (int i = 0; i < 8; ++i) x[i] = 0.f;
     }
-    const int t = row >> 7, n = row & 127;
-    const int rt = min(128, R - 128 * t);
-    const size_t off = (size_t)l * R * nk * 64 + (size_t)t * 128 * nk * 64 + (size_t)kc * rt * 64 + (size_t)n * 64 +
+    const int t = row / RT, n = row - t * RT;
+    const int rt = min(RT, R - RT * t);
+    const size_t off = (size_t)l * R * nk * 64 + (size_t)t * RT * nk * 64 + (size_t)kc * rt * 64 + (size_t)n * 64 +
                        (size_t)((grp ^ (n & 7)) << 3);
     T h[8], lw[8];
 #pragma unroll
@@ -304,16 +330,18 @@ static int grid_for(size_t n, int block) {
   return (int)g;
 }
 
-cudaError_t launch_convert_tiled(const float2* W, void* hi, void* lo, int L, int M, bool bf16_split, cudaStream_t st) {
+cudaError_t launch_convert_tiled(const float2* W, void* hi, void* lo, int L, int M, int rows_tile, bool bf16_split,
+                                 cudaStream_t st) {
   const int R = 3 * M, K8 = 8 * M, nk = (K8 + 63) / 64;
+  if (rows_tile < 1 || rows_tile > 128) return cudaErrorInvalidValue;
   const size_t total = (size_t)L * R * nk * 8;
   const float* w = reinterpret_cast<const float*>(W);
   if (bf16_split)
     convert_tiled_kernel<__nv_bfloat16, true><<<grid_for(total, 256), 256, 0, st>>>(
-        w, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(lo), L, R, K8, nk);
+        w, static_cast<__nv_bfloat16*>(hi), static_cast<__nv_bfloat16*>(lo), L, R, K8, nk, rows_tile);
   else
     convert_tiled_kernel<__half, false><<<grid_for(total, 256), 256, 0, st>>>(w, static_cast<__half*>(hi), nullptr,
-                                                                              L, R, K8, nk);
+                                                                              L, R, K8, nk, rows_tile);
   return cudaGetLastError();
 }
 
@@ -326,11 +354,11 @@ cudaError_t launch_transpose_layers(const float2* W, float2* Wt, int L, int rows
 template <typename T>
 static cudaError_t launch_phases_tc_t(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries,
                                       int max_M, int F_pad, cudaStream_t st) {
-  dim3 grid((4 * max_M + 127) / 128, n_entries);
+  dim3 grid((4 * max_M + 31) / 32, n_entries);
   if (items)
-    phases_tc_kernel<T, true><<<grid, 128, 0, st>>>(one, items, d_entries, F_pad);
+    phases_tc_kernel<T, true><<<grid, 32 * kPhaseGroups, 0, st>>>(one, items, d_entries, F_pad);
   else
-    phases_tc_kernel<T, false><<<grid, 128, 0, st>>>(one, nullptr, d_entries, F_pad);
+    phases_tc_kernel<T, false><<<grid, 32 * kPhaseGroups, 0, st>>>(one, nullptr, d_entries, F_pad);
   return cudaGetLastError();
 }
 
@@ -346,7 +374,8 @@ cudaError_t launch_phases_fp32(const Plan& p, cudaStream_t st) {
   if (n_units == 0) return cudaSuccess;
   dim3 grid((4 * p.M + 127) / 128, n_units);
   phases_fp32_kernel<<<grid, 128, 0, st>>>(p.d_units, p.d_zplanes, p.d_zbounds, p.gamma, p.alpha, p.M,
-                                           p.F_pad, 1.0 / p.lambda, p.Cf, p.I, (size_t)p.L * 4 * p.M);
+                                           p.F_pad, 1.0 / p.lambda, p.Cf, p.I, (size_t)p.L * 4 * p.M, p.item.trace,
+                                           p.item);
   return cudaGetLastError();
 }
 
@@ -355,7 +384,8 @@ cudaError_t launch_exterior(const Plan& p, cudaStream_t st) {
   dim3 grid((p.M + 127) / 128, p.n_exterior);
   const double z0 = p.z_bounds.front(), zL = p.z_bounds.back();
   exterior_kernel<<<grid, 128, 0, st>>>(p.d_ext_planes, p.d_zplanes, z0, zL, p.z_inc, p.d_sz_top, p.d_sz_bot,
-                                        p.p_inc, p.p_ref, p.p_trn, p.M, 1.0 / p.lambda, p.S_part, p.I, p.d_pupil);
+                                        p.p_inc, p.p_ref, p.p_trn, p.M, 1.0 / p.lambda, p.S_part, p.I, p.d_pupil,
+                                        p.item.trace, p.item);
   return cudaGetLastError();
 }
 

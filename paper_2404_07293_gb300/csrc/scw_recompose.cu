@@ -21,48 +21,11 @@
 // point, which has no room for T, runs them fused in one kernel.
 #include <algorithm>
 
+#include "scw_fold.cuh"
 #include "scw_internal.cuh"
 #include "scw_ptx.cuh"
 
 namespace scw {
-
-__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ void c_fma(float2& acc, float2 a, float2 b) {
-  acc.x = fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x));
-  acc.y = fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y));
-}
-
-// In-place 8-point inverse DFT, X[a] = sum_r x[r] exp(+2 pi i r a / 8):
-// one radix-2 decimation-in-frequency step, then two 4-point DFTs.
-__device__ __forceinline__ void idft8(float2 (&x)[8]) {
-  const float h = 0.70710678118654752440f;
-  const float2 u0 = c_add(x[0], x[4]), u1 = c_add(x[1], x[5]), u2 = c_add(x[2], x[6]), u3 = c_add(x[3], x[7]);
-  const float2 d0 = c_sub(x[0], x[4]), d1 = c_sub(x[1], x[5]), d2 = c_sub(x[2], x[6]), d3 = c_sub(x[3], x[7]);
-  const float2 v0 = d0;
-  const float2 v1 = make_float2(h * (d1.x - d1.y), h * (d1.x + d1.y));    // * exp(i pi/4)
-  const float2 v2 = make_float2(-d2.y, d2.x);                             // * i
-  const float2 v3 = make_float2(h * (-d3.x - d3.y), h * (d3.x - d3.y));   // * exp(3 i pi/4)
-  // 4-point inverse DFTs (twiddle i): even outputs from u, odd outputs from v
-  {
-    const float2 s0 = c_add(u0, u2), s1 = c_sub(u0, u2), s2 = c_add(u1, u3);
-    const float2 t = c_sub(u1, u3);
-    const float2 s3 = make_float2(-t.y, t.x);
-    x[0] = c_add(s0, s2);
-    x[4] = c_sub(s0, s2);
-    x[2] = c_add(s1, s3);
-    x[6] = c_sub(s1, s3);
-  }
-  {
-    const float2 s0 = c_add(v0, v2), s1 = c_sub(v0, v2), s2 = c_add(v1, v3);
-    const float2 t = c_sub(v1, v3);
-    const float2 s3 = make_float2(-t.y, t.x);
-    x[1] = c_add(s0, s2);
-    x[5] = c_sub(s0, s2);
-    x[3] = c_add(s1, s3);
-    x[7] = c_sub(s1, s3);
-  }
-}
 
 // Field stores. Row y of plane slice s (its base `dst`, column x included) goes to
 // dst + y ld, streaming; TILED: also to every other periodic tile (E repeats with
@@ -228,9 +191,12 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
   float2* tw_s = xs_row + V * Up;
   ptx::griddep_launch_dependents();
   if (staged)
-    for (int i = threadIdx.x; i < Up * Q; i += blockDim.x) tw_s[i] = __ldg(it.twx + i);
+    for (int i = threadIdx.x; i < Up * Q; i += blockDim.x)
+      tw_s[i] = in_bounds(it, BND_TWX, i) ? __ldg(it.twx + i) : make_float2(0.f, 0.f);
   ptx::griddep_wait();  // the partial spectra come from the preceding contraction
-  const float2* src = it.S_part + (size_t)f * 3 * M + (size_t)c * M;
+  trace_begin(one.trace, TRACE_XPASS);
+  const size_t sbase = (size_t)f * 3 * M + (size_t)c * M;
+  const float2* src = it.S_part + sbase;
   const int ns = it.nsplit[f];
   const size_t stride = it.split_stride;
   for (int i0 = 0; i0 < V * Up; i0 += 2 * blockDim.x) {
@@ -242,6 +208,8 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
       const int i = i0 + h * blockDim.x + threadIdx.x;
       const int vi = i / Up, ui = i < V * Up ? fold_order(i - vi * Up, U, Up) : -1;
       off[h] = ui >= 0 ? vi * U + ui : -1;
+      // the element's last partial has the largest index
+      if (off[h] >= 0 && !in_bounds(it, BND_S_PART, sbase + (size_t)(ns - 1) * stride + off[h])) off[h] = -1;
 #pragma unroll
       for (int k = 0; k < kSplitUnroll; ++k)
         v[h][k] = (off[h] >= 0 && k < ns) ? src[(size_t)k * stride + off[h]] : make_float2(0.f, 0.f);
@@ -258,10 +226,15 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
     }
   }
   __syncthreads();
-  float2* dst = it.T + ((size_t)f * 3 + c) * V * Fx;
+  const size_t tbase = ((size_t)f * 3 + c) * V * Fx;
+  float2* dst = it.T + tbase;
   const float2* twb = staged ? tw_s : it.twx;  // [p][b]: a warp's lanes read consecutive residues
   for (int t = threadIdx.x; t < V * Q; t += blockDim.x) {
     const int vi = t / Q, b = t - vi * Q;
+    // the task's largest indices: its last output (a = 7) and its last twiddle read through L1
+    if (!in_bounds(it, BND_T, tbase + (size_t)vi * Fx + b + 7 * Q) ||
+        (!staged && !in_bounds(it, BND_TWX, (size_t)(Up - 1) * Q + b)))
+      continue;
     const float2* s = xs_row + vi * Up;
     const float2* tw = twb + b;
     float2 G[8];
@@ -276,6 +249,10 @@ __global__ void __launch_bounds__(256) xpass_kernel(const __grid_constant__ Item
     float2* o = dst + (size_t)vi * Fx + b;
 #pragma unroll
     for (int a = 0; a < 8; ++a) o[a * Q] = G[a];
+  }
+  if (one.trace) {
+    __syncthreads();
+    trace_end(one.trace, TRACE_XPASS);
   }
 }
 
@@ -293,7 +270,11 @@ __device__ __forceinline__ void ypass_tile(const ItemDev& it, const float4* ys_c
   float2* out = BATCH ? outs[e.x] : out_one;
   // plane slot f = (output plane) I + illumination: slice (il 3 + c) Fz_out + fo of the field
   const int fo = f / it.I, il = f - fo * it.I;
-  float2* dst = out + ((long long)il * 3 * it.Fz_out + (long long)c * it.Fz_out + fo) * it.pstride + x;
+  const long long obase = ((long long)il * 3 * it.Fz_out + (long long)c * it.Fz_out + fo) * it.pstride + x;
+  // the thread's largest field index: element x + 1 of the last row of the last periodic tile
+  if (!in_bounds(it, BND_OUT, (size_t)(obase + 1 + (long long)(it.ty * Fy - 1) * it.ld + (long long)(it.tx - 1) * Fx)))
+    return;
+  float2* dst = out + obase;
   const float4* col = ys_col4 + lane;
   if constexpr (!PAIR) {
     for (int b = w; b < Q; b += 8) {
@@ -379,17 +360,19 @@ __device__ __forceinline__ void ypass_prefetch(const ItemDev& one, const ItemDev
     const int c = r - (r / 3) * 3;
     const ItemDev& it = BATCH ? items[e.x] : one;
     if (xb < it.Fx) {
-      const float2* src = it.T + ((size_t)e.y * 3 + c) * it.V * it.Fx;
+      const size_t tbase = ((size_t)e.y * 3 + c) * it.V * it.Fx;
+      const float2* src = it.T + tbase;
       for (int i = threadIdx.x; i < it.Vp * 32; i += blockDim.x) {  // row p = i / 32, column pair i % 32
         const int p = i >> 5, x = xb + 2 * (i & 31);
         const int v = fold_order(p, it.V, it.Vp);
-        const bool ok = v >= 0 && x < it.Fx;  // Fx is even: a pair is in or out as a whole
+        // Fx is even: a pair is in or out as a whole (its second element has the larger index)
+        const bool ok = v >= 0 && x < it.Fx && in_bounds(it, BND_T, tbase + (size_t)v * it.Fx + x + 1);
         ptx::cp_async16(ptx::smem_u32(buf + i), ok ? src + (size_t)v * it.Fx + x : src, ok ? 16u : 0u);
       }
       if constexpr (STW) {  // the fold twiddles [Fy/8][Vp] after the rows
         const float4* tw = reinterpret_cast<const float4*>(it.twy);
         for (int i = threadIdx.x; i < (it.Fy >> 3) * it.Vp / 2; i += blockDim.x)
-          ptx::cp_async16(ptx::smem_u32(buf + rows_f4 + i), tw + i, 16u);
+          ptx::cp_async16(ptx::smem_u32(buf + rows_f4 + i), tw + i, in_bounds(it, BND_TWY, 2 * (size_t)i + 1) ? 16u : 0u);
       }
     }
   }
@@ -407,6 +390,7 @@ __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_c
   int t = blockIdx.x;
   if (t >= n_tiles) return;
   ptx::griddep_wait();  // the x-pass rows come from the preceding kernel
+  trace_begin(one.trace, TRACE_YPASS);
   ypass_prefetch<BATCH, STW>(one, items, entries, t, n_tiles, nxb, rows_f4, ys_buf);
   for (int b = 0; t < n_tiles; t += gridDim.x, b ^= 1) {
     ypass_prefetch<BATCH, STW>(one, items, entries, t + gridDim.x, n_tiles, nxb, rows_f4,
@@ -425,6 +409,7 @@ __global__ void __launch_bounds__(256, PAIR ? 2 : 4) ypass_kernel(const __grid_c
     __syncthreads();          // buffer b is free for the prefetch of the next iteration
   }
   ptx::cp_async_wait<0>();
+  trace_end(one.trace, TRACE_YPASS);  // the loop's last barrier: every warp has stored its rows
 }
 
 // S[f][3M] = sum of the contraction's partial spectra (scw_spectrum).

@@ -41,7 +41,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_status_strings_and_version(lib):
     assert lib.scw_version() >= 1
-    for s in range(8):
+    for s in range(9):
         assert lib.scw_status_string(s)
     assert lib.scw_status_string(99) == b"unknown status"
 
