@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/scw_fno.h"
@@ -220,10 +221,13 @@ static scw_status forward(scw_fno_s* f, const float2* n, int B, bool keep_z, cud
                                                static_cast<const float*>(f->D), f->P, ea, BC, f->Kc, f->P, ks, st);
     FNO_TRY(launch_ok(f, e, "truncated DFT", CAT_DFT, 2.0 * BC * f->Kc * f->P));
     // Wh carries the inverse transform's 1/N^2 so that the 1x1 convolution can share its accumulator
-    FNO_TRY(launch_ok(f, launch_mix_fwd<T>(reinterpret_cast<const float2*>(f->Vh[l]), ks, vstride, ld,
-                                           at<T>(f->wcopy, f->off_R[l]), static_cast<T*>(f->Wh), inv_n2, B, f->m,
-                                           f->Kp, st),
-                      "mode mixing", CAT_MIX, 8.0 * f->m * f->m * C * C * B));
+    if constexpr (std::is_same<T, __nv_bfloat16>::value)
+      e = launch_mix_tc(false, reinterpret_cast<const float2*>(f->Vh[l]), ks, vstride, ld, at<T>(f->wcopy, f->off_R[l]),
+                        static_cast<T*>(f->Wh), inv_n2, B, f->m, f->Kp, f->d_err, f->timeout_ns, st);
+    else
+      e = launch_mix_fwd<T>(reinterpret_cast<const float2*>(f->Vh[l]), ks, vstride, ld, at<T>(f->wcopy, f->off_R[l]),
+                            static_cast<T*>(f->Wh), inv_n2, B, f->m, f->Kp, st);
+    FNO_TRY(launch_ok(f, e, "mode mixing", CAT_MIX, 8.0 * f->m * f->m * C * C * B));
     EpiArgs eb{};
     eb.alpha = 1.f;
     eb.rows = f->P;
@@ -334,12 +338,25 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     FNO_TRY(launch_ok(f, e, "weight gradient", CAT_DW, 2.0 * BC * C * P));
     reduce_into(segs, f->part_dw[l], groups * kw * 4, C * C, C * C, f->grad + f->off_W[l]);
     // mixing backward
-    const int sb = mix_sample_blocks(B);
-    FNO_TRY(launch_ok(f, launch_mix_bwd<T>(reinterpret_cast<const float2*>(f->GWh),
-                                           reinterpret_cast<const float2*>(f->Vh[l]), ks, vstride, ld,
-                                           at<T>(f->wcopy, f->off_R[l]), static_cast<T*>(f->GVh), f->part_mix[l], B,
-                                           f->m, f->Kp, f->N, st),
-                      "mode mixing backward", CAT_MIX, 16.0 * f->m * f->m * C * C * B));
+    constexpr bool tc_mix = std::is_same<T, __nv_bfloat16>::value;
+    const int sb = tc_mix ? mix_dr_blocks(B) : mix_sample_blocks(B);
+    if constexpr (tc_mix) {
+      // GVh = R^H G and the per-block dR, dc partials on the tensor cores
+      FNO_TRY(launch_ok(f, launch_mix_tc(true, reinterpret_cast<const float2*>(f->GWh), ks, vstride, ld,
+                                         at<T>(f->wcopy, f->off_R[l]), static_cast<T*>(f->GVh), 1.f, B, f->m,
+                                         f->Kp, f->d_err, f->timeout_ns, st),
+                        "mode mixing backward (data)", CAT_MIX, 8.0 * f->m * f->m * C * C * B));
+      FNO_TRY(launch_ok(f, launch_mix_dr_tc(reinterpret_cast<const float2*>(f->GWh),
+                                            reinterpret_cast<const float2*>(f->Vh[l]), ks, vstride, ld,
+                                            f->part_mix[l], B, f->m, f->N, f->d_err, f->timeout_ns, st),
+                        "mode mixing backward (weights)", CAT_MIX, 8.0 * f->m * f->m * C * C * B));
+    } else {
+      FNO_TRY(launch_ok(f, launch_mix_bwd<T>(reinterpret_cast<const float2*>(f->GWh),
+                                             reinterpret_cast<const float2*>(f->Vh[l]), ks, vstride, ld,
+                                             at<T>(f->wcopy, f->off_R[l]), static_cast<T*>(f->GVh), f->part_mix[l],
+                                             B, f->m, f->Kp, f->N, true, st),
+                        "mode mixing backward", CAT_MIX, 16.0 * f->m * f->m * C * C * B));
+    }
     reduce_into(segs, f->part_mix[l], sb, (int)mix_w, mix_w + C, f->grad + f->off_R[l]);
     reduce_into(segs, f->part_mix[l] + mix_w, sb, C, mix_w + C, f->grad + f->off_c[l]);
     // dV_l = Re IDFT(GVh) + W^T dZ, times GELU'(Z_{l-1})

@@ -281,7 +281,19 @@ cudaError_t launch_mix_fwd(const float2* Vh, int splits, long long split_stride,
                            float scale, int B, int m, int Kp, cudaStream_t st);
 template <typename T>
 cudaError_t launch_mix_bwd(const float2* G, const float2* Vh, int splits, long long split_stride, long long ld,
-                           const T* R, T* GVh, float* part, int B, int m, int Kp, int N, cudaStream_t st);
+                           const T* R, T* GVh, float* part, int B, int m, int Kp, int N, bool with_gvh,
+                           cudaStream_t st);
+// Tensor-core mixing (BF16 mode, fno_mix_tc.cu): conj = false is the forward product (out = Wh,
+// scale 1/N^2), conj = true the backward-data product (out = GVh, scale 1).
+cudaError_t launch_mix_tc(bool conj, const float2* X, int splits, long long split_stride, long long ld,
+                          const __nv_bfloat16* R, __nv_bfloat16* out, float scale, int B, int m, int Kp, int* err,
+                          uint64_t timeout_ns, cudaStream_t st);
+// Tensor-core weight gradient of the mixing (BF16 mode): per block of 128 samples the partial
+// dR[k][o][i] = sum_b G conj(Vh) and, in the DC mode's block, the bias partial (layout of mix_bwd's
+// partial rows); mix_dr_blocks(B) rows.
+cudaError_t launch_mix_dr_tc(const float2* G, const float2* V, int splits, long long split_stride, long long ld,
+                             float* part, int B, int m, int N, int* err, uint64_t timeout_ns, cudaStream_t st);
+int mix_dr_blocks(int B);
 int mix_sample_blocks(int B);
 template <typename T>
 cudaError_t launch_transpose_w(const T* wcopy, long long off_W0, long long layer_stride, T* WT, int L,

@@ -329,12 +329,14 @@ __device__ __forceinline__ void ld4s(const float2* row, int g, float2 (&v)[4]) {
 // One CTA per (kept mode, block of 32 samples), 128 threads: threads 0-63 own GVh tiles (samples
 // 4 sg .., channels 4 ig ..), threads 64-127 dR tiles (outputs 4 og .., channels 4 ig ..). G is
 // staged both as [s][o] and as [o][s], so each product reads its rows contiguously; the rows read
-// by eight different groups per warp use the split layout.
+// by eight different groups per warp use the split layout. with_gvh = 0 leaves GVh to the
+// tensor-core mixing (BF16 mode): only the dR and dc parts run.
 template <typename T>
 __global__ void __launch_bounds__(128) mix_bwd_kernel(const float2* __restrict__ G, const float2* __restrict__ Vh,
                                                       int splits, long long split_stride, long long ld,
                                                       const T* __restrict__ R, T* __restrict__ GVh,
-                                                      float* __restrict__ part, int B, int m, int Kp, int N) {
+                                                      float* __restrict__ part, int B, int m, int Kp, int N,
+                                                      int with_gvh) {
   extern __shared__ __align__(16) float2 mix_smem[];
   float2* Rs = mix_smem;                 // [o][i], split rows
   float2* Gs = mix_smem + MIX_TILE;      // [s][o], split rows
@@ -352,7 +354,7 @@ __global__ void __launch_bounds__(128) mix_bwd_kernel(const float2* __restrict__
     const size_t off = (size_t)k * ld + (size_t)b * C + col;
     const float2 g = b < B ? ld_spec(G, off, splits, split_stride) : make_float2(0.f, 0.f);
     Gs[row * MIX_LD + sc] = g;
-    Gt[col * MIX_LD + row] = g;
+    if (with_gvh) Gt[col * MIX_LD + row] = g;
     Vs[row * MIX_LD + sc] = b < B ? ld_spec(Vh, off, splits, split_stride) : make_float2(0.f, 0.f);
   }
   __syncthreads();
@@ -361,7 +363,7 @@ __global__ void __launch_bounds__(128) mix_bwd_kernel(const float2* __restrict__
   for (int a = 0; a < 4; ++a)
 #pragma unroll
     for (int c = 0; c < 4; ++c) re[a][c] = im[a][c] = 0.f;
-  if (t < 64) {
+  if (t < 64 && with_gvh) {
     // GVh tile: samples 4 sg + a, channels 4 ig + c; conj(r) g over the outputs o
     const int sg = t >> 3, ig = t & 7;
 #pragma unroll 4
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(128) mix_bwd_kernel(const float2* __restrict__
       for (int c = 0; c < 4; ++c)
         st_pair(GVh, (((size_t)b * C + 4 * ig + c) * Kp) / 2 + k, make_float2(re[a][c], im[a][c]));
     }
-  } else {
+  } else if (t >= 64) {
     // dR tile: outputs 4 og + a, channels 4 ig + c; g conj(v) over the block's samples
     const int og = (t - 64) >> 3, ig = t & 7;
 #pragma unroll 4
@@ -847,13 +849,15 @@ int mix_sample_blocks(int B) { return (B + MIX_SAMPLES - 1) / MIX_SAMPLES; }
 
 template <typename T>
 cudaError_t launch_mix_bwd(const float2* G, const float2* Vh, int splits, long long split_stride, long long ld,
-                           const T* R, T* GVh, float* part, int B, int m, int Kp, int N, cudaStream_t st) {
+                           const T* R, T* GVh, float* part, int B, int m, int Kp, int N, bool with_gvh,
+                           cudaStream_t st) {
   const size_t smem = (size_t)4 * MIX_TILE * sizeof(float2);
   const void* fn = reinterpret_cast<const void*>(mix_bwd_kernel<T>);
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const dim3 grid(m * m, mix_sample_blocks(B));
-  mix_bwd_kernel<T><<<grid, 128, smem, st>>>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N);
+  mix_bwd_kernel<T><<<grid, 128, smem, st>>>(G, Vh, splits, split_stride, ld, R, GVh, part, B, m, Kp, N,
+                                              with_gvh ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1039,7 +1043,7 @@ cudaError_t launch_head_infer(const float* part_pool, const T* params_e, float q
   template cudaError_t launch_mix_fwd<T>(const float2*, int, long long, long long, const T*, T*, float, int, int, \
                                          int, cudaStream_t);                                                        \
   template cudaError_t launch_mix_bwd<T>(const float2*, const float2*, int, long long, long long, const T*, T*,   \
-                                         float*, int, int, int, int, cudaStream_t);                                 \
+                                         float*, int, int, int, int, bool, cudaStream_t);                           \
   template cudaError_t launch_transpose_w<T>(const T*, long long, long long, T*, int, cudaStream_t);              \
   template cudaError_t launch_project_train<T>(const T*, const float2*, const T*, const float*, T*, T*, float*,   \
                                                float*, float*, int, int, cudaStream_t);                            \

@@ -77,8 +77,7 @@ static void free_item(Plan* p) {
   void* ptrs[] = {p->d_units,   p->d_zplanes, p->d_zbounds, p->d_nsplit,   p->d_nsplit1, p->d_ext_planes, p->d_pupil,
                   p->d_sz_top,  p->d_sz_bot,  p->d_twx,     p->d_twy,      p->Whi,       p->Wlo,
                   p->Wh,        p->Wt,        p->Bhi,       p->Blo,        p->Cf,        p->S_part,
-                  p->T,         p->hio_W,     p->hio_gamma, p->hio_alpha,  p->hio_p,     p->hio_out,
-                  p->d_xcount};
+                  p->T,         p->hio_W,     p->hio_gamma, p->hio_alpha,  p->hio_p,     p->hio_out};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (p->ev0) cudaEventDestroy(p->ev0);
@@ -328,14 +327,6 @@ static scw_status finish_item(Plan* p) {
   }
   SCW_TRY(upload(&p->d_nsplit, nsplit, tot));
   const int n_tiles = (3 * p->M + p->rows_tile - 1) / p->rows_tile;
-  if (p->d_xcount) {
-    cudaFree(p->d_xcount);
-    p->d_xcount = nullptr;
-  }
-  if (p->fuse_x && !p->units.empty()) {
-    SCW_TRY(dalloc(&p->d_xcount, p->units.size() * n_tiles, tot));
-    SCW_TRY(cudaMemsetAsync(p->d_xcount, 0, p->units.size() * n_tiles * sizeof(int), t_setup));
-  }
   SCW_TRY(dalloc(&p->S_part, (size_t)p->k_split * p->Fz * 3 * M, tot));
   SCW_TRY(cudaMemsetAsync(p->S_part, 0, (size_t)p->k_split * p->Fz * 3 * M * sizeof(float2), t_setup));
   ItemDev& it = p->item;
@@ -362,8 +353,6 @@ static scw_status finish_item(Plan* p) {
   it.k_split = p->k_split;
   it.n_tiles = n_tiles;
   it.rows_tile = p->rows_tile;
-  it.fuse_x = p->fuse_x ? 1 : 0;
-  it.xcount = p->d_xcount;
   if (p->flags & SCW_FLAG_DEBUG_BOUNDS) {
     const unsigned long long nk = (8 * M + 63) / 64, Fz = p->Fz, L = p->L, nu = p->units.size();
     unsigned long long* b = p->bnd_real;
@@ -605,7 +594,6 @@ struct scw_plan_s {
   float2** d_outs = nullptr;
   float2** h_outs = nullptr;       // pinned
   int max_M = 0, max_Qx = 0, max_V = 0, max_Vp = 0;
-  bool fuse_x = false;  // the contraction writes the x-pass rows itself (ItemDev::fuse_x)
   size_t xpass_smem = 0;
   size_t rec_smem = 0;
   // graph replay
@@ -781,15 +769,13 @@ static scw_status enqueue_pipelined(scw_plan_t P, float2* out_one, cudaStream_t 
     const int nb = P->gplane[g + 1] - P->gplane[g];
     if (nb == 0) continue;
     const int2* ent = P->d_plane_entries + P->gplane[g];
-    if (!P->fuse_x) {  // fused: the contraction wrote this group's x-pass rows
-      e = launch_xpass(one, nullptr, ent, nb, P->xpass_smem, P->st2);
-      if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
-    }
+    e = launch_xpass(one, nullptr, ent, nb, P->xpass_smem, P->st2);
+    if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
     int ny = 0;
     e = launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, P->max_twy, P->tiled, out_one, nullptr,
                      P->st2, &ny);
     if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
-    n += (P->fuse_x ? 0 : 1) + ny;
+    n += 1 + ny;
   }
   e = cudaEventRecord(P->ev_join, P->st2);
   if (e != cudaSuccess) return cuda_error(e, "cudaEventRecord");
@@ -806,19 +792,15 @@ static scw_status enqueue_synthesis(scw_plan_t P, float2* out_one, cudaStream_t 
   const ItemDev& one = P->items[0]->item;
   const ItemDev* items = P->batched ? P->d_items : nullptr;
   mark(P, 2, st, marks);
-  cudaError_t e = cudaSuccess;
-  if (!P->fuse_x) {  // fused: the contraction's last K split of each row tile wrote the x-pass rows
-    e = launch_xpass(one, items, P->d_plane_entries, P->n_plane_entries, P->xpass_smem, st);
-    if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
-    ++n;
-  }
+  cudaError_t e = launch_xpass(one, items, P->d_plane_entries, P->n_plane_entries, P->xpass_smem, st);
+  if (e != cudaSuccess) return cuda_error(e, "x-pass launch");
   mark(P, 3, st, marks);
   int ny = 0;
   e = launch_ypass(one, items, P->d_plane_entries, P->n_plane_entries, P->n_pair_entries, P->max_Qx, P->max_Vp, P->max_twy, P->tiled,
                    out_one, P->d_outs, st, &ny);
   if (e != cudaSuccess) return cuda_error(e, "y-pass launch");
   mark(P, 4, st, marks);
-  n += ny;
+  n += 1 + ny;
   if (marks && P->timing && P->tev_used + kMarks <= P->tev.size()) P->tev_used += kMarks;
   return SCW_OK;
 }
@@ -1024,18 +1006,6 @@ static scw_status finish_plan(scw_plan_t P, const std::vector<int>& user_ks, boo
     P->tiled = P->tiled || p->tiles_x > 1 || p->tiles_y > 1;
     P->max_twy = std::max(P->max_twy, (p->Fy / 8) * p->item.Vp);
   }
-  // The x-direction recomposition runs inside the tensor-core contraction when every item's order
-  // rows fit whole into a row tile of W (U rows each, U padded to <= 64 positions) and no plane
-  // lies outside the sample (exterior spectra come from their own kernel and take the x-pass).
-  // The fused work of a row tile grows with the unit's plane slots: with more than 16 the separate
-  // x-pass (the whole GPU at once) is faster than the last arrivals' epilogue warps.
-  bool fuse = P->tc && P->F_pad <= 16;
-  for (auto* p : P->items) fuse = fuse && p->n_exterior == 0 && fold_np(p->U) <= 64;
-  P->fuse_x = fuse;
-  for (auto* p : P->items) {
-    p->fuse_x = fuse;
-    p->rows_tile = fuse ? p->U * (128 / p->U) : 128;
-  }
   // plane entries of items with long y folds first: they run the two-residue y-pass
   std::stable_partition(pe.begin(), pe.end(),
                         [&](const int2& en) { return ypass_pairs(P->items[en.x]->item.Vp); });
@@ -1186,7 +1156,7 @@ static scw_status synthesize_host_pipelined(scw_plan_t P, const void* W, const v
     const int fb = P->hplane[g], nb = P->hplane[g + 1] - fb;
     if (nb > 0) {
       const int2* ent = P->d_plane_entries + fb;
-      if (!P->fuse_x) SCW_TRY_E(launch_xpass(one, nullptr, ent, nb, P->xpass_smem, st), "x-pass launch");
+      SCW_TRY_E(launch_xpass(one, nullptr, ent, nb, P->xpass_smem, st), "x-pass launch");
       int ny = 0;
       SCW_TRY_E(launch_ypass(one, nullptr, ent, nb, ypass_pairs(one.Vp) ? nb : 0, P->max_Qx, P->max_Vp, P->max_twy,
                              P->tiled, p->hio_out, nullptr, st, &ny), "y-pass launch");
@@ -1551,9 +1521,6 @@ scw_status scw_plan_check(scw_plan_t P, void* stream) {
   if (e != cudaSuccess) return cuda_error(e, "reading the device error word");
   if (word) {
     cudaMemset(P->d_err, 0, sizeof(int));
-    // a stopped contraction can leave K-split arrivals counted: start the next call from zero
-    for (auto* p : P->items)
-      if (p->d_xcount) cudaMemset(p->d_xcount, 0, p->units.size() * (size_t)p->item.n_tiles * sizeof(int));
     if (word == DEV_ERR_BOUNDS)
       return set_error(SCW_ERR_BOUNDS, "a kernel formed an index outside its buffer (SCW_FLAG_DEBUG_BOUNDS; the "
                                        "access was skipped, so this call's results are invalid)");

@@ -22,19 +22,6 @@
 //                   accumulator, coalesced stores of S_part[split][plane][row]
 // so loads, MMAs and the previous task's epilogue overlap. Every wait is bounded
 // by a %globaltimer deadline; a timeout sets the error word and all roles stop.
-//
-// Fused x-direction recomposition (ItemDev::fuse_x): row tiles then hold whole
-// order rows (rows_tile = U floor(128 / U) rows, i.e. complete rows of U orders
-// u for fixed (component, v)). The epilogue warps of the K split that finishes a
-// (unit, row tile) last -- an arrival counter per (unit, tile) says which --
-// add the tile's K-split partials and run the x-direction fold and radix-8
-// inverse DFT of Eq. 10 on its order rows for every plane of the unit, writing
-// the x-pass rows T[plane][c][v][x] that the y-pass reads; no separate x-pass
-// kernel runs. The arrival protocol: every epilogue thread fences its partial
-// stores, the four warps meet at a named barrier, one thread increments the
-// counter; the last arrival fences again before the partials are read through
-// L2 (ld.global.cg) and puts the counter back to 0 for the next call.
-#include "scw_fold.cuh"
 #include "scw_internal.cuh"
 #include "scw_ptx.cuh"
 
@@ -57,7 +44,7 @@ struct TcCfg {
 };
 
 struct TaskGeom {
-  int kb, kcount, layer, unit, tile, split, f0, nf, rt, ks;
+  int kb, kcount, layer, unit, tile, split, f0, nf, rt;
 };
 
 __device__ __forceinline__ TaskGeom task_geom(const int4 tk, const ItemDev& it) {
@@ -65,7 +52,6 @@ __device__ __forceinline__ TaskGeom task_geom(const int4 tk, const ItemDev& it) 
   const LayerUnit u = it.units[tk.y];
   const int ks = u.ks > 0 ? u.ks : it.k_split;
   const int per = (it.nk + ks - 1) / ks;
-  g.ks = ks;
   g.kb = tk.w * per;
   g.kcount = max(0, min(it.nk, g.kb + per) - g.kb);
   g.layer = u.layer;
@@ -76,59 +62,6 @@ __device__ __forceinline__ TaskGeom task_geom(const int4 tk, const ItemDev& it) 
   g.nf = u.nf;
   g.rt = min(it.rows_tile, 3 * it.M - it.rows_tile * tk.z);  // rows of this tile that exist
   return g;
-}
-
-// The fused x-pass of one completed (unit, row tile): for each plane f of the unit and each
-// order row (c, v) of the tile, s_p = sum over the K splits of S_part at the fold positions p
-// (order u at position u mod Up, zero padding), then for every residue b < Fx/8
-//   G[r] = sum_{p = r mod 8} s_p twx[p][b],   T[f][c][v][b + a Fx/8] = sum_r G[r] e^(2 pi i r a / 8).
-// One warp per (plane, row); lane l holds positions l and l + 32 (Up <= 64) and takes the
-// residues b = l, l + 32, ...; the positions reach the other lanes by shuffles.
-__device__ __forceinline__ void fused_xpass(const ItemDev& it, const TaskGeom& g, int ew, int lane) {
-  const int U = it.U, V = it.V, Up = it.Up, Fx = it.Fx, Q = Fx >> 3;
-  const int vrows = it.rows_tile / U;
-  const int gv0 = g.tile * vrows;
-  const int nv = min(vrows, 3 * V - gv0);
-  const int u0 = lane < Up ? fold_order(lane, U, Up) : -1;
-  const int u1 = lane + 32 < Up ? fold_order(lane + 32, U, Up) : -1;
-  for (int item = ew; item < g.nf * nv; item += 4) {
-    const int f = g.f0 + item / nv, gv = gv0 + item % nv;
-    const int c = gv / V, v = gv - c * V;
-    const size_t sbase = (size_t)f * 3 * it.M + (size_t)gv * U;
-    const float2* src = it.S_part + sbase;
-    float2 s0 = make_float2(0.f, 0.f), s1 = make_float2(0.f, 0.f);
-    for (int k = 0; k < g.ks; ++k) {
-      const size_t ko = (size_t)k * it.split_stride;
-      if (u0 >= 0 && in_bounds(it, BND_S_PART, sbase + ko + u0)) s0 = c_add(s0, __ldcg(src + ko + u0));
-      if (u1 >= 0 && in_bounds(it, BND_S_PART, sbase + ko + u1)) s1 = c_add(s1, __ldcg(src + ko + u1));
-    }
-    const size_t tbase = (((size_t)f * 3 + c) * V + v) * Fx;
-    float2* dst = it.T + tbase;
-    for (int b0 = 0; b0 < Q; b0 += 32) {
-      const int b = b0 + lane;
-      // the residue's largest indices: its last output (a = 7) and its last twiddle
-      const bool on = b < Q && in_bounds(it, BND_T, tbase + b + 7 * (size_t)Q) &&
-                      in_bounds(it, BND_TWX, (size_t)(Up - 1) * Q + b);
-      float2 G[8];
-#pragma unroll
-      for (int r = 0; r < 8; ++r) G[r] = make_float2(0.f, 0.f);
-      for (int p0 = 0; p0 < Up; p0 += 8) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          const int p = p0 + r;
-          const float2 sv = p < 32 ? make_float2(__shfl_sync(0xffffffffu, s0.x, p), __shfl_sync(0xffffffffu, s0.y, p))
-                                   : make_float2(__shfl_sync(0xffffffffu, s1.x, p - 32),
-                                                 __shfl_sync(0xffffffffu, s1.y, p - 32));
-          if (on) c_fma(G[r], sv, __ldg(it.twx + (size_t)p * Q + b));
-        }
-      }
-      if (on) {
-        idft8(G);
-#pragma unroll
-        for (int a = 0; a < 8; ++a) dst[b + a * Q] = G[a];
-      }
-    }
-  }
 }
 
 template <int NB, bool SPLIT, bool BATCH>
@@ -148,8 +81,6 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_base_s;
   __shared__ volatile int abort_s;
-  __shared__ volatile int last_s;      // fused x-pass: this CTA's split completed its (unit, row tile)
-  __shared__ volatile int epi_fail_s;  // fused x-pass: an epilogue warp's accumulator wait ran out
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -169,8 +100,6 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
     }
     ptx::mbar_init(ptx::smem_u32(&drain_bar), 1);
     abort_s = 0;
-    last_s = 0;
-    epi_fail_s = 0;
     ptx::fence_mbar_init();
   }
   if (warp == 0) {
@@ -325,24 +254,14 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
     const int grp = warp & 3;  // TMEM lanes 32*grp .. 32*grp+31
     // partial spectra are read back right after this kernel: keep them in L2 while W streams through
     const uint64_t pol_s = ptx::policy_evict_last();
-    // With the fused x-pass the four epilogue warps meet at named barriers, so they must leave the
-    // task loop together: they agree on a timed-out accumulator wait at a barrier every one of them
-    // reaches, and do not stop on the other roles' abort flag (their own bounded wait then fails).
-    const bool fuse = one.fuse_x != 0;
     int lt = 0;
-    for (int t = t_begin; t < t_end && (fuse || !abort_s); ++t, ++lt) {
+    for (int t = t_begin; t < t_end && !abort_s; ++t, ++lt) {
       const int4 tk = tasks[t];
       const ItemDev& it = BATCH ? items[tk.x] : one;
       const TaskGeom g = task_geom(tk, it);
       const int acc = lt & 1;
       const bool ok = ptx::mbar_wait(ptx::smem_u32(&accf_bar[acc]), (uint32_t)(lt >> 1) & 1u, deadline);
-      bool fail = !__all_sync(0xffffffffu, ok);
-      if (fuse) {
-        if (fail && lane == 0) epi_fail_s = 1;
-        ptx::named_bar_sync(1, 128);
-        fail = epi_fail_s != 0;  // the same value in every epilogue warp (written only before this barrier)
-      }
-      if (fail) {
+      if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) atomicOr(err, DEV_ERR_TIMEOUT_ACCUM);
         abort_s = 1;
         break;
@@ -376,22 +295,6 @@ __global__ void __launch_bounds__(192) contract_tc_kernel(const __grid_constant_
       ptx::tc_fence_before();
       __syncwarp();
       if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&acce_bar[acc]));
-      if (fuse) {
-        // the accumulator is released first, so the MMAs of the following tasks are not held up
-        __threadfence();              // this thread's partial rows, before the arrival
-        ptx::named_bar_sync(1, 128);  // the four epilogue warps have stored and fenced
-        if (warp == 2 && lane == 0) {
-          int* cnt = it.xcount + (size_t)g.unit * it.n_tiles + g.tile;
-          const int prior = atomicAdd(cnt, 1);
-          last_s = prior == g.ks - 1;
-          if (prior == g.ks - 1) *cnt = 0;  // every split has arrived: ready for the next call
-        }
-        ptx::named_bar_sync(1, 128);
-        if (last_s) {  // read by every epilogue warp before any of them reaches the next barrier
-          __threadfence();  // the other splits' partials, after their arrivals
-          fused_xpass(it, g, warp - 2, lane);
-        }
-      }
     }
   }
 

@@ -1,5 +1,5 @@
-// Complex helpers and the in-register 8-point inverse DFT shared by the recomposition
-// kernels (step (c)) and the x-direction recomposition fused into the contraction.
+// Complex helpers and the in-register 8-point inverse DFT of the recomposition kernels
+// (step (c)).
 #pragma once
 
 #include <cuda_runtime.h>

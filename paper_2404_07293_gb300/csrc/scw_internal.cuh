@@ -91,10 +91,7 @@ struct ItemDev {
   int tx, ty;              // periodic tiles of the field along x and y
   long long ld, pstride;   // field row pitch and plane-slice stride (complex elements)
   unsigned long long* trace;  // kernel trace stamps [TRACE_SLOTS][2], or null (tracing off)
-  int rows_tile;           // rows of W per contraction row tile (a whole number of order rows U when
-                           // the x-direction recomposition is fused into the contraction, else 128)
-  int fuse_x;              // the contraction's last K split of each (unit, row tile) writes T itself
-  int* xcount;             // [n_units][n_tiles] arrivals of the K splits (fuse_x; each step leaves 0)
+  int rows_tile;           // rows of W per contraction row tile (<= 128)
   int dbg;                 // SCW_FLAG_DEBUG_BOUNDS: kernels check every global index against bnd
   int* err;                // the plan's device error word (DEV_ERR_BOUNDS)
   unsigned long long bnd[BND_COUNT];  // extents in elements of the checked buffers (dbg only)
@@ -131,8 +128,6 @@ struct Plan {
   int NB = 16;        // 2 * F_pad: real columns of the tensor-core B operand
   int k_split = 1;                // the largest K split over the units (S_part holds that many partials)
   int rows_tile = 128;            // rows of W per contraction row tile (ItemDev::rows_tile)
-  bool fuse_x = false;            // x-direction recomposition fused into the contraction
-  int* d_xcount = nullptr;        // [units][tiles] K-split arrival counters (fuse_x)
   unsigned long long bnd_real[BND_COUNT] = {};  // buffer extents (SCW_FLAG_DEBUG_BOUNDS plans)
   std::vector<int> unit_ks;        // per-unit K split (tensor-core plans; empty = k_split everywhere)
   int n_exterior = 0;

@@ -209,12 +209,6 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t smem_addr) {
   return d;
 }
 
-// Named barrier `id` (1..15; 0 is __syncthreads) for `count` threads, a multiple of 32. Every warp
-// that takes part must reach it: it has no time limit.
-__device__ __forceinline__ void named_bar_sync(int id, int count) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
-}
-
 // Instruction descriptor, kind::f16: D format F32 (bits [4,6) = 1), A and B
 // format in bits [7,10) and [10,13) (0 = F16, 1 = BF16), both K-major (bits 15,
 // 16 = 0), N >> 3 in bits [17,23), M >> 4 in bits [24,29).
