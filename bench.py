@@ -589,6 +589,20 @@ def kernel_times(plan, fn, calls=3):
     return {k: kt[k] for k in ("phases_ms", "contract_ms", "xpass_ms", "ypass_ms", "recompose_ms", "total_ms")}
 
 
+def step_timeline(plan, fn, reps=5):
+    """Begin / end of each kernel of one graph-replayed step (us from the step's first kernel),
+    from the plan's %globaltimer trace; the median over `reps` isolated steps."""
+    plan.enable_trace(True)
+    traces = []
+    for _ in range(reps):
+        fn()
+        traces.append(plan.trace())
+    plan.enable_trace(False)
+    fn()  # recapture the untraced graph
+    return {k: [statistics.median(t[k][0] for t in traces), statistics.median(t[k][1] for t in traces)]
+            for k in traces[0]}
+
+
 def oracle_volume(W, g, a, zb, zp, U=None, X=None, Fxy=None):
     """The FP64 oracle's field of every voxel (spectrum per plane, then the direct sum
     of Eq. 10) and the seconds it took on the host cores."""
@@ -824,6 +838,7 @@ def run_ours(args, world, rank, local):
     plan.enable_timing(False)
     plan.check()
     direct_ms = d0.elapsed_time(d1) / args.steps
+    timeline = step_timeline(plan, lambda: plan.synthesize(out))
     value, seconds = replica_throughput(voxels * args.steps, ms * 1e-3, dev)
     ms = seconds * 1e3
     info = plan.info()
@@ -1009,6 +1024,7 @@ def run_ours(args, world, rank, local):
             "timing": "CUDA-graph replay of scw_synthesize (the library's default path); kernel_ms from a "
                       "second pass of direct launches with events between kernels",
             "direct_launch": {"ms_per_step": direct_ms, "value": world * voxels / (direct_ms * 1e-3)},
+            "timeline_us": timeline,
             "plan_convert_ms": plan_ms,
             "gpu_launches": info["kernels_per_synthesis"] * args.steps,
             "clocks": clocks.summary(),
