@@ -1008,7 +1008,8 @@ def run_ours(args, world, rank, local):
             "config": {"workload": workload_name(), "orders": "21x21", "M": M, "layers": L_LAYERS,
                        "grid": [F_XY, F_XY, Fz], "precision": args.precision, "k_split": info["k_split"],
                        "inputs": inputs,
-                       "l2": "inputs larger than L2 (W 597 MB, field 403 MB)",
+                       "l2": (f"inputs larger than L2 (W {L_LAYERS * 3 * M * 4 * M * 8 / 1e6:.0f} MB, field "
+                              f"{3 * voxels * 8 / 1e6:.0f} MB)"),
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
             "step_roofline": {"bytes": whole_bytes, "ms": step_roofline_ms,
