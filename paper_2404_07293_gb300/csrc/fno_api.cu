@@ -56,7 +56,8 @@ struct scw_fno_s {
   uint64_t timeout_ns = 2000000000ull;
 
   CUtensorMap map_Vcf[9], map_dZcf[2], map_D, map_E, map_Wh, map_GVh;
-  CUtensorMap map_Vcl[8], map_dZcl[2], map_W[8], map_WT[8];  // 1x1-convolution operands (64-byte swizzle)
+  // 1x1-convolution operands: channel-first activations read MN-major (3D maps), W and W^T
+  CUtensorMap map_Vx[8], map_dZx[2], map_W[8], map_WT[8];
 
   std::vector<void*> allocs;
   size_t bytes = 0;
@@ -199,8 +200,11 @@ static cudaError_t refresh_wt(scw_fno_s* f, cudaStream_t st) {
 template <typename T>
 static scw_status forward(scw_fno_s* f, const float2* n, int B, bool keep_z, cudaStream_t st) {
   const int BC = B * C;
+  // BF16 mode reads the layer inputs channel-first only; the FP32 (SIMT) mode also reads them
+  // channel-last
   FNO_TRY(launch_ok(f, launch_lift<T>(n, at<T>(f->wcopy, f->off_P), static_cast<T*>(f->Vcf[0]),
-                                      static_cast<T*>(f->Vcl[0]), B, f->S, f->in_grid, f->N, st),
+                                      f->bf16 ? nullptr : static_cast<T*>(f->Vcl[0]), B, f->S, f->in_grid, f->N,
+                                      st),
                     "lift"));
   const long long ld = (long long)f->Bmax * C;                // complex elements per mode
   const long long vstride = ld * (f->Kc / 2);                 // complex elements per split
@@ -238,10 +242,12 @@ static scw_status forward(scw_fno_s* f, const float2* n, int B, bool keep_z, cud
     eb.bias = at<T>(f->wcopy, f->off_c[l]);
     eb.x_cl = f->Vcl[l];
     eb.z_out = (keep_z && l < f->L - 1) ? f->Zcl[l] : nullptr;
-    eb.out_cf = f->Vcf[l + 1];
-    eb.out_cl = f->Vcl[l + 1];
+    // V_L feeds the projection (channel-last) only; the others feed the next layer and the
+    // weight gradients (channel-first)
+    eb.out_cf = l < f->L - 1 ? f->Vcf[l + 1] : nullptr;
+    eb.out_cl = (!f->bf16 || l == f->L - 1) ? f->Vcl[l + 1] : nullptr;
     eb.gelu = l < f->L - 1 ? 1 : 0;
-    e = f->bf16 ? launch_gemm_tc(EPI_LAYER_FWD, 256, f->map_E, f->map_Wh, f->map_Vcl[l], f->map_W[l], eb, f->P, BC,
+    e = f->bf16 ? launch_gemm_tc(EPI_LAYER_FWD, 256, f->map_E, f->map_Wh, f->map_Vx[l], f->map_W[l], eb, f->P, BC,
                                  f->Kp, 1, f->d_err, f->timeout_ns, st)
                 : launch_gemm_simt(EPI_LAYER_FWD, static_cast<const float*>(f->E), f->Kp,
                                    static_cast<const float*>(f->Wh), f->Kp, eb, f->P, BC, f->Kp, 1, st);
@@ -293,8 +299,8 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
   FNO_TRY(launch_ok(f, launch_target_norm(target, f->part_tn, B, P, st), "target norm"));
   FNO_TRY(launch_ok(f, launch_project_train<T>(static_cast<const T*>(f->Vcl[f->L]), target, at<T>(f->wcopy, f->off_Q),
                                                f->part_tn, static_cast<T*>(f->dZcf[0]),
-                                               static_cast<T*>(f->dZcl[0]), f->part_err, f->part_pool, f->part_proj, B,
-                                               P, st),
+                                               f->bf16 ? nullptr : static_cast<T*>(f->dZcl[0]), f->part_err,
+                                               f->part_pool, f->part_proj, B, P, st),
                     "projection"));
   reduce_into(segs, f->part_proj, B * nblk, OUT * C + OUT, OUT * C + OUT, f->grad + f->off_Q);
   FNO_TRY(launch_ok(f, launch_head<T>(f->part_tn, f->part_err, f->part_pool, at<T>(f->wcopy, f->off_e), f->part_head,
@@ -369,9 +375,9 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     eb.w = at<T>(f->wcopy, f->off_W[l]);
     eb.x_cl = f->dZcl[cur];
     eb.z_in = l > 0 ? f->Zcl[l - 1] : nullptr;
-    eb.out_cf = l > 0 ? f->dZcf[1 - cur] : nullptr;  // dV_0 is consumed channel-last only
-    eb.out_cl = f->dZcl[1 - cur];
-    e = f->bf16 ? launch_gemm_tc(EPI_LAYER_BWD, 256, f->map_E, f->map_GVh, f->map_dZcl[cur], f->map_WT[l], eb, P, BC,
+    eb.out_cf = l > 0 ? f->dZcf[1 - cur] : nullptr;  // dV_0 is consumed channel-last only (lift backward)
+    eb.out_cl = (!f->bf16 || l == 0) ? f->dZcl[1 - cur] : nullptr;
+    e = f->bf16 ? launch_gemm_tc(EPI_LAYER_BWD, 256, f->map_E, f->map_GVh, f->map_dZx[cur], f->map_WT[l], eb, P, BC,
                                  f->Kp, 1, f->d_err, f->timeout_ns, st)
                 : launch_gemm_simt(EPI_LAYER_BWD, static_cast<const float*>(f->E), f->Kp,
                                    static_cast<const float*>(f->GVh), f->Kp, eb, P, BC, f->Kp, 1, st);
@@ -566,13 +572,13 @@ scw_status scw_surrogate_create(const scw_fno_desc* d, scw_fno_t* out) {
     for (int l = 0; l <= f->L && s == SCW_OK; ++l) s = make_map_bf16(&f->map_Vcf[l], f->Vcf[l], f->P, BCm, f->P, 128);
     for (int i = 0; i < 2 && s == SCW_OK; ++i) s = make_map_bf16(&f->map_dZcf[i], f->dZcf[i], f->P, BCm, f->P, 128);
     for (int l = 0; l < f->L && s == SCW_OK; ++l) {
-      s = make_map_act3d(&f->map_Vcl[l], f->Vcl[l], f->P, f->Bmax);
+      s = make_map_act3d(&f->map_Vx[l], f->Vcf[l], f->P, f->Bmax);
       if (s == SCW_OK)
         s = make_map_bf16(&f->map_W[l], static_cast<__nv_bfloat16*>(f->wcopy) + f->off_W[l], C, C, C, C, 32);
       if (s == SCW_OK)
         s = make_map_bf16(&f->map_WT[l], static_cast<__nv_bfloat16*>(f->WT) + (size_t)l * C * C, C, C, C, C, 32);
     }
-    for (int i = 0; i < 2 && s == SCW_OK; ++i) s = make_map_act3d(&f->map_dZcl[i], f->dZcl[i], f->P, f->Bmax);
+    for (int i = 0; i < 2 && s == SCW_OK; ++i) s = make_map_act3d(&f->map_dZx[i], f->dZcf[i], f->P, f->Bmax);
     if (s != SCW_OK) {
       free_all(f);
       delete f;

@@ -13,9 +13,12 @@
 //   warps 2-9       epilogue
 // The layer products add the 1x1 convolution as a second K segment: for each
 // sample s of the tile, D[:, 32 s .. 32 s + 32) += X_s W^T (X_s = that sample's
-// channel-last activations of the tile's 128 pixels, K = 32, 64-byte swizzle,
-// N = 32 MMAs into the sample's own accumulator columns); one 3D TMA box brings
-// the X_s of four samples into one operand stage, beside W.
+// activations at the tile's 128 pixels, K = 32 channels, N = 32 MMAs into the
+// sample's own accumulator columns). X_s is read from the channel-first layout
+// [B][C][P] as an MN-major operand (pixels contiguous, 128-byte swizzle): two 3D
+// TMA boxes of {64 pixels, 32 channels, 4 samples} bring the X_s of four samples
+// into one operand stage, beside W, so no channel-last copy of the activations
+// is needed.
 // Every wait is bounded by a %globaltimer deadline; on timeout the CTA sets the
 // error word, lets issued copies and MMAs land, frees its tensor memory and exits.
 //
@@ -54,9 +57,11 @@ struct GemmCfg {
 };
 
 constexpr int kGemmThreads = 320;
-// one operand stage of the 1x1 convolution: kSeg2Samples X_s tiles [128][32] and the W tile [32][32]
-constexpr uint32_t kSeg2XBytes = 128u * 64u;
-constexpr uint32_t kSeg2Bytes = kSeg2Samples * kSeg2XBytes + 32u * 64u;
+// one operand stage of the 1x1 convolution: two pixel halves, each kSeg2Samples x [32 channels][64
+// pixels] (4 KB per sample, 128-byte rows), then the W tile [32][32] (64-byte rows)
+constexpr uint32_t kSeg2SampleBytes = 32u * 128u;
+constexpr uint32_t kSeg2HalfBytes = kSeg2Samples * kSeg2SampleBytes;
+constexpr uint32_t kSeg2Bytes = 2u * kSeg2HalfBytes + 32u * 64u;
 
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kGemmThreads, 2) gemm_tc_kernel(const __grid_constant__ CUtensorMap mA,
@@ -326,11 +331,13 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
           ptx::tma_load_2d(sa, &mA, i * 64, m0, fb);
           ptx::tma_load_2d(sa + A_BYTES, &mB, i * 64, n0, fb);
         } else {
-          // X_s for samples smp0 .. smp0 + kSeg2Samples - 1 (pixels m0 .. m0 + 127), then W
+          // X_s for samples smp0 .. smp0 + kSeg2Samples - 1 (pixels m0 .. m0 + 63, then
+          // m0 + 64 .. m0 + 127; the pixel count is a multiple of 128), then W
           const int smp0 = n0 / C + kSeg2Samples * (i - nkb);
           ptx::mbar_arrive_expect_tx(fb, kSeg2Bytes);
-          ptx::tma_load_3d(sa, &mA2, 0, m0, smp0, fb);
-          ptx::tma_load_2d(sa + kSeg2Samples * kSeg2XBytes, &mW, 0, 0, fb);
+          ptx::tma_load_3d(sa, &mA2, m0, 0, smp0, fb);
+          ptx::tma_load_3d(sa + kSeg2HalfBytes, &mA2, m0 + 64, 0, smp0, fb);
+          ptx::tma_load_2d(sa + 2u * kSeg2HalfBytes, &mW, 0, 0, fb);
         }
         ++issued;
         if (++st == STAGES) {
@@ -352,7 +359,7 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
   } else if (warp == 1 && lane == 0) {
     // ---------------- tcgen05.mma issuer ----------------
     constexpr uint32_t idesc = ptx::idesc_f16(true, 128, BN);
-    constexpr uint32_t idesc32 = ptx::idesc_f16(true, 128, 32);
+    constexpr uint32_t idesc32 = ptx::idesc_f16(true, 128, 32, true);  // A (activations) MN-major
     int st = 0, lt = 0;
     uint32_t ph = 0;
     for (int t = blockIdx.x; t < n_tasks && !abort_s; t += gridDim.x, ++lt) {
@@ -384,15 +391,14 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
           }
         } else {
           const int s0 = kSeg2Samples * (i - nkb);
-          const uint64_t db = ptx::sw64_desc(sa + kSeg2Samples * kSeg2XBytes);
+          const uint64_t db = ptx::sw64_desc(sa + 2u * kSeg2HalfBytes);
           for (int j = 0; j < kSeg2Samples && s0 + j < nseg; ++j) {
-            const uint64_t da = ptx::sw64_desc(sa + (uint32_t)j * kSeg2XBytes);
+            // the two 64-pixel halves of sample j are kSeg2HalfBytes apart; K = 16 channels = 2048 bytes
+            const uint64_t da = ptx::sw128_mn_desc(sa + (uint32_t)j * kSeg2SampleBytes, kSeg2HalfBytes);
             const uint32_t d = d_tmem + (uint32_t)(C * (s0 + j));
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-              const uint64_t o = (uint64_t)(2 * kk);
-              ptx::mma_f16(d, da + o, db + o, idesc32, 1u);
-            }
+            for (int kk = 0; kk < 2; ++kk)
+              ptx::mma_f16(d, da + (uint64_t)(kk * (2048 >> 4)), db + (uint64_t)(2 * kk), idesc32, 1u);
           }
         }
         ptx::mma_commit(ptx::smem_u32(&empty_bar[st]));
@@ -663,14 +669,14 @@ scw_status make_map_bf16(CUtensorMap* m, const void* base, long long cols, long 
 scw_status make_map_act3d(CUtensorMap* m, const void* base, long long P, long long samples) {
   auto fn = encode_fn();
   if (!fn) return set_error(SCW_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  if ((reinterpret_cast<uintptr_t>(base) & 15u) || P < 1 || samples < 1)
+  if ((reinterpret_cast<uintptr_t>(base) & 15u) || P < 128 || P % 128 != 0 || samples < 1)
     return set_error(SCW_ERR_INVALID_ARGUMENT, "tensor map: base or extent out of range");
-  cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)P, (cuuint64_t)samples};
-  cuuint64_t strides[2] = {(cuuint64_t)(C * 2), (cuuint64_t)(P * C * 2)};
-  cuuint32_t box[3] = {(cuuint32_t)C, 128u, (cuuint32_t)kSeg2Samples};
+  cuuint64_t dims[3] = {(cuuint64_t)P, (cuuint64_t)C, (cuuint64_t)samples};
+  cuuint64_t strides[2] = {(cuuint64_t)(P * 2), (cuuint64_t)(P * C * 2)};
+  cuuint32_t box[3] = {64u, (cuuint32_t)C, (cuuint32_t)kSeg2Samples};
   cuuint32_t estr[3] = {1u, 1u, 1u};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(SCW_ERR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
   return SCW_OK;

@@ -41,11 +41,12 @@ struct EpiArgs {
   int splits;          // EPI_DW: K splits per group
   const void* w;       // EPI_LAYER_*: W [C][C] (row = output channel), element type T
   const void* bias;    // EPI_LAYER_FWD: c [C] (T), may be null
-  const void* x_cl;    // FWD: V_l channel-last [B][P][C]; BWD: dZ_l channel-last
+  const void* x_cl;    // SIMT form: FWD V_l channel-last [B][P][C]; BWD dZ_l channel-last
   const void* z_in;    // BWD: Z_{l-1} channel-last (GELU'), null for l = 0
   void* z_out;         // FWD: Z_l channel-last, null when not needed
-  void* out_cf;        // FWD: V_{l+1} [B][C][P]; BWD: dZ_{l-1} [B][C][P], null for l = 0
-  void* out_cl;        // FWD: V_{l+1} [B][P][C]; BWD: dZ_{l-1} (or dV_0 for l = 0) [B][P][C]
+  void* out_cf;        // FWD: V_{l+1} [B][C][P]; BWD: dZ_{l-1} [B][C][P]; null where not read
+  void* out_cl;        // FWD: V_{l+1} [B][P][C]; BWD: dZ_{l-1} (or dV_0 for l = 0) [B][P][C]; null
+                       // where not read
   int gelu;            // FWD: apply GELU
   int fz_out;          // FIELD: output planes per illumination
   int illum;           // FIELD: illuminations I
@@ -195,10 +196,12 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
 #pragma unroll
       for (int o = 0; o < C; ++o) z[o] = gelu_f(z[o]);
     }
-    st32(static_cast<T*>(a.out_cl) + cl, z);
-    T* cf = static_cast<T*>(a.out_cf) + (size_t)b * C * a.P + p;
+    if (a.out_cl) st32(static_cast<T*>(a.out_cl) + cl, z);
+    if (a.out_cf) {
+      T* cf = static_cast<T*>(a.out_cf) + (size_t)b * C * a.P + p;
 #pragma unroll
-    for (int o = 0; o < C; ++o) cf[(size_t)o * a.P] = from_f<T>(z[o]);
+      for (int o = 0; o < C; ++o) cf[(size_t)o * a.P] = from_f<T>(z[o]);
+    }
   } else if constexpr (EPI == EPI_LAYER_BWD) {
     const int p = row, b = col0 / C;
     if (p >= a.P || b >= a.B) return;
@@ -246,10 +249,11 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
 // a 64-element inner box): A rows in boxes of 128, B rows in boxes of BN (32..256).
 // grid = (ceil(M/128), ceil(N/BN), splits); EPI_DW uses grid.x = groups and the same row
 // offset for A and B. Each split covers kper 64-wide K blocks.
-// EPI_LAYER_*: mA2 / mW are the 1x1-convolution operands (channel-last activations [B][P][C]
-// as a 3D map with box {32, 128, kSeg2Samples}, and W or W^T [C][C] with box {32, 32}; 64-byte
-// swizzle); they run on the tensor cores as one extra K = 32 segment per sample of the tile,
-// into that sample's 32 columns, kSeg2Samples samples per operand stage.
+// EPI_LAYER_*: mA2 / mW are the 1x1-convolution operands (channel-first activations [B][C][P]
+// as a 3D map with box {64, 32, kSeg2Samples} and 128-byte swizzle, read MN-major; W or W^T
+// [C][C] with box {32, 32} and 64-byte swizzle); they run on the tensor cores as one extra
+// K = 32 segment per sample of the tile, into that sample's 32 columns, kSeg2Samples samples
+// per operand stage.
 cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
                            const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int splits, int* err,
                            uint64_t timeout_ns, cudaStream_t st);
@@ -266,8 +270,9 @@ scw_status make_map_bf16(CUtensorMap* m, const void* base, long long cols, long 
                          int box_rows, int box_cols = 64);
 // 1x1-convolution samples per operand stage of the layer products
 constexpr int kSeg2Samples = 4;
-// encode the 3D bf16 tensor map of channel-last activations [samples][P][C]: box
-// {C, 128 pixels, kSeg2Samples samples}, 64-byte swizzle, out-of-bounds elements read as zero
+// encode the 3D bf16 tensor map of channel-first activations [samples][C][P] (P a multiple of
+// 128) for the 1x1 convolution: box {64 pixels, C, kSeg2Samples samples}, 128-byte swizzle,
+// out-of-bounds samples read as zero
 scw_status make_map_act3d(CUtensorMap* m, const void* base, long long P, long long samples);
 
 template <typename T>

@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(256, 3) lift_kernel(const float2* __restrict__
     }
     for (int dy = 0; dy < r; ++dy) {
       const int row = (yi * r + dy) * N + xi * r;
-      for (int dx = 0; dx < r; ++dx) st8(Vcl + ((size_t)b * P + row + dx) * C + 8 * q, o);
+      if (Vcl != nullptr)  // the channel-last copy only where a consumer reads it (FP32 mode)
+        for (int dx = 0; dx < r; ++dx) st8(Vcl + ((size_t)b * P + row + dx) * C + 8 * q, o);
       T* cf = Vcf + ((size_t)b * C + 8 * q) * P + row;
       if ((r & 1) == 0) {
         for (int dx = 0; dx < r; dx += 2) {
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(256, 2) project_train_kernel(const T* __restri
     v[4 * i + 2] = acc.z;
     v[4 * i + 3] = acc.w;
   }
-  st32(dZcl + ((size_t)b * P + p) * C, v);
+  if (dZcl != nullptr) st32(dZcl + ((size_t)b * P + p) * C, v);  // read channel-last in FP32 mode only
   T* cf = dZcf + (size_t)b * C * P + p;
 #pragma unroll
   for (int o = 0; o < C; ++o) cf[(size_t)o * P] = from_f<T>(v[o]);

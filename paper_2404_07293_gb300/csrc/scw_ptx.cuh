@@ -209,12 +209,29 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t smem_addr) {
   return d;
 }
 
+// Descriptor for an MN-major operand (M or N contiguous) written by TMA with 128-byte
+// swizzling from a box of [K rows][64 16-bit elements]: each K row is 128 bytes of 64
+// consecutive M (or N) elements, 8 K rows make one 1024-byte swizzle atom. The stride
+// between the atoms of consecutive 64-element M blocks goes in the leading-dimension
+// field, the stride between consecutive groups of 8 K rows (1024 bytes here) in the
+// stride-dimension field. A K = 16 step advances the start address by 16 rows (2048 bytes).
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t smem_addr, uint32_t mn_block_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((smem_addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((mn_block_bytes >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1u << 46;
+  d |= (uint64_t)2u << 61;
+  return d;
+}
+
 // Instruction descriptor, kind::f16: D format F32 (bits [4,6) = 1), A and B
-// format in bits [7,10) and [10,13) (0 = F16, 1 = BF16), both K-major (bits 15,
-// 16 = 0), N >> 3 in bits [17,23), M >> 4 in bits [24,29).
-__host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int M, int N) {
-  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// format in bits [7,10) and [10,13) (0 = F16, 1 = BF16), A and B K-major unless
+// bit 15 (A) or bit 16 (B) marks them MN-major, N >> 3 in bits [17,23), M >> 4 in
+// bits [24,29).
+__host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int M, int N, bool a_mn_major = false) {
+  return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) | ((a_mn_major ? 1u : 0u) << 15) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 }  // namespace ptx
