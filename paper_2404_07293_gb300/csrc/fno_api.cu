@@ -35,7 +35,7 @@ struct scw_fno_s {
   void* E = nullptr;        // [P][Kp]
   void* Vcf[9] = {};        // [Bmax][C][P]
   void* Vcl[9] = {};        // [Bmax][P][C]
-  void* Zcl[8] = {};        // [Bmax][P][C]
+  void* Gcl[8] = {};        // GELU'(Z_l) [Bmax][P][C], stored by the training forward
   float* Vh[8] = {};        // complex [kMaxSplit][Kc/2][Bmax C] (mode-major)
   float* GWh = nullptr;     // same shape as one Vh
   void* WT = nullptr;       // [L][C][C]: W_l transposed (tensor-core operand of the backward 1x1)
@@ -241,7 +241,7 @@ static scw_status forward(scw_fno_s* f, const float2* n, int B, bool keep_z, cud
     eb.w = at<T>(f->wcopy, f->off_W[l]);
     eb.bias = at<T>(f->wcopy, f->off_c[l]);
     eb.x_cl = f->Vcl[l];
-    eb.z_out = (keep_z && l < f->L - 1) ? f->Zcl[l] : nullptr;
+    eb.g_out = (keep_z && l < f->L - 1) ? f->Gcl[l] : nullptr;
     // V_L feeds the projection (channel-last) only; the others feed the next layer and the
     // weight gradients (channel-first)
     eb.out_cf = l < f->L - 1 ? f->Vcf[l + 1] : nullptr;
@@ -374,7 +374,7 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     eb.B = B;
     eb.w = at<T>(f->wcopy, f->off_W[l]);
     eb.x_cl = f->dZcl[cur];
-    eb.z_in = l > 0 ? f->Zcl[l - 1] : nullptr;
+    eb.g_in = l > 0 ? f->Gcl[l - 1] : nullptr;
     eb.out_cf = l > 0 ? f->dZcf[1 - cur] : nullptr;  // dV_0 is consumed channel-last only (lift backward)
     eb.out_cl = (!f->bf16 || l == 0) ? f->dZcl[1 - cur] : nullptr;
     e = f->bf16 ? launch_gemm_tc(EPI_LAYER_BWD, 256, f->map_E, f->map_GVh, f->map_dZx[cur], f->map_WT[l], eb, P, BC,
@@ -495,7 +495,7 @@ scw_status scw_surrogate_create(const scw_fno_desc* d, scw_fno_t* out) {
     A(&f->Vcf[l], act);
     A(&f->Vcl[l], act);
   }
-  for (int l = 0; l + 1 < f->L; ++l) A(&f->Zcl[l], act);
+  for (int l = 0; l + 1 < f->L; ++l) A(&f->Gcl[l], act);
   for (int l = 0; l < f->L; ++l) A((void**)&f->Vh[l], (size_t)kMaxSplit * Bm * C * f->Kc * 4);
   A((void**)&f->GWh, (size_t)kMaxSplit * Bm * C * f->Kc * 4);
   A(&f->Wh, Bm * C * f->Kp * esz);

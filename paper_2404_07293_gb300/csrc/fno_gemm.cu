@@ -241,6 +241,51 @@ constexpr uint32_t kLayerSmem = kLayerStages * kLayerStage + 1024u;
 constexpr int kLayerEpiWarps = 12;  // three per 32-lane TMEM quadrant
 constexpr int kLayerThreads = 32 * (2 + kLayerEpiWarps);
 
+// Backward layer epilogue with the GELU'(Z) values (channel-last, BF16, stored by the forward) of
+// its row and chunk already in registers: dV = D (the 1x1 convolution is in the accumulator), times
+// GELU'(Z) where Z exists. Those rows come from DRAM and do not depend on the accumulator, so the
+// persistent kernel loads them one chunk ahead (the first chunk of a tile before the wait for its
+// accumulator).
+__device__ __forceinline__ void zrow_load(const EpiArgs& a, int row, int col0, uint4 (&q)[4]) {
+  const int b = col0 / C;
+  if (a.g_in != nullptr && row < a.P && b < a.B) {
+    const uint4* s = reinterpret_cast<const uint4*>(static_cast<const __nv_bfloat16*>(a.g_in) +
+                                                    ((size_t)b * a.P + row) * C);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) q[j] = __ldg(s + j);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) q[j] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+__device__ __forceinline__ void epilogue_bwd_z(const EpiArgs& a, int row, int col0, const float (&acc)[32],
+                                               const uint4 (&q)[4]) {
+  const int p = row, b = col0 / C;
+  if (p >= a.P || b >= a.B) return;
+  const size_t cl = ((size_t)b * a.P + p) * C;
+  float d[32];
+#pragma unroll
+  for (int i = 0; i < C; ++i) d[i] = a.alpha * acc[i];
+  if (a.g_in) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t w[4] = {q[j].x, q[j].y, q[j].z, q[j].w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        d[8 * j + 2 * h] *= __uint_as_float(w[h] << 16);
+        d[8 * j + 2 * h + 1] *= __uint_as_float(w[h] & 0xffff0000u);
+      }
+    }
+  }
+  if (a.out_cl) st32(static_cast<__nv_bfloat16*>(a.out_cl) + cl, d);
+  if (a.out_cf) {
+    __nv_bfloat16* cf = static_cast<__nv_bfloat16*>(a.out_cf) + (size_t)b * C * a.P + p;
+#pragma unroll
+    for (int i = 0; i < C; ++i) cf[(size_t)i * a.P] = __float2bfloat16_rn(d[i]);
+  }
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const __grid_constant__ CUtensorMap mA,
                                                                          const __grid_constant__ CUtensorMap mB,
@@ -265,10 +310,10 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
 
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n_tasks = m_tiles * n_tiles;
   const int nkb = K / 64;
   const uint64_t deadline = ptx::globaltimer() + timeout_ns;
   constexpr bool SEG2 = (EPI == EPI_LAYER_FWD || EPI == EPI_LAYER_BWD);
+  const int n_tasks = m_tiles * n_tiles;
   // the layer products walk the row tiles fastest (CTAs in flight share a Wh / GVh tile); the
   // field product and the truncated DFT walk the column tiles fastest (they share a row tile of
   // the points table / the activations)
@@ -423,6 +468,9 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
     for (int t = blockIdx.x; t < n_tasks; t += gridDim.x, ++lt) {
       const int m0 = tile_m0(t), n0 = tile_n0(t);
       const int acc = lt & 1;
+      const int row = m0 + grp * 32 + lane;
+      uint4 zc[4], zn[4];  // EPI_LAYER_BWD: GELU'(Z) of the current and the next chunk
+      if constexpr (EPI == EPI_LAYER_BWD) zrow_load(ea, row, n0 + 32 * third, zc);
       bool ok = true;
       for (;;) {
         if (ptx::mbar_try_wait(ptx::smem_u32(&accf_bar[acc]), (uint32_t)(lt >> 1) & 1u)) break;
@@ -437,11 +485,13 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
         break;
       }
       ptx::tc_fence_after();
-      const int row = m0 + grp * 32 + lane;
       const uint32_t lane_addr = tmem + (uint32_t)(acc * BN) + ((uint32_t)(grp * 32) << 16);
 #pragma unroll 1
       for (int c = third; c < BN / 32; c += 3) {
         if (n0 + 32 * c >= ea.cols) break;  // warp-uniform
+        if constexpr (EPI == EPI_LAYER_BWD) {
+          if (c + 3 < BN / 32) zrow_load(ea, row, n0 + 32 * (c + 3), zn);
+        }
         uint32_t r0[8], r1[8], r2[8], r3[8];
         ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c), r0);
         ptx::tmem_ld_x8(lane_addr + (uint32_t)(32 * c + 8), r1);
@@ -456,7 +506,13 @@ __global__ void __launch_bounds__(kLayerThreads, 1) gemm_layer_persistent(const 
           a[16 + j] = __uint_as_float(r2[j]);
           a[24 + j] = __uint_as_float(r3[j]);
         }
-        epilogue<EPI, __nv_bfloat16, true>(ea, w_s, b_s, row, n0 + 32 * c, 0, a);
+        if constexpr (EPI == EPI_LAYER_BWD) {
+          epilogue_bwd_z(ea, row, n0 + 32 * c, a, zc);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) zc[j] = zn[j];
+        } else {
+          epilogue<EPI, __nv_bfloat16, true>(ea, w_s, b_s, row, n0 + 32 * c, 0, a);
+        }
       }
       ptx::tc_fence_before();
       __syncwarp();

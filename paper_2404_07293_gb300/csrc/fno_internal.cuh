@@ -24,6 +24,7 @@ enum Epi : int {
                       // out[split][mode][row] (truncated DFTs)
   EPI_LAYER_FWD = 1,  // rows = pixels, columns = (sample, channel): Z = alpha D + c + W V; V' = GELU(Z)
   EPI_LAYER_BWD = 2,  // rows = pixels, columns = (sample, channel): dV = D + W^T dZ; dZ' = dV GELU'(Z)
+                      // (GELU'(Z) stored by the forward)
   EPI_DW = 3,         // rows = (sample, o), columns = (sample, i) of 4 samples: keep the diagonal blocks
   EPI_FIELD = 4       // field synthesis at points: rows = points, columns = (plane slot f, component c,
                       // re/im); complex E[(f, c)][p] -> out[il][c][fo][p], f = fo I + il (streaming stores)
@@ -42,8 +43,8 @@ struct EpiArgs {
   const void* w;       // EPI_LAYER_*: W [C][C] (row = output channel), element type T
   const void* bias;    // EPI_LAYER_FWD: c [C] (T), may be null
   const void* x_cl;    // SIMT form: FWD V_l channel-last [B][P][C]; BWD dZ_l channel-last
-  const void* z_in;    // BWD: Z_{l-1} channel-last (GELU'), null for l = 0
-  void* z_out;         // FWD: Z_l channel-last, null when not needed
+  const void* g_in;    // BWD: GELU'(Z_{l-1}) channel-last, stored by the forward; null for l = 0
+  void* g_out;         // FWD: GELU'(Z_l) channel-last (for the backward), null when not needed
   void* out_cf;        // FWD: V_{l+1} [B][C][P]; BWD: dZ_{l-1} [B][C][P]; null where not read
   void* out_cl;        // FWD: V_{l+1} [B][P][C]; BWD: dZ_{l-1} (or dV_0 for l = 0) [B][P][C]; null
                        // where not read
@@ -126,24 +127,51 @@ __device__ __forceinline__ void st32(T* p, const float (&v)[32]) {
 // density. Phi(z) = (1 + sign(z) erf(|z| / sqrt 2)) / 2 with erf from Abramowitz & Stegun, Handbook of
 // Mathematical Functions, formula 7.1.26: erf(x) = 1 - t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-x^2},
 // t = 1 / (1 + p x), x >= 0, |error| <= 1.5e-7. Its factor e^{-x^2} = e^{-z^2/2} is also phi(z) sqrt(2 pi),
-// so GELU' costs one exponential and one reciprocal.
-__device__ __forceinline__ void normal_cdf_and_gauss(float z, float& Phi, float& E) {
-  const float x = fabsf(z) * 0.70710678118654752f;
-  const float t = __fdividef(1.f, fmaf(0.3275911f, x, 1.f));
-  const float poly =
-      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-  E = __expf(-0.5f * z * z);
-  Phi = 0.5f + copysignf(0.5f * (1.f - poly * E), z);
+// so GELU and GELU' together cost one exponential and one reciprocal.
+//
+// GELU and GELU' of four values with one reciprocal between them: with d_i = 1 + p x_i and
+// r = 1 / (d_0 d_1 d_2 d_3), t_i = r times the other three d_j (a few roundings more than a
+// reciprocal each, far below the formula's 1.5e-7). x is clamped at 8, where t poly(t) e^{-x^2}
+// is below 1e-28 in either case, so every d_i lies in [1, 3.63] and the product cannot overflow.
+// The rest runs on value pairs with the packed FP32x2 instructions (FFMA2 / FMUL2 / FADD2), which
+// issue two lanes' worth of arithmetic per instruction: the layer epilogues that apply GELU are
+// bound by instruction issue. e^{-z^2/2} = 2^{-z^2 log2(e) / 2} on the special-function unit.
+// The poly coefficients carry the factor 1/2 of Phi, so that m = poly E / 2 and
+// Phi = 1/2 + sign(z) (1/2 - m).
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
-__device__ __forceinline__ float gelu_f(float z) {
-  float Phi, E;
-  normal_cdf_and_gauss(z, Phi, E);
-  return z * Phi;
-}
-__device__ __forceinline__ float gelu_grad_f(float z) {
-  float Phi, E;
-  normal_cdf_and_gauss(z, Phi, E);
-  return fmaf(z * 0.39894228040143268f, E, Phi);
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+
+__device__ __forceinline__ void gelu4(float (&z)[4], float (&gp)[4]) {
+  float d[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[i] = fmaf(0.3275911f, fminf(fabsf(z[i]) * 0.70710678118654752f, 8.f), 1.f);
+  const float d01 = d[0] * d[1], d23 = d[2] * d[3];
+  const float r = __fdividef(1.f, d01 * d23);
+  const float2 T[2] = {__fmul2_rn(make_float2(d[1], d[0]), f2(r * d23)),
+                       __fmul2_rn(make_float2(d[3], d[2]), f2(r * d01))};
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const float2 Z = make_float2(z[2 * h], z[2 * h + 1]), t = T[h];
+    float2 q = __ffma2_rn(t, f2(0.5f * 1.061405429f), f2(0.5f * -1.453152027f));
+    q = __ffma2_rn(q, t, f2(0.5f * 1.421413741f));
+    q = __ffma2_rn(q, t, f2(0.5f * -0.284496736f));
+    q = __ffma2_rn(q, t, f2(0.5f * 0.254829592f));
+    q = __fmul2_rn(q, t);  // poly / 2
+    const float2 a = __fmul2_rn(__fmul2_rn(Z, Z), f2(-0.72134752044448170f));  // -z^2 log2(e) / 2
+    const float2 E = make_float2(ex2_approx(a.x), ex2_approx(a.y));
+    const float2 hm = __ffma2_rn(q, make_float2(-E.x, -E.y), f2(0.5f));  // 1/2 - m
+    const float2 Phi = __fadd2_rn(make_float2(copysignf(hm.x, Z.x), copysignf(hm.y, Z.y)), f2(0.5f));
+    const float2 g = __ffma2_rn(__fmul2_rn(Z, f2(0.39894228040143268f)), E, Phi);
+    const float2 o = __fmul2_rn(Z, Phi);
+    gp[2 * h] = g.x;
+    gp[2 * h + 1] = g.y;
+    z[2 * h] = o.x;
+    z[2 * h + 1] = o.y;
+  }
 }
 
 // ---- epilogues, shared by the tensor-core and the SIMT GEMM ------------------------------
@@ -179,7 +207,11 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
     const size_t cl = ((size_t)b * a.P + p) * C;
     float z[32];
 #pragma unroll
-    for (int o = 0; o < C; ++o) z[o] = a.alpha * acc[o] + b_s[o];
+    for (int o = 0; o < C; o += 2) {
+      const float2 v = __ffma2_rn(make_float2(acc[o], acc[o + 1]), f2(a.alpha), make_float2(b_s[o], b_s[o + 1]));
+      z[o] = v.x;
+      z[o + 1] = v.y;
+    }
     if constexpr (!WACC) {
       float x[32];
       ld32(static_cast<const T*>(a.x_cl) + cl, x);
@@ -191,10 +223,20 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
         z[o] = s;
       }
     }
-    if (a.z_out) st32(static_cast<T*>(a.z_out) + cl, z);
     if (a.gelu) {
+      // GELU in place, GELU' for the backward (the same exponentials and reciprocals)
+      float gp[32];
 #pragma unroll
-      for (int o = 0; o < C; ++o) z[o] = gelu_f(z[o]);
+      for (int q = 0; q < C / 4; ++q) {
+        float zz[4] = {z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]}, gg[4];
+        gelu4(zz, gg);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          z[4 * q + i] = zz[i];
+          gp[4 * q + i] = gg[i];
+        }
+      }
+      if (a.g_out) st32(static_cast<T*>(a.g_out) + cl, gp);
     }
     if (a.out_cl) st32(static_cast<T*>(a.out_cl) + cl, z);
     if (a.out_cf) {
@@ -220,11 +262,11 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
         d[i] = s;
       }
     }
-    if (a.z_in) {
-      float z[32];
-      ld32(static_cast<const T*>(a.z_in) + cl, z);
+    if (a.g_in) {
+      float g[32];
+      ld32(static_cast<const T*>(a.g_in) + cl, g);
 #pragma unroll
-      for (int i = 0; i < C; ++i) d[i] *= gelu_grad_f(z[i]);
+      for (int i = 0; i < C; ++i) d[i] *= g[i];
     }
     if (a.out_cl) st32(static_cast<T*>(a.out_cl) + cl, d);
     if (a.out_cf) {
