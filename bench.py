@@ -741,6 +741,13 @@ def run_surrogate(args, dev, bf16_peaks):
     tf = {k: (t[k + "_flops"] / calls) / (fam[k] * 1e-3) / 1e12 for k in ("dft", "layer", "dw") if fam[k] > 0}
     dom = max(("dft", "layer"), key=lambda k: fam[k])
     peak = bf16_peaks[1]
+    # the layer products' DRAM bytes per training step: activation layouts of B C P BF16 values,
+    # forward layers 0..L-2 read V_l and write V_{l+1} and GELU'(Z_l), the last writes V_L;
+    # backward layers L-1..1 read dZ_l and GELU'(Z_{l-1}) and write dZ_{l-1}, layer 0 writes dV_0
+    L_fno, C_fno, P_fno = 4, 32, 64 * 64
+    layer_bytes = 2 * (3 * (L_fno - 1) + 2) * B * C_fno * P_fno * 2
+    hbm = bf16_peaks[2]
+    layer_gbs = layer_bytes / (fam["layer"] * 1e-3) / 1e9
     s.close()
     return {
         "workload": "fno_4_layers_width_32_modes_16x16_grid_64x64_from_8x32x32", "batch": B,
@@ -753,6 +760,14 @@ def run_surrogate(args, dev, bf16_peaks):
                      "bound": "tensor", "achieved": tf[dom], "peak": peak, "unit": "TFLOP/s",
                      "frac": tf[dom] / peak, "traffic": None,
                      "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (measured; fallback 1700 if absent)"},
+        # the layer family against both ceilings: its activation traffic takes longer at the
+        # measured HBM rate than its MMAs at the sustained tensor rate, so HBM is the binding one
+        "layer_rooflines": {
+            "hbm": {"bytes_per_step": layer_bytes, "achieved_gbs": layer_gbs, "peak_gbs": hbm,
+                    "frac": layer_gbs / hbm, "floor_ms": layer_bytes / (hbm * 1e9) * 1e3},
+            "tensor": {"achieved_tflops": tf["layer"], "peak_tflops": peak, "frac": tf["layer"] / peak,
+                       "floor_ms": t["layer_flops"] / calls / (peak * 1e12) * 1e3},
+            "binding": "hbm" if layer_bytes / (hbm * 1e9) > t["layer_flops"] / calls / (peak * 1e12) else "tensor"},
         "gpu_launches": {"train_step": launches["train_step"], "infer": launches["infer"]},
         "dtype": "bf16 activations and weights, fp32 accumulation and master weights",
     }
@@ -983,7 +998,7 @@ def run_ours(args, world, rank, local):
     surrogate = None
     if not args.no_surrogate:
         torch.cuda.empty_cache()
-        surrogate = run_surrogate(args, dev, (bf16_tf, bf16_sustained()))
+        surrogate = run_surrogate(args, dev, (bf16_tf, bf16_sustained(), peaks()[0]))
 
     # the oracle leg: the FP64 oracle synthesises every voxel of the same inputs on the host
     # cores (timed: cpu_baseline); both GPU arms are compared with it voxel by voxel
@@ -1087,7 +1102,7 @@ def main():
         import torch
         dev = torch.device("cuda", local)
         torch.cuda.set_device(dev)
-        print(json.dumps({"surrogate": run_surrogate(args, dev, (peaks()[1], bf16_sustained()))}), flush=True)
+        print(json.dumps({"surrogate": run_surrogate(args, dev, (peaks()[1], bf16_sustained(), peaks()[0]))}), flush=True)
         return 0
     return run_ours(args, world, rank, local)
 
