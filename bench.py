@@ -773,6 +773,68 @@ def run_surrogate(args, dev, bf16_peaks):
     }
 
 
+def _r(x, sig=4):
+    """x with `sig` significant digits (floats in nested lists / dicts; other values as they are)."""
+    if isinstance(x, float):
+        return float(f"{x:.{sig}g}")
+    if isinstance(x, (list, tuple)):
+        return [_r(v, sig) for v in x]
+    if isinstance(x, dict):
+        return {k: _r(v, sig) for k, v in x.items()}
+    return x
+
+
+def _get(d, *keys):
+    """d[k0][k1]..., or None where a level is missing."""
+    for k in keys:
+        if not isinstance(d, dict):
+            return None
+        d = d.get(k)
+    return d
+
+
+def summary(line):
+    """The line's key figures in a compact block: headline and its rooflines, the kernel timeline of
+    one replayed step, the FP32 arm and the split/FP32 ratios with their bound, the error of every
+    voxel against the FP64 oracle, the compute-bound variants and the other workloads' headlines."""
+    out = {"ms_per_step": line["ms_per_step"], "voxels_per_s": line["value"],
+           "step_roofline_frac": _get(line, "step_roofline", "frac"),
+           "contraction": {"frac_of_hbm": _get(line, "roofline", "frac"), "gbs": _get(line, "roofline", "achieved"),
+                           "traffic_over_algorithmic": (line["roofline"]["traffic"] / line["roofline"]["algorithmic_bytes"]
+                                                        if line["roofline"].get("traffic") else None)},
+           "timeline_us": line.get("timeline_us"),
+           "fp32": {"ms_per_step": _get(line, "fp32", "ms_per_step"), "contract_ms": _get(line, "fp32", "kernel_ms", "contract_ms"),
+                    "voxels_per_s": _get(line, "fp32", "value")},
+           "split_bf16_vs_fp32": {k: v for k, v in (line.get("split_bf16_vs_fp32") or {}).items() if k != "note"}}
+    err = line.get("error_vs_fp64")
+    if err:
+        out["error_vs_fp64"] = {"voxels": err.get("voxels"), "components": "Ex Ey Ez",
+                                **{f"{p}_{m}": _get(err, p, m) for p in ("split_bf16", "fp32")
+                                   for m in ("rel_l2", "max_abs_over_max")}}
+    c3 = line.get("config3") or {}
+    out["config3"] = {k: {m: v.get(m) for m in ("contract_speedup_split_bf16_vs_fp32", "step_speedup_split_bf16_vs_fp32",
+                                                 "step_speedup_bound")}
+                      for k, v in c3.items() if isinstance(v, dict) and "step_speedup_split_bf16_vs_fp32" in v}
+    out["e2e_voxels_per_s"] = _get(line, "e2e", "value")
+    out["cpu_baseline_voxels_per_s"] = _get(line, "cpu_baseline", "value")
+    out["sweep"] = {"voxels_per_s": _get(line, "sweep", "value"), "roofline_frac": _get(line, "sweep", "roofline_frac")}
+    out["illumination16"] = {"ms": _get(line, "illumination", "split_bf16", "ms_per_step"),
+                             "contract_tflops": _get(line, "illumination", "split_bf16", "contract_tflops")}
+    out["points_window"] = {"tflops": _get(line, "points", "window_256x256_of_4um", "split_bf16", "point_product_tflops"),
+                            "vs_fp32": _get(line, "points", "window_256x256_of_4um", "point_product_speedup_split_bf16_vs_fp32")}
+    out["tiling"] = {"periodic_frac": _get(line, "tiling", "periodic_4x4", "roofline_frac"),
+                     "mosaic_frac": _get(line, "tiling", "mosaic_4x4_patches", "roofline_frac")}
+    out["solve_s"] = {"gpu": _get(line, "solve", "gpu_s"), "oracle_scaled": _get(line, "solve", "cpu_baseline", "value")}
+    sg = line.get("surrogate")
+    if sg:
+        out["surrogate"] = {"train_ms": sg.get("train_ms_per_step"), "infer_ms": sg.get("infer_ms_per_batch"),
+                            "kernel_ms": sg.get("kernel_ms_per_train_step"),
+                            "layer_hbm_frac": _get(sg, "layer_rooflines", "hbm", "frac"),
+                            "layer_tensor_frac": _get(sg, "layer_rooflines", "tensor", "frac"),
+                            "launches": sg.get("gpu_launches")}
+    return _r(out)
+
+
 def run_ours(args, world, rank, local):
     import torch
     import paper_2404_07293_gb300 as scw
@@ -1055,6 +1117,7 @@ def run_ours(args, world, rank, local):
             "solve": solve,
             "surrogate": surrogate,
         }
+        line["summary"] = summary(line)  # last: the part of a long line that a tail of the output keeps
         print(json.dumps(line), flush=True)
     if dist:
         torch.distributed.destroy_process_group()
