@@ -12,7 +12,9 @@ Without the learned part, every field needs a solve; the best field-free guess
 (the mean training field) is what the method offers without solving. The test
 checks that the trained network
   - predicts held-out fields far better than that guess,
-  - is orders of magnitude faster than a solve,
+  - is orders of magnitude faster than the plain method on the GPU at the same
+    orders (scw_solve + recomposition of the exit field, timed here on the
+    held-out seeds, whose fields also agree with the oracle's),
   - has an error head whose estimates track the true error, and
   - after split-conformal calibration, accepts samples whose true error is
     mostly below the threshold (the rest fall back to the plain method).
@@ -79,7 +81,15 @@ def test_surrogate_gain_over_plain_method(cuda_device):
     accepted = ~flag
     violations = float(np.mean(err[accepted] > THRESHOLD)) if accepted.any() else 0.0
 
-    # speed: one batched inference against one solve per sample
+    # the plain method on the GPU at the same orders, on the held-out seeds (two solves in flight,
+    # after a warm-up that creates the solvers' library handles)
+    fno_data.exit_fields_gpu(seeds[-2:], U=7, workers=2)
+    t0 = time.perf_counter()
+    _, E_gpu, _ = fno_data.exit_fields_gpu(seeds[-N_TEST:], U=7, workers=2)
+    plain_per_sample = (time.perf_counter() - t0) / N_TEST
+    assert _rel(E_gpu, Ete).max() <= 1e-5
+
+    # speed: one batched inference against the plain method per sample
     for _ in range(3):
         s.infer(nte_d)
     torch.cuda.synchronize()
@@ -88,13 +98,14 @@ def test_surrogate_gain_over_plain_method(cuda_device):
         s.infer(nte_d)
     torch.cuda.synchronize()
     per_sample = (time.perf_counter() - t0) / 20 / N_TEST
-    speedup = float(np.mean(solve_s)) / per_sample
+    speedup = plain_per_sample / per_sample
     s.close()
 
     print(f"train field loss {first:.3f} -> {last:.2e}; held-out rel-L2 median {np.median(err):.3f} "
           f"(max {err.max():.3f}) vs mean-field guess {np.median(guess):.3f}; head log-corr {corr:.2f}; "
           f"q {q:.2f}; accepted {accepted.mean():.2f} at threshold {THRESHOLD} with {violations:.2f} above it; "
-          f"inference {per_sample * 1e6:.1f} us/sample vs solve {np.mean(solve_s):.3f} s: {speedup:.2e}x")
+          f"inference {per_sample * 1e6:.1f} us/sample vs the GPU plain method {plain_per_sample * 1e3:.2f} ms/sample "
+          f"({speedup:.2e}x; the FP64 oracle solve takes {np.mean(solve_s):.3f} s)")
     assert last < 0.05 * first
     assert np.median(err) < 0.35 * np.median(guess)
     assert speedup > 1e3
