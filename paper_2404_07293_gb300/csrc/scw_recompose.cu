@@ -489,7 +489,10 @@ static cudaError_t launch_ypass_p(bool tiled, const ItemDev& one, const ItemDev*
 #undef SCW_YP
 }
 
-bool ypass_pairs(int Vp) { return Vp >= 24; }
+// Pairs pay where the fold is long enough for the saved shared-memory loads to outweigh the halved
+// occupancy: measured on 21 x 21 orders (Vp = 24), one residue per warp is 3 us faster per
+// 256^3 step (and 0.08 ms per 128-item sweep), so pairs start at Vp = 32.
+bool ypass_pairs(int Vp) { return Vp >= 32; }
 
 cudaError_t launch_ypass(const ItemDev& one, const ItemDev* items, const int2* d_entries, int n_entries, int n_pair,
                          int max_Qx, int max_Vp, int max_twy, bool tiled, float2* out_one, float2* const* d_outs,
