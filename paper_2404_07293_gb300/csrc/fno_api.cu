@@ -324,24 +324,35 @@ static scw_status forward_backward(scw_fno_s* f, const float2* n, const float2* 
     ea.out = f->GWh;
     ea.ld = ld;
     ea.split_stride = vstride;
-    e = f->bf16 ? launch_gemm_tc(EPI_MODES, bn, f->map_dZcf[cur], f->map_D, f->map_D, f->map_D, ea, BC, f->Kc, P, ks,
-                                 f->d_err, f->timeout_ns, st)
-                : launch_gemm_simt(EPI_MODES, static_cast<const float*>(f->dZcf[cur]), P,
-                                   static_cast<const float*>(f->D), P, ea, BC, f->Kc, P, ks, st);
-    FNO_TRY(launch_ok(f, e, "truncated DFT of dZ", CAT_DFT, 2.0 * BC * f->Kc * P));
     // dW_l = sum_b dZ_b V_b^T
-    const int kw = dw_splits(f, B);
     const int groups = (B + 3) / 4;
     EpiArgs ew{};
     ew.rows = BC;
     ew.B = B;
     ew.out = f->part_dw[l];
+    // at 2 m^2 = 512 kept-mode columns both products run in one kernel that reads dZ once (the two
+    // column tiles of the DFT each take one half of the pixels of dW: two partials)
+    const bool fused = f->bf16 && bn == 256 && ks == 1 && f->Kc == 512 && P % 128 == 0;
+    const int kw = fused ? 2 : dw_splits(f, B);
     ew.splits = kw;
-    e = f->bf16 ? launch_gemm_tc(EPI_DW, 128, f->map_dZcf[cur], f->map_Vcf[l], f->map_D, f->map_D, ew, groups * 128,
-                                 groups * 128, P, kw, f->d_err, f->timeout_ns, st)
-                : launch_gemm_simt(EPI_DW, static_cast<const float*>(f->dZcf[cur]), P,
-                                   static_cast<const float*>(f->Vcf[l]), P, ew, groups * 128, groups * 128, P, kw, st);
-    FNO_TRY(launch_ok(f, e, "weight gradient", CAT_DW, 2.0 * BC * C * P));
+    if (fused) {
+      e = launch_gemm_dft_dw(f->map_dZcf[cur], f->map_D, f->map_Vcf[l], ea, ew, BC, f->Kc, P, f->d_err,
+                             f->timeout_ns, st);
+      FNO_TRY(launch_ok(f, e, "truncated DFT of dZ and weight gradient", CAT_DFT,
+                        2.0 * BC * f->Kc * P + 2.0 * BC * C * P));
+    } else {
+      e = f->bf16 ? launch_gemm_tc(EPI_MODES, bn, f->map_dZcf[cur], f->map_D, f->map_D, f->map_D, ea, BC, f->Kc, P,
+                                   ks, f->d_err, f->timeout_ns, st)
+                  : launch_gemm_simt(EPI_MODES, static_cast<const float*>(f->dZcf[cur]), P,
+                                     static_cast<const float*>(f->D), P, ea, BC, f->Kc, P, ks, st);
+      FNO_TRY(launch_ok(f, e, "truncated DFT of dZ", CAT_DFT, 2.0 * BC * f->Kc * P));
+      e = f->bf16 ? launch_gemm_tc(EPI_DW, 128, f->map_dZcf[cur], f->map_Vcf[l], f->map_D, f->map_D, ew, groups * 128,
+                                   groups * 128, P, kw, f->d_err, f->timeout_ns, st)
+                  : launch_gemm_simt(EPI_DW, static_cast<const float*>(f->dZcf[cur]), P,
+                                     static_cast<const float*>(f->Vcf[l]), P, ew, groups * 128, groups * 128, P, kw,
+                                     st);
+      FNO_TRY(launch_ok(f, e, "weight gradient", CAT_DW, 2.0 * BC * C * P));
+    }
     reduce_into(segs, f->part_dw[l], groups * kw * 4, C * C, C * C, f->grad + f->off_W[l]);
     // mixing backward
     constexpr bool tc_mix = std::is_same<T, __nv_bfloat16>::value;

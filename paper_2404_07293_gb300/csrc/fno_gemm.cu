@@ -594,6 +594,233 @@ static cudaError_t launch_tc_t(const CUtensorMap& mA, const CUtensorMap& mB, con
   return cudaGetLastError();
 }
 
+// ---- backward truncated DFT of dZ fused with the weight gradient dW = sum_b dZ_b V_b^T ----
+// Both products read dZ (channel-first, rows (b, o), K = pixels) as A. Tile (m0, n0) of the DFT
+// (2m^2 = 512 output columns, two column tiles of 256) also multiplies, over one half of K (the
+// first half for n0 = 0, the second for n0 = 256), its 128 rows of dZ by the same 128 rows of V
+// (rows (b, i), a third operand in the stage) into a 128-column accumulator beside the DFT's; the
+// diagonal 32 x 32 blocks are the four samples' dW_b partials (K half = split 0 or 1). dZ is then
+// read once per layer instead of twice. Stages: A 16 KB + D 32 KB + V 16 KB, three in flight.
+// One accumulator pair per CTA (no double buffering: at batch <= 256 every CTA has one tile).
+constexpr int kDwStages = 3;
+constexpr uint32_t kDwStage = 128u * 128u + 256u * 128u + 128u * 128u;
+constexpr uint32_t kDwSmem = kDwStages * kDwStage + 1024u;
+
+__global__ void __launch_bounds__(kLayerThreads, 1) gemm_dft_dw_kernel(const __grid_constant__ CUtensorMap mA,
+                                                                      const __grid_constant__ CUtensorMap mB,
+                                                                      const __grid_constant__ CUtensorMap mV,
+                                                                      const __grid_constant__ EpiArgs ea,
+                                                                      const __grid_constant__ EpiArgs ew, int K,
+                                                                      int m_tiles, int* err, uint64_t timeout_ns) {
+  constexpr int BN = 256, STAGES = kDwStages, n_tiles = 2;
+  constexpr uint32_t A_BYTES = 128u * 128u, B_BYTES = 256u * 128u;
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accf_bar;
+  __shared__ __align__(8) uint64_t acce_bar;
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ volatile int abort_s;
+
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_tasks = m_tiles * n_tiles;
+  const int nkb = K / 64, half = nkb / 2;  // K blocks; the dW half of tile (m, n): [n half, (n + 1) half)
+  const uint64_t deadline = ptx::globaltimer() + timeout_ns;
+  // column tiles fastest: the two tiles of a row tile run side by side and share its dZ rows in L2
+  auto tile_m0 = [&](int t) { return (t / n_tiles) * 128; };
+  auto tile_n = [&](int t) { return t % n_tiles; };
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) {
+      ptx::mbar_init(ptx::smem_u32(&full_bar[i]), 1);
+      ptx::mbar_init(ptx::smem_u32(&empty_bar[i]), 1);
+    }
+    ptx::mbar_init(ptx::smem_u32(&accf_bar), 1);
+    ptx::mbar_init(ptx::smem_u32(&acce_bar), kLayerEpiWarps);
+    ptx::mbar_init(ptx::smem_u32(&drain_bar), 1);
+    abort_s = 0;
+    ptx::fence_mbar_init();
+    ptx::prefetch_tensormap(&mA);
+    ptx::prefetch_tensormap(&mB);
+    ptx::prefetch_tensormap(&mV);
+  }
+  if (warp == 0) {
+    ptx::tmem_alloc(ptx::smem_u32(&tmem_base_s), 512);  // DFT columns [0, 256), dW columns [256, 384)
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = tmem_base_s;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    int st = 0, issued = 0;
+    uint32_t ph = 0;
+    for (int t = blockIdx.x; t < n_tasks && !abort_s; t += gridDim.x) {
+      const int m0 = tile_m0(t), n = tile_n(t);
+      for (int i = 0; i < nkb && !abort_s; ++i) {
+        if (!ptx::mbar_wait(ptx::smem_u32(&empty_bar[st]), ph ^ 1u, deadline)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_EMPTY);
+          abort_s = 1;
+          break;
+        }
+        const bool dw = i >= n * half && i < (n + 1) * half;
+        const uint32_t fb = ptx::smem_u32(&full_bar[st]);
+        const uint32_t sa = ptx::smem_u32(smem + (size_t)st * kDwStage);
+        ptx::mbar_arrive_expect_tx(fb, A_BYTES + B_BYTES + (dw ? A_BYTES : 0u));
+        ptx::tma_load_2d(sa, &mA, i * 64, m0, fb);
+        ptx::tma_load_2d(sa + A_BYTES, &mB, i * 64, n * BN, fb);
+        if (dw) ptx::tma_load_2d(sa + A_BYTES + B_BYTES, &mV, i * 64, m0, fb);
+        ++issued;
+        if (++st == STAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+    }
+    if (abort_s) {
+      const uint64_t d2 = ptx::drain_deadline(timeout_ns);
+      for (int back = 1; back <= STAGES && back <= issued; ++back) {
+        const int i = issued - back;
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[i % STAGES]), (uint32_t)(i / STAGES) & 1u, d2)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
+          break;
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- tcgen05.mma issuer ----------------
+    constexpr uint32_t idesc = ptx::idesc_f16(true, 128, BN);
+    constexpr uint32_t idesc_dw = ptx::idesc_f16(true, 128, 128);
+    int st = 0, lt = 0;
+    uint32_t ph = 0;
+    for (int t = blockIdx.x; t < n_tasks && !abort_s; t += gridDim.x, ++lt) {
+      const int n = tile_n(t);
+      // the epilogue has read the previous tile's accumulators
+      if (!ptx::mbar_wait(ptx::smem_u32(&acce_bar), ((uint32_t)lt & 1u) ^ 1u, deadline)) {
+        atomicOr(err, DEV_ERR_TIMEOUT_ACCUM);
+        abort_s = 1;
+        break;
+      }
+      ptx::tc_fence_after();
+      for (int i = 0; i < nkb; ++i) {
+        if (!ptx::mbar_wait(ptx::smem_u32(&full_bar[st]), ph, deadline)) {
+          atomicOr(err, DEV_ERR_TIMEOUT_FULL);
+          abort_s = 1;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t sa = ptx::smem_u32(smem + (size_t)st * kDwStage);
+        const uint64_t da = ptx::sw128_desc(sa), db = ptx::sw128_desc(sa + A_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          ptx::mma_f16(tmem, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+        const int j = i - n * half;  // position in this tile's dW half of K
+        if (j >= 0 && j < half) {
+          const uint64_t dv = ptx::sw128_desc(sa + A_BYTES + B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < 4; ++kk)
+            ptx::mma_f16(tmem + 256u, da + (uint64_t)(2 * kk), dv + (uint64_t)(2 * kk), idesc_dw,
+                         (j > 0 || kk > 0) ? 1u : 0u);
+        }
+        ptx::mma_commit(ptx::smem_u32(&empty_bar[st]));
+        if (++st == STAGES) {
+          st = 0;
+          ph ^= 1u;
+        }
+      }
+      if (abort_s) break;
+      ptx::mma_commit(ptx::smem_u32(&accf_bar));
+    }
+    if (abort_s) {
+      ptx::mma_commit(ptx::smem_u32(&drain_bar));
+      if (!ptx::mbar_wait(ptx::smem_u32(&drain_bar), 0u, ptx::drain_deadline(timeout_ns)))
+        atomicOr(err, DEV_ERR_TIMEOUT_DRAIN);
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int grp = warp & 3;           // TMEM lanes 32 grp .. 32 grp + 31
+    const int third = (warp - 2) >> 2;  // DFT column chunks third, third + 3, ...; third 0 also takes dW
+    int lt = 0;
+    for (int t = blockIdx.x; t < n_tasks; t += gridDim.x, ++lt) {
+      const int m0 = tile_m0(t), n = tile_n(t);
+      bool ok = true;
+      for (;;) {
+        if (ptx::mbar_try_wait(ptx::smem_u32(&accf_bar), (uint32_t)lt & 1u)) break;
+        if (abort_s || ptx::globaltimer() > deadline) {
+          ok = false;
+          break;
+        }
+      }
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0 && !abort_s) atomicOr(err, DEV_ERR_TIMEOUT_ACCUM);
+        abort_s = 1;
+        break;
+      }
+      ptx::tc_fence_after();
+      const int row = m0 + grp * 32 + lane;
+      const uint32_t lane_addr = tmem + ((uint32_t)(grp * 32) << 16);
+      auto load32 = [&](uint32_t col, float (&a)[32]) {
+        uint32_t r0[8], r1[8], r2[8], r3[8];
+        ptx::tmem_ld_x8(lane_addr + col, r0);
+        ptx::tmem_ld_x8(lane_addr + col + 8u, r1);
+        ptx::tmem_ld_x8(lane_addr + col + 16u, r2);
+        ptx::tmem_ld_x8(lane_addr + col + 24u, r3);
+        ptx::tmem_wait_ld();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          a[q] = __uint_as_float(r0[q]);
+          a[8 + q] = __uint_as_float(r1[q]);
+          a[16 + q] = __uint_as_float(r2[q]);
+          a[24 + q] = __uint_as_float(r3[q]);
+        }
+      };
+#pragma unroll 1
+      for (int c = third; c < BN / 32; c += 3) {
+        if (n * BN + 32 * c >= ea.cols) break;  // warp-uniform
+        float a[32];
+        load32((uint32_t)(32 * c), a);
+        epilogue<EPI_MODES, __nv_bfloat16, true>(ea, nullptr, nullptr, row, n * BN + 32 * c, 0, a);
+      }
+      if (third == 0) {  // the diagonal block of this quadrant's sample: dW_b partial, K half n
+        float a[32];
+        load32(256u + (uint32_t)(32 * grp), a);
+        epilogue<EPI_DW, __nv_bfloat16, true>(ew, nullptr, nullptr, row, 32 * grp, n, a);
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(&acce_bar));
+    }
+  }
+
+  // ---------------- teardown ----------------
+  __syncwarp();
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 512);
+  }
+}
+
+cudaError_t launch_gemm_dft_dw(const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mV,
+                               const EpiArgs& ea, const EpiArgs& ew, int M, int N, int K, int* err,
+                               uint64_t timeout_ns, cudaStream_t st) {
+  if (N != 512 || K % 128 != 0 || ew.splits != 2) return cudaErrorInvalidValue;
+  const void* fn = reinterpret_cast<const void*>(gemm_dft_dw_kernel);
+  cudaError_t e = allow_max_smem(fn);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int m_tiles = (M + 127) / 128;
+  const int grid = std::max(1, std::min(2 * m_tiles, sms));
+  gemm_dft_dw_kernel<<<grid, kLayerThreads, kDwSmem, st>>>(mA, mB, mV, ea, ew, K, m_tiles, err, timeout_ns);
+  return cudaGetLastError();
+}
+
 template <int EPI>
 static cudaError_t launch_layer_persistent(const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
                                            const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int* err,

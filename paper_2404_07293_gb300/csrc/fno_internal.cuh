@@ -299,6 +299,13 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
 cudaError_t launch_gemm_tc(int epi, int BN, const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mA2,
                            const CUtensorMap& mW, const EpiArgs& ea, int M, int N, int K, int splits, int* err,
                            uint64_t timeout_ns, cudaStream_t st);
+// Backward truncated DFT of dZ (EPI_MODES into ea, N = 2 m^2 = 512 columns, two tiles of 256)
+// fused with the weight gradient (EPI_DW into ew, ew.splits = 2: the two column tiles each take one
+// half of K = pixels, a multiple of 128): mA = dZ channel-first, mB = the DFT table D, mV = V
+// channel-first (box 128 rows). Tensor-core (BF16) mode only.
+cudaError_t launch_gemm_dft_dw(const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mV,
+                               const EpiArgs& ea, const EpiArgs& ew, int M, int N, int K, int* err,
+                               uint64_t timeout_ns, cudaStream_t st);
 // FP32 SIMT GEMM with the same semantics (A [M][lda], B [N][ldb] row-major FP32; for EPI_DW
 // rows of B are offset like rows of A).
 cudaError_t launch_gemm_simt(int epi, const float* A, long long lda, const float* B, long long ldb,
