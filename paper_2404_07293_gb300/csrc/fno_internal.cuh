@@ -145,6 +145,8 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 __device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
 
+// GP = false (inference): GELU only.
+template <bool GP = true>
 __device__ __forceinline__ void gelu4(float (&z)[4], float (&gp)[4]) {
   float d[4];
 #pragma unroll
@@ -165,10 +167,12 @@ __device__ __forceinline__ void gelu4(float (&z)[4], float (&gp)[4]) {
     const float2 E = make_float2(ex2_approx(a.x), ex2_approx(a.y));
     const float2 hm = __ffma2_rn(q, make_float2(-E.x, -E.y), f2(0.5f));  // 1/2 - m
     const float2 Phi = __fadd2_rn(make_float2(copysignf(hm.x, Z.x), copysignf(hm.y, Z.y)), f2(0.5f));
-    const float2 g = __ffma2_rn(__fmul2_rn(Z, f2(0.39894228040143268f)), E, Phi);
+    if constexpr (GP) {
+      const float2 g = __ffma2_rn(__fmul2_rn(Z, f2(0.39894228040143268f)), E, Phi);
+      gp[2 * h] = g.x;
+      gp[2 * h + 1] = g.y;
+    }
     const float2 o = __fmul2_rn(Z, Phi);
-    gp[2 * h] = g.x;
-    gp[2 * h + 1] = g.y;
     z[2 * h] = o.x;
     z[2 * h + 1] = o.y;
   }
@@ -223,20 +227,28 @@ __device__ __forceinline__ void epilogue(const EpiArgs& a, const float* w_s, con
         z[o] = s;
       }
     }
-    if (a.gelu) {
+    if (a.gelu && a.g_out) {
       // GELU in place, GELU' for the backward (the same exponentials and reciprocals)
       float gp[32];
 #pragma unroll
       for (int q = 0; q < C / 4; ++q) {
         float zz[4] = {z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]}, gg[4];
-        gelu4(zz, gg);
+        gelu4<true>(zz, gg);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           z[4 * q + i] = zz[i];
           gp[4 * q + i] = gg[i];
         }
       }
-      if (a.g_out) st32(static_cast<T*>(a.g_out) + cl, gp);
+      st32(static_cast<T*>(a.g_out) + cl, gp);
+    } else if (a.gelu) {  // inference: no GELU' to keep
+#pragma unroll
+      for (int q = 0; q < C / 4; ++q) {
+        float zz[4] = {z[4 * q], z[4 * q + 1], z[4 * q + 2], z[4 * q + 3]}, gg[4];
+        gelu4<false>(zz, gg);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) z[4 * q + i] = zz[i];
+      }
     }
     if (a.out_cl) st32(static_cast<T*>(a.out_cl) + cl, z);
     if (a.out_cf) {
