@@ -168,3 +168,26 @@ def test_calibration_matches_conformal_rule(cuda_device):
     ref = fno.conformal_offset(np.log(est.astype(np.float64)), true.astype(np.float64), 0.05)
     assert q == pytest.approx(ref, abs=1e-5)
     s.close()
+
+
+def test_backward_with_several_tiles_per_cta_matches_half_batches(cuda_device):
+    """Full size at 320 samples: the backward DFT + weight-gradient kernel then has 160 tiles for at
+    most 152 CTAs, so some CTAs run two tiles through their single accumulator pair. The loss is a
+    mean over samples, so the gradient of the 320-sample batch is the mean of the gradients of its
+    two 160-sample halves (80 tiles: one per CTA). Per-sample arithmetic is the same in both, only
+    the sums over samples are grouped differently."""
+    import torch
+    sh, B = FULL, 320
+    flat, n, E = _case(sh, B, seed=33)
+    grads = []
+    for lo, hi in ((0, B), (0, B // 2), (B // 2, B)):
+        s = _surrogate(sh, hi - lo, "bf16")
+        s.set_params(flat)
+        nd = torch.from_numpy(np.ascontiguousarray(n[lo:hi])).to(cuda_device)
+        Ed = torch.from_numpy(np.ascontiguousarray(E[lo:hi])).to(cuda_device)
+        s.forward_backward(nd, Ed)
+        torch.cuda.synchronize()
+        grads.append(s.grads().astype(np.float64))
+        s.close()
+    whole, half = grads[0], 0.5 * (grads[1] + grads[2])
+    _compare_grads(whole, half, sh, 1e-4)
